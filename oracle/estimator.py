@@ -1,0 +1,132 @@
+"""Oracle of the rank-revealing leverage-score estimator (FP64, numpy).
+
+TEST INFRASTRUCTURE ONLY: nothing in the product path may import this module.
+
+The estimator is Alg. 10 (LS-HRN-approx): Alg. 4 (CountGaussSRRQR: the
+CountGauss sketch of Alg. 3, then a rank-revealing QR of the sketch) selects
+the columns K and gives R_11; then steps 4-5 of Alg. 8 run on A_{:,K} with
+the orthogonaliser R_11 and a Gaussian JL matrix Omega (eq. (24):
+theta~_i = ||e_i^T A_K R_11^{-1} Omega||^2).
+
+Step order (each function cites its step):
+ 1. hash and sign of every row (CountSketch definition, Sec. 2.3.3);
+ 2. B = S A, summed in FP64 (Alg. 3, step 3, first product);
+ 3. A~ = G B with G = N(0,1)/sqrt(m) (Alg. 3 step 3, Sec. 2.3.1 scaling);
+ 4. pivoted QR of A~, rank r, R_11 (Alg. 4 step 2, xGEQP3-style, Sec. 6);
+ 5. Omega (r x k) = N(0,1)/sqrt(k), rows indexed by pivot position;
+ 6. M = R_11^{-1} Omega (Alg. 8 step 4 with the QR orthogonaliser);
+ 7. theta~_i = sum_q (sum_{p<r} A[i, P_p] M[p, q])^2 (Alg. 8 step 5).
+
+Readings where the paper is silent (also listed in the design notes):
+ * G is scaled by 1/sqrt(m) and Omega by 1/sqrt(k) so that theta~ ~ theta;
+ * Alg. 10 re-uses the sketch and R_11 of Alg. 4 for Alg. 8 (no second sketch);
+ * Omega is indexed by pivot position p (theta~ depends on the pivot order);
+ * an all-zero row gets theta~ = 0; a rank-0 input gives theta~ = 0.
+
+Modes: ``sketch_identity`` replaces S and G by identities (s = m = n) and
+``omega_identity`` replaces Omega by I_r (k = r); with both, theta~ is the exact
+leverage of A_K (Thm 1 with k = rank(A) gives equality).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import rng
+from .linalg import pivoted_qr, back_substitute
+
+
+def _as_float64(A):
+    if sp.issparse(A):
+        return A.astype(np.float64).tocsr()
+    return np.asarray(A, dtype=np.float64)
+
+
+def count_sketch(A, s: int, seed: int, block: int = 1 << 18) -> np.ndarray:
+    """B = S A (s x d), S the CountSketch of rows 0..n-1 (Sec. 2.3.3), FP64 sums."""
+    n, d = A.shape
+    B = np.zeros((s, d))
+    for r0 in range(0, n, block):
+        r1 = min(n, r0 + block)
+        b, sign = rng.bucket_and_sign(r1 - r0, s, seed, start=r0)
+        S = sp.csr_matrix((sign, (b, np.arange(r1 - r0))), shape=(s, r1 - r0))
+        blk = _as_float64(A[r0:r1])
+        prod = S @ blk
+        B += prod.toarray() if sp.issparse(prod) else prod
+    return B
+
+
+def gaussian_stage(B: np.ndarray, m: int, seed: int, block: int = 1 << 14) -> np.ndarray:
+    """A~ = G B with G (m x s) = N(0,1)/sqrt(m), generated in column blocks."""
+    s, d = B.shape
+    At = np.zeros((m, d))
+    for c0 in range(0, s, block):
+        c1 = min(s, c0 + block)
+        At += rng.gaussian_sketch_block(m, s, seed, c0, c1) @ B[c0:c1]
+    return At
+
+
+def sketch(A, s: int, m: int, seed: int) -> np.ndarray:
+    """CountGauss sketch A~ = G (S A) of Alg. 3 (FP64)."""
+    return gaussian_stage(count_sketch(A, s, seed), m, seed)
+
+
+def omega_factor(R11: np.ndarray, k: int, seed: int, omega_identity: bool = False) -> np.ndarray:
+    """M = R_11^{-1} Omega (r x k), Alg. 8 step 4 with X = R^{-1} Pi_2."""
+    r = R11.shape[0]
+    Om = np.eye(r) if omega_identity else rng.omega(r, k, seed)
+    return back_substitute(R11, Om)
+
+
+def m_full(M: np.ndarray, perm, d: int) -> np.ndarray:
+    """Scatter M (r x k) into a d x k matrix: row perm[p] holds M[p, :], other rows 0."""
+    r, k = M.shape
+    out = np.zeros((d, k))
+    out[np.asarray(perm[:r])] = M
+    return out
+
+
+def final_pass(A, perm, r: int, M: np.ndarray, block: int = 1 << 16) -> np.ndarray:
+    """theta~_i = sum_q (sum_{p<r} A[i, P_p] M[p, q])^2 (Alg. 8 step 5), FP64."""
+    n = A.shape[0]
+    cols = np.asarray(perm[:r], dtype=np.int64)
+    theta = np.zeros(n)
+    if r == 0:
+        return theta
+    for r0 in range(0, n, block):
+        blk = _as_float64(A[r0:r0 + block])
+        AK = blk[:, cols]
+        Y = AK @ M
+        Y = Y.toarray() if sp.issparse(Y) else np.asarray(Y)
+        theta[r0:r0 + block] = np.sum(Y * Y, axis=1)
+    return theta
+
+
+class Estimate:
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def estimate(A, s: int, m: int, k: int, tau: float, seed: int, *,
+             sketch_identity: bool = False, omega_identity: bool = False,
+             forced_perm=None, forced_rank=None, Atilde=None) -> Estimate:
+    """Alg. 10 end to end: returns theta (n), rank, perm (d), Atilde, R (r x d), M (r x k).
+
+    ``Atilde`` may be passed in to run steps 4-7 on a given sketch.
+    """
+    n, d = A.shape
+    if Atilde is None:
+        if sketch_identity:
+            Atilde = _as_float64(A)
+            Atilde = Atilde.toarray() if sp.issparse(Atilde) else np.array(Atilde)
+        else:
+            Atilde = sketch(A, s, m, seed)
+    qr = pivoted_qr(Atilde, tau, forced_perm=forced_perm, forced_rank=forced_rank)
+    r = qr.rank
+    if r == 0:
+        return Estimate(theta=np.zeros(n), rank=0, perm=qr.perm, Atilde=Atilde,
+                        R=qr.R, M=np.zeros((0, k)), qr=qr)
+    R11 = qr.R[:, :r]
+    M = omega_factor(R11, k, seed, omega_identity)
+    theta = final_pass(A, qr.perm, r, M)
+    return Estimate(theta=theta, rank=r, perm=qr.perm, Atilde=Atilde, R=qr.R, M=M, qr=qr)

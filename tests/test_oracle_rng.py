@@ -1,0 +1,93 @@
+"""Pins for the oracle's counter-based generators (no GPU)."""
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import rng
+
+
+def _read_golden(golden_dir, name):
+    with open(os.path.join(golden_dir, name)) as f:
+        return [ln.strip() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def test_splitmix64_reference_vectors(golden_dir):
+    want = [int(x, 16) for x in _read_golden(golden_dir, "splitmix64_seed0.txt")]
+    got = [int(x) for x in rng.splitmix64(0, np.arange(len(want)))]
+    assert got == want
+
+
+def test_splitmix64_counter_is_state_stride():
+    # output c from key equals output 0 from key + c * golden (mod 2^64)
+    key = 0x1234_5678_9ABC_DEF0
+    c = 17
+    shifted = (key + c * 0x9E3779B97F4A7C15) % (1 << 64)
+    assert int(rng.splitmix64(key, [c])[0]) == int(rng.splitmix64(shifted, [0])[0])
+
+
+def test_stream_keys_distinct():
+    keys = {rng.stream_key(s, t) for s in range(4) for t in (1, 2, 3)}
+    assert len(keys) == 12
+
+
+def test_bucket_uniform_chi2():
+    n, s = 200_000, 1000
+    b, sign = rng.bucket_and_sign(n, s, seed=5)
+    assert b.min() >= 0 and b.max() < s
+    counts = np.bincount(b, minlength=s)
+    chi2 = ((counts - n / s) ** 2 / (n / s)).sum()
+    assert stats.chi2.sf(chi2, s - 1) > 1e-4
+    # signs: balanced and uncorrelated with the bucket parity and the neighbour
+    assert abs(sign.mean()) < 5 / np.sqrt(n)
+    assert abs(np.mean(sign[:-1] * sign[1:])) < 5 / np.sqrt(n)
+    assert abs(np.mean(sign * np.where(b % 2 == 0, 1.0, -1.0))) < 5 / np.sqrt(n)
+
+
+def test_bucket_is_multiply_shift_of_high_word():
+    x = rng.splitmix64(rng.stream_key(9, rng.STREAM_HASH), np.arange(64))
+    b, sign = rng.bucket_and_sign(64, 77, seed=9)
+    for i in range(64):
+        xi = int(x[i])
+        assert b[i] == ((xi >> 32) * 77) >> 32
+        assert sign[i] == (1.0 if xi % 2 == 0 else -1.0)
+
+
+def test_bucket_offset_start():
+    b0, s0 = rng.bucket_and_sign(100, 13, seed=2)
+    b1, s1 = rng.bucket_and_sign(60, 13, seed=2, start=40)
+    assert np.array_equal(b0[40:], b1) and np.array_equal(s0[40:], s1)
+
+
+def test_box_muller_is_standard_normal():
+    g = rng.gaussian(3, rng.STREAM_G, np.arange(400_000))
+    assert abs(g.mean()) < 5 / np.sqrt(g.size)
+    assert abs(g.var() - 1) < 5 * np.sqrt(2 / g.size)
+    assert abs(stats.kurtosis(g, fisher=False) - 3) < 0.05
+    assert stats.kstest(g, "norm").pvalue > 1e-4
+
+
+def test_box_muller_components():
+    # u1 in (0,1] so the log is finite; cosine branch only
+    key = rng.stream_key(3, rng.STREAM_OMEGA)
+    c = np.arange(10, dtype=np.uint64)
+    x1 = rng.splitmix64(key, 2 * c)
+    x2 = rng.splitmix64(key, 2 * c + 1)
+    for i in range(10):
+        u1 = ((int(x1[i]) >> 11) + 1) / 2.0 ** 53
+        u2 = (int(x2[i]) >> 11) / 2.0 ** 53
+        want = np.sqrt(-2 * np.log(u1)) * np.cos(2 * np.pi * u2)
+        assert rng.gaussian(3, rng.STREAM_OMEGA, [i])[0] == pytest.approx(want, rel=1e-14, abs=1e-15)
+
+
+def test_gaussian_sketch_and_omega_scaling():
+    G = rng.gaussian_sketch_block(64, 4096, 1, 0, 4096)
+    assert G.shape == (64, 4096)
+    assert abs(G.var() * 64 - 1) < 0.05
+    # column blocks agree with the full matrix
+    assert np.array_equal(rng.gaussian_sketch_block(64, 4096, 1, 100, 300), G[:, 100:300])
+    Om = rng.omega(50, 40, 1)
+    assert abs(Om.var() * 40 - 1) < 0.1
+    # Omega rows depend on the pivot position only, not on r
+    assert np.array_equal(rng.omega(20, 40, 1), Om[:20])
