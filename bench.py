@@ -1,0 +1,319 @@
+"""Benchmark of the rank-revealing leverage-score estimator on one GB300.
+
+One step = one pass of the whole method (Alg. 10) over the dense 1,000,000 x 256
+FP32 workload of rank 200 with lognormal(0, 2) row scaling: bucket
+permutation, CountSketch, Gaussian stage (s = 65,536, m = 1,024), FP64 pivoted
+QR and rank, M = R_11^{-1} Omega (k = 256), fused final pass writing theta~.
+The handle caches G (m x s, generated once per seed); every other stage runs
+in every step. A (1.02 GB) is larger than L2 (129 MB), so no L2 flush is used.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--sketch-prec fp32|tf32|bf16|bf16x3] [--final-prec ...]
+
+Prints one JSON line (rank 0). For N > 1 (torchrun) every rank runs its own
+replica on its own GPU (the path is run as replicas; no data is exchanged).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "dense_1e6x256_rank200"
+METRIC = "leverage rows/s & HBM GB/s: BF16/TF32-TC vs FP32 path at equal rel err; bwd/fwd"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            pk = json.load(f)
+        return pk, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms in a thread."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sel = [p for (t, p) in self.samples if t0 - 0.25 <= t <= t1 + 0.25]
+        if not sel:
+            sel = [p for (_, p) in self.samples[-5:]]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in sel if num(p[1]) is not None]
+        mx = [num(p[2]) for p in sel if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in sel for i in range(4) if p[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sel),
+                "power_w_max": max((num(p[3]) or 0.0) for p in sel)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_input(cfg):
+    return W.dense_lowrank_skewed(cfg["n"], cfg["d"], cfg["rank"], seed=cfg["data_seed"])
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_step(A, cfg):
+    from oracle import estimator as E
+    return E.estimate(A.astype(np.float64, copy=False), cfg["s"], cfg["m"], cfg["k"], cfg["tau"], cfg["seed"])
+
+
+def run_reference(args, cfg):
+    """The FP64 CPU oracle as it stands, on row-prefix samples of the workload."""
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    A = make_input(cfg)
+    budget = 200.0 / max(1, args.steps + args.warmup)            # seconds of CPU work per step
+    n_s = cfg["n"] if budget >= 20 else max(65536, int(cfg["n"] * budget / 20.0))
+    sample = A[:n_s]
+    for _ in range(args.warmup):
+        oracle_step(sample, cfg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(sample, cfg)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n_s / dt
+    desc = f"row prefix of {n_s} of {cfg['n']} rows per step, same s, m, k (fixed costs included)"
+    out = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "n": cfg["n"], "d": cfg["d"], "s": cfg["s"], "m": cfg["m"],
+                      "k": cfg["k"], "parallelism": "replicas"},
+           "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cpu_threads(), "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sketch-prec", default="fp32")
+    ap.add_argument("--final-prec", default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    cfg = W.CONFIGS[WORKLOAD]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    import paper_2105_11004_gb300 as L
+
+    n, d = cfg["n"], cfg["d"]
+    A_np = make_input(cfg)
+    A_host = torch.from_numpy(A_np).pin_memory()
+    A = A_host.cuda()
+    h = L.Handle(local)
+    p = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
+                      sketch_prec=args.sketch_prec, final_prec=args.final_prec)
+    theta = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    kernels_per_step = 11
+
+    rank_found = L.lev_estimate_dense(h, A, p, theta)          # also generates and caches G
+    for _ in range(args.warmup):
+        L.lev_estimate_dense(h, A, p, theta, want_rank=False)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        L.lev_estimate_dense(h, A, p, theta, want_rank=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier(world)
+    ms = allmax(world, e0.elapsed_time(e1) / args.steps)
+    clocks = sampler.summary(t_wall0, t_wall1)
+    sampler.stop()
+
+    # per-stage times (same inputs, same stream), for the roofline of the dominant kernel
+    At = torch.empty((cfg["m"], d), dtype=torch.float32, device="cuda")
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    Mf = torch.empty((d, cfg["k"]), dtype=torch.float32, device="cuda")
+    L.lev_sketch_dense(h, A, p, At)
+    r = L.lev_rrqr(h, At, cfg["tau"], perm, R)
+    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
+    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
+    stages = {}
+    reps = max(3, min(args.steps, 20))
+
+    def timed(name, fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        stages[name] = a.elapsed_time(b) / reps
+
+    timed("sketch", lambda: L.lev_sketch_dense(h, A, p, At))
+    timed("rrqr", lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R))
+    timed("omega", lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf))
+    timed("final", lambda: L.lev_final_dense(h, A, Mf, args.final_prec, theta))
+
+    peaks, peak_src = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    final_bytes = n * d * 4 + n * 4 + d * cfg["k"] * 4
+    final_flops = 2.0 * n * r * cfg["k"]
+    t_final = stages["final"] * 1e-3
+    if args.final_prec == "fp32":
+        fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        roof = {"kernel": "k_final_dense_fp32", "bound": "alu", "achieved": final_flops / t_final / 1e12,
+                "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
+    else:
+        roof = {"kernel": "k_final_dense_tc", "bound": "hbm", "achieved": final_bytes / t_final / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["algorithmic"] = final_flops if roof["unit"] == "TFLOP/s" else final_bytes
+    roof["ms"] = stages["final"]
+
+    out = {"metric": METRIC, "value": n * world / (ms * 1e-3), "unit": "rows/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "d": d, "rank": cfg["rank"], "s": cfg["s"], "m": cfg["m"],
+                      "k": cfg["k"], "tau": cfg["tau"], "sketch_prec": args.sketch_prec,
+                      "final_prec": args.final_prec, "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs larger than L2 (A is 1.02 GB), no flush",
+                      "cached": "G (m x s) generated once per seed in the handle; all other stages every step"},
+           "rank_found": rank_found, "stages_ms": stages,
+           "hbm_gbs_step": (n * d * 4 * 2) / (ms * 1e-3) / 1e9,
+           "roofline": roof, "clocks": clocks, "gpu_launches": kernels_per_step * args.steps}
+
+    if not args.no_e2e:
+        theta_host = torch.empty(n, dtype=torch.float32).pin_memory()
+        L.lev_estimate_dense(h, A_host, p, theta_host)
+        torch.cuda.synchronize()
+        barrier(world)
+        ke = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            L.lev_estimate_dense(h, A_host, p, theta_host)    # synchronises (host result)
+        te = allmax(world, (time.perf_counter() - t0) / ke)
+        out["e2e"] = {"value": n * world / te, "unit": "rows/s", "h2d_bytes_per_step": n * d * 4,
+                      "d2h_bytes_per_step": n * 4, "ms_per_step": te * 1e3,
+                      "api": "lev_estimate_dense with pinned host A and theta"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        oracle_step(A_np, cfg)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n / dt, "unit": "rows/s", "cores": cpu_threads(), "kind": "oracle",
+                               "sample": "one run of the FP64 oracle on the full workload", "seconds": dt}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def lib_rrqr_nosync(L, h, At, tau, perm, R):
+    import ctypes
+    import torch
+    m, d = At.shape
+    L._check(L.lib.lev_rrqr(h.ptr, L._ptr(At), m, d, float(tau), L._ptr(perm), L._ptr(R), None,
+                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+
+
+if __name__ == "__main__":
+    main()

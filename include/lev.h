@@ -1,0 +1,201 @@
+/*
+ * lev.h -- C ABI of the GB300 (sm_103a) rank-revealing leverage-score estimator.
+ *
+ * The library computes the estimator of Alg. 10 (LS-HRN-approx) of Sobczyk and
+ * Gallopoulos, "Estimating leverage scores via rank revealing methods and
+ * randomization": a CountGauss sketch A~ = G S A (Alg. 3), a column-pivoted QR
+ * of the sketch that reveals the numerical rank r and the selected columns K
+ * (Alg. 4), and the squared row norms theta~_i = ||A_{i,K} R_11^{-1} Omega||^2
+ * (Alg. 8 steps 4-5, eq. (24)). The problem statement (Sec. 1; Alg. 10
+ * Require/Ensure): a tall matrix A (n x d, n >> d, dense or sparse, any rank)
+ * in; the estimated leverage scores theta~ (n) and the numerical rank r out.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: LEV_OK (0) or one of the LEV_E* codes below; no C++
+ *    exception crosses the ABI. lev_last_error() gives a message for the last
+ *    failing call on the calling thread.
+ *  - Ownership: every array is owned by the caller. Device pointers are plain
+ *    CUDA device pointers. The handle owns its scratch memory (grown on demand
+ *    with cudaMalloc) and a cache of the Gaussian sketch matrix G per
+ *    (seed, m, s, precision).
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Work is enqueued on it; a call returns before the work finishes
+ *    unless it writes a host-side result (rank), in which case it synchronises
+ *    `stream` once at the end.
+ *  - Layouts: dense matrices are row-major with a leading dimension (elements);
+ *    CSR uses int64 row_ptr (n+1), int32 col (nnz, any order within a row,
+ *    duplicates are summed) and FP32 values.
+ *  - Limits: 1 <= d <= 4096, 1 <= n < 2^31, 1 <= s < 2^31, m >= d, 1 <= k <= 4096.
+ *  - Thread safety: a handle may be used by one host thread at a time.
+ *
+ * Random streams (both the library and its test oracle implement these from
+ * the published definitions; no code is shared):
+ *  - splitmix64(key, c): state = key + (c+1) * 0x9E3779B97F4A7C15 (mod 2^64),
+ *    then the splitmix64 finaliser (Steele, Lea and Flood 2014);
+ *  - key_t = seed XOR (t * 0xD1B54A32D192ED03), t = 1 hash, 2 G, 3 Omega;
+ *  - CountSketch (Sec. 2.3.3): x = splitmix64(key_1, i), bucket h(i) =
+ *    (hi32(x) * s) >> 32, sign = +1 if bit 0 of x is 0 else -1;
+ *  - N(0,1) number c of stream t: Box-Muller, cosine branch, with
+ *    u1 = ((splitmix64(key_t, 2c) >> 11) + 1) 2^-53, u2 = (splitmix64(key_t, 2c+1) >> 11) 2^-53;
+ *  - G[j, b] = N_{j*s + b} / sqrt(m) (Sec. 2.3.1 scaling); Omega[p, q] = N_{p*k + q} / sqrt(k),
+ *    p the pivot position (0 <= p < r), q < k.
+ */
+#ifndef LEV_H
+#define LEV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define LEV_OK        0
+#define LEV_EINVAL    1  /* bad shape, pointer, parameter, or CSR structure */
+#define LEV_ENOMEM    2  /* cudaMalloc of handle scratch failed */
+#define LEV_ECUDA     3  /* a CUDA runtime call or kernel launch failed */
+#define LEV_ETIMEOUT  4  /* a bounded device-side wait gave up (the kernel returned early) */
+#define LEV_ERANK0    5  /* numerical rank 0 (A = 0 or |R_00| = 0): theta~ is set to 0 */
+
+/* Arithmetic of a stage (the sketch's Gaussian product, or the final pass). */
+#define LEV_FP32    0   /* FP32 SIMT FMA */
+#define LEV_TF32    1   /* tcgen05 kind::tf32, FP32 accumulate */
+#define LEV_BF16    2   /* tcgen05 kind::f16 with BF16 operands, FP32 accumulate */
+#define LEV_BF16X3  3   /* split hi+lo BF16: hi*hi + lo*hi + hi*lo, FP32 accumulate */
+
+/* Flags (lev_params.flags). */
+#define LEV_OMEGA_IDENTITY  1u  /* Omega = I_r, k = r (the Pi_2-free mode of Sec. 6.4) */
+#define LEV_SKETCH_IDENTITY 2u  /* S = I, G = I, A~ = A (tests; needs n <= 65536) */
+#define LEV_FORCE_PIVOTS    4u  /* take perm_in[0..rank_in) as the pivots, no rank test */
+
+typedef struct lev_handle lev_handle;
+
+typedef struct lev_params {
+    double   eps;          /* CountSketch OSE parameter (Alg. 3 step 1), used when s == 0 */
+    double   delta;        /* CountSketch OSE failure probability, used when s == 0 */
+    double   gamma;        /* oversampling, m = ceil(gamma d) when m == 0 (Alg. 3 step 2) */
+    int64_t  s;            /* CountSketch buckets (the paper's r); 0 = from eps, delta */
+    int64_t  m;            /* rows of G; 0 = ceil(gamma d) */
+    int64_t  k;            /* columns of Omega; 0 = JL size 4 ln n / (eps^2/2 - eps^3/3) */
+    double   tau;          /* rank rule |R_jj| > tau |R_00| (Sec. 6.2); <= 0 means 1e-5 */
+    uint64_t seed;         /* seed of the three random streams */
+    int32_t  sketch_prec;  /* LEV_FP32 | LEV_TF32 | LEV_BF16 | LEV_BF16X3 for A~ = G B */
+    int32_t  final_prec;   /* same set for theta~ = ||A M_full||^2 */
+    uint32_t flags;        /* LEV_* flags above */
+    int32_t  reserved;
+    const int32_t* perm_in;  /* device, d entries; read with LEV_FORCE_PIVOTS */
+    int64_t  rank_in;        /* number of forced pivots; read with LEV_FORCE_PIVOTS */
+} lev_params;
+
+/* Create a handle on CUDA device `device` (the device is made current for every
+ * call on the handle). *out receives the handle. Errors: LEV_EINVAL (NULL out or
+ * bad device), LEV_ECUDA. */
+int lev_create(lev_handle** out, int device);
+
+/* Free the handle and all its scratch memory. NULL is accepted. Waits for
+ * pending work on the handle's device. */
+int lev_destroy(lev_handle* h);
+
+/* Message of the last failing call on this thread ("" if none). Never NULL. */
+const char* lev_last_error(void);
+
+/* Fill *p with the paper's practical defaults (Alg. 3: eps = 1/2, delta = 1/3,
+ * gamma = 2), tau = 1e-5, seed 0, FP32 stages, sizes 0 (derived), no flags. */
+int lev_params_init(lev_params* p);
+
+/* Resolve the sizes a call with (p, n, d) would use: s = ceil((d^2+d) /
+ * ((2 eps - eps^2)^2 delta)) (Alg. 3 step 1), m = ceil(gamma d) (Alg. 3 step 2),
+ * k = ceil(4 ln n / (eps^2/2 - eps^3/3)) (Gaussian JLT lemma, Sec. 2.3.1),
+ * each unless set explicitly in p. Any output pointer may be NULL. */
+int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d,
+                      int64_t* s, int64_t* m, int64_t* k);
+
+/* CountGauss sketch of dense A (Alg. 3): Atilde (m x d, row-major, ld = d,
+ * FP32, device) = G (S A). A: device, n x d FP32, leading dimension lda >= d.
+ * p->sketch_prec selects the arithmetic of the product G B.
+ * Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA. */
+int lev_sketch_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
+                     const lev_params* p, float* Atilde, void* stream);
+
+/* CountGauss sketch of CSR A (Alg. 3); arguments as lev_sketch_dense, with A
+ * given by device arrays row_ptr (n+1, int64, row_ptr[0] = 0, non-decreasing,
+ * row_ptr[n] = nnz), col (nnz, int32 in [0, d)) and val (nnz, FP32). Column
+ * indices are not checked on the device; out-of-range columns are skipped. */
+int lev_sketch_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
+                   int64_t n, int64_t d, int64_t nnz, const lev_params* p,
+                   float* Atilde, void* stream);
+
+/* Column-pivoted Householder QR of the sketch in FP64 (Alg. 4 step 2, with the
+ * xGEQP3-style pivoting of Sec. 6): at step j the remaining column with the
+ * largest trailing norm (recomputed exactly, ties to the lowest original index)
+ * becomes column j; the factorisation stops at the first j with
+ * |R_jj| <= tau |R_00| and *rank = j (Sec. 6.2 rank check); diag(R) >= 0.
+ * Atilde: device, m x d FP32 row-major (ld = d). perm: device, d int32; entries
+ * 0..r-1 are the pivots in order, r..d-1 the other columns in increasing order.
+ * R: device, d x d FP64 row-major; rows 0..r-1 hold [R_11 R_12] in pivoted
+ * column order, rows r..d-1 are zero. rank: host, may be NULL (then the call
+ * does not synchronise). Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA,
+ * LEV_ETIMEOUT, LEV_ERANK0 (rank 0; perm = identity, R = 0). */
+int lev_rrqr(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double tau,
+             int32_t* perm, double* R, int64_t* rank, void* stream);
+
+/* The small factor of the final pass (Alg. 8 step 4 with the QR
+ * orthogonaliser): M = R_11^{-1} Omega (r x k) by FP64 back-substitution, with
+ * Omega drawn from stream 3 of `seed` (or I_r with LEV_OMEGA_IDENTITY, k = r),
+ * scattered into Mfull (device, d x k FP32 row-major): row perm[p] holds M[p, :]
+ * and the d - r rows outside K are 0. R, perm as produced by lev_rrqr; d_rank:
+ * device int64 holding r (read on the device, no host round trip).
+ * Errors: LEV_EINVAL, LEV_ECUDA. */
+int lev_omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int64_t* d_rank,
+                     int64_t d, int64_t k, uint64_t seed, uint32_t flags,
+                     float* Mfull, void* stream);
+
+/* Fused final pass over dense A (Alg. 8 step 5): theta[i] = sum_q (A[i,:] Mfull[:, q])^2
+ * for i < n; the n x k product is never written to memory. A: device n x d
+ * FP32 (lda >= d); Mfull: device d x k FP32 row-major; theta: device n FP32.
+ * prec: LEV_FP32 (SIMT), LEV_TF32, LEV_BF16 or LEV_BF16X3 (tensor cores).
+ * Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA. */
+int lev_final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
+                    const float* Mfull, int64_t k, int32_t prec, float* theta, void* stream);
+
+/* Fused final pass over CSR A: theta[i] = sum_q (sum_t val_t Mfull[col_t, q])^2
+ * (Lemma 1, product form). Arrays as lev_sketch_csr; Mfull as lev_final_dense;
+ * prec must be LEV_FP32. Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA. */
+int lev_final_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
+                  int64_t n, int64_t d, int64_t nnz, const float* Mfull, int64_t k,
+                  int32_t prec, float* theta, void* stream);
+
+/* The whole estimator (Alg. 10) on dense A: sketch, rrqr, omega_factor and the
+ * final pass on one stream. A and theta may be device pointers or host
+ * pointers (pageable or pinned); host buffers are staged through handle scratch
+ * with cudaMemcpyAsync on `stream` and theta is copied back before return.
+ * rank: host, may be NULL (then the call does not synchronise unless buffers
+ * are on the host). perm: device d int32, may be NULL. Errors: any of the above. */
+int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
+                       const lev_params* p, float* theta, int64_t* rank, int32_t* perm,
+                       void* stream);
+
+/* The whole estimator on CSR A (arrays as lev_sketch_csr, device or host). */
+int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
+                     int64_t n, int64_t d, int64_t nnz, const lev_params* p,
+                     float* theta, int64_t* rank, int32_t* perm, void* stream);
+
+/* Gradient of g(A) = sum_i w_i theta~_i(A) with respect to dense A, with the
+ * sketch S, G, Omega, the pivots and the rank held at the values a preceding
+ * lev_estimate_dense(h, A, ..., p, ...) produced (the handle keeps its sketch
+ * state: Atilde, perm, rank). All pointers are device pointers: A (n x d,
+ * lda), w (n FP32), gradA (n x d FP32, ld = d; columns outside K are 0).
+ * The paper has no backward pass; the formulas are the reverse-mode adjoint of
+ * Alg. 10 (QR adjoint with zero Q cotangent). Errors: LEV_EINVAL (no matching
+ * forward state), LEV_ENOMEM, LEV_ECUDA. */
+int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
+                       const lev_params* p, const float* w, float* gradA, void* stream);
+
+/* Device-side status word of the handle: nonzero after a bounded wait gave up. */
+int lev_device_status(lev_handle* h, int32_t* status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LEV_H */

@@ -1,0 +1,240 @@
+"""GB300 (sm_103a) rank-revealing leverage-score estimator -- Python binding.
+
+A thin ctypes layer over ``liblev.so`` (the C ABI of ``include/lev.h``). The
+functions keep the C names (``lev_sketch_dense``, ``lev_rrqr``, ...); they take
+torch tensors, pass their device pointers and the current CUDA stream, and
+translate status codes into ``LevError``. Every step of the method runs in the
+library's CUDA kernels: there is no Python or CPU fallback, and importing this
+package fails if ``liblev.so`` has not been built (``build.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB_PATH, build as build_library  # noqa: F401
+
+LEV_OK, LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0 = 0, 1, 2, 3, 4, 5
+LEV_FP32, LEV_TF32, LEV_BF16, LEV_BF16X3 = 0, 1, 2, 3
+LEV_OMEGA_IDENTITY, LEV_SKETCH_IDENTITY, LEV_FORCE_PIVOTS = 1, 2, 4
+PRECISIONS = {"fp32": LEV_FP32, "tf32": LEV_TF32, "bf16": LEV_BF16, "bf16x3": LEV_BF16X3}
+
+# Every symbol include/lev.h declares, with (restype, argtypes).
+_c_void_p, _i64, _i32, _u32, _u64, _dbl = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                           ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double)
+
+
+class lev_params(ctypes.Structure):
+    _fields_ = [
+        ("eps", _dbl), ("delta", _dbl), ("gamma", _dbl),
+        ("s", _i64), ("m", _i64), ("k", _i64),
+        ("tau", _dbl), ("seed", _u64),
+        ("sketch_prec", _i32), ("final_prec", _i32), ("flags", _u32), ("reserved", _i32),
+        ("perm_in", _c_void_p), ("rank_in", _i64),
+    ]
+
+
+_P = ctypes.POINTER
+SIGNATURES = {
+    "lev_create": (ctypes.c_int, [_P(_c_void_p), ctypes.c_int]),
+    "lev_destroy": (ctypes.c_int, [_c_void_p]),
+    "lev_last_error": (ctypes.c_char_p, []),
+    "lev_params_init": (ctypes.c_int, [_P(lev_params)]),
+    "lev_resolve_sizes": (ctypes.c_int, [_P(lev_params), _i64, _i64, _P(_i64), _P(_i64), _P(_i64)]),
+    "lev_sketch_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p, _c_void_p]),
+    "lev_sketch_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64,
+                                      _P(lev_params), _c_void_p, _c_void_p]),
+    "lev_rrqr": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
+    "lev_omega_factor": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _u64, _u32,
+                                        _c_void_p, _c_void_p]),
+    "lev_final_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _c_void_p, _i64, _i32, _c_void_p,
+                                       _c_void_p]),
+    "lev_final_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64, _c_void_p,
+                                     _i64, _i32, _c_void_p, _c_void_p]),
+    "lev_estimate_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p,
+                                          _P(_i64), _c_void_p, _c_void_p]),
+    "lev_estimate_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64,
+                                        _P(lev_params), _c_void_p, _P(_i64), _c_void_p, _c_void_p]),
+    "lev_backward_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p,
+                                          _c_void_p, _c_void_p]),
+    "lev_device_status": (ctypes.c_int, [_c_void_p, _P(_i32)]),
+}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"liblev.so is not built ({LIB_PATH}); run paper_2105_11004_gb300.build.build()")
+lib = ctypes.CDLL(LIB_PATH)
+for _name, (_res, _args) in SIGNATURES.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class LevError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[lev status {code}] {msg}")
+        self.code = code
+
+
+def _check(rc, allow=()):
+    if rc != LEV_OK and rc not in allow:
+        raise LevError(rc, lib.lev_last_error().decode(errors="replace"))
+    return rc
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """Owns one lev_handle (scratch memory, G cache) on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(lib.lev_create(ctypes.byref(self._h), int(device)))
+        self.device = int(device)
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib.lev_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles = {}
+_lock = threading.Lock()
+
+
+def default_handle(device: int = 0) -> Handle:
+    with _lock:
+        if device not in _handles:
+            _handles[device] = Handle(device)
+        return _handles[device]
+
+
+def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec="fp32", eps=0.5,
+                delta=1.0 / 3.0, gamma=2.0, omega_identity=False, sketch_identity=False,
+                perm_in=None, rank_in=0) -> lev_params:
+    p = lev_params()
+    _check(lib.lev_params_init(ctypes.byref(p)))
+    p.eps, p.delta, p.gamma = eps, delta, gamma
+    p.s, p.m, p.k, p.tau, p.seed = int(s), int(m), int(k), float(tau), int(seed)
+    p.sketch_prec = PRECISIONS[sketch_prec] if isinstance(sketch_prec, str) else int(sketch_prec)
+    p.final_prec = PRECISIONS[final_prec] if isinstance(final_prec, str) else int(final_prec)
+    flags = 0
+    if omega_identity:
+        flags |= LEV_OMEGA_IDENTITY
+    if sketch_identity:
+        flags |= LEV_SKETCH_IDENTITY
+    if perm_in is not None:
+        flags |= LEV_FORCE_PIVOTS
+        p.perm_in = perm_in.data_ptr()
+        p.rank_in = int(rank_in)
+    p.flags = flags
+    return p
+
+
+def lev_resolve_sizes(p: lev_params, n: int, d: int):
+    s, m, k = _i64(), _i64(), _i64()
+    _check(lib.lev_resolve_sizes(ctypes.byref(p), n, d, ctypes.byref(s), ctypes.byref(m), ctypes.byref(k)))
+    return s.value, m.value, k.value
+
+
+# ---- C-ABI entry points (torch tensors in, status-checked) ----
+
+def lev_sketch_dense(h: Handle, A, p: lev_params, Atilde, stream=None):
+    n, d = A.shape
+    _check(lib.lev_sketch_dense(h.ptr, _ptr(A), n, d, A.stride(0), ctypes.byref(p), _ptr(Atilde), _stream(stream)))
+
+
+def lev_sketch_csr(h: Handle, row_ptr, col, val, n, d, p: lev_params, Atilde, stream=None):
+    _check(lib.lev_sketch_csr(h.ptr, _ptr(row_ptr), _ptr(col), _ptr(val), n, d, col.numel(), ctypes.byref(p),
+                              _ptr(Atilde), _stream(stream)))
+
+
+def lev_rrqr(h: Handle, Atilde, tau, perm, R, stream=None) -> int:
+    m, d = Atilde.shape
+    r = _i64()
+    rc = _check(lib.lev_rrqr(h.ptr, _ptr(Atilde), m, d, float(tau), _ptr(perm), _ptr(R), ctypes.byref(r),
+                             _stream(stream)), allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_omega_factor(h: Handle, R, perm, d_rank, d, k, seed, flags, Mfull, stream=None):
+    _check(lib.lev_omega_factor(h.ptr, _ptr(R), _ptr(perm), _ptr(d_rank), d, k, int(seed), int(flags), _ptr(Mfull),
+                                _stream(stream)))
+
+
+def lev_final_dense(h: Handle, A, Mfull, prec, theta, stream=None):
+    n, d = A.shape
+    k = Mfull.shape[1]
+    prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    _check(lib.lev_final_dense(h.ptr, _ptr(A), n, d, A.stride(0), _ptr(Mfull), k, prec, _ptr(theta),
+                               _stream(stream)))
+
+
+def lev_final_csr(h: Handle, row_ptr, col, val, n, d, Mfull, prec, theta, stream=None):
+    k = Mfull.shape[1]
+    prec = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+    _check(lib.lev_final_csr(h.ptr, _ptr(row_ptr), _ptr(col), _ptr(val), n, d, col.numel(), _ptr(Mfull), k, prec,
+                             _ptr(theta), _stream(stream)))
+
+
+def lev_estimate_dense(h: Handle, A, p: lev_params, theta, perm=None, stream=None, want_rank=True):
+    n, d = A.shape
+    r = _i64(-1)
+    rc = _check(lib.lev_estimate_dense(h.ptr, _ptr(A), n, d, A.stride(0), ctypes.byref(p), _ptr(theta),
+                                       ctypes.byref(r) if want_rank else None, _ptr(perm), _stream(stream)),
+                allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_estimate_csr(h: Handle, row_ptr, col, val, n, d, p: lev_params, theta, perm=None, stream=None,
+                     want_rank=True):
+    r = _i64(-1)
+    rc = _check(lib.lev_estimate_csr(h.ptr, _ptr(row_ptr), _ptr(col), _ptr(val), n, d, col.numel(),
+                                     ctypes.byref(p), _ptr(theta), ctypes.byref(r) if want_rank else None,
+                                     _ptr(perm), _stream(stream)), allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_backward_dense(h: Handle, A, p: lev_params, w, gradA, stream=None):
+    n, d = A.shape
+    _check(lib.lev_backward_dense(h.ptr, _ptr(A), n, d, A.stride(0), ctypes.byref(p), _ptr(w), _ptr(gradA),
+                                  _stream(stream)))
+
+
+def lev_device_status(h: Handle) -> int:
+    s = _i32()
+    _check(lib.lev_device_status(h.ptr, ctypes.byref(s)))
+    return s.value
+
+
+# ---- convenience ----
+
+def estimate(A, *, s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec="fp32",
+             omega_identity=False, sketch_identity=False, handle: Handle | None = None):
+    """theta~ (n, FP32), rank, perm (d, int32) for dense FP32 A (torch, on a CUDA device)."""
+    import torch
+    h = handle or default_handle(A.device.index or 0)
+    p = make_params(s=s, m=m, k=k, tau=tau, seed=seed, sketch_prec=sketch_prec, final_prec=final_prec,
+                    omega_identity=omega_identity, sketch_identity=sketch_identity)
+    theta = torch.empty(A.shape[0], dtype=torch.float32, device=A.device)
+    perm = torch.empty(A.shape[1], dtype=torch.int32, device=A.device)
+    r = lev_estimate_dense(h, A, p, theta, perm)
+    return theta, r, perm

@@ -1,0 +1,535 @@
+// C ABI of the leverage-score library: handle, scratch, argument checks and
+// the composition of the stages of Alg. 10 (see include/lev.h).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "lev_common.cuh"
+#include "lev_kernels.cuh"
+#include "lev_tc.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define LEV_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? LEV_ENOMEM : LEV_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+    } while (0)
+
+#define LEV_TRY(expr)              \
+    do {                           \
+        int rc_ = (expr);          \
+        if (rc_ != LEV_OK) return rc_; \
+    } while (0)
+
+struct Buf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct GCache {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    uint64_t seed = 0;
+    int64_t m = -1, s = -1;
+    int kind = -1;   // 0: FP32, 1: BF16 hi+lo
+};
+
+}  // namespace
+
+struct lev_handle {
+    int device = 0;
+    int num_sms = 0;
+    int32_t* status = nullptr;      // device status word
+    int64_t* host_rank = nullptr;   // pinned
+    Buf count, off, tmp, perm_rows, B, partial, Atilde, qr, R, perm_d, Mfull, stageA, stageTheta,
+        tc_ws, csr_rp, csr_col, csr_val;
+    GCache g;
+};
+
+namespace {
+
+int ensure(Buf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return LEV_OK;
+    if (b.ptr) {
+        cudaError_t e = cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return fail(LEV_ECUDA, "cudaFree: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMalloc(&b.ptr, bytes);
+    if (e != cudaSuccess) {
+        b.ptr = nullptr;
+        cudaGetLastError();
+        return fail(LEV_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return LEV_OK;
+}
+
+void release(Buf& b) {
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+int set_device(lev_handle* h) {
+    if (!h) return fail(LEV_EINVAL, "handle is NULL");
+    LEV_CUDA(cudaSetDevice(h->device));
+    return LEV_OK;
+}
+
+bool is_host_pointer(const void* p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+struct Sizes {
+    int64_t s, m, k;
+};
+
+int resolve(const lev_params* p, int64_t n, int64_t d, Sizes* z) {
+    if (!p) return fail(LEV_EINVAL, "params is NULL");
+    if (n < 1 || n >= (int64_t)1 << 31) return fail(LEV_EINVAL, "n = %lld out of range [1, 2^31)", (long long)n);
+    if (d < 1 || d > 4096) return fail(LEV_EINVAL, "d = %lld out of range [1, 4096]", (long long)d);
+    const double eps = p->eps, delta = p->delta;
+    int64_t s = p->s, m = p->m, k = p->k;
+    if (s == 0) {
+        if (!(eps > 0 && eps < 1 && delta > 0 && delta < 1)) return fail(LEV_EINVAL, "eps, delta must be in (0,1)");
+        const double t = 2 * eps - eps * eps;
+        s = (int64_t)std::ceil(((double)d * d + d) / (t * t * delta));
+    }
+    if (m == 0) {
+        if (!(p->gamma > 0)) return fail(LEV_EINVAL, "gamma must be > 0");
+        m = (int64_t)std::ceil(p->gamma * (double)d);
+    }
+    if (k == 0) {
+        if (!(eps > 0 && eps < 1)) return fail(LEV_EINVAL, "eps must be in (0,1)");
+        k = (int64_t)std::ceil(4.0 * std::log((double)(n > 1 ? n : 2)) / (eps * eps / 2 - eps * eps * eps / 3));
+    }
+    if (p->flags & LEV_SKETCH_IDENTITY) {
+        s = n;
+        m = n;
+        if (n > 65536) return fail(LEV_EINVAL, "LEV_SKETCH_IDENTITY needs n <= 65536");
+    }
+    if (p->flags & LEV_OMEGA_IDENTITY) k = d;
+    if (s < 1 || s >= (int64_t)1 << 31) return fail(LEV_EINVAL, "s = %lld out of range [1, 2^31)", (long long)s);
+    if (m < 1 || m > (int64_t)1 << 20) return fail(LEV_EINVAL, "m = %lld out of range [1, 2^20]", (long long)m);
+    if (k < 1 || k > 4096) return fail(LEV_EINVAL, "k = %lld out of range [1, 4096]", (long long)k);
+    if ((double)m * (double)s > 8.0e9) return fail(LEV_EINVAL, "m * s = %.3g too large", (double)m * s);
+    z->s = s;
+    z->m = m;
+    z->k = k;
+    return LEV_OK;
+}
+
+int check_prec(int32_t prec, const char* what) {
+    if (prec < LEV_FP32 || prec > LEV_BF16X3) return fail(LEV_EINVAL, "%s precision %d unknown", what, prec);
+    return LEV_OK;
+}
+
+double tau_of(const lev_params* p) { return p->tau > 0 ? p->tau : 1e-5; }
+
+// Make sure G (m x s) for (seed, kind) is in the cache; returns its pointers.
+int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
+             const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo) {
+    GCache& g = h->g;
+    const size_t elems = (size_t)m * (size_t)s;
+    const size_t bytes = kind == 0 ? elems * sizeof(float) : elems * 2 * sizeof(__nv_bfloat16);
+    if (!(g.ptr && g.seed == seed && g.m == m && g.s == s && g.kind == kind)) {
+        if (g.bytes < bytes) {
+            if (g.ptr) cudaFree(g.ptr);
+            g.ptr = nullptr;
+            g.bytes = 0;
+            cudaError_t e = cudaMalloc(&g.ptr, bytes);
+            if (e != cudaSuccess) {
+                g.ptr = nullptr;
+                cudaGetLastError();
+                return fail(LEV_ENOMEM, "cudaMalloc(G, %zu bytes) failed", bytes);
+            }
+            g.bytes = bytes;
+        }
+        cudaError_t e;
+        if (kind == 0)
+            e = lev::launch_gen_gaussian(m, s, seed, (float*)g.ptr, nullptr, nullptr, st);
+        else
+            e = lev::launch_gen_gaussian(m, s, seed, nullptr, (__nv_bfloat16*)g.ptr,
+                                         (__nv_bfloat16*)g.ptr + elems, st);
+        if (e != cudaSuccess) return fail(LEV_ECUDA, "G generation: %s", cudaGetErrorString(e));
+        g.seed = seed;
+        g.m = m;
+        g.s = s;
+        g.kind = kind;
+    }
+    if (g32) *g32 = kind == 0 ? (const float*)g.ptr : nullptr;
+    if (ghi) *ghi = kind == 1 ? (const __nv_bfloat16*)g.ptr : nullptr;
+    if (glo) *glo = kind == 1 ? (const __nv_bfloat16*)g.ptr + elems : nullptr;
+    return LEV_OK;
+}
+
+// Gaussian stage A~ = G B for the selected precision.
+int gaussian_stage(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d, uint64_t seed,
+                   int32_t prec, float* Atilde, cudaStream_t st) {
+    if (prec == LEV_FP32) {
+        const float* g32 = nullptr;
+        LEV_TRY(ensure_g(h, m, s, seed, 0, st, &g32, nullptr, nullptr));
+        const int splits = lev::gaussian_stage_splits(m, d, s);
+        LEV_TRY(ensure(h->partial, sizeof(float) * (size_t)splits * m * d));
+        LEV_CUDA(lev::launch_gaussian_stage_fp32(g32, B, m, s, d, (float*)h->partial.ptr, splits, Atilde, st));
+        return LEV_OK;
+    }
+    return lev::tc_gaussian_stage(h, B, m, s, d, seed, prec, Atilde, st);
+}
+
+int sketch_common_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
+                        const lev_params* p, const Sizes& z, float* Atilde, cudaStream_t st) {
+    if (p->flags & LEV_SKETCH_IDENTITY) {
+        LEV_CUDA(lev::launch_copy_dense(A, lda, n, d, Atilde, st));
+        return LEV_OK;
+    }
+    LEV_TRY(ensure(h->count, sizeof(int) * (size_t)(z.s + 1)));
+    LEV_TRY(ensure(h->off, sizeof(int) * (size_t)(z.s + 1)));
+    LEV_TRY(ensure(h->tmp, sizeof(uint32_t) * (size_t)n));
+    LEV_TRY(ensure(h->perm_rows, sizeof(uint32_t) * (size_t)n));
+    LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
+    LEV_CUDA(lev::launch_bucket_perm(n, z.s, p->seed, (int*)h->count.ptr, (int*)h->off.ptr,
+                                     (uint32_t*)h->tmp.ptr, (uint32_t*)h->perm_rows.ptr, st));
+    LEV_CUDA(lev::launch_countsketch_dense(A, lda, d, z.s, (const int*)h->off.ptr,
+                                           (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));
+    return gaussian_stage(h, (const float*)h->B.ptr, z.m, z.s, d, p->seed, p->sketch_prec, Atilde, st);
+}
+
+int sketch_common_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
+                      int64_t n, int64_t d, const lev_params* p, const Sizes& z, float* Atilde,
+                      cudaStream_t st) {
+    if (p->flags & LEV_SKETCH_IDENTITY) return fail(LEV_EINVAL, "LEV_SKETCH_IDENTITY is for dense A only");
+    LEV_TRY(ensure(h->count, sizeof(int) * (size_t)(z.s + 1)));
+    LEV_TRY(ensure(h->off, sizeof(int) * (size_t)(z.s + 1)));
+    LEV_TRY(ensure(h->tmp, sizeof(uint32_t) * (size_t)n));
+    LEV_TRY(ensure(h->perm_rows, sizeof(uint32_t) * (size_t)n));
+    LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
+    LEV_CUDA(lev::launch_bucket_perm(n, z.s, p->seed, (int*)h->count.ptr, (int*)h->off.ptr,
+                                     (uint32_t*)h->tmp.ptr, (uint32_t*)h->perm_rows.ptr, st));
+    LEV_CUDA(lev::launch_countsketch_csr(row_ptr, col, val, d, z.s, (const int*)h->off.ptr,
+                                         (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));
+    return gaussian_stage(h, (const float*)h->B.ptr, z.m, z.s, d, p->seed, p->sketch_prec, Atilde, st);
+}
+
+int rrqr_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double tau,
+                const int32_t* forced, int64_t forced_rank, int32_t* perm, double* R,
+                lev::QrScratch* qs, cudaStream_t st) {
+    LEV_TRY(ensure(h->qr, lev::qr_scratch_bytes(m, d)));
+    lev::qr_scratch_carve(h->qr.ptr, m, d, qs);
+    LEV_CUDA(lev::launch_pivoted_qr(Atilde, m, d, tau, forced, forced_rank, *qs, perm, R, h->status,
+                                    h->num_sms, st));
+    return LEV_OK;
+}
+
+// Synchronise, read the rank and the device status word.
+int finish(lev_handle* h, const lev::QrScratch& qs, int64_t* rank, cudaStream_t st) {
+    LEV_CUDA(cudaMemcpyAsync(h->host_rank, qs.rank, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    int32_t status = 0;
+    LEV_CUDA(cudaMemcpyAsync(h->host_rank + 1, h->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    LEV_CUDA(cudaStreamSynchronize(st));
+    memcpy(&status, h->host_rank + 1, sizeof(int32_t));
+    if (status != 0) {
+        cudaMemsetAsync(h->status, 0, sizeof(int32_t), st);
+        return fail(LEV_ETIMEOUT, "a bounded device wait gave up (status %d)", status);
+    }
+    if (rank) *rank = h->host_rank[0];
+    if (h->host_rank[0] == 0) return fail(LEV_ERANK0, "numerical rank is 0");
+    return LEV_OK;
+}
+
+int final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const float* Mfull,
+                int64_t k, int32_t prec, float* theta, cudaStream_t st) {
+    if (prec == LEV_FP32) {
+        LEV_CUDA(lev::launch_final_dense_fp32(A, lda, n, d, Mfull, k, theta, st));
+        return LEV_OK;
+    }
+    return lev::tc_final_dense(h, A, n, d, lda, Mfull, k, prec, theta, st);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// scratch access for the tensor-core module
+// ---------------------------------------------------------------------------
+namespace lev {
+int handle_scratch(lev_handle* h, int which, size_t bytes, void** out) {
+    Buf* b = which == 0 ? &h->tc_ws : &h->partial;
+    LEV_TRY(ensure(*b, bytes));
+    *out = b->ptr;
+    return LEV_OK;
+}
+int handle_num_sms(lev_handle* h) { return h->num_sms; }
+int handle_gaussian(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
+                    const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo) {
+    return ensure_g(h, m, s, seed, kind, st, g32, ghi, glo);
+}
+int handle_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace lev
+
+extern "C" {
+
+const char* lev_last_error(void) { return g_last_error.c_str(); }
+
+int lev_params_init(lev_params* p) {
+    if (!p) return fail(LEV_EINVAL, "params is NULL");
+    memset(p, 0, sizeof(*p));
+    p->eps = 0.5;
+    p->delta = 1.0 / 3.0;
+    p->gamma = 2.0;
+    p->tau = 1e-5;
+    p->sketch_prec = LEV_FP32;
+    p->final_prec = LEV_FP32;
+    return LEV_OK;
+}
+
+int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d, int64_t* s, int64_t* m, int64_t* k) {
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (s) *s = z.s;
+    if (m) *m = z.m;
+    if (k) *k = z.k;
+    return LEV_OK;
+}
+
+int lev_create(lev_handle** out, int device) {
+    if (!out) return fail(LEV_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    LEV_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(LEV_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    LEV_CUDA(cudaSetDevice(device));
+    lev_handle* h = new lev_handle();
+    h->device = device;
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&h->status, 64) != cudaSuccess || cudaMemset(h->status, 0, 64) != cudaSuccess ||
+        cudaMallocHost(&h->host_rank, 64) != cudaSuccess) {
+        cudaGetLastError();
+        lev_destroy(h);
+        return fail(LEV_ENOMEM, "handle allocation failed");
+    }
+    *out = h;
+    return LEV_OK;
+}
+
+int lev_destroy(lev_handle* h) {
+    if (!h) return LEV_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
+                  &h->R, &h->perm_d, &h->Mfull, &h->stageA, &h->stageTheta, &h->tc_ws, &h->csr_rp,
+                  &h->csr_col, &h->csr_val};
+    for (Buf* b : all) release(*b);
+    if (h->g.ptr) cudaFree(h->g.ptr);
+    if (h->status) cudaFree(h->status);
+    if (h->host_rank) cudaFreeHost(h->host_rank);
+    delete h;
+    return LEV_OK;
+}
+
+int lev_device_status(lev_handle* h, int32_t* status) {
+    LEV_TRY(set_device(h));
+    if (!status) return fail(LEV_EINVAL, "status is NULL");
+    LEV_CUDA(cudaMemcpy(status, h->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return LEV_OK;
+}
+
+int lev_sketch_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
+                     const lev_params* p, float* Atilde, void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!A || !Atilde) return fail(LEV_EINVAL, "NULL array");
+    if (lda < d) return fail(LEV_EINVAL, "lda < d");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    return sketch_common_dense(h, A, n, d, lda, p, z, Atilde, (cudaStream_t)stream);
+}
+
+int lev_sketch_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
+                   int64_t n, int64_t d, int64_t nnz, const lev_params* p, float* Atilde, void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!row_ptr || (nnz > 0 && (!col || !val)) || !Atilde) return fail(LEV_EINVAL, "NULL array");
+    if (nnz < 0) return fail(LEV_EINVAL, "nnz < 0");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    return sketch_common_csr(h, row_ptr, col, val, n, d, p, z, Atilde, (cudaStream_t)stream);
+}
+
+int lev_rrqr(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double tau, int32_t* perm,
+             double* R, int64_t* rank, void* stream) {
+    LEV_TRY(set_device(h));
+    if (!Atilde || !perm || !R) return fail(LEV_EINVAL, "NULL array");
+    if (m < 1 || d < 1 || d > 4096 || m > (1 << 20)) return fail(LEV_EINVAL, "bad shape m=%lld d=%lld", (long long)m, (long long)d);
+    if (tau <= 0) tau = 1e-5;
+    cudaStream_t st = (cudaStream_t)stream;
+    lev::QrScratch qs;
+    LEV_TRY(rrqr_common(h, Atilde, m, d, tau, nullptr, 0, perm, R, &qs, st));
+    if (!rank) return LEV_OK;
+    return finish(h, qs, rank, st);
+}
+
+int lev_omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int64_t* d_rank,
+                     int64_t d, int64_t k, uint64_t seed, uint32_t flags, float* Mfull, void* stream) {
+    LEV_TRY(set_device(h));
+    if (!R || !perm || !d_rank || !Mfull) return fail(LEV_EINVAL, "NULL array");
+    if (d < 1 || d > 4096 || k < 1 || k > 4096) return fail(LEV_EINVAL, "bad shape d=%lld k=%lld", (long long)d, (long long)k);
+    LEV_CUDA(lev::launch_omega_factor(R, perm, d_rank, d, k, seed, (flags & LEV_OMEGA_IDENTITY) != 0, nullptr,
+                                      Mfull, (cudaStream_t)stream));
+    return LEV_OK;
+}
+
+int lev_final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const float* Mfull,
+                    int64_t k, int32_t prec, float* theta, void* stream) {
+    LEV_TRY(set_device(h));
+    if (!A || !Mfull || !theta) return fail(LEV_EINVAL, "NULL array");
+    if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > 4096 || k < 1 || k > 4096 || lda < d)
+        return fail(LEV_EINVAL, "bad shape");
+    LEV_TRY(check_prec(prec, "final"));
+    return final_dense(h, A, n, d, lda, Mfull, k, prec, theta, (cudaStream_t)stream);
+}
+
+int lev_final_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                  int64_t d, int64_t nnz, const float* Mfull, int64_t k, int32_t prec, float* theta,
+                  void* stream) {
+    LEV_TRY(set_device(h));
+    if (!row_ptr || (nnz > 0 && (!col || !val)) || !Mfull || !theta) return fail(LEV_EINVAL, "NULL array");
+    if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > 4096 || k < 1 || k > 4096 || nnz < 0)
+        return fail(LEV_EINVAL, "bad shape");
+    if (prec != LEV_FP32) return fail(LEV_EINVAL, "the CSR final pass supports LEV_FP32 only");
+    LEV_CUDA(lev::launch_final_csr_fp32(row_ptr, col, val, n, d, Mfull, k, theta, (cudaStream_t)stream));
+    return LEV_OK;
+}
+
+static int estimate_tail(lev_handle* h, const Sizes& z, int64_t d, const lev_params* p, int32_t* perm_out,
+                         lev::QrScratch* qs, cudaStream_t st) {
+    LEV_TRY(ensure(h->R, sizeof(double) * (size_t)d * d));
+    LEV_TRY(ensure(h->perm_d, sizeof(int32_t) * (size_t)d));
+    int32_t* perm = perm_out ? perm_out : (int32_t*)h->perm_d.ptr;
+    const bool forced = (p->flags & LEV_FORCE_PIVOTS) != 0;
+    if (forced && (!p->perm_in || p->rank_in < 0 || p->rank_in > d))
+        return fail(LEV_EINVAL, "LEV_FORCE_PIVOTS needs perm_in and 0 <= rank_in <= d");
+    LEV_TRY(rrqr_common(h, (const float*)h->Atilde.ptr, z.m, d, tau_of(p), forced ? p->perm_in : nullptr,
+                        forced ? p->rank_in : 0, perm, (double*)h->R.ptr, qs, st));
+    if (perm != (int32_t*)h->perm_d.ptr)
+        LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
+    LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * z.k));
+    LEV_CUDA(lev::launch_omega_factor((const double*)h->R.ptr, perm, qs->rank, d, z.k, p->seed,
+                                      (p->flags & LEV_OMEGA_IDENTITY) != 0, nullptr, (float*)h->Mfull.ptr, st));
+    return LEV_OK;
+}
+
+int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const lev_params* p,
+                       float* theta, int64_t* rank, int32_t* perm, void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!A || !theta) return fail(LEV_EINVAL, "NULL array");
+    if (lda < d) return fail(LEV_EINVAL, "lda < d");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    LEV_TRY(check_prec(p->final_prec, "final"));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool hostA = is_host_pointer(A), hostT = is_host_pointer(theta);
+    const float* dA = A;
+    int64_t ldA = lda;
+    if (hostA) {
+        LEV_TRY(ensure(h->stageA, sizeof(float) * (size_t)n * d));
+        LEV_CUDA(cudaMemcpy2DAsync(h->stageA.ptr, sizeof(float) * d, A, sizeof(float) * lda, sizeof(float) * d, n,
+                                   cudaMemcpyHostToDevice, st));
+        dA = (const float*)h->stageA.ptr;
+        ldA = d;
+    }
+    float* dT = theta;
+    if (hostT) {
+        LEV_TRY(ensure(h->stageTheta, sizeof(float) * (size_t)n));
+        dT = (float*)h->stageTheta.ptr;
+    }
+    LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
+    LEV_TRY(sketch_common_dense(h, dA, n, d, ldA, p, z, (float*)h->Atilde.ptr, st));
+    lev::QrScratch qs;
+    LEV_TRY(estimate_tail(h, z, d, p, perm, &qs, st));
+    LEV_TRY(final_dense(h, dA, n, d, ldA, (const float*)h->Mfull.ptr, z.k, p->final_prec, dT, st));
+    if (hostT) LEV_CUDA(cudaMemcpyAsync(theta, dT, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    if (!rank && !hostA && !hostT) return LEV_OK;
+    return finish(h, qs, rank, st);
+}
+
+int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                     int64_t d, int64_t nnz, const lev_params* p, float* theta, int64_t* rank, int32_t* perm,
+                     void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!row_ptr || (nnz > 0 && (!col || !val)) || !theta) return fail(LEV_EINVAL, "NULL array");
+    if (nnz < 0) return fail(LEV_EINVAL, "nnz < 0");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    if (p->final_prec != LEV_FP32) return fail(LEV_EINVAL, "the CSR final pass supports LEV_FP32 only");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool hostA = is_host_pointer(row_ptr), hostT = is_host_pointer(theta);
+    const int64_t* rp = row_ptr;
+    const int32_t* cl = col;
+    const float* vl = val;
+    if (hostA) {
+        LEV_TRY(ensure(h->csr_rp, sizeof(int64_t) * (size_t)(n + 1)));
+        LEV_TRY(ensure(h->csr_col, sizeof(int32_t) * (size_t)nnz));
+        LEV_TRY(ensure(h->csr_val, sizeof(float) * (size_t)nnz));
+        LEV_CUDA(cudaMemcpyAsync(h->csr_rp.ptr, row_ptr, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st));
+        if (nnz > 0) {
+            LEV_CUDA(cudaMemcpyAsync(h->csr_col.ptr, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, st));
+            LEV_CUDA(cudaMemcpyAsync(h->csr_val.ptr, val, sizeof(float) * (size_t)nnz, cudaMemcpyHostToDevice, st));
+        }
+        rp = (const int64_t*)h->csr_rp.ptr;
+        cl = (const int32_t*)h->csr_col.ptr;
+        vl = (const float*)h->csr_val.ptr;
+    }
+    float* dT = theta;
+    if (hostT) {
+        LEV_TRY(ensure(h->stageTheta, sizeof(float) * (size_t)n));
+        dT = (float*)h->stageTheta.ptr;
+    }
+    LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
+    LEV_TRY(sketch_common_csr(h, rp, cl, vl, n, d, p, z, (float*)h->Atilde.ptr, st));
+    lev::QrScratch qs;
+    LEV_TRY(estimate_tail(h, z, d, p, perm, &qs, st));
+    LEV_CUDA(lev::launch_final_csr_fp32(rp, cl, vl, n, d, (const float*)h->Mfull.ptr, z.k, dT, st));
+    if (hostT) LEV_CUDA(cudaMemcpyAsync(theta, dT, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    if (!rank && !hostA && !hostT) return LEV_OK;
+    return finish(h, qs, rank, st);
+}
+
+int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const lev_params* p,
+                       const float* w, float* gradA, void* stream) {
+    LEV_TRY(set_device(h));
+    (void)A; (void)n; (void)d; (void)lda; (void)p; (void)w; (void)gradA; (void)stream;
+    return fail(LEV_EINVAL, "lev_backward_dense: no forward state");
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Host-side launch functions of the CUDA kernels (one .cu file per stage).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lev {
+
+// ---- sketch.cu: hash, bucket permutation, CountSketch, G, Gaussian stage ----
+
+// Bucket permutation of rows 0..n-1 (counting sort by h(i), rows ascending in
+// each bucket). count: s+1 ints (scratch), off: s+1 ints (out), tmp and perm:
+// n uint32 each (perm out). A perm entry is row | (sign < 0) << 31.
+cudaError_t launch_bucket_perm(int64_t n, int64_t s, uint64_t seed, int* count, int* off,
+                               uint32_t* tmp, uint32_t* perm, cudaStream_t st);
+
+// B (s x d, ld = d, FP32) = S A for dense A (n x d, lda).
+cudaError_t launch_countsketch_dense(const float* A, int64_t lda, int64_t d, int64_t s,
+                                     const int* off, const uint32_t* perm, float* B, cudaStream_t st);
+
+// B (s x d, ld = d, FP32) = S A for CSR A.
+cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, const float* val,
+                                   int64_t d, int64_t s, const int* off, const uint32_t* perm,
+                                   float* B, cudaStream_t st);
+
+// G (m x s): FP32 copy and/or BF16 hi/lo copies (any pointer may be null).
+cudaError_t launch_gen_gaussian(int64_t m, int64_t s, uint64_t seed, float* g32,
+                                __nv_bfloat16* ghi, __nv_bfloat16* glo, cudaStream_t st);
+
+// Atilde (m x d) = G (m x s) B (s x d), FP32 SIMT, split-K with a fixed-order
+// reduction. partial: splits * m * d floats of scratch; returns splits used.
+int gaussian_stage_splits(int64_t m, int64_t d, int64_t s);
+cudaError_t launch_gaussian_stage_fp32(const float* G, const float* B, int64_t m, int64_t s,
+                                       int64_t d, float* partial, int splits, float* Atilde,
+                                       cudaStream_t st);
+
+// Identity sketch: Atilde = A (n x d) copied densely (ld = d).
+cudaError_t launch_copy_dense(const float* A, int64_t lda, int64_t n, int64_t d, float* out,
+                              cudaStream_t st);
+
+// ---- qr.cu: pivoted QR (FP64), omega factor ----
+
+struct QrScratch {
+    double* W;        // m x d FP64, column-major (ld = m)
+    double* norms;    // 2 x d FP64 (double-buffered trailing norms^2)
+    double* Rorig;    // d x d FP64: row j, original column c
+    int32_t* piv;     // d int32: pivot order (original column ids)
+    int64_t* rank;    // 1 int64 (device)
+    unsigned* barrier;  // 1 uint32 grid-barrier counter
+};
+size_t qr_scratch_bytes(int64_t m, int64_t d);
+void qr_scratch_carve(void* base, int64_t m, int64_t d, QrScratch* q);
+
+// Pivoted QR of Atilde (m x d FP32 row-major). forced_perm may be null.
+// Writes perm (d), R (d x d row-major), d_rank. status: device status word.
+cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double tau,
+                              const int32_t* forced_perm, int64_t forced_rank,
+                              const QrScratch& q, int32_t* perm, double* R, int32_t* status,
+                              int num_sms, cudaStream_t st);
+
+// Mfull (d x k FP32) = scatter of R_11^{-1} Omega by perm; reads r from d_rank.
+cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int64_t* d_rank,
+                                int64_t d, int64_t k, uint64_t seed, bool omega_identity,
+                                double* Mscratch, float* Mfull, cudaStream_t st);
+
+// ---- final.cu: fused final pass (SIMT) ----
+
+cudaError_t launch_final_dense_fp32(const float* A, int64_t lda, int64_t n, int64_t d,
+                                    const float* Mfull, int64_t k, float* theta, cudaStream_t st);
+cudaError_t launch_final_csr_fp32(const int64_t* row_ptr, const int32_t* col, const float* val,
+                                  int64_t n, int64_t d, const float* Mfull, int64_t k,
+                                  float* theta, cudaStream_t st);
+
+}  // namespace lev

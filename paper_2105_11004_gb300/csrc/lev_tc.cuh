@@ -1,0 +1,27 @@
+// Tensor-core (tcgen05) forms of the Gaussian stage and of the final pass.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+struct lev_handle;
+
+namespace lev {
+
+// Handle services used by the tensor-core module (defined in api.cu).
+int handle_scratch(lev_handle* h, int which, size_t bytes, void** out);
+int handle_num_sms(lev_handle* h);
+int handle_gaussian(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
+                    const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo);
+int handle_fail(int code, const char* msg);
+
+// A~ (m x d) = G B with prec in {LEV_TF32, LEV_BF16, LEV_BF16X3}.
+int tc_gaussian_stage(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d, uint64_t seed,
+                      int32_t prec, float* Atilde, cudaStream_t st);
+
+// theta = rowsum((A Mfull)^2) with prec in {LEV_TF32, LEV_BF16, LEV_BF16X3}.
+int tc_final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const float* Mfull,
+                   int64_t k, int32_t prec, float* theta, cudaStream_t st);
+
+}  // namespace lev

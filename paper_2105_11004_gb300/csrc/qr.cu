@@ -1,0 +1,271 @@
+// Rank-revealing QR of the sketch and the small factor M = R_11^{-1} Omega, FP64.
+//
+// Pivoted QR (Alg. 4 step 2 with the xGEQP3-style pivoting the paper's
+// implementation uses, Sec. 6): one cooperatively launched persistent kernel.
+// The FP64 working copy W (m x d, column-major) stays in global memory (it is
+// L2 resident: 32 MB at 4096 x 1024). Every CTA owns a fixed set of columns.
+// Step j, in every CTA after a grid barrier:
+//   1. the pivot p_j is the active column with the largest trailing norm
+//      ||W[j:, c]||^2 (recomputed exactly in step j-1, double-buffered by
+//      parity; ties to the lowest column id) -- every CTA computes the same
+//      argmax from the same data;
+//   2. rank test |R_jj| = ||W[j:, p]|| <= tau |R_00| ends the factorisation;
+//   3. the Householder vector of column p is read straight from W (v_j =
+//      x_j - alpha, v_i = x_i) and applied to the CTA's own active columns,
+//      which also write their new trailing norms and row j of R.
+// A second small kernel orders the columns (pivots first, then the rest in
+// increasing id) and writes R in pivoted order with diag(R) >= 0.
+#include "lev_common.cuh"
+#include "lev_kernels.cuh"
+
+namespace lev {
+
+namespace {
+
+constexpr int QR_THREADS = 128;
+constexpr int QR_WARPS = QR_THREADS / 32;
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < QR_WARPS; ++i) t += red[i];
+    return t;
+}
+
+struct QrArgs {
+    const float* At;
+    int m, d;
+    double tau;
+    const int32_t* forced;
+    int forced_rank;
+    QrScratch q;
+    int32_t* status;
+};
+
+__global__ void __launch_bounds__(QR_THREADS) k_pivoted_qr(QrArgs a) {
+    __shared__ double red[QR_WARPS];
+    __shared__ double redv[QR_WARPS];
+    __shared__ int redi[QR_WARPS];
+    const int m = a.m, d = a.d;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double* W = a.q.W;
+    double* norms = a.q.norms;
+    unsigned epoch = 0;
+
+    // Phase 0: FP64 copy of the owned columns and their full norms.
+    for (int c = blockIdx.x; c < d; c += gridDim.x) {
+        double acc = 0.0;
+        for (int i = tid; i < m; i += QR_THREADS) {
+            const double x = (double)a.At[(int64_t)i * d + c];
+            W[(int64_t)c * m + i] = x;
+            acc += x * x;
+        }
+        acc = block_sum(acc, red);
+        if (tid == 0) norms[c] = acc;
+    }
+    if (!grid_barrier(a.q.barrier, epoch, a.status)) return;
+
+    const int steps = a.forced ? min(a.forced_rank, min(m, d)) : min(m, d);
+    double r00 = 0.0;
+    int j = 0;
+    for (; j < steps; ++j) {
+        const double* cur = norms + (j & 1) * d;
+        double* nxt = norms + ((j + 1) & 1) * d;
+        // 1. pivot
+        int p;
+        if (a.forced) {
+            p = a.forced[j];
+            if (p < 0 || p >= d || cur[p] < 0.0) break;       // invalid or repeated pivot
+        } else {
+            double bv = -2.0;
+            int bi = d;
+            for (int c = tid; c < d; c += QR_THREADS) {
+                const double v = cur[c];
+                if (v > bv) { bv = v; bi = c; }                   // c ascending: first max kept
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            __syncthreads();
+            if (lane == 0) { redv[wid] = bv; redi[wid] = bi; }
+            __syncthreads();
+            bv = redv[0]; bi = redi[0];
+            for (int i = 1; i < QR_WARPS; ++i)
+                if (redv[i] > bv || (redv[i] == bv && redi[i] < bi)) { bv = redv[i]; bi = redi[i]; }
+            p = bi;
+        }
+        const double nrm2 = cur[p];
+        const double nrm = sqrt(fmax(nrm2, 0.0));
+        // 2. rank test
+        if (j == 0) r00 = nrm;
+        if (!(nrm2 > 0.0)) break;
+        if (!a.forced && nrm <= a.tau * r00) break;
+        // 3. reflector from column p: H x = alpha e_j
+        const double* x = W + (int64_t)p * m;
+        const double x0 = x[j];
+        const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+        const double v0 = x0 - alpha;
+        const double beta = 1.0 / (nrm * (nrm + fabs(x0)));   // 2 / (v^T v)
+        for (int c = blockIdx.x; c < d; c += gridDim.x) {
+            if (c == p) continue;
+            if (cur[c] < 0.0) {                                 // pivoted earlier: stays inactive
+                if (tid == 0) nxt[c] = -1.0;
+                continue;
+            }
+            double* w = W + (int64_t)c * m;
+            double dot = 0.0;
+            for (int i = j + 1 + tid; i < m; i += QR_THREADS) dot += x[i] * w[i];
+            dot = block_sum(dot, red) + v0 * w[j];
+            const double f = beta * dot;
+            double acc = 0.0;
+            for (int i = j + 1 + tid; i < m; i += QR_THREADS) {
+                const double nv = w[i] - f * x[i];
+                w[i] = nv;
+                acc += nv * nv;
+            }
+            acc = block_sum(acc, red);
+            if (tid == 0) {
+                const double wj = w[j] - f * v0;
+                w[j] = wj;
+                a.q.Rorig[(int64_t)j * d + c] = wj;
+                nxt[c] = acc;
+            }
+        }
+        if (blockIdx.x == 0 && tid == 0) {
+            a.q.Rorig[(int64_t)j * d + p] = alpha;
+            a.q.piv[j] = p;
+        }
+        // the pivot column's owner retires it
+        if ((p % gridDim.x) == (int)blockIdx.x && tid == 0) nxt[p] = -1.0;
+        if (!grid_barrier(a.q.barrier, epoch, a.status)) return;
+    }
+    if (blockIdx.x == 0 && tid == 0) *a.q.rank = j;
+}
+
+// perm: pivots first, then the other columns ascending; R row-major in pivoted
+// column order with diag(R) >= 0; rows >= rank are zero. One CTA.
+__global__ void k_assemble_qr(QrScratch q, int d, int32_t* perm, double* R) {
+    extern __shared__ int mark[];
+    const int r = (int)*q.rank;
+    for (int c = threadIdx.x; c < d; c += blockDim.x) mark[c] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += blockDim.x) mark[q.piv[j]] = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = r;
+        for (int c = 0; c < d; ++c)
+            if (!mark[c]) perm[t++] = c;
+    }
+    for (int j = threadIdx.x; j < r; j += blockDim.x) perm[j] = q.piv[j];
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < (int64_t)d * d; e += blockDim.x) {
+        const int j = (int)(e / d), t = (int)(e % d);
+        double v = 0.0;
+        if (j < r && t >= j) {
+            const double sgn = (q.Rorig[(int64_t)j * d + q.piv[j]] < 0.0) ? -1.0 : 1.0;
+            v = sgn * q.Rorig[(int64_t)j * d + perm[t]];
+        }
+        R[e] = v;
+    }
+}
+
+// M = R_11^{-1} Omega by back-substitution, one warp per column q of Omega;
+// the column lives in shared memory (Omega first, overwritten in place).
+__global__ void k_omega_factor(const double* __restrict__ R, const int32_t* __restrict__ perm,
+                               const int64_t* __restrict__ d_rank, int d, int k, uint64_t key,
+                               double inv_sqrt_k, int identity, float* __restrict__ Mfull) {
+    extern __shared__ double colbuf[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (q >= k) return;
+    int r = (int)*d_rank;
+    r = r < 0 ? 0 : (r > d ? d : r);
+    double* Ms = colbuf + (int64_t)wib * d;
+    for (int p = lane; p < r; p += 32)
+        Ms[p] = identity ? (p == q ? 1.0 : 0.0) : box_muller(key, (uint64_t)p * k + q) * inv_sqrt_k;
+    __syncwarp();
+    for (int p = r - 1; p >= 0; --p) {
+        const double* Rp = R + (int64_t)p * d;
+        double dot = 0.0;
+        for (int t = p + 1 + lane; t < r; t += 32) dot += Rp[t] * Ms[t];
+        dot = warp_sum(dot);
+        if (lane == 0) Ms[p] = (Ms[p] - dot) / Rp[p];
+        __syncwarp();
+    }
+    for (int p = lane; p < r; p += 32) Mfull[(int64_t)perm[p] * k + q] = (float)Ms[p];
+}
+
+}  // namespace
+
+size_t qr_scratch_bytes(int64_t m, int64_t d) {
+    size_t b = 0;
+    b += sizeof(double) * (size_t)(m * d);    // W
+    b += sizeof(double) * (size_t)(2 * d);    // norms
+    b += sizeof(double) * (size_t)(d * d);    // Rorig
+    b += sizeof(int32_t) * (size_t)d + 64;    // piv
+    b += 64;                                  // rank
+    b += 64;                                  // barrier
+    return b + 256;
+}
+
+void qr_scratch_carve(void* base, int64_t m, int64_t d, QrScratch* q) {
+    char* p = static_cast<char*>(base);
+    auto take = [&](size_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return r; };
+    q->W = reinterpret_cast<double*>(take(sizeof(double) * (size_t)(m * d)));
+    q->norms = reinterpret_cast<double*>(take(sizeof(double) * (size_t)(2 * d)));
+    q->Rorig = reinterpret_cast<double*>(take(sizeof(double) * (size_t)(d * d)));
+    q->piv = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)d));
+    q->rank = reinterpret_cast<int64_t*>(take(64));
+    q->barrier = reinterpret_cast<unsigned*>(take(64));
+}
+
+cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double tau,
+                              const int32_t* forced_perm, int64_t forced_rank,
+                              const QrScratch& q, int32_t* perm, double* R, int32_t* status,
+                              int num_sms, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(q.barrier, 0, 64, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(q.Rorig, 0, sizeof(double) * (size_t)(d * d), st)) != cudaSuccess) return e;
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pivoted_qr, QR_THREADS, 0)) != cudaSuccess)
+        return e;
+    int64_t grid = (int64_t)num_sms * (occ < 1 ? 1 : (occ > 2 ? 2 : occ));
+    if (grid > d) grid = d;
+    if (grid < 1) grid = 1;
+    QrArgs args{Atilde, (int)m, (int)d, tau, forced_perm, (int)forced_rank, q, status};
+    void* kargs[] = {&args};
+    e = cudaLaunchCooperativeKernel((const void*)k_pivoted_qr, dim3((unsigned)grid), dim3(QR_THREADS),
+                                    kargs, 0, st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(int) * (size_t)d;
+    k_assemble_qr<<<1, 1024, smem, st>>>(q, (int)d, perm, R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int64_t* d_rank,
+                                int64_t d, int64_t k, uint64_t seed, bool omega_identity,
+                                double* /*Mscratch*/, float* Mfull, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(Mfull, 0, sizeof(float) * (size_t)(d * k), st);
+    if (e != cudaSuccess) return e;
+    const int warps = 4;
+    const size_t smem = sizeof(double) * (size_t)d * warps;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_omega_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = (int)((k + warps - 1) / warps);
+    k_omega_factor<<<grid, 32 * warps, smem, st>>>(R, perm, d_rank, (int)d, (int)k,
+                                                   stream_key(seed, kStreamOmega),
+                                                   1.0 / sqrt((double)k), omega_identity ? 1 : 0, Mfull);
+    return cudaGetLastError();
+}
+
+}  // namespace lev

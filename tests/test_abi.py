@@ -1,0 +1,73 @@
+"""The C-ABI library loads and exports what include/lev.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            with open(os.path.join(ROOT, "include", fn)) as f:
+                txt = f.read()
+            names |= set(re.findall(r"^(?:int|const char\*)\s+(lev_[a-z0-9_]+)\s*\(", txt, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lev():
+    from paper_2105_11004_gb300 import build
+    build.build()
+    import paper_2105_11004_gb300 as L
+    return L
+
+
+def test_library_exports_every_declared_symbol(lev):
+    declared = _declared_symbols()
+    assert {"lev_create", "lev_sketch_dense", "lev_rrqr", "lev_estimate_dense", "lev_final_dense"} <= declared
+    out = subprocess.run(["nm", "-D", "--defined-only", lev.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (lev_[a-z0-9_]+)", out))
+    assert declared <= exported, declared - exported
+    for name in declared:
+        assert hasattr(lev.lib, name)
+        assert name in lev.SIGNATURES
+
+
+def test_params_struct_layout_matches_header(lev):
+    # eps, delta, gamma (3 doubles), s, m, k (3 int64), tau, seed, 4 x int32, perm_in, rank_in
+    assert ctypes.sizeof(lev.lev_params) == 3 * 8 + 3 * 8 + 8 + 8 + 4 * 4 + 8 + 8
+    p = lev.make_params()
+    assert p.eps == 0.5 and abs(p.delta - 1 / 3) < 1e-15 and p.gamma == 2.0 and p.tau == 1e-5
+
+
+def test_resolve_sizes_follow_the_paper(lev):
+    # Alg. 3: s = ceil((d^2 + d) / ((2 eps - eps^2)^2 delta)), m = ceil(gamma d);
+    # JL size k = ceil(4 ln n / (eps^2 / 2 - eps^3 / 3)).
+    import math
+    s, m, k = lev.lev_resolve_sizes(lev.make_params(), 10**6, 256)
+    assert s == math.ceil((256 ** 2 + 256) / ((1 - 0.25) ** 2 / 3))
+    assert m == 512
+    assert k == math.ceil(4 * math.log(10**6) / (0.125 - 0.125 / 3))
+    s, m, k = lev.lev_resolve_sizes(lev.make_params(s=65536, m=1024, k=256), 10**6, 256)
+    assert (s, m, k) == (65536, 1024, 256)
+    s, m, k = lev.lev_resolve_sizes(lev.make_params(sketch_identity=True, omega_identity=True), 500, 8)
+    assert (s, m, k) == (500, 500, 8)
+
+
+@pytest.mark.parametrize("n,d,kw", [(0, 8, {}), (10, 0, {}), (10, 5000, {}), (10, 8, {"k": 5000}),
+                                    (70000, 8, {"sketch_identity": True})])
+def test_resolve_sizes_rejects_bad_shapes(lev, n, d, kw):
+    with pytest.raises(lev.LevError) as e:
+        lev.lev_resolve_sizes(lev.make_params(**kw), n, d)
+    assert e.value.code == lev.LEV_EINVAL
+
+
+def test_null_handle_is_einval(lev):
+    rc = lev.lib.lev_sketch_dense(None, None, 10, 4, 4, ctypes.byref(lev.make_params()), None, None)
+    assert rc == lev.LEV_EINVAL
+    assert b"handle" in lev.lib.lev_last_error()

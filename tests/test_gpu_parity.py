@@ -1,0 +1,289 @@
+"""GPU parity: every stage of the CUDA path against the FP64 oracle (through the C ABI).
+
+Tolerances (FP32 path):
+* sketch entries: |A~_gpu - A~_oracle| <= 2e-5 * (|G| |S| |A|) entrywise -- FP32
+  sums of at most a few thousand terms per split, fixed order;
+* pivots bit-exact on the first r positions, rank bit-exact;
+* R: relative 1e-10 (FP64 on both sides, different summation order);
+* Mfull: relative 1e-6 to the FP64 solve rounded once to FP32;
+* final pass with identical inputs: relative 1e-5 per row (FP32 products);
+* end to end theta~: max relative error 1e-4 against the oracle's FP64 theta~.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import estimator as E, exact as X, linalg as OL
+
+from ._gpu import lev_module, max_rel, sketch_abs_scale, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    assert torch.cuda.is_available()
+    return lev_module()
+
+
+@pytest.fixture(scope="module")
+def h(L):
+    return L.Handle(0)
+
+
+# ---------------------------------------------------------------- sketch
+
+@pytest.mark.parametrize("n,d,s,m", [(5000, 24, 1024, 96), (3001, 37, 700, 150), (20000, 256, 2048, 1024),
+                                     (777, 130, 5000, 300), (1, 4, 3, 8)])
+def test_sketch_dense_parity(L, h, n, d, s, m):
+    import torch
+    A = W.dense_gaussian(n, d, seed=n + d).astype(np.float32)
+    p = L.make_params(s=s, m=m, seed=5)
+    At = torch.empty((m, d), dtype=torch.float32, device="cuda")
+    L.lev_sketch_dense(h, to_dev(A), p, At)
+    torch.cuda.synchronize()
+    A64 = A.astype(np.float64)
+    want = E.sketch(A64, s, m, 5)
+    scale = sketch_abs_scale(A64, s, m, 5)
+    err = np.abs(to_np(At) - want)
+    assert np.all(err <= 2e-5 * scale + 1e-30), float(np.max(err / (scale + 1e-30)))
+
+
+def test_sketch_dense_strided_and_repeatable(L, h):
+    import torch
+    A = W.dense_gaussian(4099, 64, seed=3).astype(np.float32)
+    big = torch.zeros((4099, 80), dtype=torch.float32, device="cuda")
+    big[:, :64] = to_dev(A)
+    view = big[:, :64]
+    p = L.make_params(s=512, m=128, seed=9)
+    out1 = torch.empty((128, 64), device="cuda")
+    out2 = torch.empty((128, 64), device="cuda")
+    L.lev_sketch_dense(h, view, p, out1)
+    L.lev_sketch_dense(h, to_dev(A), p, out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out1, out2)             # fixed summation order: bit-identical
+    want = E.sketch(A.astype(np.float64), 512, 128, 9)
+    assert np.max(np.abs(to_np(out1) - want)) <= 2e-5 * np.max(sketch_abs_scale(A.astype(np.float64), 512, 128, 9))
+
+
+def test_sketch_csr_parity(L, h):
+    import torch
+    C = W.csr_uniform(6000, 200, nnz_per_row=5, heavy_frac=0.02, heavy_nnz=60, seed=4)
+    p = L.make_params(s=1500, m=400, seed=2)
+    At = torch.empty((400, 200), device="cuda")
+    L.lev_sketch_csr(h, to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val), 6000, 200, p, At)
+    torch.cuda.synchronize()
+    dense = C.to_dense()
+    want = E.sketch(dense, 1500, 400, 2)
+    scale = sketch_abs_scale(dense, 1500, 400, 2)
+    assert np.all(np.abs(to_np(At) - want) <= 2e-5 * scale + 1e-30)
+
+
+# ---------------------------------------------------------------- rrqr + omega
+
+def _rank_deficient_sketch(m, d, r, seed):
+    rs = np.random.default_rng(seed)
+    X_ = rs.standard_normal((m, r)) @ rs.standard_normal((r, d))
+    X_ *= np.exp(rs.standard_normal(d))[None, :]
+    return X_.astype(np.float32)
+
+
+@pytest.mark.parametrize("m,d,r,tau", [(96, 24, 24, 1e-5), (300, 64, 40, 1e-5), (1024, 256, 200, 1e-4),
+                                       (50, 70, 50, 1e-5), (8, 1, 1, 1e-5)])
+def test_rrqr_parity(L, h, m, d, r, tau):
+    import torch
+    At = _rank_deficient_sketch(m, d, r, seed=m + d)
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    rank = L.lev_rrqr(h, to_dev(At), tau, perm, R)
+    q = OL.pivoted_qr(At.astype(np.float64), tau)
+    assert rank == q.rank == min(r, m, d)
+    gp = to_np(perm)
+    assert np.array_equal(gp[:rank], q.perm[:rank])
+    assert sorted(gp.tolist()) == list(range(d))
+    assert np.all(np.diff(gp[rank:]) > 0)               # the rest in increasing order
+    gR = to_np(R)
+    want = q.R                                           # oracle R columns are in its pivot order
+    # compare R_11 and R_12 in the pivoted order
+    Rg = gR[:rank]
+    Rw = np.zeros_like(Rg)
+    colpos = {c: t for t, c in enumerate(gp)}
+    for t, c in enumerate(q.perm):
+        Rw[:, colpos[c]] = want[:, t]
+    assert np.all(np.diag(Rg[:, :rank]) > 0)
+    assert np.max(np.abs(Rg - Rw)) <= 1e-10 * np.max(np.abs(Rw))
+    assert np.all(gR[rank:] == 0)
+
+
+def test_rrqr_rank_zero(L, h):
+    import torch
+    perm = torch.empty(5, dtype=torch.int32, device="cuda")
+    R = torch.empty((5, 5), dtype=torch.float64, device="cuda")
+    assert L.lev_rrqr(h, torch.zeros((12, 5), device="cuda"), 1e-5, perm, R) == 0
+    assert to_np(perm).tolist() == list(range(5))
+    assert np.all(to_np(R) == 0)
+
+
+@pytest.mark.parametrize("k,identity", [(64, False), (100, False), (0, True)])
+def test_omega_factor_parity(L, h, k, identity):
+    import torch
+    m, d, r = 300, 64, 40
+    At = _rank_deficient_sketch(m, d, r, seed=7)
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    rank = L.lev_rrqr(h, to_dev(At), 1e-5, perm, R)
+    kk = d if identity else k
+    Mf = torch.empty((d, kk), dtype=torch.float32, device="cuda")
+    d_rank = torch.tensor([rank], dtype=torch.int64, device="cuda")
+    L.lev_omega_factor(h, R, perm, d_rank, d, kk, 13, L.LEV_OMEGA_IDENTITY if identity else 0, Mf)
+    torch.cuda.synchronize()
+    R64, gp = to_np(R), to_np(perm)
+    M = E.omega_factor(R64[:rank, :rank], kk, 13, omega_identity=identity)
+    if identity:
+        M = np.hstack([M, np.zeros((rank, kk - rank))])
+    want = E.m_full(M, gp, d)
+    got = to_np(Mf).astype(np.float64)
+    assert np.max(np.abs(got - want)) <= 1e-6 * np.max(np.abs(want))
+    assert np.all(got[gp[rank:]] == 0)
+
+
+# ---------------------------------------------------------------- final pass
+
+@pytest.mark.parametrize("n,d,k,lda", [(10007, 256, 256, 256), (999, 37, 100, 37), (5000, 64, 512, 80),
+                                       (64, 16, 8, 16), (1, 4, 4, 4)])
+def test_final_dense_parity(L, h, n, d, k, lda):
+    import torch
+    rs = np.random.default_rng(n)
+    A = rs.standard_normal((n, lda)).astype(np.float32)
+    Mf = (rs.standard_normal((d, k)) / np.sqrt(d)).astype(np.float32)
+    Mf[rs.random(d) < 0.2] = 0.0
+    Ad = to_dev(A)[:, :d]
+    theta = torch.empty(n, device="cuda")
+    L.lev_final_dense(h, Ad, to_dev(Mf), "fp32", theta)
+    torch.cuda.synchronize()
+    want = np.sum((A[:, :d].astype(np.float64) @ Mf.astype(np.float64)) ** 2, axis=1)
+    assert max_rel(to_np(theta), want) <= 1e-5
+
+
+def test_final_csr_parity(L, h):
+    import torch
+    C = W.csr_uniform(5003, 300, nnz_per_row=6, heavy_frac=0.01, heavy_nnz=200, seed=8)
+    rs = np.random.default_rng(1)
+    Mf = (rs.standard_normal((300, 256)) / 17).astype(np.float32)
+    theta = torch.empty(5003, device="cuda")
+    L.lev_final_csr(h, to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val), 5003, 300, to_dev(Mf), "fp32", theta)
+    torch.cuda.synchronize()
+    want = np.sum((C.to_dense() @ Mf.astype(np.float64)) ** 2, axis=1)
+    assert max_rel(to_np(theta), want) <= 1e-5
+
+
+# ---------------------------------------------------------------- end to end
+
+def _oracle_estimate(A32, cfg):
+    return E.estimate(A32.astype(np.float64), cfg["s"], cfg["m"], cfg["k"], cfg["tau"], cfg["seed"])
+
+
+def test_estimate_small_dense_workload(L, h):
+    cfg = W.CONFIGS["dense_2000x20_f64"]
+    A = W.dense_gaussian(cfg["n"], cfg["d"], cfg["data_seed"]).astype(np.float32)
+    theta, r, perm = L.estimate(to_dev(A), s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
+                                handle=h)
+    e = _oracle_estimate(A, cfg)
+    assert r == e.rank == 20
+    assert np.array_equal(to_np(perm)[:r], e.perm[:r])
+    assert max_rel(to_np(theta), e.theta) <= 1e-4
+
+
+def test_estimate_lowrank_skewed(L, h):
+    A = W.dense_lowrank_skewed(60000, 64, 40, seed=21)
+    cfg = dict(s=8192, m=256, k=128, tau=1e-4, seed=3)
+    theta, r, perm = L.estimate(to_dev(A), handle=h, **cfg)
+    e = _oracle_estimate(A, cfg)
+    assert r == e.rank == 40
+    assert np.array_equal(to_np(perm)[:r], e.perm[:r])
+    assert max_rel(to_np(theta), e.theta) <= 1e-4
+
+
+def test_estimate_csr(L, h):
+    import torch
+    C = W.csr_uniform(40000, 128, nnz_per_row=8, heavy_frac=0.01, heavy_nnz=64, seed=6)
+    cfg = dict(s=8192, m=512, k=64, tau=1e-5, seed=4)
+    p = L.make_params(**cfg)
+    theta = torch.empty(40000, device="cuda")
+    perm = torch.empty(128, dtype=torch.int32, device="cuda")
+    r = L.lev_estimate_csr(h, to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val), 40000, 128, p, theta, perm)
+    import scipy.sparse as sp
+    Asp = sp.csr_matrix((C.val.astype(np.float64), C.col, C.row_ptr), shape=C.shape)
+    e = E.estimate(Asp, **cfg)
+    assert r == e.rank == 128
+    assert np.array_equal(to_np(perm)[:r], e.perm[:r])
+    assert max_rel(to_np(theta), e.theta) <= 1e-4
+
+
+def test_identity_modes_give_exact_leverage(L, h):
+    A = W.dense_gaussian(3000, 12, seed=5).astype(np.float32)
+    theta, r, _ = L.estimate(to_dev(A), tau=1e-6, sketch_identity=True, omega_identity=True, handle=h)
+    th, rx = X.exact_leverage_qr(A.astype(np.float64), 1e-6)
+    assert r == rx == 12
+    assert max_rel(to_np(theta), th) <= 1e-4
+    assert abs(float(to_np(theta).sum()) - 12) < 1e-3
+
+
+def test_forced_pivots_match_oracle(L, h):
+    import torch
+    A = W.dense_gaussian(5000, 16, seed=8).astype(np.float32)
+    forced = np.random.default_rng(0).permutation(16).astype(np.int32)
+    p = L.make_params(s=2048, m=64, k=32, seed=1, perm_in=to_dev(forced), rank_in=10)
+    theta = torch.empty(5000, device="cuda")
+    perm = torch.empty(16, dtype=torch.int32, device="cuda")
+    r = L.lev_estimate_dense(h, to_dev(A), p, theta, perm)
+    e = E.estimate(A.astype(np.float64), 2048, 64, 32, 1e-5, 1, forced_perm=forced, forced_rank=10)
+    assert r == 10
+    assert np.array_equal(to_np(perm)[:10], forced[:10])
+    assert max_rel(to_np(theta), e.theta) <= 1e-4
+
+
+def test_scale_invariance_bit_exact(L, h):
+    A = W.dense_gaussian(7000, 32, seed=9).astype(np.float32)
+    t1, r1, p1 = L.estimate(to_dev(A), s=1024, m=128, k=64, seed=2, handle=h)
+    t2, r2, p2 = L.estimate(to_dev(2.0 * A), s=1024, m=128, k=64, seed=2, handle=h)
+    assert r1 == r2 and np.array_equal(to_np(p1), to_np(p2))
+    assert np.array_equal(to_np(t1), to_np(t2))
+
+
+def test_zero_rows_and_rank_zero(L, h):
+    A = W.dense_gaussian(3000, 8, seed=10).astype(np.float32)
+    A[[0, 17, 2999]] = 0
+    theta, r, _ = L.estimate(to_dev(A), s=512, m=32, k=16, seed=3, handle=h)
+    assert r == 8 and np.all(to_np(theta)[[0, 17, 2999]] == 0)
+    theta0, r0, _ = L.estimate(to_dev(np.zeros((100, 6), np.float32)), s=64, m=24, k=8, handle=h)
+    assert r0 == 0 and np.all(to_np(theta0) == 0)
+
+
+def test_host_buffers_match_device_path(L, h):
+    import torch
+    A = W.dense_gaussian(9000, 48, seed=11).astype(np.float32)
+    p = L.make_params(s=2048, m=192, k=64, seed=6)
+    th_dev = torch.empty(9000, device="cuda")
+    r1 = L.lev_estimate_dense(h, to_dev(A), p, th_dev)
+    A_host = torch.from_numpy(A).pin_memory()
+    th_host = torch.empty(9000, dtype=torch.float32).pin_memory()
+    r2 = L.lev_estimate_dense(h, A_host, p, th_host)
+    A_page = torch.from_numpy(A.copy())
+    th_page = torch.empty(9000, dtype=torch.float32)
+    r3 = L.lev_estimate_dense(h, A_page, p, th_page)
+    assert r1 == r2 == r3 == 48
+    assert torch.equal(th_dev.cpu(), th_host) and torch.equal(th_host, th_page)
+
+
+def test_invalid_arguments(L, h):
+    import torch
+    A = torch.zeros((10, 4), device="cuda")
+    theta = torch.empty(10, device="cuda")
+    with pytest.raises(L.LevError) as e:
+        L.lev_estimate_dense(h, A, L.make_params(s=0, eps=1.5), theta)
+    assert e.value.code == L.LEV_EINVAL
+    with pytest.raises(L.LevError):
+        L.lev_final_dense(h, A, torch.zeros((4, 8), device="cuda"), 9, theta)
+    assert L.lev_device_status(h) == 0
