@@ -462,8 +462,11 @@ int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
     int64_t ldA = lda;
     if (hostA) {
         LEV_TRY(ensure(h->stageA, sizeof(float) * (size_t)n * d));
-        LEV_CUDA(cudaMemcpy2DAsync(h->stageA.ptr, sizeof(float) * d, A, sizeof(float) * lda, sizeof(float) * d, n,
-                                   cudaMemcpyHostToDevice, st));
+        if (lda == d)
+            LEV_CUDA(cudaMemcpyAsync(h->stageA.ptr, A, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, st));
+        else
+            LEV_CUDA(cudaMemcpy2DAsync(h->stageA.ptr, sizeof(float) * d, A, sizeof(float) * lda, sizeof(float) * d,
+                                       n, cudaMemcpyHostToDevice, st));
         dA = (const float*)h->stageA.ptr;
         ldA = d;
     }

@@ -205,26 +205,35 @@ __global__ void k_omega_factor(const double* __restrict__ R, const int32_t* __re
 
 }  // namespace
 
-size_t qr_scratch_bytes(int64_t m, int64_t d) {
-    size_t b = 0;
-    b += sizeof(double) * (size_t)(m * d);    // W
-    b += sizeof(double) * (size_t)(2 * d);    // norms
-    b += sizeof(double) * (size_t)(d * d);    // Rorig
-    b += sizeof(int32_t) * (size_t)d + 64;    // piv
-    b += 64;                                  // rank
-    b += 64;                                  // barrier
-    return b + 256;
+// One layout for both the size and the carve: every piece starts on a 256-byte boundary.
+static size_t qr_layout(int64_t m, int64_t d, char* base, QrScratch* q) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* r = base ? base + off : nullptr;
+        off += (bytes + 255) / 256 * 256;
+        return r;
+    };
+    char* W = take(sizeof(double) * (size_t)(m * d));
+    char* norms = take(sizeof(double) * (size_t)(2 * d));
+    char* Rorig = take(sizeof(double) * (size_t)(d * d));
+    char* piv = take(sizeof(int32_t) * (size_t)d);
+    char* rank = take(sizeof(int64_t));
+    char* barrier = take(sizeof(unsigned));
+    if (q) {
+        q->W = reinterpret_cast<double*>(W);
+        q->norms = reinterpret_cast<double*>(norms);
+        q->Rorig = reinterpret_cast<double*>(Rorig);
+        q->piv = reinterpret_cast<int32_t*>(piv);
+        q->rank = reinterpret_cast<int64_t*>(rank);
+        q->barrier = reinterpret_cast<unsigned*>(barrier);
+    }
+    return off;
 }
 
+size_t qr_scratch_bytes(int64_t m, int64_t d) { return qr_layout(m, d, nullptr, nullptr); }
+
 void qr_scratch_carve(void* base, int64_t m, int64_t d, QrScratch* q) {
-    char* p = static_cast<char*>(base);
-    auto take = [&](size_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return r; };
-    q->W = reinterpret_cast<double*>(take(sizeof(double) * (size_t)(m * d)));
-    q->norms = reinterpret_cast<double*>(take(sizeof(double) * (size_t)(2 * d)));
-    q->Rorig = reinterpret_cast<double*>(take(sizeof(double) * (size_t)(d * d)));
-    q->piv = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)d));
-    q->rank = reinterpret_cast<int64_t*>(take(64));
-    q->barrier = reinterpret_cast<unsigned*>(take(64));
+    qr_layout(m, d, static_cast<char*>(base), q);
 }
 
 cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double tau,
@@ -232,7 +241,7 @@ cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double 
                               const QrScratch& q, int32_t* perm, double* R, int32_t* status,
                               int num_sms, cudaStream_t st) {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(q.barrier, 0, 64, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(q.barrier, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(q.Rorig, 0, sizeof(double) * (size_t)(d * d), st)) != cudaSuccess) return e;
     int occ = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pivoted_qr, QR_THREADS, 0)) != cudaSuccess)

@@ -5,8 +5,8 @@ from oracle import rng as orng
 
 
 def lev_module():
-    from paper_2105_11004_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2105_11004_gb300 as L
     return L
 

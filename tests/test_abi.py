@@ -21,8 +21,8 @@ def _declared_symbols():
 
 @pytest.fixture(scope="module")
 def lev():
-    from paper_2105_11004_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2105_11004_gb300 as L
     return L
 

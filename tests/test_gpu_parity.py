@@ -277,6 +277,18 @@ def test_host_buffers_match_device_path(L, h):
     assert torch.equal(th_dev.cpu(), th_host) and torch.equal(th_host, th_page)
 
 
+def test_fresh_handle_first_call(L):
+    """First call on a new handle: every scratch buffer is freshly allocated."""
+    A = W.dense_gaussian(2000, 20, seed=0).astype(np.float32)
+    for _ in range(2):
+        h2 = L.Handle(0)
+        theta, r, perm = L.estimate(to_dev(A), s=1600, m=80, k=64, tau=1e-10, seed=0, handle=h2)
+        h2.close()
+        assert r == 20
+        e = E.estimate(A.astype(np.float64), 1600, 80, 64, 1e-10, 0)
+        assert max_rel(to_np(theta), e.theta) <= 1e-4
+
+
 def test_invalid_arguments(L, h):
     import torch
     A = torch.zeros((10, 4), device="cuda")
