@@ -194,6 +194,25 @@ int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
 /* Device-side status word of the handle: nonzero after a bounded wait gave up. */
 int lev_device_status(lev_handle* h, int32_t* status);
 
+/* lev_rrqr without any allocation. The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code that lives inside
+ * another allocator's fixed memory budget (for example a serving framework's
+ * pool) and latency-critical paths that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree. It computes exactly what lev_rrqr
+ * computes (same kernels, same arguments and results; no handle), on the
+ * calling thread's current device, with its scratch in a fixed 8 MiB device
+ * array that every GPU which loads the library holds until the process exits.
+ * Limit: 8 (m d + d^2 + 2 d) bytes plus a few hundred must fit in 8 MiB (for
+ * example m = 1024, d = 256 uses 2.6 MiB); larger shapes return LEV_EINVAL.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call clears what must start at zero; all calls share the one array,
+ * so calls that overlap on the GPU (different streams, or different host
+ * threads) race and give wrong results. Errors: LEV_EINVAL, LEV_ECUDA,
+ * LEV_ETIMEOUT, LEV_ERANK0. */
+int lev_rrqr_noalloc(const float* Atilde, int64_t m, int64_t d, double tau,
+                     int32_t* perm, double* R, int64_t* rank, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,6 +59,7 @@ SIGNATURES = {
     "lev_backward_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p,
                                           _c_void_p, _c_void_p]),
     "lev_device_status": (ctypes.c_int, [_c_void_p, _P(_i32)]),
+    "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
 }
 
 if not os.path.exists(LIB_PATH):
@@ -217,6 +218,15 @@ def lev_backward_dense(h: Handle, A, p: lev_params, w, gradA, stream=None):
     n, d = A.shape
     _check(lib.lev_backward_dense(h.ptr, _ptr(A), n, d, A.stride(0), ctypes.byref(p), _ptr(w), _ptr(gradA),
                                   _stream(stream)))
+
+
+def lev_rrqr_noalloc(Atilde, tau, perm, R, stream=None) -> int:
+    """lev_rrqr without allocation (fixed device scratch; see include/lev.h)."""
+    m, d = Atilde.shape
+    r = _i64()
+    rc = _check(lib.lev_rrqr_noalloc(_ptr(Atilde), m, d, float(tau), _ptr(perm), _ptr(R), ctypes.byref(r),
+                                     _stream(stream)), allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
 
 
 def lev_device_status(h: Handle) -> int:

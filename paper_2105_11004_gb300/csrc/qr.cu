@@ -15,8 +15,11 @@
 //      which also write their new trailing norms and row j of R.
 // A second small kernel orders the columns (pivots first, then the rest in
 // increasing id) and writes R in pivoted order with diag(R) >= 0.
+#include <mutex>
+
 #include "lev_common.cuh"
 #include "lev_kernels.cuh"
+#include "lev_tc.cuh"
 
 namespace lev {
 
@@ -277,4 +280,83 @@ cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int6
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// lev_rrqr_noalloc: the same pivoted QR with its scratch in a fixed device array.
+//
+// For callers that must not call cudaMalloc: code that runs inside another
+// allocator's fixed memory budget (a serving framework's pool), and
+// latency-critical paths where the implicit device synchronisation of
+// cudaMalloc/cudaFree is not acceptable. The scratch is a file-scope
+// __device__ array of kRrqrNoAllocBytes that every GPU which loads the library
+// holds until the process exits. Host code must not pass the array's name to a
+// kernel (in host code it is only a stand-in for the device symbol); its device
+// address is looked up with cudaGetSymbolAddress once per device, on the first
+// call made with that device current, and that first call should come before
+// any stream capture. All calls share the array: the pieces that must start at
+// zero (barrier counter, status word, R scratch) are cleared by every call on
+// its stream, and calls that overlap on the GPU race with one another.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kRrqrNoAllocBytes = size_t(8) << 20;   // 8 MiB
+__device__ __align__(256) unsigned char g_rrqr_noalloc_scratch[kRrqrNoAllocBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
 }  // namespace lev
+
+extern "C" int lev_rrqr_noalloc(const float* Atilde, int64_t m, int64_t d, double tau, int32_t* perm,
+                                double* R, int64_t* rank, void* stream) {
+    using namespace lev;
+    if (!Atilde || !perm || !R) return handle_fail(LEV_EINVAL, "lev_rrqr_noalloc: NULL array");
+    if (m < 1 || d < 1 || d > 4096 || m > (1 << 20))
+        return handle_fail(LEV_EINVAL, "lev_rrqr_noalloc: bad shape");
+    const size_t need = qr_layout(m, d, nullptr, nullptr) + 256;    // + status word
+    if (need > kRrqrNoAllocBytes)
+        return handle_fail(LEV_EINVAL,
+                           "lev_rrqr_noalloc: m x d too large for the fixed 8 MiB scratch "
+                           "(needs 8 (m d + d^2 + 2 d) bytes plus small terms)");
+    if (tau <= 0) tau = 1e-5;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return handle_fail(LEV_ECUDA, "lev_rrqr_noalloc: no current CUDA device");
+    }
+    char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&addr, g_rrqr_noalloc_scratch);
+            if (e != cudaSuccess || !addr) {
+                cudaGetLastError();
+                return handle_fail(LEV_ECUDA, "lev_rrqr_noalloc: cudaGetSymbolAddress failed");
+            }
+            g_noalloc_addr[dev] = addr;
+        }
+        base = static_cast<char*>(g_noalloc_addr[dev]);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    QrScratch q;
+    const size_t status_off = qr_layout(m, d, base, &q);
+    int32_t* status = reinterpret_cast<int32_t*>(base + status_off);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = launch_pivoted_qr(Atilde, m, d, tau, nullptr, 0, q, perm, R, status, sms, st);
+    if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
+    if (!rank) return LEV_OK;
+    int64_t r = 0;
+    int32_t flag = 0;
+    e = cudaMemcpyAsync(&r, q.rank, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
+    if (flag != 0) return handle_fail(LEV_ETIMEOUT, "lev_rrqr_noalloc: a bounded device wait gave up");
+    *rank = r;
+    if (r == 0) return handle_fail(LEV_ERANK0, "numerical rank is 0");
+    return LEV_OK;
+}
+
