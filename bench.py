@@ -169,6 +169,15 @@ def run_reference(args, cfg):
     print(json.dumps(out), flush=True)
 
 
+def qr_flops(m, d, r):
+    """FP64 flops of the pivoted Householder QR that stops at rank r (norm recompute included)."""
+    f = 0.0
+    for j in range(r):
+        rows, cols = m - j, d - j - 1
+        f += 6.0 * rows * cols + 2.0 * rows
+    return f
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,7 +185,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sketch-prec", default="fp32")
-    ap.add_argument("--final-prec", default="fp32")
+    ap.add_argument("--final-prec", default="bf16x3")
+    ap.add_argument("--forms", default="fp32,bf16,tf32,bf16x3",
+                    help="final-pass forms timed and checked besides the main one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -196,11 +207,15 @@ def main():
     A_host = torch.from_numpy(A_np).pin_memory()
     A = A_host.cuda()
     h = L.Handle(local)
-    p = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
-                      sketch_prec=args.sketch_prec, final_prec=args.final_prec)
+
+    def params(final_prec):
+        return L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
+                             sketch_prec=args.sketch_prec, final_prec=final_prec)
+
+    p = params(args.final_prec)
     theta = torch.empty(n, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    kernels_per_step = 11
+    kernels_per_step = 11 if args.final_prec == "fp32" else 12
 
     rank_found = L.lev_estimate_dense(h, A, p, theta)          # also generates and caches G
     for _ in range(args.warmup):
@@ -223,19 +238,7 @@ def main():
     clocks = sampler.summary(t_wall0, t_wall1)
     sampler.stop()
 
-    # per-stage times (same inputs, same stream), for the roofline of the dominant kernel
-    At = torch.empty((cfg["m"], d), dtype=torch.float32, device="cuda")
-    perm = torch.empty(d, dtype=torch.int32, device="cuda")
-    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
-    Mf = torch.empty((d, cfg["k"]), dtype=torch.float32, device="cuda")
-    L.lev_sketch_dense(h, A, p, At)
-    r = L.lev_rrqr(h, At, cfg["tau"], perm, R)
-    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
-    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
-    stages = {}
-    reps = max(3, min(args.steps, 20))
-
-    def timed(name, fn):
+    def time_steps(fn, reps):
         fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -244,29 +247,77 @@ def main():
             fn()
         b.record(stream)
         torch.cuda.synchronize()
-        stages[name] = a.elapsed_time(b) / reps
+        return a.elapsed_time(b) / reps
 
-    timed("sketch", lambda: L.lev_sketch_dense(h, A, p, At))
-    timed("rrqr", lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R))
-    timed("omega", lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf))
-    timed("final", lambda: L.lev_final_dense(h, A, Mf, args.final_prec, theta))
+    reps = max(3, min(args.steps, 20))
+    # every final-pass form: whole-step time and theta~ for the accuracy check
+    forms = {}
+    form_theta = {}
+    for f in [x for x in args.forms.split(",") if x]:
+        pf = params(f)
+        tf = torch.empty(n, dtype=torch.float32, device="cuda")
+        L.lev_estimate_dense(h, A, pf, tf)
+        form_theta[f] = tf.cpu().numpy()
+        t_ms = time_steps(lambda: L.lev_estimate_dense(h, A, pf, tf, want_rank=False), reps)
+        forms[f] = {"ms_per_step": t_ms, "rows_per_s": n / (t_ms * 1e-3)}
+
+    # per-stage times (same inputs, same stream) for the rooflines
+    At = torch.empty((cfg["m"], d), dtype=torch.float32, device="cuda")
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    Mf = torch.empty((d, cfg["k"]), dtype=torch.float32, device="cuda")
+    L.lev_sketch_dense(h, A, p, At)
+    r = L.lev_rrqr(h, At, cfg["tau"], perm, R)
+    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
+    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
+    stages = {
+        "sketch": time_steps(lambda: L.lev_sketch_dense(h, A, p, At), reps),
+        "rrqr": time_steps(lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R), reps),
+        "omega": time_steps(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf), reps),
+    }
+    final_ms = {f: time_steps(lambda f=f: L.lev_final_dense(h, A, Mf, f, theta), reps)
+                for f in sorted(set(list(forms) + [args.final_prec]))}
+    stages["final"] = final_ms[args.final_prec]
 
     peaks, peak_src = load_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
+    fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     final_bytes = n * d * 4 + n * 4 + d * cfg["k"] * 4
     final_flops = 2.0 * n * r * cfg["k"]
-    t_final = stages["final"] * 1e-3
-    if args.final_prec == "fp32":
-        fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-        roof = {"kernel": "k_final_dense_fp32", "bound": "alu", "achieved": final_flops / t_final / 1e12,
-                "peak": fp32_peak, "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
-    else:
-        roof = {"kernel": "k_final_dense_tc", "bound": "hbm", "achieved": final_bytes / t_final / 1e9,
-                "peak": hbm_peak, "unit": "GB/s", "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["algorithmic"] = final_flops if roof["unit"] == "TFLOP/s" else final_bytes
-    roof["ms"] = stages["final"]
+
+    def final_roof(f):
+        t = final_ms[f] * 1e-3
+        if f == "fp32":
+            roof = {"kernel": "k_final_dense_fp32", "bound": "alu", "achieved": final_flops / t / 1e12,
+                    "peak": fp32_peak, "unit": "TFLOP/s",
+                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock",
+                    "algorithmic": final_flops}
+        else:
+            roof = {"kernel": f"k_final_tc<{f}>", "bound": "hbm", "achieved": final_bytes / t / 1e9,
+                    "peak": hbm_peak, "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})",
+                    "algorithmic": final_bytes}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
+        roof["ms"] = final_ms[f]
+        return roof
+
+    rooflines = {"final": final_roof(args.final_prec)}
+    sk_bytes = n * d * 4 + cfg["s"] * d * 4
+    rooflines["sketch"] = {"kernels": "k_countsketch_dense_v4 + k_sgemm_splitk + permutation", "bound": "mixed",
+                           "ms": stages["sketch"],
+                           "countsketch_bytes": sk_bytes, "gemm_flops": 2.0 * cfg["m"] * cfg["s"] * d}
+    qf = qr_flops(cfg["m"], d, r)
+    rooflines["rrqr"] = {"kernel": "k_pivoted_qr", "bound": "latency", "ms": stages["rrqr"], "fp64_flops": qf,
+                         "achieved_tflops": qf / (stages["rrqr"] * 1e-3) / 1e12,
+                         "note": f"{r} sequential steps, one grid barrier each"}
+    dominant = max(stages, key=stages.get)
+    roof = rooflines["final"] if dominant == "final" else dict(rooflines[dominant])
+    if dominant != "final":
+        roof.setdefault("frac", None)
+        roof.setdefault("achieved", None)
+        roof.setdefault("peak", None)
+        roof.setdefault("unit", None)
+        roof.setdefault("traffic", None)
 
     out = {"metric": METRIC, "value": n * world / (ms * 1e-3), "unit": "rows/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -276,9 +327,10 @@ def main():
                       "final_prec": args.final_prec, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (A is 1.02 GB), no flush",
                       "cached": "G (m x s) generated once per seed in the handle; all other stages every step"},
-           "rank_found": rank_found, "stages_ms": stages,
-           "hbm_gbs_step": (n * d * 4 * 2) / (ms * 1e-3) / 1e9,
-           "roofline": roof, "clocks": clocks, "gpu_launches": kernels_per_step * args.steps}
+           "rank_found": rank_found, "stages_ms": stages, "final_ms_by_form": final_ms, "forms": forms,
+           "roofline": roof, "dominant_stage": dominant, "rooflines": rooflines,
+           "roofline_final_pass": rooflines["final"],
+           "clocks": clocks, "gpu_launches": kernels_per_step * args.steps}
 
     if not args.no_e2e:
         theta_host = torch.empty(n, dtype=torch.float32).pin_memory()
@@ -296,10 +348,15 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
-        oracle_step(A_np, cfg)
+        est = oracle_step(A_np, cfg)
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": n / dt, "unit": "rows/s", "cores": cpu_threads(), "kind": "oracle",
                                "sample": "one run of the FP64 oracle on the full workload", "seconds": dt}
+        out["oracle_rank"] = est.rank
+        for f, th in form_theta.items():
+            rel = np.abs(th.astype(np.float64) - est.theta) / est.theta
+            forms[f]["max_rel_err_vs_oracle"] = float(rel.max())
+            forms[f]["p99_rel_err_vs_oracle"] = float(np.quantile(rel, 0.99))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

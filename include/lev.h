@@ -202,8 +202,9 @@ int lev_device_status(lev_handle* h, int32_t* status);
  * computes (same kernels, same arguments and results; no handle), on the
  * calling thread's current device, with its scratch in a fixed 8 MiB device
  * array that every GPU which loads the library holds until the process exits.
- * Limit: 8 (m d + d^2 + 2 d) bytes plus a few hundred must fit in 8 MiB (for
- * example m = 1024, d = 256 uses 2.6 MiB); larger shapes return LEV_EINVAL.
+ * Limit: the QR working set (about 8 (m d + 2 d^2) bytes plus the partial sums
+ * of the Gram matrix) must fit in 8 MiB; for example m = 1024, d = 256 uses
+ * 5.6 MiB. Larger shapes return LEV_EINVAL.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call clears what must start at zero; all calls share the one array,

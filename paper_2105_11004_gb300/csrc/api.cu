@@ -288,6 +288,7 @@ int handle_scratch(lev_handle* h, int which, size_t bytes, void** out) {
     return LEV_OK;
 }
 int handle_num_sms(lev_handle* h) { return h->num_sms; }
+int32_t* handle_status(lev_handle* h) { return h->status; }
 int handle_gaussian(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
                     const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo) {
     return ensure_g(h, m, s, seed, kind, st, g32, ghi, glo);

@@ -48,7 +48,17 @@ struct QrScratch {
     int32_t* piv;     // d int32: pivot order (original column ids)
     int64_t* rank;    // 1 int64 (device)
     unsigned* barrier;  // 1 uint32 grid-barrier counter
+    double* G;        // d x d FP64 Gram matrix (Gram route)
+    double* Gp;       // split partials of the Gram matrix (Gram route)
 };
+
+// Gram route of the pivoted QR (gramqr.cu): G = A~^T A~ in FP64, then a
+// pivoted Cholesky on one thread-block cluster; fills Rorig, piv and rank.
+int gram_splits(int64_t m, int64_t d);
+size_t gram_partial_doubles(int64_t m, int64_t d);
+cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t d, double tau,
+                                         const int32_t* forced, int64_t forced_rank, const QrScratch& q,
+                                         int32_t* status, cudaStream_t st);
 size_t qr_scratch_bytes(int64_t m, int64_t d);
 void qr_scratch_carve(void* base, int64_t m, int64_t d, QrScratch* q);
 

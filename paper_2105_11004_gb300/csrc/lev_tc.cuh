@@ -12,6 +12,7 @@ namespace lev {
 // Handle services used by the tensor-core module (defined in api.cu).
 int handle_scratch(lev_handle* h, int which, size_t bytes, void** out);
 int handle_num_sms(lev_handle* h);
+int32_t* handle_status(lev_handle* h);
 int handle_gaussian(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
                     const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo);
 int handle_fail(int code, const char* msg);

@@ -154,34 +154,72 @@ __global__ void __launch_bounds__(QR_THREADS) k_pivoted_qr(QrArgs a) {
 }
 
 // perm: pivots first, then the other columns ascending; R row-major in pivoted
-// column order with diag(R) >= 0; rows >= rank are zero. One CTA.
-__global__ void k_assemble_qr(QrScratch q, int d, int32_t* perm, double* R) {
+// column order with diag(R) >= 0; rows >= rank are zero. k_assemble_perm runs
+// in one CTA (a block-wide scan places the unpivoted columns), k_assemble_r on
+// a grid over the rows of R.
+__global__ void __launch_bounds__(1024) k_assemble_perm(QrScratch q, int d, int32_t* perm) {
     extern __shared__ int mark[];
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
     const int r = (int)*q.rank;
-    for (int c = threadIdx.x; c < d; c += blockDim.x) mark[c] = 0;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int c = t; c < d; c += blockDim.x) mark[c] = 0;
+    if (t == 0) carry = r;
     __syncthreads();
-    for (int j = threadIdx.x; j < r; j += blockDim.x) mark[q.piv[j]] = 1;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = r;
-        for (int c = 0; c < d; ++c)
-            if (!mark[c]) perm[t++] = c;
+    for (int j = t; j < r; j += blockDim.x) {
+        mark[q.piv[j]] = 1;
+        perm[j] = q.piv[j];
     }
-    for (int j = threadIdx.x; j < r; j += blockDim.x) perm[j] = q.piv[j];
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)d * d; e += blockDim.x) {
-        const int j = (int)(e / d), t = (int)(e % d);
-        double v = 0.0;
-        if (j < r && t >= j) {
-            const double sgn = (q.Rorig[(int64_t)j * d + q.piv[j]] < 0.0) ? -1.0 : 1.0;
-            v = sgn * q.Rorig[(int64_t)j * d + perm[t]];
+    for (int base = 0; base < d; base += blockDim.x) {
+        const int c = base + t;
+        const int un = (c < d && !mark[c]) ? 1 : 0;
+        int incl = un;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
-        R[e] = v;
+        if (lane == 31) warp_tot[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const int wt = warp_tot[lane];
+            int wi = wt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            warp_tot[lane] = wi - wt;
+        }
+        __syncthreads();
+        const int pos = carry + warp_tot[w] + incl - un;
+        if (un) perm[pos] = c;
+        __syncthreads();
+        if (t == blockDim.x - 1) carry = pos + un;
+        __syncthreads();
     }
 }
 
-// M = R_11^{-1} Omega by back-substitution, one warp per column q of Omega;
-// the column lives in shared memory (Omega first, overwritten in place).
+__global__ void k_assemble_r(QrScratch q, int d, const int32_t* __restrict__ perm, double* __restrict__ R) {
+    const int r = (int)*q.rank;
+    const int j = blockIdx.x;                        // one CTA per row of R
+    if (j >= d) return;
+    double sgn = 1.0;
+    if (j < r) sgn = (q.Rorig[(int64_t)j * d + q.piv[j]] < 0.0) ? -1.0 : 1.0;
+    for (int t = threadIdx.x; t < d; t += blockDim.x) {
+        double v = 0.0;
+        if (j < r && t >= j) v = sgn * q.Rorig[(int64_t)j * d + perm[t]];
+        R[(int64_t)j * d + t] = v;
+    }
+}
+
+// M = R_11^{-1} Omega by back-substitution in blocks of 32 rows, one warp per
+// column q of Omega (the column lives in shared memory: Omega first, then M).
+// For the block of rows p0..p0+31 lane l owns row i = p0 + l: it first sums
+// the contributions of the rows below the block (already solved) on its own,
+// then the 32 x 32 triangle is solved bottom-up, each solved entry broadcast
+// with one shuffle and applied by the lanes above it.
 __global__ void k_omega_factor(const double* __restrict__ R, const int32_t* __restrict__ perm,
                                const int64_t* __restrict__ d_rank, int d, int k, uint64_t key,
                                double inv_sqrt_k, int identity, float* __restrict__ Mfull) {
@@ -195,18 +233,45 @@ __global__ void k_omega_factor(const double* __restrict__ R, const int32_t* __re
     for (int p = lane; p < r; p += 32)
         Ms[p] = identity ? (p == q ? 1.0 : 0.0) : box_muller(key, (uint64_t)p * k + q) * inv_sqrt_k;
     __syncwarp();
-    for (int p = r - 1; p >= 0; --p) {
-        const double* Rp = R + (int64_t)p * d;
-        double dot = 0.0;
-        for (int t = p + 1 + lane; t < r; t += 32) dot += Rp[t] * Ms[t];
-        dot = warp_sum(dot);
-        if (lane == 0) Ms[p] = (Ms[p] - dot) / Rp[p];
+    for (int p0 = ((r - 1) / 32) * 32; r > 0 && p0 >= 0; p0 -= 32) {
+        const int i = p0 + lane;
+        const bool valid = i < r;
+        const double* Ri = R + (int64_t)(valid ? i : 0) * d;
+        double rhs = valid ? Ms[i] : 0.0;
+        double acc0 = 0.0, acc1 = 0.0;
+        if (valid) {
+            int t = p0 + 32;
+            for (; t + 1 < r; t += 2) {
+                acc0 = fma(Ri[t], Ms[t], acc0);
+                acc1 = fma(Ri[t + 1], Ms[t + 1], acc1);
+            }
+            if (t < r) acc0 = fma(Ri[t], Ms[t], acc0);
+        }
+        rhs -= acc0 + acc1;
+        double rb[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) rb[jj] = (valid && p0 + jj < r) ? Ri[p0 + jj] : 0.0;
+        const double inv = valid ? 1.0 / Ri[i] : 0.0;
+        double x = 0.0;
+#pragma unroll
+        for (int jj = 31; jj >= 0; --jj) {
+            if (lane == jj) x = rhs * inv;
+            const double xj = __shfl_sync(0xffffffffu, x, jj);
+            if (lane < jj) rhs = fma(-rb[jj], xj, rhs);
+        }
+        if (valid) Ms[i] = x;
         __syncwarp();
     }
     for (int p = lane; p < r; p += 32) Mfull[(int64_t)perm[p] * k + q] = (float)Ms[p];
 }
 
 }  // namespace
+
+// The Gram route serves d <= kGramMaxD (the Schur complement of a d x d Gram
+// matrix fits in the distributed shared memory of one 16-CTA cluster) and
+// thresholds tau >= kGramMinTau (above its noise floor of about sqrt(m u)).
+constexpr int64_t kGramMaxD = 512;
+constexpr double kGramMinTau = 1e-6;
 
 // One layout for both the size and the carve: every piece starts on a 256-byte boundary.
 static size_t qr_layout(int64_t m, int64_t d, char* base, QrScratch* q) {
@@ -222,6 +287,9 @@ static size_t qr_layout(int64_t m, int64_t d, char* base, QrScratch* q) {
     char* piv = take(sizeof(int32_t) * (size_t)d);
     char* rank = take(sizeof(int64_t));
     char* barrier = take(sizeof(unsigned));
+    const bool gram = d <= kGramMaxD;
+    char* G = gram ? take(sizeof(double) * (size_t)(d * d)) : nullptr;
+    char* Gp = gram ? take(sizeof(double) * gram_partial_doubles(m, d)) : nullptr;
     if (q) {
         q->W = reinterpret_cast<double*>(W);
         q->norms = reinterpret_cast<double*>(norms);
@@ -229,6 +297,8 @@ static size_t qr_layout(int64_t m, int64_t d, char* base, QrScratch* q) {
         q->piv = reinterpret_cast<int32_t*>(piv);
         q->rank = reinterpret_cast<int64_t*>(rank);
         q->barrier = reinterpret_cast<unsigned*>(barrier);
+        q->G = reinterpret_cast<double*>(G);
+        q->Gp = reinterpret_cast<double*>(Gp);
     }
     return off;
 }
@@ -246,19 +316,24 @@ cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double 
     cudaError_t e;
     if ((e = cudaMemsetAsync(q.barrier, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(q.Rorig, 0, sizeof(double) * (size_t)(d * d), st)) != cudaSuccess) return e;
-    int occ = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pivoted_qr, QR_THREADS, 0)) != cudaSuccess)
-        return e;
-    int64_t grid = (int64_t)num_sms * (occ < 1 ? 1 : (occ > 2 ? 2 : occ));
-    if (grid > d) grid = d;
-    if (grid < 1) grid = 1;
-    QrArgs args{Atilde, (int)m, (int)d, tau, forced_perm, (int)forced_rank, q, status};
-    void* kargs[] = {&args};
-    e = cudaLaunchCooperativeKernel((const void*)k_pivoted_qr, dim3((unsigned)grid), dim3(QR_THREADS),
-                                    kargs, 0, st);
-    if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(int) * (size_t)d;
-    k_assemble_qr<<<1, 1024, smem, st>>>(q, (int)d, perm, R);
+    if (d <= kGramMaxD && (forced_perm || tau >= kGramMinTau)) {
+        e = launch_gram_pivoted_cholesky(Atilde, m, d, tau, forced_perm, forced_rank, q, status, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        int occ = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pivoted_qr, QR_THREADS, 0)) != cudaSuccess)
+            return e;
+        int64_t grid = (int64_t)num_sms * (occ < 1 ? 1 : (occ > 2 ? 2 : occ));
+        if (grid > d) grid = d;
+        if (grid < 1) grid = 1;
+        QrArgs args{Atilde, (int)m, (int)d, tau, forced_perm, (int)forced_rank, q, status};
+        void* kargs[] = {&args};
+        e = cudaLaunchCooperativeKernel((const void*)k_pivoted_qr, dim3((unsigned)grid), dim3(QR_THREADS),
+                                        kargs, 0, st);
+        if (e != cudaSuccess) return e;
+    }
+    k_assemble_perm<<<1, 1024, sizeof(int) * (size_t)d, st>>>(q, (int)d, perm);
+    k_assemble_r<<<(unsigned)d, 256, 0, st>>>(q, (int)d, perm, R);
     return cudaGetLastError();
 }
 
@@ -267,15 +342,14 @@ cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int6
                                 double* /*Mscratch*/, float* Mfull, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(Mfull, 0, sizeof(float) * (size_t)(d * k), st);
     if (e != cudaSuccess) return e;
-    const int warps = 4;
+    const int warps = 1;                              // spread the FP64 work over the SMs
     const size_t smem = sizeof(double) * (size_t)d * warps;
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_omega_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const int grid = (int)((k + warps - 1) / warps);
-    k_omega_factor<<<grid, 32 * warps, smem, st>>>(R, perm, d_rank, (int)d, (int)k,
-                                                   stream_key(seed, kStreamOmega),
+    k_omega_factor<<<grid, 32 * warps, smem, st>>>(R, perm, d_rank, (int)d, (int)k, stream_key(seed, kStreamOmega),
                                                    1.0 / sqrt((double)k), omega_identity ? 1 : 0, Mfull);
     return cudaGetLastError();
 }
@@ -317,7 +391,7 @@ extern "C" int lev_rrqr_noalloc(const float* Atilde, int64_t m, int64_t d, doubl
     if (need > kRrqrNoAllocBytes)
         return handle_fail(LEV_EINVAL,
                            "lev_rrqr_noalloc: m x d too large for the fixed 8 MiB scratch "
-                           "(needs 8 (m d + d^2 + 2 d) bytes plus small terms)");
+                           "(the QR working set is about 8 (m d + 2 d^2) bytes plus the Gram split partials)");
     if (tau <= 0) tau = 1e-5;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

@@ -28,25 +28,51 @@ __global__ void k_bucket_hist(int64_t n, uint32_t s, uint64_t key, int* count) {
     }
 }
 
-// Exclusive scan of count[0..s) into off[0..s], single CTA of 1024 threads.
+// Exclusive scan of count[0..s) into off[0..s], single CTA of 1024 threads:
+// tiles of 4096 counts loaded as int4 (coalesced), warp-shuffle scans, a
+// running carry between tiles.
 __global__ void __launch_bounds__(1024) k_scan_offsets(const int* count, int* off, int s) {
-    __shared__ int part[1024];
-    const int t = threadIdx.x;
-    const int per = (s + 1023) / 1024;
-    const int b0 = min(s, t * per), b1 = min(s, b0 + per);
-    int sum = 0;
-    for (int b = b0; b < b1; ++b) sum += count[b];
-    part[t] = sum;
+    __shared__ int warp_tot[32];
+    __shared__ int carry_s;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) carry_s = 0;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {          // Hillis-Steele inclusive scan
-        int v = (t >= o) ? part[t - o] : 0;
+    for (int base = 0; base < s; base += 4096) {
+        const int i0 = base + t * 4;
+        int v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (i0 + q < s) ? count[i0 + q] : 0;
+        const int local = v[0] + v[1] + v[2] + v[3];
+        int incl = local;                                   // inclusive warp scan of the thread sums
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) warp_tot[w] = incl;
         __syncthreads();
-        part[t] += v;
+        if (w == 0) {
+            int wt = warp_tot[lane];
+            int wi = wt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            warp_tot[lane] = wi - wt;                       // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        int run = carry_s + warp_tot[w] + incl - local;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i0 + q < s) off[i0 + q] = run;
+            run += v[q];
+        }
+        __syncthreads();
+        if (t == 1023) carry_s = run;                       // thread 1023 holds the tile's end
         __syncthreads();
     }
-    int run = (t == 0) ? 0 : part[t - 1];
-    for (int b = b0; b < b1; ++b) { off[b] = run; run += count[b]; }
-    if (t == 1023) off[s] = part[1023];
+    if (t == 0) off[s] = carry_s;
 }
 
 __global__ void k_bucket_scatter(int64_t n, uint32_t s, uint64_t key, const int* off,
