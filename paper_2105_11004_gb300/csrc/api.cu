@@ -51,7 +51,7 @@ struct GCache {
     size_t bytes = 0;
     uint64_t seed = 0;
     int64_t m = -1, s = -1;
-    int kind = -1;   // 0: FP32, 1: BF16 hi+lo
+    int kind = -1;   // 0: FP32 (ld = s); 2: BF16 hi + lo (ld = s rounded up to 64); 3: TF32-rounded FP32 (ld)
 };
 
 }  // namespace
@@ -62,7 +62,7 @@ struct lev_handle {
     int32_t* status = nullptr;      // device status word
     int64_t* host_rank = nullptr;   // pinned
     Buf count, off, tmp, perm_rows, B, partial, Atilde, qr, R, perm_d, Mfull, stageA, stageTheta,
-        tc_ws, csr_rp, csr_col, csr_val;
+        tc_ws, tc_ws2, csr_rp, csr_col, csr_val;
     GCache g;
 };
 
@@ -156,11 +156,15 @@ int check_prec(int32_t prec, const char* what) {
 double tau_of(const lev_params* p) { return p->tau > 0 ? p->tau : 1e-5; }
 
 // Make sure G (m x s) for (seed, kind) is in the cache; returns its pointers.
+// Kind 0: FP32, leading dimension s. Kind 2: BF16 hi then lo, leading dimension
+// s rounded up to 64 (TMA rows of whole 128-byte lines). Kind 3: FP32 rounded
+// to TF32, same padded leading dimension.
 int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
              const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo) {
     GCache& g = h->g;
-    const size_t elems = (size_t)m * (size_t)s;
-    const size_t bytes = kind == 0 ? elems * sizeof(float) : elems * 2 * sizeof(__nv_bfloat16);
+    const int64_t ld = kind == 0 ? s : (s + 63) / 64 * 64;
+    const size_t elems = (size_t)m * (size_t)ld;
+    const size_t bytes = kind == 2 ? elems * 2 * sizeof(__nv_bfloat16) : elems * sizeof(float);
     if (!(g.ptr && g.seed == seed && g.m == m && g.s == s && g.kind == kind)) {
         if (g.bytes < bytes) {
             if (g.ptr) cudaFree(g.ptr);
@@ -175,20 +179,20 @@ int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaS
             g.bytes = bytes;
         }
         cudaError_t e;
-        if (kind == 0)
-            e = lev::launch_gen_gaussian(m, s, seed, (float*)g.ptr, nullptr, nullptr, st);
-        else
-            e = lev::launch_gen_gaussian(m, s, seed, nullptr, (__nv_bfloat16*)g.ptr,
+        if (kind == 2)
+            e = lev::launch_gen_gaussian(m, s, ld, seed, nullptr, false, (__nv_bfloat16*)g.ptr,
                                          (__nv_bfloat16*)g.ptr + elems, st);
+        else
+            e = lev::launch_gen_gaussian(m, s, ld, seed, (float*)g.ptr, kind == 3, nullptr, nullptr, st);
         if (e != cudaSuccess) return fail(LEV_ECUDA, "G generation: %s", cudaGetErrorString(e));
         g.seed = seed;
         g.m = m;
         g.s = s;
         g.kind = kind;
     }
-    if (g32) *g32 = kind == 0 ? (const float*)g.ptr : nullptr;
-    if (ghi) *ghi = kind == 1 ? (const __nv_bfloat16*)g.ptr : nullptr;
-    if (glo) *glo = kind == 1 ? (const __nv_bfloat16*)g.ptr + elems : nullptr;
+    if (g32) *g32 = kind != 2 ? (const float*)g.ptr : nullptr;
+    if (ghi) *ghi = kind == 2 ? (const __nv_bfloat16*)g.ptr : nullptr;
+    if (glo) *glo = kind == 2 ? (const __nv_bfloat16*)g.ptr + elems : nullptr;
     return LEV_OK;
 }
 
@@ -282,7 +286,7 @@ int final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda
 // ---------------------------------------------------------------------------
 namespace lev {
 int handle_scratch(lev_handle* h, int which, size_t bytes, void** out) {
-    Buf* b = which == 0 ? &h->tc_ws : &h->partial;
+    Buf* b = which == 0 ? &h->tc_ws : (which == 1 ? &h->partial : &h->tc_ws2);
     LEV_TRY(ensure(*b, bytes));
     *out = b->ptr;
     return LEV_OK;
@@ -346,7 +350,7 @@ int lev_destroy(lev_handle* h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
-                  &h->R, &h->perm_d, &h->Mfull, &h->stageA, &h->stageTheta, &h->tc_ws, &h->csr_rp,
+                  &h->R, &h->perm_d, &h->Mfull, &h->stageA, &h->stageTheta, &h->tc_ws, &h->tc_ws2, &h->csr_rp,
                   &h->csr_col, &h->csr_val};
     for (Buf* b : all) release(*b);
     if (h->g.ptr) cudaFree(h->g.ptr);

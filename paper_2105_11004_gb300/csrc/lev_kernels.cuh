@@ -24,8 +24,9 @@ cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, c
                                    int64_t d, int64_t s, const int* off, const uint32_t* perm,
                                    float* B, cudaStream_t st);
 
-// G (m x s): FP32 copy and/or BF16 hi/lo copies (any pointer may be null).
-cudaError_t launch_gen_gaussian(int64_t m, int64_t s, uint64_t seed, float* g32,
+// G (m x s) with leading dimension ld >= s (columns s..ld zero): FP32 copy
+// (optionally TF32-rounded) and/or BF16 hi/lo copies (any pointer may be null).
+cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, bool tf32_round,
                                 __nv_bfloat16* ghi, __nv_bfloat16* glo, cudaStream_t st);
 
 // Atilde (m x d) = G (m x s) B (s x d), FP32 SIMT, split-K with a fixed-order

@@ -50,6 +50,40 @@ def test_sketch_dense_parity(L, h, n, d, s, m):
     assert np.all(err <= 2e-5 * scale + 1e-30), float(np.max(err / (scale + 1e-30)))
 
 
+SKETCH_TC_TOL = {"bf16x3": 1e-4, "tf32": 2e-3, "bf16": 1.6e-2}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("n,d,s,m", [(5000, 24, 1024, 96), (3001, 36, 700, 150), (20000, 256, 2048, 1024),
+                                     (777, 300, 5000, 300), (1, 4, 3, 8)])
+def test_sketch_dense_tensor_core_parity(L, h, prec, n, d, s, m):
+    """tcgen05 Gaussian stage: |A~_gpu - A~_oracle| <= tol (|G| |S| |A|) entrywise, tol from the
+    operand rounding of the form (2^-16 split BF16, 2^-11 TF32, 2^-8 BF16) and FP32 accumulation."""
+    import torch
+    A = W.dense_gaussian(n, d, seed=n + d + 1).astype(np.float32)
+    p = L.make_params(s=s, m=m, seed=7, sketch_prec=prec)
+    At = torch.full((m, d), float("nan"), dtype=torch.float32, device="cuda")
+    L.lev_sketch_dense(h, to_dev(A), p, At)
+    torch.cuda.synchronize()
+    A64 = A.astype(np.float64)
+    want = E.sketch(A64, s, m, 7)
+    scale = sketch_abs_scale(A64, s, m, 7)
+    err = np.abs(to_np(At) - want)
+    assert np.all(err <= SKETCH_TC_TOL[prec] * scale + 1e-30), float(np.max(err / (scale + 1e-30)))
+    assert L.lev_device_status(h) == 0
+
+
+def test_estimate_tensor_core_sketch_and_final(L, h):
+    """Split-BF16 Gaussian stage and split-BF16 final pass: rank exact, theta~ within 1e-4."""
+    A = W.dense_lowrank_skewed(60000, 64, 40, seed=21)
+    cfg = dict(s=8192, m=256, k=128, tau=1e-4, seed=3)
+    theta, r, perm = L.estimate(to_dev(A), handle=h, sketch_prec="bf16x3", final_prec="bf16x3", **cfg)
+    e = _oracle_estimate(A, cfg)
+    assert r == e.rank == 40
+    assert np.array_equal(to_np(perm)[:r], e.perm[:r])
+    assert max_rel(to_np(theta), e.theta) <= 1e-4
+
+
 def test_sketch_dense_strided_and_repeatable(L, h):
     import torch
     A = W.dense_gaussian(4099, 64, seed=3).astype(np.float32)
