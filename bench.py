@@ -190,6 +190,7 @@ def main():
                     help="final-pass forms timed and checked besides the main one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     cfg = W.CONFIGS[WORKLOAD]
@@ -332,6 +333,10 @@ def main():
            "roofline_final_pass": rooflines["final"],
            "clocks": clocks, "gpu_launches": kernels_per_step * args.steps}
 
+    # backward workload: dense 200,000 x 64, s = 16,384, m = 256, k = 128; forward = the four stages
+    if not args.no_backward:
+        out["backward"] = backward_timing(L, h, reps)
+
     if not args.no_e2e:
         theta_host = torch.empty(n, dtype=torch.float32).pin_memory()
         L.lev_estimate_dense(h, A_host, p, theta_host)
@@ -362,6 +367,43 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def backward_timing(L, h, reps):
+    """Forward (sketch, rrqr, omega factor, final pass) and backward times on the backward workload."""
+    import torch
+    cfg = W.CONFIGS["dense_2e5x64_backward"]
+    A = torch.from_numpy(W.dense_heavy_rows(cfg["n"], cfg["d"], seed=cfg["data_seed"])).cuda()
+    w = torch.from_numpy(W.uniform_weights(cfg["n"], seed=cfg["weight_seed"])).cuda()
+    p = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
+                      sketch_prec="bf16x3", final_prec="bf16x3")
+    theta, st = L.forward_state(A, p, handle=h)
+    g = torch.empty_like(A)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        L.lev_sketch_dense(h, A, p, st["Atilde"])
+        lib_rrqr_nosync(L, h, st["Atilde"], cfg["tau"], st["perm"], st["R"])
+        L.lev_omega_factor(h, st["R"], st["perm"], st["d_rank"], cfg["d"], cfg["k"], cfg["seed"], 0, st["Mfull"])
+        L.lev_final_dense(h, A, st["Mfull"], "bf16x3", theta)
+
+    def bwd():
+        L.lev_backward_dense(h, A, p, st["Atilde"], st["perm"], st["d_rank"], st["R"], st["Mfull"], w, g)
+
+    res = {}
+    for name, fn in (("forward_ms", fwd), ("backward_ms", bwd)):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / reps
+    res["bwd_over_fwd"] = res["backward_ms"] / res["forward_ms"]
+    res["workload"] = "dense_2e5x64_backward (200,000 x 64, 5% rows x100; s=16384, m=256, k=128; split-BF16 forms)"
+    return res
 
 
 def lib_rrqr_nosync(L, h, At, tau, perm, R):

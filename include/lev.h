@@ -181,15 +181,22 @@ int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, 
                      float* theta, int64_t* rank, int32_t* perm, void* stream);
 
 /* Gradient of g(A) = sum_i w_i theta~_i(A) with respect to dense A, with the
- * sketch S, G, Omega, the pivots and the rank held at the values a preceding
- * lev_estimate_dense(h, A, ..., p, ...) produced (the handle keeps its sketch
- * state: Atilde, perm, rank). All pointers are device pointers: A (n x d,
- * lda), w (n FP32), gradA (n x d FP32, ld = d; columns outside K are 0).
- * The paper has no backward pass; the formulas are the reverse-mode adjoint of
- * Alg. 10 (QR adjoint with zero Q cotangent). Errors: LEV_EINVAL (no matching
- * forward state), LEV_ENOMEM, LEV_ECUDA. */
+ * sketch S, G, Omega, the pivots and the rank held at the values of a forward
+ * pass. The paper has no backward pass; this is the reverse-mode adjoint of
+ * Alg. 10 (QR adjoint with a zero Q cotangent): with Y = A_K M, Z = 2 W Y,
+ * C = A_K^T Z, Rbar = -R_11^{-T} C M^T, Xbar = Q_1 copyltu(R_11 Rbar^T) R_11^{-T}
+ * and T = G^T Xbar, row i of the gradient on the columns of K is
+ * Z_i M^T + sigma_i T[h(i), :]; the columns outside K are 0. The n x k
+ * intermediate Y is recomputed in both passes, never stored.
+ * The forward state is passed explicitly (all device pointers), as produced by
+ * lev_sketch_dense / lev_rrqr / lev_omega_factor with the same p: Atilde
+ * (m x d FP32), perm (d int32), d_rank (int64), R (d x d FP64), Mfull (d x k
+ * FP32). A: n x d FP32 (lda); w: n FP32 (= dL/dtheta~); gradA: n x d FP32
+ * (ld = d). Limits: d <= 256, k <= 256. Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA. */
 int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
-                       const lev_params* p, const float* w, float* gradA, void* stream);
+                       const lev_params* p, const float* Atilde, const int32_t* perm,
+                       const int64_t* d_rank, const double* R, const float* Mfull,
+                       const float* w, float* gradA, void* stream);
 
 /* Device-side status word of the handle: nonzero after a bounded wait gave up. */
 int lev_device_status(lev_handle* h, int32_t* status);

@@ -57,7 +57,8 @@ SIGNATURES = {
     "lev_estimate_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64,
                                         _P(lev_params), _c_void_p, _P(_i64), _c_void_p, _c_void_p]),
     "lev_backward_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p,
-                                          _c_void_p, _c_void_p]),
+                                          _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p,
+                                          _c_void_p]),
     "lev_device_status": (ctypes.c_int, [_c_void_p, _P(_i32)]),
     "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
 }
@@ -214,10 +215,10 @@ def lev_estimate_csr(h: Handle, row_ptr, col, val, n, d, p: lev_params, theta, p
     return 0 if rc == LEV_ERANK0 else r.value
 
 
-def lev_backward_dense(h: Handle, A, p: lev_params, w, gradA, stream=None):
+def lev_backward_dense(h: Handle, A, p: lev_params, Atilde, perm, d_rank, R, Mfull, w, gradA, stream=None):
     n, d = A.shape
-    _check(lib.lev_backward_dense(h.ptr, _ptr(A), n, d, A.stride(0), ctypes.byref(p), _ptr(w), _ptr(gradA),
-                                  _stream(stream)))
+    _check(lib.lev_backward_dense(h.ptr, _ptr(A), n, d, A.stride(0), ctypes.byref(p), _ptr(Atilde), _ptr(perm),
+                                  _ptr(d_rank), _ptr(R), _ptr(Mfull), _ptr(w), _ptr(gradA), _stream(stream)))
 
 
 def lev_rrqr_noalloc(Atilde, tau, perm, R, stream=None) -> int:
@@ -248,3 +249,64 @@ def estimate(A, *, s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_pr
     perm = torch.empty(A.shape[1], dtype=torch.int32, device=A.device)
     r = lev_estimate_dense(h, A, p, theta, perm)
     return theta, r, perm
+
+
+def forward_state(A, p: lev_params, handle: Handle | None = None):
+    """Run the estimator stage by stage and keep every intermediate the backward needs.
+
+    Returns (theta, state) where state holds Atilde, perm, d_rank (device), rank, R, Mfull.
+    """
+    import torch
+    h = handle or default_handle(A.device.index or 0)
+    n, d = A.shape
+    s, m, k = lev_resolve_sizes(p, n, d)
+    dev = A.device
+    Atilde = torch.empty((m, d), dtype=torch.float32, device=dev)
+    perm = torch.empty(d, dtype=torch.int32, device=dev)
+    R = torch.empty((d, d), dtype=torch.float64, device=dev)
+    Mfull = torch.empty((d, k), dtype=torch.float32, device=dev)
+    theta = torch.empty(n, dtype=torch.float32, device=dev)
+    lev_sketch_dense(h, A, p, Atilde)
+    r = lev_rrqr(h, Atilde, p.tau, perm, R)
+    d_rank = torch.tensor([r], dtype=torch.int64, device=dev)
+    lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, p.flags, Mfull)
+    lev_final_dense(h, A, Mfull, p.final_prec, theta)
+    return theta, dict(Atilde=Atilde, perm=perm, d_rank=d_rank, rank=r, R=R, Mfull=Mfull, handle=h)
+
+
+def _autograd_class():
+    import torch
+
+    class LevScore(torch.autograd.Function):
+        """theta~ = LevScore.apply(A, params); backward gives dL/dA through lev_backward_dense."""
+
+        @staticmethod
+        def forward(ctx, A, p):
+            theta, st = forward_state(A, p)
+            ctx.p = p
+            ctx.st = st
+            ctx.save_for_backward(A)
+            return theta
+
+        @staticmethod
+        def backward(ctx, grad_theta):
+            (A,) = ctx.saved_tensors
+            st = ctx.st
+            gradA = torch.empty(A.shape, dtype=torch.float32, device=A.device)
+            lev_backward_dense(st["handle"], A, ctx.p, st["Atilde"], st["perm"], st["d_rank"], st["R"],
+                               st["Mfull"], grad_theta.contiguous().float(), gradA)
+            return gradA, None
+
+    return LevScore
+
+
+class _LazyAutograd:
+    _cls = None
+
+    def apply(self, A, p):
+        if _LazyAutograd._cls is None:
+            _LazyAutograd._cls = _autograd_class()
+        return _LazyAutograd._cls.apply(A, p)
+
+
+LevScore = _LazyAutograd()

@@ -62,7 +62,7 @@ struct lev_handle {
     int32_t* status = nullptr;      // device status word
     int64_t* host_rank = nullptr;   // pinned
     Buf count, off, tmp, perm_rows, B, partial, Atilde, qr, R, perm_d, Mfull, stageA, stageTheta,
-        tc_ws, tc_ws2, csr_rp, csr_col, csr_val;
+        tc_ws, tc_ws2, csr_rp, csr_col, csr_val, bwd;
     GCache g;
 };
 
@@ -350,7 +350,7 @@ int lev_destroy(lev_handle* h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
-                  &h->R, &h->perm_d, &h->Mfull, &h->stageA, &h->stageTheta, &h->tc_ws, &h->tc_ws2, &h->csr_rp,
+                  &h->R, &h->perm_d, &h->Mfull, &h->stageA, &h->stageTheta, &h->tc_ws, &h->tc_ws2, &h->bwd, &h->csr_rp,
                   &h->csr_col, &h->csr_val};
     for (Buf* b : all) release(*b);
     if (h->g.ptr) cudaFree(h->g.ptr);
@@ -534,10 +534,32 @@ int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, 
 }
 
 int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const lev_params* p,
-                       const float* w, float* gradA, void* stream) {
+                       const float* Atilde, const int32_t* perm, const int64_t* d_rank, const double* R,
+                       const float* Mfull, const float* w, float* gradA, void* stream) {
     LEV_TRY(set_device(h));
-    (void)A; (void)n; (void)d; (void)lda; (void)p; (void)w; (void)gradA; (void)stream;
-    return fail(LEV_EINVAL, "lev_backward_dense: no forward state");
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!A || !Atilde || !perm || !d_rank || !R || !Mfull || !w || !gradA) return fail(LEV_EINVAL, "NULL array");
+    if (lda < d) return fail(LEV_EINVAL, "lda < d");
+    if (d > 256 || z.k > 256) return fail(LEV_EINVAL, "lev_backward_dense needs d <= 256 and k <= 256");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool identity = (p->flags & LEV_SKETCH_IDENTITY) != 0;
+    const float* g32 = nullptr;
+    const __nv_bfloat16 *ghi = nullptr, *glo = nullptr;
+    int64_t ldg = z.s;
+    if (!identity) {
+        // the G image the forward's sketch used (cached in the handle)
+        const int kind = p->sketch_prec == LEV_FP32 ? 0 : (p->sketch_prec == LEV_TF32 ? 3 : 2);
+        LEV_TRY(ensure_g(h, z.m, z.s, p->seed, kind, st, &g32, &ghi, &glo));
+        if (kind != 0) ldg = (z.s + 63) / 64 * 64;
+        if (p->sketch_prec == LEV_BF16) glo = nullptr;      // that form multiplies by the BF16 hi part only
+    }
+    const int chunks = lev::backward_chunks(n, d, z.k);
+    LEV_TRY(ensure(h->bwd, lev::backward_scratch_bytes(n, d, z.k, z.s, z.m, chunks)));
+    LEV_CUDA(lev::launch_backward_dense(A, lda, n, d, z.s, z.m, z.k, p->seed, Atilde, perm, d_rank, R, Mfull, w, g32,
+                                        ghi, glo, ldg, identity, h->bwd.ptr, chunks, gradA, st));
+    return LEV_OK;
 }
 
 }  // extern "C"

@@ -75,6 +75,16 @@ cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int6
                                 int64_t d, int64_t k, uint64_t seed, bool omega_identity,
                                 double* Mscratch, float* Mfull, cudaStream_t st);
 
+// ---- backward.cu: gradient of sum_i w_i theta~_i ----
+
+int backward_chunks(int64_t n, int64_t d, int64_t k);
+size_t backward_scratch_bytes(int64_t n, int64_t d, int64_t k, int64_t s, int64_t m, int chunks);
+cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_t d, int64_t s, int64_t m, int64_t k,
+                                  uint64_t seed, const float* Atilde, const int32_t* perm, const int64_t* d_rank,
+                                  const double* R, const float* Mfull, const float* w, const float* G32,
+                                  const __nv_bfloat16* Ghi, const __nv_bfloat16* Glo, int64_t ldg, bool identity,
+                                  void* scratch, int chunks, float* gradA, cudaStream_t st);
+
 // ---- final.cu: fused final pass (SIMT) ----
 
 cudaError_t launch_final_dense_fp32(const float* A, int64_t lda, int64_t n, int64_t d,
