@@ -191,6 +191,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-csr", action="store_true", help="skip the CSR 8e6 x 1024 measurement")
+    ap.add_argument("--csr-large", action="store_true", help="also measure the CSR 8e7 x 1024 (~1e9 nnz) workload")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     cfg = W.CONFIGS[WORKLOAD]
@@ -337,6 +339,11 @@ def main():
     if not args.no_backward:
         out["backward"] = backward_timing(L, h, reps)
 
+    if not args.no_csr:
+        out["csr"] = {"csr_8e6x1024": csr_timing(L, h, "csr_8e6x1024", reps)}
+        if args.csr_large:
+            out["csr"]["csr_8e7x1024_rank1014"] = csr_timing(L, h, "csr_8e7x1024_rank1014", 3)
+
     if not args.no_e2e:
         theta_host = torch.empty(n, dtype=torch.float32).pin_memory()
         L.lev_estimate_dense(h, A_host, p, theta_host)
@@ -367,6 +374,53 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def csr_timing(L, h, name, reps):
+    """Whole estimate on a CSR workload (split-BF16 Gaussian stage, FP32 CSR final pass), with stages."""
+    import torch
+    cfg = W.CONFIGS[name]
+    n, d = cfg["n"], cfg["d"]
+    t0 = time.perf_counter()
+    C = W.csr_uniform(n, d, seed=cfg["data_seed"]) if name == "csr_8e6x1024" else \
+        W.csr_dup_columns(n, d, seed=cfg["data_seed"])
+    gen_s = time.perf_counter() - t0
+    rp = torch.from_numpy(C.row_ptr).cuda()
+    cl = torch.from_numpy(C.col).cuda()
+    vl = torch.from_numpy(C.val).cuda()
+    p = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3")
+    theta = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    r = L.lev_estimate_csr(h, rp, cl, vl, n, d, p, theta)
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    ms = timed(lambda: L.lev_estimate_csr(h, rp, cl, vl, n, d, p, theta, want_rank=False), reps)
+    At = torch.empty((cfg["m"], d), dtype=torch.float32, device="cuda")
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    Mf = torch.empty((d, cfg["k"]), dtype=torch.float32, device="cuda")
+    L.lev_sketch_csr(h, rp, cl, vl, n, d, p, At)
+    L.lev_rrqr(h, At, cfg["tau"], perm, R)
+    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
+    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
+    stages = {"sketch": timed(lambda: L.lev_sketch_csr(h, rp, cl, vl, n, d, p, At), reps),
+              "rrqr": timed(lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R), reps),
+              "omega": timed(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf), reps),
+              "final": timed(lambda: L.lev_final_csr(h, rp, cl, vl, n, d, Mf, "fp32", theta), reps)}
+    csr_bytes = C.nnz * 8 + (n + 1) * 8
+    return {"n": n, "d": d, "nnz": C.nnz, "rank": r, "ms_per_step": ms, "rows_per_s": n / (ms * 1e-3),
+            "csr_gbs_two_passes": 2 * csr_bytes / (ms * 1e-3) / 1e9, "stages_ms": stages,
+            "sketch_prec": "bf16x3", "final_prec": "fp32", "generation_s": gen_s}
 
 
 def backward_timing(L, h, reps):

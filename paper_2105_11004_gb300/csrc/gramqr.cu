@@ -36,6 +36,7 @@ namespace {
 constexpr int GT = 32;                 // Gram tile
 constexpr uint64_t kClusterWaitNs = 2000000000ull;
 constexpr int32_t kStatusClusterTimeout = 3;
+constexpr int64_t kClusterMaxD = 512;   // larger Gram matrices do not fit one cluster's shared memory
 
 __host__ __device__ inline int gram_tiles(int d) {
     const int nt = (d + GT - 1) / GT;
@@ -339,6 +340,142 @@ __global__ void __launch_bounds__(256, 1) k_pchol(const double* __restrict__ G, 
     if (ok) cluster_exit_barrier(ctl, CL, status);
 }
 
+// Pivoted Cholesky of G for larger d: one cooperative grid (one CTA per SM), the
+// Schur complement updated in place in global memory (L2 resident), CTA c owning
+// the columns l = c mod gridDim. As in the cluster kernel every CTA keeps a
+// replicated diagonal and takes the same pivots; the owner of the next pivot
+// updates that column first and publishes its progress in a global flag, which
+// readers poll (bounded) before copying the column from L2.
+__device__ __forceinline__ unsigned ld_acquire_gpu_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(256, 1) k_pchol_grid(double* __restrict__ S, int d, int m, double tau,
+                                                       const int32_t* __restrict__ forced, int forced_rank,
+                                                       double* __restrict__ Rorig, int32_t* __restrict__ piv,
+                                                       int64_t* __restrict__ rank_out, unsigned* progress,
+                                                       int32_t* status) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    double* rbuf = reinterpret_cast<double*>(smem);               // d
+    double* diag = rbuf + d;                                      // d
+    int* active = reinterpret_cast<int*>(diag + d);               // d
+    __shared__ long long red_b[8];
+    __shared__ int red_i[8];
+    __shared__ int s_next, s_stop, s_abort;
+    __shared__ double s_inv, s_rjj;
+    const int G = gridDim.x, me = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < d; i += 256) {
+        active[i] = 1;
+        diag[i] = __ldcg(S + (int64_t)i * d + i);
+    }
+    if (tid == 0) s_abort = 0;
+    __syncthreads();
+    auto pick = [&]() -> int {
+        long long bb = LLONG_MIN;
+        int bi = 0x7fffffff;
+        for (int i = tid; i < d; i += 256)
+            if (active[i]) {
+                const long long v = __double_as_longlong(diag[i]);
+                if (v > bb || (v == bb && i < bi)) { bb = v; bi = i; }
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_xor_sync(0xffffffffu, bb, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bb || (ov == bb && oi < bi)) { bb = ov; bi = oi; }
+        }
+        if (lane == 0) { red_b[wid] = bb; red_i[wid] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < 8; ++w)
+                if (red_b[w] > bb || (red_b[w] == bb && red_i[w] < bi)) { bb = red_b[w]; bi = red_i[w]; }
+            s_next = bi;
+        }
+        __syncthreads();
+        return s_next;
+    };
+    const int steps = forced ? min(forced_rank, min(m, d)) : min(m, d);
+    double s00 = 0.0;
+    int j = 0;
+    int p = forced ? (steps > 0 ? forced[0] : -1) : pick();
+    for (; j < steps; ++j) {
+        if (p < 0 || p >= d || !active[p]) break;
+        if (tid == 0) {
+            const double bv = diag[p];
+            if (j == 0) s00 = bv;
+            int stop = !(bv > 0.0);
+            if (!forced && bv <= tau * tau * s00) stop = 1;
+            s_stop = stop;
+            if (!stop) {
+                s_rjj = sqrt(bv);
+                s_inv = 1.0 / s_rjj;
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const double rjj = s_rjj, inv = s_inv;
+        const int own = p % G;
+        if (tid == 0) {
+            const uint64_t t0 = gtimer();
+            for (uint32_t it = 0;; ++it) {
+                if (ld_acquire_gpu_u32(progress + own) >= (unsigned)j) break;
+                if ((it & 31u) == 31u && gtimer() - t0 > kClusterWaitNs) {
+                    atomicExch(status, kStatusClusterTimeout);
+                    s_abort = 1;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const double* colp = S + (int64_t)p * d;
+        for (int i = tid; i < d; i += 256) rbuf[i] = active[i] ? __ldcg(colp + i) * inv : 0.0;
+        __syncthreads();
+        if (tid == 0) {
+            active[p] = 0;
+            if (me == 0) {
+                piv[j] = p;
+                Rorig[(int64_t)j * d + p] = rjj;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < d; i += 256)
+            if (active[i]) diag[i] = fma(-rbuf[i], rbuf[i], diag[i]);
+        __syncthreads();
+        const int pn = forced ? (j + 1 < steps ? forced[j + 1] : -1) : pick();
+        const bool own_next = pn >= 0 && pn < d && (pn % G) == me && active[pn];
+        if (own_next) {
+            double* col = S + (int64_t)pn * d;
+            const double rc = rbuf[pn];
+            for (int i = tid; i < d; i += 256)
+                if (active[i]) __stcg(col + i, fma(-rbuf[i], rc, __ldcg(col + i)));
+            if (tid == 0) Rorig[(int64_t)j * d + pn] = rc;
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                st_release_gpu_u32(progress + me, (unsigned)(j + 1));
+            }
+        }
+        for (int c = me; c < d; c += G) {
+            if (c == pn || !active[c]) continue;
+            const double rc = rbuf[c];
+            if (tid == 0) Rorig[(int64_t)j * d + c] = rc;
+            double* col = S + (int64_t)c * d;
+            for (int i = tid; i < d; i += 256)
+                if (active[i]) __stcg(col + i, fma(-rbuf[i], rc, __ldcg(col + i)));
+        }
+        __syncthreads();
+        p = pn;
+    }
+    if (me == 0 && tid == 0) *rank_out = j;
+}
+
 }  // namespace
 
 int gram_splits(int64_t m, int64_t d) {
@@ -397,8 +534,26 @@ cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t
         return cudaLaunchKernelEx(&cfg, kern, (const double*)q.G, (int)d, (int)m, tau, forced, (int)forced_rank,
                                   q.Rorig, q.piv, q.rank, status);
     };
-    e = launch(k_pchol<16>, 16);
-    if (e == cudaErrorNotSupported) e = launch(k_pchol<8>, 8);
+    if (d <= kClusterMaxD) {
+        e = launch(k_pchol<16>, 16);
+        if (e == cudaErrorNotSupported) e = launch(k_pchol<8>, 8);
+        return e;
+    }
+    // larger d: cooperative grid over the SMs, Schur complement in place in G
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = 2 * sizeof(double) * (size_t)d + sizeof(int) * (size_t)d + 64;
+    if ((e = cudaFuncSetAttribute(k_pchol_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    const int pgrid = sms < (int)d ? sms : (int)d;
+    if ((e = cudaMemsetAsync(q.flags, 0, sizeof(unsigned) * (size_t)pgrid, st)) != cudaSuccess) return e;
+    double* S = q.G;
+    const int32_t* fp = forced;
+    int fr = (int)forced_rank, di = (int)d, mi = (int)m;
+    void* kargs[] = {&S, &di, &mi, &tau, &fp, &fr, (void*)&q.Rorig, (void*)&q.piv, (void*)&q.rank, (void*)&q.flags,
+                     &status};
+    e = cudaLaunchCooperativeKernel((const void*)k_pchol_grid, dim3((unsigned)pgrid), dim3(256), kargs, smem, st);
     return e;
 }
 

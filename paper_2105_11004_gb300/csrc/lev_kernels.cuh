@@ -51,6 +51,7 @@ struct QrScratch {
     unsigned* barrier;  // 1 uint32 grid-barrier counter
     double* G;        // d x d FP64 Gram matrix (Gram route)
     double* Gp;       // split partials of the Gram matrix (Gram route)
+    unsigned* flags;  // per-CTA progress flags of the grid pivoted Cholesky (Gram route, d > 512)
 };
 
 // Gram route of the pivoted QR (gramqr.cu): G = A~^T A~ in FP64, then a

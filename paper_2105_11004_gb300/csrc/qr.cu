@@ -267,10 +267,10 @@ __global__ void k_omega_factor(const double* __restrict__ R, const int32_t* __re
 
 }  // namespace
 
-// The Gram route serves d <= kGramMaxD (the Schur complement of a d x d Gram
-// matrix fits in the distributed shared memory of one 16-CTA cluster) and
-// thresholds tau >= kGramMinTau (above its noise floor of about sqrt(m u)).
-constexpr int64_t kGramMaxD = 512;
+// The Gram route serves d <= kGramMaxD (one 16-CTA cluster up to d = 512, a
+// cooperative grid over the SMs above) and thresholds tau >= kGramMinTau (above
+// its noise floor of about sqrt(m u)).
+constexpr int64_t kGramMaxD = 1024;
 constexpr double kGramMinTau = 1e-6;
 
 // One layout for both the size and the carve: every piece starts on a 256-byte boundary.
@@ -290,6 +290,7 @@ static size_t qr_layout(int64_t m, int64_t d, char* base, QrScratch* q) {
     const bool gram = d <= kGramMaxD;
     char* G = gram ? take(sizeof(double) * (size_t)(d * d)) : nullptr;
     char* Gp = gram ? take(sizeof(double) * gram_partial_doubles(m, d)) : nullptr;
+    char* flags = gram ? take(sizeof(unsigned) * 1024) : nullptr;
     if (q) {
         q->W = reinterpret_cast<double*>(W);
         q->norms = reinterpret_cast<double*>(norms);
@@ -299,6 +300,7 @@ static size_t qr_layout(int64_t m, int64_t d, char* base, QrScratch* q) {
         q->barrier = reinterpret_cast<unsigned*>(barrier);
         q->G = reinterpret_cast<double*>(G);
         q->Gp = reinterpret_cast<double*>(Gp);
+        q->flags = reinterpret_cast<unsigned*>(flags);
     }
     return off;
 }

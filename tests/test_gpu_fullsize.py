@@ -1,0 +1,175 @@
+"""Full-size parity: the workload sizes, in the launch configuration bench.py times.
+
+At these sizes the oracle recomputes what it can one entry at a time, on the GPU's
+own intermediates:
+* sketch: sampled entries A~[j, c] = G[j, :] . (S A)[:, c] (one G row, one sketch column);
+* QR: pivots form a permutation, diag(R) > 0, the Gram identity
+  (A~ P)^T (A~ P) = R^T R on sampled entries of the leading r x r block, the rank;
+* final pass: theta~ of sampled rows from the GPU's Mfull, in FP64.
+The end-to-end comparison with the oracle's own sketch runs at the dense workload
+size (the oracle finishes it in seconds).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import estimator as E, rng as orng
+
+from ._gpu import lev_module, max_rel, to_dev, to_np
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    assert torch.cuda.is_available()
+    return lev_module()
+
+
+@pytest.fixture(scope="module")
+def h(L):
+    return L.Handle(0)
+
+
+def _sketch_entries(col_of, n, s, m, seed, js, cs):
+    """A~[j, c] for j in js, c in cs from the oracle streams; col_of(c) -> dense column c of A (FP64)."""
+    b, sign = orng.bucket_and_sign(n, s, seed)
+    out = np.zeros((len(js), len(cs)))
+    Grows = np.stack([orng.gaussian_sketch_block(m, s, seed, 0, s)[j] for j in js]) if m * s <= 2 ** 26 else None
+    for ci, c in enumerate(cs):
+        Bc = np.zeros(s)
+        np.add.at(Bc, b, sign * col_of(c))
+        for ji, j in enumerate(js):
+            if Grows is not None:
+                g = Grows[ji]
+            else:
+                idx = np.uint64(j) * np.uint64(s) + np.arange(s, dtype=np.uint64)
+                g = orng.gaussian(seed, orng.STREAM_G, idx) / np.sqrt(m)
+            out[ji, ci] = g @ Bc
+    return out
+
+
+def _abs_entries(col_of, n, s, m, seed, js, cs):
+    b, _ = orng.bucket_and_sign(n, s, seed)
+    out = np.zeros((len(js), len(cs)))
+    for ci, c in enumerate(cs):
+        Bc = np.zeros(s)
+        np.add.at(Bc, b, np.abs(col_of(c)))
+        for ji, j in enumerate(js):
+            idx = np.uint64(j) * np.uint64(s) + np.arange(s, dtype=np.uint64)
+            out[ji, ci] = np.abs(orng.gaussian(seed, orng.STREAM_G, idx) / np.sqrt(m)) @ Bc
+    return out
+
+
+def _check_qr(At, perm, R, r, rs):
+    d = perm.size
+    assert sorted(perm.tolist()) == list(range(d))
+    Rk = R[:r, :r]
+    assert np.all(np.diag(Rk) > 0)
+    assert np.all(np.tril(Rk, -1) == 0)
+    # (A~ P)^T (A~ P) = R^T R on sampled entries of the leading block
+    AP = At.astype(np.float64)[:, perm[:r]]
+    for _ in range(40):
+        a, c = rs.integers(0, r, 2)
+        lhs = AP[:, a] @ AP[:, c]
+        rhs = R[:, a] @ R[:, c]
+        scale = np.linalg.norm(AP[:, a]) * np.linalg.norm(AP[:, c])
+        assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def _rows_theta(C, rows, Mf):
+    """theta~ of the given CSR rows from Mfull, FP64, straight from the CSR arrays."""
+    M64 = Mf.astype(np.float64)
+    out = np.empty(len(rows))
+    for t, i in enumerate(rows):
+        a, b = C.row_ptr[i], C.row_ptr[i + 1]
+        y = C.val[a:b].astype(np.float64) @ M64[C.col[a:b]]
+        out[t] = y @ y
+    return out
+
+
+def _run_stages(L, h, p, sketch, final, d, m, k):
+    import torch
+    At = torch.empty((m, d), dtype=torch.float32, device="cuda")
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    Mf = torch.empty((d, k), dtype=torch.float32, device="cuda")
+    sketch(At)
+    r = L.lev_rrqr(h, At, p.tau, perm, R)
+    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
+    L.lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, 0, Mf)
+    theta = final(Mf)
+    torch.cuda.synchronize()
+    return to_np(At), to_np(perm), to_np(R), r, to_np(Mf), theta
+
+
+def test_dense_1e6x256_end_to_end(L, h):
+    """Dense 1e6 x 256 of rank 200 in the bench configuration: rank, pivots and every theta~
+    against the oracle's own FP64 estimate (split-BF16 sketch and final pass: 1e-4)."""
+    cfg = W.CONFIGS["dense_1e6x256_rank200"]
+    A = W.dense_lowrank_skewed(cfg["n"], cfg["d"], cfg["rank"], seed=cfg["data_seed"])
+    theta, r, perm = L.estimate(to_dev(A), s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
+                                sketch_prec="bf16x3", final_prec="bf16x3", handle=h)
+    e = E.estimate(A.astype(np.float64), cfg["s"], cfg["m"], cfg["k"], cfg["tau"], cfg["seed"])
+    assert r == e.rank == 200
+    assert np.array_equal(to_np(perm)[:r], e.perm[:r])
+    assert max_rel(to_np(theta), e.theta) <= 1e-4
+
+
+def test_csr_8e6x1024(L, h):
+    """CSR 8e6 x 1024 (8 nnz/row, 1% rows with 256), s = 262144, m = 4096, k = 256, full rank."""
+    import torch
+    cfg = W.CONFIGS["csr_8e6x1024"]
+    n, d, s, m, k = cfg["n"], cfg["d"], cfg["s"], cfg["m"], cfg["k"]
+    C = W.csr_uniform(n, d, seed=cfg["data_seed"])
+    rp, cl, vl = to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val)
+    p = L.make_params(s=s, m=m, k=k, tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3")
+    theta_t = torch.empty(n, device="cuda")
+    At, perm, R, r, Mf, _ = _run_stages(
+        L, h, p, lambda out: L.lev_sketch_csr(h, rp, cl, vl, n, d, p, out),
+        lambda Mf_: (L.lev_final_csr(h, rp, cl, vl, n, d, Mf_, "fp32", theta_t), to_np(theta_t))[1], d, m, k)
+    theta = to_np(theta_t)
+    rs = np.random.default_rng(0)
+    Asp = sp.csr_matrix((C.val.astype(np.float64), C.col, C.row_ptr), shape=(n, d)).tocsc()
+    col_of = lambda c: Asp[:, c].toarray().ravel()
+    js, cs = rs.integers(0, m, 3), rs.integers(0, d, 3)
+    want = _sketch_entries(col_of, n, s, m, cfg["seed"], js, cs)
+    scale = _abs_entries(col_of, n, s, m, cfg["seed"], js, cs)
+    assert np.all(np.abs(At[np.ix_(js, cs)] - want) <= 1e-4 * scale)
+    assert r == d
+    _check_qr(At, perm, R, r, rs)
+    rows = rs.integers(0, n, 2000)
+    assert max_rel(theta[rows], _rows_theta(C, rows, Mf)) <= 1e-5
+
+
+def test_csr_8e7x1024_rank1014(L, h):
+    """CSR 8e7 x 1024, ~12 nnz/row (~1e9 nnz), column j + 512 = 2 x column j for j < 10:
+    rank exactly 1014, no dependent pair both selected, sampled sketch entries and theta~."""
+    import torch
+    cfg = W.CONFIGS["csr_8e7x1024_rank1014"]
+    n, d, s, m, k = cfg["n"], cfg["d"], cfg["s"], cfg["m"], cfg["k"]
+    C = W.csr_dup_columns(n, d, seed=cfg["data_seed"])
+    rp, cl, vl = to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val)
+    p = L.make_params(s=s, m=m, k=k, tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3")
+    theta_t = torch.empty(n, device="cuda")
+    At, perm, R, r, Mf, _ = _run_stages(
+        L, h, p, lambda out: L.lev_sketch_csr(h, rp, cl, vl, n, d, p, out),
+        lambda Mf_: (L.lev_final_csr(h, rp, cl, vl, n, d, Mf_, "fp32", theta_t), to_np(theta_t))[1], d, m, k)
+    theta = to_np(theta_t)
+    assert r == 1014
+    sel = set(perm[:r].tolist())
+    for j in range(10):
+        assert not ({j, j + 512} <= sel)
+    # dependent columns of the sketch stay exactly dependent (sums in a fixed order)
+    for j in range(10):
+        assert np.array_equal(At[:, j + 512], 2.0 * At[:, j])
+    rs = np.random.default_rng(1)
+    _check_qr(At, perm, R, r, rs)
+    rows = rs.integers(0, n, 2000)
+    assert max_rel(theta[rows], _rows_theta(C, rows, Mf)) <= 1e-5
+    # sum_i theta~_i = ||A_K R_11^{-1} Omega||_F^2; with an m-row Gaussian stage its expectation is
+    # r m / (m - r - 1) (mean of the inverse Wishart), about 1348 here
+    want_sum = r * m / (m - r - 1)
+    assert abs(float(theta.astype(np.float64).sum()) / want_sum - 1) < 0.03
