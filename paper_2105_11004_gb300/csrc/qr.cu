@@ -209,7 +209,13 @@ __global__ void k_assemble_r(QrScratch q, int d, const int32_t* __restrict__ per
     if (j < r) sgn = (q.Rorig[(int64_t)j * d + q.piv[j]] < 0.0) ? -1.0 : 1.0;
     for (int t = threadIdx.x; t < d; t += blockDim.x) {
         double v = 0.0;
-        if (j < r && t >= j) v = sgn * q.Rorig[(int64_t)j * d + perm[t]];
+        if (j < r && t >= j) {
+            v = q.Rorig[(int64_t)j * d + perm[t]];
+            // entries the Gram route never wrote (columns retired before step j) hold its
+            // "unwritten" pattern, a signalling NaN that arithmetic never produces
+            if (__double_as_longlong(v) == (long long)0xFFF40000DEADBEEFull) v = 0.0;
+            v *= sgn;
+        }
         R[(int64_t)j * d + t] = v;
     }
 }
