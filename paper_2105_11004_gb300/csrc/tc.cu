@@ -2,24 +2,29 @@
 // theta~_i = ||A_i Mfull||^2 with the product accumulated in TMEM and squared
 // in the epilogue, so the n x k product never reaches memory.
 //
-// One persistent CTA per SM (one pair of CTAs for the half-width forms):
-//   * warp 12 (MMA warp): allocates TMEM (two accumulators), loads the packed
-//     operand image of Mfull^T into shared memory once with bulk TMA copies,
-//     and one thread issues tcgen05.mma (M = 128 rows, N = NT columns, 32 bytes
-//     of K per instruction) for every K block of every tile;
-//   * warps 4..11 (converters): coalesced 128-bit loads of A rows, rounding to
-//     the operand type (BF16, BF16 hi + lo, or TF32), stores into the 128-byte
-//     swizzled K-major operand layout, one K block (128 bytes of K per row) per
-//     pipeline stage;
+// One persistent CTA per SM (BF16) or per SM of a 2-CTA cluster (BF16X3, TF32).
+//   * warp 13 (producer): 2-D tensor TMA of the CTA's 128 rows of A, one box
+//     of 32 FP32 columns at a time (128-byte swizzle), into a staging ring;
+//   * warps 4..11 (converters): round each staged box to the operand type
+//     (BF16, BF16 hi + lo, or TF32) into a 128-byte swizzled K-major operand
+//     buffer holding one K block (128 bytes of every row);
+//   * warp 12 (MMA): allocates TMEM (two accumulators of 256 columns), loads
+//     the CTA's part of the packed operand image of Mfull^T once with bulk
+//     copies, and one thread issues tcgen05.mma (N = 256, 32 bytes of K per
+//     instruction);
 //   * warps 0..3 (epilogue): tcgen05.ld of the accumulator (TMEM lane = row),
-//     sum of squares per row, one FP32 store (or atomic add of the half-width
-//     partial) per row.
-// Forms: BF16 (N = 256, one CTA per tile); BF16X3 (hi*hi + lo*hi + hi*lo,
-// N = 128 per CTA, a pair of CTAs per tile); TF32 (N = 128 per CTA, pair).
-// The half-width forms exist because a K x 256 operand of 4-byte (TF32) or
-// split (2 x 2-byte) values is 256 KB, more than a CTA's shared memory.
-// Every wait is bounded (2 s of %globaltimer); on expiry the CTA records the
-// failure in the status word and leaves its loops.
+//     sum of squares over the 256 columns, one store per row.
+// BF16: M = 128 per CTA; the 128 KB image of Mfull^T (256 x 256 BF16) fits one
+// CTA. BF16X3 (hi*hi + lo*hi + hi*lo) and TF32 need 256 KB for the image, so
+// they run as CTA pairs with cta_group::2: one thread of the even CTA issues an
+// M = 256 MMA for the pair; each CTA holds its own 128 rows of A and half of
+// the image (128 columns of Mfull), and each CTA's TMEM receives its own rows
+// with all 256 columns. Nothing is loaded twice and no operand crosses between
+// the CTAs except through the MMA itself. The odd CTA reports "operand ready"
+// and "accumulator drained" to the even CTA's mbarriers; the MMA completion is
+// multicast to both. Every wait is bounded (2 s of %globaltimer); on expiry the
+// CTA records the failure in the status word and leaves its loops.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "lev_common.cuh"
@@ -32,48 +37,52 @@ namespace {
 
 using namespace tcx;
 
-// ------------------------------------------------------------------ forms
-
 enum Form { kBF16 = 0, kBF16X3 = 1, kTF32 = 2 };
 
+// kKbe: operand elements per K block (128 bytes of a row); kNt: rows of the Mfull^T image one CTA
+// holds; kPair: CTAs per MMA; kStg: staged boxes; kOp: operand buffers.
 template <int F>
 struct FormTraits;
 template <>
 struct FormTraits<kBF16> {
     static constexpr bool kTf32 = false, kSplit = false;
-    static constexpr int kElem = 2, kKbe = 64, kNt = 256, kStages = 4, kPair = 1;
+    static constexpr int kElem = 2, kKbe = 64, kNt = 256, kPair = 1, kStg = 4, kOp = 2;
 };
 template <>
 struct FormTraits<kBF16X3> {
     static constexpr bool kTf32 = false, kSplit = true;
-    static constexpr int kElem = 2, kKbe = 64, kNt = 128, kStages = 2, kPair = 2;
+    static constexpr int kElem = 2, kKbe = 64, kNt = 128, kPair = 2, kStg = 2, kOp = 2;
 };
 template <>
 struct FormTraits<kTF32> {
     static constexpr bool kTf32 = true, kSplit = false;
-    static constexpr int kElem = 4, kKbe = 32, kNt = 128, kStages = 4, kPair = 2;
+    static constexpr int kElem = 4, kKbe = 32, kNt = 128, kPair = 2, kStg = 4, kOp = 2;
 };
 
-constexpr int kTileRows = 128;
+constexpr int kTileRows = 128;                    // rows of A per CTA per tile (TMEM lanes)
 constexpr int kKBlockBytes = kTileRows * 128;     // one K block of the A operand: 16 KB
+constexpr int kBoxBytes = kTileRows * 128;        // one staged box: 128 rows x 32 FP32
+constexpr int kNOut = 256;                        // MMA N: accumulator columns per row
 constexpr int kEpiWarps = 4, kCvtWarps = 8;
 constexpr int kMmaWarp = kEpiWarps + kCvtWarps;   // warp 12
-constexpr int kThreads = (kMmaWarp + 1) * 32;     // 416
+constexpr int kTmaWarp = kMmaWarp + 1;            // warp 13
+constexpr int kThreads = (kTmaWarp + 1) * 32;     // 448
 constexpr uint64_t kWaitNs = 2000000000ull;       // 2 s
+constexpr uint64_t kExitWaitNs = 5000000000ull;   // 5 s: a peer that timed out reaches the exit within one kWaitNs
 constexpr int32_t kStatusTcTimeout = 2;
 
 struct TcSmemCtl {
-    uint64_t full[4], empty[4], tfull[2], tempty[2], mfull;
+    uint64_t sfull[4], sempty[4], ofull[4], oempty[4], tfull[2], tempty[2], mfull, ipeer, mdone, xbar;
     uint32_t tmem_base;
     int32_t abort;
 };
 
-// Bounded wait on an mbarrier phase; false if this CTA gave up.
+// Bounded wait on an mbarrier phase (acquire at cluster scope); false if this CTA gave up.
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, TcSmemCtl* ctl, int32_t* status) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_cluster(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_cluster(bar, parity)) return true;
         if ((it & 63u) == 0) {
             if (*(volatile int32_t*)&ctl->abort) return false;
             if (global_ns() - t0 > kWaitNs) {
@@ -85,187 +94,247 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, TcSmemCt
     }
 }
 
+// Bounded wait that an abort does not cut short: used to drain copies, MMAs and peer
+// arrivals still in flight before TMEM is freed and the CTA exits.
+__device__ __forceinline__ bool drain_bar(uint32_t bar, uint32_t parity, uint64_t limit_ns, int32_t* status) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait_cluster(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) {
+            atomicExch(status, kStatusTcTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Arrive on the mbarrier at `bar` in the even CTA of the pair (this CTA when unpaired).
+template <int PAIR>
+__device__ __forceinline__ void arrive_leader(uint32_t bar, uint32_t me) {
+    if constexpr (PAIR == 2) {
+        if (me == 0)
+            mbar_arrive_cluster(bar);
+        else
+            mbar_arrive_cluster(mapa_shared(bar, 0));
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+// Row of the 128-row box handled by converter slot g: the two rows a half-warp stores
+// (slots 2j, 2j+1) sit 4 apart in their 8-row swizzle group, so their 64-byte halves of
+// the 128-byte swizzled rows fall in different banks.
+__device__ __forceinline__ uint32_t cvt_row(uint32_t g) {
+    return (g & ~7u) | ((g & 1u) << 2) | ((g >> 1) & 3u);
+}
+
 template <int F>
-__global__ void __launch_bounds__(kThreads, 1) k_final_tc(const float* __restrict__ A, int64_t lda, int64_t n,
-                                                          int d, int nkb, const uint8_t* __restrict__ image,
+__global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant__ CUtensorMap tmA, int64_t n,
+                                                          int nkb, const uint8_t* __restrict__ image,
                                                           uint32_t image_bytes, float* __restrict__ theta,
                                                           int32_t* status) {
     using T = FormTraits<F>;
-    constexpr int NT = T::kNt;
-    constexpr int STAGES = T::kStages;
-    constexpr int A_STAGE_BYTES = kKBlockBytes * (T::kSplit ? 2 : 1);
-    constexpr uint32_t IDESC = make_idesc(T::kTf32, kTileRows, NT);
+    constexpr int PAIR = T::kPair;
+    constexpr int BOXES = T::kKbe / 32;                       // staged boxes per K block
+    constexpr int OP_BYTES = kKBlockBytes * (T::kSplit ? 2 : 1);
+    constexpr uint32_t IDESC = make_idesc(T::kTf32, kTileRows * PAIR, kNOut);
+    static_assert(T::kNt * PAIR == kNOut, "the MMA covers 256 columns of Mfull");
     extern __shared__ uint8_t smem_raw[];
-    // 1024-byte aligned operand area: [image | A stages], control block after it
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
-    uint8_t* base = smem_raw + pad;
-    uint8_t* img = base;                                   // image_bytes (multiple of 1024)
-    uint8_t* astage = base + image_bytes;                  // STAGES x A_STAGE_BYTES
-    TcSmemCtl* ctl = reinterpret_cast<TcSmemCtl*>(astage + STAGES * A_STAGE_BYTES);
+    uint8_t* img = smem_raw + pad;                            // image_bytes (multiple of 1024)
+    uint8_t* opbuf = img + image_bytes;                       // kOp x OP_BYTES
+    uint8_t* stg = opbuf + T::kOp * OP_BYTES;                 // kStg x kBoxBytes
+    TcSmemCtl* ctl = reinterpret_cast<TcSmemCtl*>(stg + T::kStg * kBoxBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int half = (T::kPair == 2) ? (int)(blockIdx.x & 1) : 0;
-    const int group = (T::kPair == 2) ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-    const int ngroups = (T::kPair == 2) ? (int)(gridDim.x >> 1) : (int)gridDim.x;
-    const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
-    const uint32_t img_half_bytes = image_bytes;           // this CTA's half (or the whole image)
+    const uint32_t me = PAIR == 2 ? cluster_ctarank() : 0u;
+    const bool leader = me == 0;
+    const int64_t group = blockIdx.x / PAIR, ngroups = gridDim.x / PAIR;
+    constexpr int64_t kGroupRows = (int64_t)kTileRows * PAIR;
+    const int64_t ntiles = (n + kGroupRows - 1) / kGroupRows;
+    const int64_t my_tiles = ntiles > group ? (ntiles - group + ngroups - 1) / ngroups : 0;
+    const int64_t nbox = (int64_t)nkb * BOXES;
+    const int64_t kblocks = my_tiles * nkb;                   // operand-buffer uses
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(smem_u32(&ctl->full[s]), kCvtWarps);
-            mbar_init(smem_u32(&ctl->empty[s]), 1);
+        for (int s = 0; s < T::kStg; ++s) {
+            mbar_init(smem_u32(&ctl->sfull[s]), 1);
+            mbar_init(smem_u32(&ctl->sempty[s]), kCvtWarps);
+        }
+        for (int o = 0; o < T::kOp; ++o) {
+            mbar_init(smem_u32(&ctl->ofull[o]), kCvtWarps * PAIR);
+            mbar_init(smem_u32(&ctl->oempty[o]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl->tfull[a]), 1);
-            mbar_init(smem_u32(&ctl->tempty[a]), kEpiWarps);
+            mbar_init(smem_u32(&ctl->tempty[a]), kEpiWarps * PAIR);
         }
         mbar_init(smem_u32(&ctl->mfull), 1);
+        mbar_init(smem_u32(&ctl->ipeer), 1);
+        mbar_init(smem_u32(&ctl->mdone), 1);
+        mbar_init(smem_u32(&ctl->xbar), PAIR);
         ctl->abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
+    if (PAIR == 2) asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     if (warp == kMmaWarp) {
-        tmem_alloc(smem_u32(&ctl->tmem_base), 2 * NT);
-        tmem_relinquish();
+        tmem_alloc_cg<PAIR>(smem_u32(&ctl->tmem_base), 2 * kNOut);
+        tmem_relinquish_cg<PAIR>();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
-    if (warp == kMmaWarp) {
+    if (warp == kTmaWarp) {
+        // ---------------- producer: this CTA's 128 rows, one 32-column box per stage
         if (lane == 0) {
-            // Operand image of Mfull^T for this CTA's column half: bulk TMA copies, 16 KB each.
-            const uint8_t* src = image + (size_t)half * img_half_bytes;
+            int s = 0;
+            uint32_t ph = 0;
+            int64_t issued = 0;
+            for (int64_t it = 0; it < my_tiles * nbox; ++it) {
+                if (!wait_bar(smem_u32(&ctl->sempty[s]), ph ^ 1u, ctl, status)) break;
+                const int64_t t = group + (it / nbox) * ngroups;
+                const int32_t x = (int32_t)(it % nbox) * 32;
+                const int32_t y = (int32_t)(t * kGroupRows + (int64_t)me * kTileRows);
+                const uint32_t bar = smem_u32(&ctl->sfull[s]);
+                mbar_arrive_expect_tx(bar, (uint32_t)kBoxBytes);
+                tma_load_2d(smem_u32(stg + s * kBoxBytes), &tmA, x, y, bar);
+                ++issued;
+                if (++s == T::kStg) { s = 0; ph ^= 1u; }
+            }
+            // no copy may still be landing in this CTA's shared memory when it exits
+            for (int64_t j = issued > T::kStg ? issued - T::kStg : 0; j < issued; ++j)
+                drain_bar(smem_u32(&ctl->sfull[j % T::kStg]), (uint32_t)((j / T::kStg) & 1), kWaitNs, status);
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            const uint8_t* src = image + (size_t)me * image_bytes;
             const uint32_t mbar = smem_u32(&ctl->mfull);
-            mbar_arrive_expect_tx(mbar, img_half_bytes);
-            for (uint32_t off = 0; off < img_half_bytes; off += 16384u) {
-                const uint32_t len = min(16384u, img_half_bytes - off);
+            mbar_arrive_expect_tx(mbar, image_bytes);
+            for (uint32_t off = 0; off < image_bytes; off += 16384u) {
+                const uint32_t len = min(16384u, image_bytes - off);
                 bulk_g2s(smem_u32(img + off), src + off, len, mbar);
             }
             bool ok = wait_bar(mbar, 0, ctl, status);
-            int stage = 0;
-            uint32_t phase = 0;
-            int acc = 0;
-            uint32_t acc_phase = 0;
-            const uint32_t img_addr = smem_u32(img);
-            const uint32_t a_addr = smem_u32(astage);
-            const uint32_t kb_img_bytes = (uint32_t)NT * 128u;     // one K block of the image
-            for (int64_t t = group; ok && t < ntiles; t += ngroups) {
-                if (!wait_bar(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, ctl, status)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(acc * NT);
-                for (int kb = 0; kb < nkb; ++kb) {
-                    if (!wait_bar(smem_u32(&ctl->full[stage]), phase, ctl, status)) { ok = false; break; }
+            if (PAIR == 2 && !leader) {
+                // the even CTA's MMAs read this CTA's half of the image
+                if (ok) mbar_arrive_cluster(mapa_shared(smem_u32(&ctl->ipeer), 0));
+            } else {
+                if (PAIR == 2) ok = ok && wait_bar(smem_u32(&ctl->ipeer), 0, ctl, status);
+                int o = 0;
+                uint32_t oph = 0;
+                int acc = 0;
+                uint32_t acc_phase = 0;
+                const uint32_t img_addr = smem_u32(img);
+                const uint32_t op_addr = smem_u32(opbuf);
+                const uint32_t kb_img_bytes = (uint32_t)T::kNt * 128u;
+                for (int64_t tt = 0; ok && tt < my_tiles; ++tt) {
+                    if (!wait_bar(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, ctl, status)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a_hi = a_addr + (uint32_t)stage * A_STAGE_BYTES;
-                    const uint32_t m_hi = img_addr + (uint32_t)kb * kb_img_bytes;
+                    const uint32_t d_tmem = tmem + (uint32_t)(acc * kNOut);
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        if (!wait_bar(smem_u32(&ctl->ofull[o]), oph, ctl, status)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t a_hi = op_addr + (uint32_t)o * OP_BYTES;
+                        const uint32_t m_hi = img_addr + (uint32_t)kb * kb_img_bytes;
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint32_t koff = (uint32_t)ks * 32u;
-                        const uint32_t first = (kb | ks) != 0 ? 1u : 0u;
-                        tc_mma<T::kTf32>(d_tmem, sw128_desc(a_hi + koff), sw128_desc(m_hi + koff), IDESC, first);
-                        if constexpr (T::kSplit) {
-                            const uint32_t a_lo = a_hi + kKBlockBytes;
-                            const uint32_t m_lo = m_hi + (uint32_t)nkb * kb_img_bytes;
-                            tc_mma<false>(d_tmem, sw128_desc(a_lo + koff), sw128_desc(m_hi + koff), IDESC, 1u);
-                            tc_mma<false>(d_tmem, sw128_desc(a_hi + koff), sw128_desc(m_lo + koff), IDESC, 1u);
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint32_t koff = (uint32_t)ks * 32u;
+                            const uint32_t accum = (kb | ks) != 0 ? 1u : 0u;
+                            tc_mma_cg<PAIR, T::kTf32>(d_tmem, sw128_desc(a_hi + koff), sw128_desc(m_hi + koff),
+                                                      IDESC, accum);
+                            if constexpr (T::kSplit) {
+                                const uint32_t a_lo = a_hi + kKBlockBytes;
+                                const uint32_t m_lo = m_hi + (uint32_t)nkb * kb_img_bytes;
+                                tc_mma_cg<PAIR, false>(d_tmem, sw128_desc(a_lo + koff), sw128_desc(m_hi + koff),
+                                                       IDESC, 1u);
+                                tc_mma_cg<PAIR, false>(d_tmem, sw128_desc(a_hi + koff), sw128_desc(m_lo + koff),
+                                                       IDESC, 1u);
+                            }
                         }
+                        // operand buffer o is free again in both CTAs once these MMAs finish
+                        tc_commit_mc<PAIR>(smem_u32(&ctl->oempty[o]), (uint16_t)(PAIR == 2 ? 0x3 : 0x1));
+                        if (++o == T::kOp) { o = 0; oph ^= 1u; }
                     }
-                    tc_commit(smem_u32(&ctl->empty[stage]));      // frees the A stage when these MMAs finish
-                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    if (!ok) break;
+                    tc_commit_mc<PAIR>(smem_u32(&ctl->tfull[acc]), (uint16_t)(PAIR == 2 ? 0x3 : 0x1));
+                    acc ^= 1;
+                    if (acc == 0) acc_phase ^= 1u;
                 }
-                if (!ok) break;
-                tc_commit(smem_u32(&ctl->tfull[acc]));            // accumulator ready for the epilogue
-                acc ^= 1;
-                if (acc == 0) acc_phase ^= 1u;
+                // every MMA has finished before TMEM is freed
+                tc_commit_mc<PAIR>(smem_u32(&ctl->mdone), (uint16_t)0x1);
+                drain_bar(smem_u32(&ctl->mdone), 0, kWaitNs, status);
+            }
+            // the last "operand buffer free" signals have landed in this CTA
+            if (ok) {
+                for (int q = 0; q < T::kOp; ++q) {
+                    const int64_t uses = kblocks / T::kOp + (q < kblocks % T::kOp ? 1 : 0);
+                    if (uses > 0) drain_bar(smem_u32(&ctl->oempty[q]), (uint32_t)((uses - 1) & 1), kWaitNs, status);
+                }
             }
         }
         __syncwarp();
     } else if (warp >= kEpiWarps) {
-        // ---------------- converters: A rows -> operand layout
-        // Work items are (tile, K block) in order. The loads of the next PD items
-        // are in flight while the current item is rounded and stored.
-        const int cw = warp - kEpiWarps;                   // 0..7, 16 rows each
-        constexpr int LPR = T::kKbe / 4;                   // lanes per row (one float4 each)
-        constexpr int RPI = 32 / LPR;                      // rows per warp iteration
-        constexpr int ITERS = 16 / RPI;
-        constexpr int PD = T::kTf32 ? 4 : 2;               // K blocks of loads in flight
-        const int sub = lane % LPR, rsub = lane / LPR;
-        const int64_t my_tiles = (ntiles - group + ngroups - 1) / ngroups;
-        const int64_t total = (my_tiles > 0 ? my_tiles : 0) * nkb;
-        float4 v[PD][ITERS];
-        auto load_item = [&](int64_t item, float4 (&dst)[ITERS]) {
-            const int64_t t = group + (item / nkb) * ngroups;
-            const int kb = (int)(item % nkb);
-            const int64_t row0 = t * kTileRows;
-            const int col = kb * T::kKbe + sub * 4;
-#pragma unroll
-            for (int it = 0; it < ITERS; ++it) {
-                const int64_t gr = row0 + cw * 16 + it * RPI + rsub;
-                dst[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (gr < n && col < d) dst[it] = __ldg(reinterpret_cast<const float4*>(A + gr * lda + col));
-            }
-        };
-#pragma unroll
-        for (int p = 0; p < PD; ++p)
-            if (p < total) load_item(p, v[p]);
-        int stage = 0;
-        uint32_t phase = 0;
+        // ---------------- converters: staged FP32 boxes -> operand K blocks
+        const int ctid = (warp - kEpiWarps) * 32 + lane;      // 0..255
+        int s = 0, o = 0;
+        uint32_t sph = 0, oph = 0;
         bool ok = true;
-        for (int64_t i0 = 0; ok && i0 < total; i0 += PD) {
+        for (int64_t u = 0; ok && u < kblocks; ++u) {
+            if (!wait_bar(smem_u32(&ctl->oempty[o]), oph ^ 1u, ctl, status)) break;
+            uint8_t* ob = opbuf + o * OP_BYTES;
+            for (int b = 0; b < BOXES; ++b) {
+                if (!wait_bar(smem_u32(&ctl->sfull[s]), sph, ctl, status)) { ok = false; break; }
+                const uint8_t* sb = stg + s * kBoxBytes;
 #pragma unroll
-            for (int p = 0; p < PD; ++p) {
-                const int64_t item = i0 + p;
-                if (item >= total) break;
-                if (!wait_bar(smem_u32(&ctl->empty[stage]), phase ^ 1u, ctl, status)) { ok = false; break; }
-                uint8_t* dst = astage + stage * A_STAGE_BYTES;
-#pragma unroll
-                for (int it = 0; it < ITERS; ++it) {
-                    const uint32_t r = (uint32_t)(cw * 16 + it * RPI + rsub);
-                    const float4 x = v[p][it];
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t task = (uint32_t)(ctid + q * 256);       // 1024 = 128 rows x 8 chunks
+                    const uint32_t c = task & 7u, row = cvt_row(task >> 3);
+                    const float4 x = *reinterpret_cast<const float4*>(sb + sw128_offset(row, c * 16u));
                     if constexpr (T::kTf32) {
-                        uint4 w = make_uint4(f32_to_tf32(x.x), f32_to_tf32(x.y), f32_to_tf32(x.z), f32_to_tf32(x.w));
-                        *reinterpret_cast<uint4*>(dst + sw128_offset(r, (uint32_t)sub * 16u)) = w;
+                        *reinterpret_cast<uint4*>(ob + sw128_offset(row, c * 16u)) =
+                            make_uint4(f32_to_tf32(x.x), f32_to_tf32(x.y), f32_to_tf32(x.z), f32_to_tf32(x.w));
                     } else {
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(x.x), h1 = __float2bfloat16_rn(x.y);
-                        const __nv_bfloat16 h2 = __float2bfloat16_rn(x.z), h3 = __float2bfloat16_rn(x.w);
-                        uint2 w;
-                        w.x = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                        w.y = (uint32_t)__bfloat16_as_ushort(h2) | ((uint32_t)__bfloat16_as_ushort(h3) << 16);
-                        const uint32_t off = sw128_offset(r, (uint32_t)sub * 8u);
-                        *reinterpret_cast<uint2*>(dst + off) = w;
+                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y);
+                        const __nv_bfloat162 h23 = __floats2bfloat162_rn(x.z, x.w);
+                        const uint32_t off = sw128_offset(row, (uint32_t)b * 64u + c * 8u);
+                        *reinterpret_cast<uint2*>(ob + off) =
+                            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
                         if constexpr (T::kSplit) {
-                            const __nv_bfloat16 l0 = __float2bfloat16_rn(x.x - __bfloat162float(h0));
-                            const __nv_bfloat16 l1 = __float2bfloat16_rn(x.y - __bfloat162float(h1));
-                            const __nv_bfloat16 l2 = __float2bfloat16_rn(x.z - __bfloat162float(h2));
-                            const __nv_bfloat16 l3 = __float2bfloat16_rn(x.w - __bfloat162float(h3));
-                            uint2 u;
-                            u.x = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-                            u.y = (uint32_t)__bfloat16_as_ushort(l2) | ((uint32_t)__bfloat16_as_ushort(l3) << 16);
-                            *reinterpret_cast<uint2*>(dst + kKBlockBytes + off) = u;
+                            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                            const __nv_bfloat162 l01 = __floats2bfloat162_rn(x.x - f01.x, x.y - f01.y);
+                            const __nv_bfloat162 l23 = __floats2bfloat162_rn(x.z - f23.x, x.w - f23.y);
+                            *reinterpret_cast<uint2*>(ob + kKBlockBytes + off) =
+                                make_uint2(*reinterpret_cast<const uint32_t*>(&l01),
+                                           *reinterpret_cast<const uint32_t*>(&l23));
                         }
                     }
                 }
-                fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&ctl->full[stage]));
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
-                if (item + PD < total) load_item(item + PD, v[p]);
+                if (lane == 0) mbar_arrive(smem_u32(&ctl->sempty[s]));
+                if (++s == T::kStg) { s = 0; sph ^= 1u; }
             }
+            if (!ok) break;
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) arrive_leader<PAIR>(smem_u32(&ctl->ofull[o]), me);
+            if (++o == T::kOp) { o = 0; oph ^= 1u; }
         }
     } else {
-        // ---------------- epilogue: TMEM lane = tile row
+        // ---------------- epilogue: TMEM lane = row of this CTA's 128
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int64_t t = group; t < ntiles; t += ngroups) {
+        for (int64_t tt = 0; tt < my_tiles; ++tt) {
+            const int64_t t = group + tt * ngroups;
             if (!wait_bar(smem_u32(&ctl->tfull[acc]), acc_phase, ctl, status)) break;
             tc_fence_after();
             float sum = 0.f;
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * NT);
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kNOut);
 #pragma unroll
-            for (int c = 0; c < NT; c += 32) {
+            for (int c = 0; c < kNOut; c += 32) {
                 uint32_t r[32];
                 tmem_ld32(taddr + (uint32_t)c, r);
                 tmem_ld_wait();
@@ -277,14 +346,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const float* __restric
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&ctl->tempty[acc]));
-            const int64_t row = t * kTileRows + warp * 32 + lane;
-            if (row < n) {
-                if constexpr (T::kPair == 2)
-                    atomicAdd(theta + row, sum);
-                else
-                    theta[row] = sum;
-            }
+            if (lane == 0) arrive_leader<PAIR>(smem_u32(&ctl->tempty[acc]), me);
+            const int64_t row = t * kGroupRows + (int64_t)me * kTileRows + warp * 32 + lane;
+            if (row < n) theta[row] = sum;
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
         }
@@ -293,7 +357,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const float* __restric
     __syncthreads();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        tmem_dealloc(tmem, 2 * NT);
+        tmem_dealloc_cg<PAIR>(tmem, 2 * kNOut);
+    }
+    if (PAIR == 2) {
+        // neither CTA leaves while its peer may still signal its mbarriers (bounded)
+        if (threadIdx.x == 0) {
+            const uint32_t xb = smem_u32(&ctl->xbar);
+            mbar_arrive_cluster(xb);
+            mbar_arrive_cluster(mapa_shared(xb, me ^ 1u));
+            drain_bar(xb, 0, kExitWaitNs, status);
+        }
+        __syncthreads();
     }
 }
 
@@ -344,22 +418,47 @@ int run_final_tc(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t ld
     k_pack_image<F><<<64, 256, 0, st>>>(Mfull, (int)d, (int)k, nkb, image, half_bytes);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
-    if (T::kPair == 2) {
-        e = cudaMemsetAsync(theta, 0, sizeof(float) * (size_t)n, st);
-        if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
-    }
-    const int stage_bytes = kKBlockBytes * (T::kSplit ? 2 : 1);
-    const size_t smem = 1024 + (size_t)half_bytes + (size_t)T::kStages * stage_bytes + sizeof(TcSmemCtl) + 64;
+    CUtensorMap tmA;
+    if (!make_map_2d(&tmA, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, n, d, lda, 32, kTileRows))
+        return handle_fail(LEV_ECUDA, "cuTensorMapEncodeTiled failed for the final pass");
+    const int op_bytes = kKBlockBytes * (T::kSplit ? 2 : 1);
+    const size_t smem = 1024 + (size_t)half_bytes + (size_t)T::kOp * op_bytes + (size_t)T::kStg * kBoxBytes +
+                        sizeof(TcSmemCtl) + 64;
     e = cudaFuncSetAttribute(k_final_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
-    const int64_t ntiles = (n + kTileRows - 1) / kTileRows;
-    const int sms = handle_num_sms(h);
-    int64_t groups = T::kPair == 2 ? sms / 2 : sms;
+    const int64_t ntiles = (n + (int64_t)kTileRows * T::kPair - 1) / ((int64_t)kTileRows * T::kPair);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)T::kPair;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = T::kPair == 2 ? 1 : 0;
+    // persistent grid: as many CTAs (pairs) as can be resident at once, so that the static tile
+    // split never leaves a group waiting for a free SM (or SM pair) behind the others
+    int64_t groups = handle_num_sms(h);
+    if (T::kPair == 2) {
+        static int cached[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int clusters = dev < 64 ? cached[dev] : 0;
+        if (clusters == 0) {
+            cfg.gridDim = dim3((unsigned)(groups & ~1));
+            e = cudaOccupancyMaxActiveClusters(&clusters, k_final_tc<F>, &cfg);
+            if (e != cudaSuccess || clusters < 1)
+                return handle_fail(LEV_ECUDA, "no resident 2-CTA cluster for the final pass");
+            if (dev < 64) cached[dev] = clusters;
+        }
+        groups = clusters;
+    }
     if (groups > ntiles) groups = ntiles;
     if (groups < 1) groups = 1;
-    k_final_tc<F><<<(unsigned)(groups * T::kPair), kThreads, smem, st>>>(A, lda, n, (int)d, nkb, image, half_bytes,
-                                                                          theta, status);
-    e = cudaGetLastError();
+    cfg.gridDim = dim3((unsigned)(groups * T::kPair));
+    e = cudaLaunchKernelEx(&cfg, k_final_tc<F>, tmA, n, nkb, (const uint8_t*)image, half_bytes, theta, status);
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     return LEV_OK;
 }
@@ -372,6 +471,7 @@ int tc_final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t 
         return handle_fail(LEV_EINVAL, "tensor-core final pass needs A 16-byte aligned, lda and d multiples of 4");
     if (d > 256 || k > 256)
         return handle_fail(LEV_EINVAL, "tensor-core final pass needs d <= 256 and k <= 256");
+    if (n == 0) return LEV_OK;
     int32_t* status = handle_status(h);
     switch (prec) {
         case LEV_BF16: return run_final_tc<kBF16>(h, A, n, d, lda, Mfull, k, theta, status, st);
