@@ -3,15 +3,19 @@
 // in the epilogue, so the n x k product never reaches memory.
 //
 // One persistent CTA per SM (BF16) or per SM of a 2-CTA cluster (BF16X3, TF32).
-//   * warp 13 (producer): 2-D tensor TMA of the CTA's 128 rows of A, one box
-//     of 32 FP32 columns at a time (128-byte swizzle), into a staging ring;
-//   * warps 4..11 (converters): round each staged box to the operand type
-//     (BF16, BF16 hi + lo, or TF32) into a 128-byte swizzled K-major operand
-//     buffer holding one K block (128 bytes of every row);
-//   * warp 12 (MMA): allocates TMEM (two accumulators of 256 columns), loads
-//     the CTA's part of the packed operand image of Mfull^T once with bulk
-//     copies, and one thread issues tcgen05.mma (N = 256, 32 bytes of K per
-//     instruction);
+// Shared memory holds the CTA's part of the packed operand image of Mfull^T and
+// a ring of slots; a slot holds one K block of the CTA's 128 rows of A.
+//   * warp 13 (producer): 2-D tensor TMA of a slot's FP32 boxes (32 columns x
+//     128 rows each, 128-byte swizzle);
+//   * warps 4..11 (converters): round the slot IN PLACE to the operand type.
+//     With 64-column K blocks the two FP32 boxes of row r occupy exactly the
+//     bytes that the BF16 hi row r and lo row r take in the 128-byte swizzled
+//     K-major operand layout (same row, same swizzle phase), so a warp that owns
+//     whole rows reads them, syncs, and writes them back; TF32 rounds each
+//     16-byte chunk where it lies;
+//   * warp 12 (MMA): allocates TMEM (two accumulators of 256 columns), loads the
+//     image once with bulk copies, and one thread issues tcgen05.mma (N = 256,
+//     32 bytes of K per instruction); the MMA completion frees the slot;
 //   * warps 0..3 (epilogue): tcgen05.ld of the accumulator (TMEM lane = row),
 //     sum of squares over the 256 columns, one store per row.
 // BF16: M = 128 per CTA; the 128 KB image of Mfull^T (256 x 256 BF16) fits one
@@ -20,8 +24,8 @@
 // M = 256 MMA for the pair; each CTA holds its own 128 rows of A and half of
 // the image (128 columns of Mfull), and each CTA's TMEM receives its own rows
 // with all 256 columns. Nothing is loaded twice and no operand crosses between
-// the CTAs except through the MMA itself. The odd CTA reports "operand ready"
-// and "accumulator drained" to the even CTA's mbarriers; the MMA completion is
+// the CTAs except through the MMA itself. The odd CTA reports "slot converted"
+// and "accumulator drained" to the even CTA's mbarriers; MMA completions are
 // multicast to both. Every wait is bounded (2 s of %globaltimer); on expiry the
 // CTA records the failure in the status word and leaves its loops.
 #include <cuda.h>
@@ -40,39 +44,39 @@ using namespace tcx;
 enum Form { kBF16 = 0, kBF16X3 = 1, kTF32 = 2 };
 
 // kKbe: operand elements per K block (128 bytes of a row); kNt: rows of the Mfull^T image one CTA
-// holds; kPair: CTAs per MMA; kStg: staged boxes; kOp: operand buffers.
+// holds; kPair: CTAs per MMA; kSlots: slots in the ring.
 template <int F>
 struct FormTraits;
 template <>
 struct FormTraits<kBF16> {
     static constexpr bool kTf32 = false, kSplit = false;
-    static constexpr int kElem = 2, kKbe = 64, kNt = 256, kPair = 1, kStg = 4, kOp = 2;
+    static constexpr int kElem = 2, kKbe = 64, kNt = 256, kPair = 1, kSlots = 3;
 };
 template <>
 struct FormTraits<kBF16X3> {
     static constexpr bool kTf32 = false, kSplit = true;
-    static constexpr int kElem = 2, kKbe = 64, kNt = 128, kPair = 2, kStg = 2, kOp = 2;
+    static constexpr int kElem = 2, kKbe = 64, kNt = 128, kPair = 2, kSlots = 3;
 };
 template <>
 struct FormTraits<kTF32> {
     static constexpr bool kTf32 = true, kSplit = false;
-    static constexpr int kElem = 4, kKbe = 32, kNt = 128, kPair = 2, kStg = 4, kOp = 2;
+    static constexpr int kElem = 4, kKbe = 32, kNt = 128, kPair = 2, kSlots = 6;
 };
 
 constexpr int kTileRows = 128;                    // rows of A per CTA per tile (TMEM lanes)
-constexpr int kKBlockBytes = kTileRows * 128;     // one K block of the A operand: 16 KB
-constexpr int kBoxBytes = kTileRows * 128;        // one staged box: 128 rows x 32 FP32
+constexpr int kBoxBytes = kTileRows * 128;        // one FP32 box: 128 rows x 32 columns = one 16 KB K block
 constexpr int kNOut = 256;                        // MMA N: accumulator columns per row
 constexpr int kEpiWarps = 4, kCvtWarps = 8;
 constexpr int kMmaWarp = kEpiWarps + kCvtWarps;   // warp 12
 constexpr int kTmaWarp = kMmaWarp + 1;            // warp 13
 constexpr int kThreads = (kTmaWarp + 1) * 32;     // 448
+constexpr int kMaxSlots = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;       // 2 s
 constexpr uint64_t kExitWaitNs = 5000000000ull;   // 5 s: a peer that timed out reaches the exit within one kWaitNs
 constexpr int32_t kStatusTcTimeout = 2;
 
 struct TcSmemCtl {
-    uint64_t sfull[4], sempty[4], ofull[4], oempty[4], tfull[2], tempty[2], mfull, ipeer, mdone, xbar;
+    uint64_t sfull[kMaxSlots], cfull[kMaxSlots], sempty[kMaxSlots], tfull[2], tempty[2], mfull, ipeer, mdone, xbar;
     uint32_t tmem_base;
     int32_t abort;
 };
@@ -120,11 +124,53 @@ __device__ __forceinline__ void arrive_leader(uint32_t bar, uint32_t me) {
     }
 }
 
-// Row of the 128-row box handled by converter slot g: the two rows a half-warp stores
-// (slots 2j, 2j+1) sit 4 apart in their 8-row swizzle group, so their 64-byte halves of
-// the 128-byte swizzled rows fall in different banks.
-__device__ __forceinline__ uint32_t cvt_row(uint32_t g) {
-    return (g & ~7u) | ((g & 1u) << 2) | ((g >> 1) & 3u);
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b, float* ra, float* rb) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 f = __bfloat1622float2(h);
+    *ra = a - f.x;
+    *rb = b - f.y;
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Round one slot in place. Converter warp w owns rows 16w .. 16w+15 of the slot.
+template <int F>
+__device__ __forceinline__ void convert_slot(uint8_t* slot, int cw, int lane) {
+    using T = FormTraits<F>;
+    if constexpr (T::kTf32) {
+        // one box; each 16-byte chunk is rounded where it lies
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t task = (uint32_t)(q * 32 + lane);           // 16 rows x 8 chunks
+            const uint32_t row = (uint32_t)cw * 16u + (task >> 3), c = task & 7u;
+            uint4* p = reinterpret_cast<uint4*>(slot + sw128_offset(row, c * 16u));
+            const float4 x = *reinterpret_cast<const float4*>(p);
+            *p = make_uint4(f32_to_tf32(x.x), f32_to_tf32(x.y), f32_to_tf32(x.z), f32_to_tf32(x.w));
+        }
+    } else {
+        // two boxes (columns 0..31 and 32..63) -> BF16 hi K block in box 0's bytes, lo in box 1's
+        float4 x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t task = (uint32_t)(q * 32 + lane);           // 16 rows x 16 chunks
+            const uint32_t row = (uint32_t)cw * 16u + (task >> 4), ch = task & 15u;
+            x[q] = *reinterpret_cast<const float4*>(slot + (ch >> 3) * kBoxBytes + sw128_offset(row, (ch & 7u) * 16u));
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t task = (uint32_t)(q * 32 + lane);
+            const uint32_t row = (uint32_t)cw * 16u + (task >> 4), ch = task & 15u;
+            const uint32_t off = sw128_offset(row, ch * 8u);
+            float r0, r1, r2, r3;
+            const uint2 hi = make_uint2(pack_bf16x2(x[q].x, x[q].y, &r0, &r1), pack_bf16x2(x[q].z, x[q].w, &r2, &r3));
+            *reinterpret_cast<uint2*>(slot + off) = hi;
+            if constexpr (T::kSplit) {
+                float u0, u1;
+                const uint2 lo = make_uint2(pack_bf16x2(r0, r1, &u0, &u1), pack_bf16x2(r2, r3, &u0, &u1));
+                *reinterpret_cast<uint2*>(slot + kBoxBytes + off) = lo;
+            }
+        }
+    }
 }
 
 template <int F>
@@ -134,17 +180,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
                                                           int32_t* status) {
     using T = FormTraits<F>;
     constexpr int PAIR = T::kPair;
-    constexpr int BOXES = T::kKbe / 32;                       // staged boxes per K block
-    constexpr int OP_BYTES = kKBlockBytes * (T::kSplit ? 2 : 1);
+    constexpr int NS = T::kSlots;
+    constexpr int BOXES = T::kKbe / 32;                       // FP32 boxes per K block
+    constexpr int SLOT_BYTES = BOXES * kBoxBytes;
     constexpr uint32_t IDESC = make_idesc(T::kTf32, kTileRows * PAIR, kNOut);
     static_assert(T::kNt * PAIR == kNOut, "the MMA covers 256 columns of Mfull");
+    static_assert(NS <= kMaxSlots, "slot barriers");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     uint8_t* img = smem_raw + pad;                            // image_bytes (multiple of 1024)
-    uint8_t* opbuf = img + image_bytes;                       // kOp x OP_BYTES
-    uint8_t* stg = opbuf + T::kOp * OP_BYTES;                 // kStg x kBoxBytes
-    TcSmemCtl* ctl = reinterpret_cast<TcSmemCtl*>(stg + T::kStg * kBoxBytes);
+    uint8_t* slots = img + image_bytes;                       // NS x SLOT_BYTES
+    TcSmemCtl* ctl = reinterpret_cast<TcSmemCtl*>(slots + NS * SLOT_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t me = PAIR == 2 ? cluster_ctarank() : 0u;
@@ -153,17 +200,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
     constexpr int64_t kGroupRows = (int64_t)kTileRows * PAIR;
     const int64_t ntiles = (n + kGroupRows - 1) / kGroupRows;
     const int64_t my_tiles = ntiles > group ? (ntiles - group + ngroups - 1) / ngroups : 0;
-    const int64_t nbox = (int64_t)nkb * BOXES;
-    const int64_t kblocks = my_tiles * nkb;                   // operand-buffer uses
+    const int64_t uses = my_tiles * nkb;                      // slot fills (one K block each)
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < T::kStg; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&ctl->sfull[s]), 1);
-            mbar_init(smem_u32(&ctl->sempty[s]), kCvtWarps);
-        }
-        for (int o = 0; o < T::kOp; ++o) {
-            mbar_init(smem_u32(&ctl->ofull[o]), kCvtWarps * PAIR);
-            mbar_init(smem_u32(&ctl->oempty[o]), 1);
+            mbar_init(smem_u32(&ctl->cfull[s]), kCvtWarps * PAIR);
+            mbar_init(smem_u32(&ctl->sempty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&ctl->tfull[a]), 1);
@@ -188,25 +231,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
     const uint32_t tmem = ctl->tmem_base;
 
     if (warp == kTmaWarp) {
-        // ---------------- producer: this CTA's 128 rows, one 32-column box per stage
+        // ---------------- producer: this CTA's 128 rows of one K block per slot
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0;
             int64_t issued = 0;
-            for (int64_t it = 0; it < my_tiles * nbox; ++it) {
+            for (int64_t u = 0; u < uses; ++u) {
                 if (!wait_bar(smem_u32(&ctl->sempty[s]), ph ^ 1u, ctl, status)) break;
-                const int64_t t = group + (it / nbox) * ngroups;
-                const int32_t x = (int32_t)(it % nbox) * 32;
+                const int64_t t = group + (u / nkb) * ngroups;
+                const int32_t x = (int32_t)(u % nkb) * T::kKbe;
                 const int32_t y = (int32_t)(t * kGroupRows + (int64_t)me * kTileRows);
                 const uint32_t bar = smem_u32(&ctl->sfull[s]);
-                mbar_arrive_expect_tx(bar, (uint32_t)kBoxBytes);
-                tma_load_2d(smem_u32(stg + s * kBoxBytes), &tmA, x, y, bar);
+                mbar_arrive_expect_tx(bar, (uint32_t)SLOT_BYTES);
+                const uint32_t dst = smem_u32(slots + s * SLOT_BYTES);
+#pragma unroll
+                for (int b = 0; b < BOXES; ++b) tma_load_2d(dst + b * kBoxBytes, &tmA, x + b * 32, y, bar);
                 ++issued;
-                if (++s == T::kStg) { s = 0; ph ^= 1u; }
+                if (++s == NS) { s = 0; ph ^= 1u; }
             }
-            // no copy may still be landing in this CTA's shared memory when it exits
-            for (int64_t j = issued > T::kStg ? issued - T::kStg : 0; j < issued; ++j)
-                drain_bar(smem_u32(&ctl->sfull[j % T::kStg]), (uint32_t)((j / T::kStg) & 1), kWaitNs, status);
+            // no copy may still be landing in this CTA's shared memory when it exits, and the
+            // last "slot free" signals of the MMA (multicast in a pair) have landed here
+            for (int64_t j = issued > NS ? issued - NS : 0; j < issued; ++j)
+                drain_bar(smem_u32(&ctl->sfull[j % NS]), (uint32_t)((j / NS) & 1), kWaitNs, status);
+            if (issued == uses && !*(volatile int32_t*)&ctl->abort) {
+                for (int q = 0; q < NS; ++q) {
+                    const int64_t k_uses = uses / NS + (q < uses % NS ? 1 : 0);
+                    if (k_uses > 0) drain_bar(smem_u32(&ctl->sempty[q]), (uint32_t)((k_uses - 1) & 1), kWaitNs, status);
+                }
+            }
         }
         __syncwarp();
     } else if (warp == kMmaWarp) {
@@ -224,21 +276,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
                 if (ok) mbar_arrive_cluster(mapa_shared(smem_u32(&ctl->ipeer), 0));
             } else {
                 if (PAIR == 2) ok = ok && wait_bar(smem_u32(&ctl->ipeer), 0, ctl, status);
-                int o = 0;
-                uint32_t oph = 0;
+                int s = 0;
+                uint32_t sph = 0;
                 int acc = 0;
                 uint32_t acc_phase = 0;
                 const uint32_t img_addr = smem_u32(img);
-                const uint32_t op_addr = smem_u32(opbuf);
+                const uint32_t slot_addr = smem_u32(slots);
                 const uint32_t kb_img_bytes = (uint32_t)T::kNt * 128u;
+                const uint16_t both = (uint16_t)(PAIR == 2 ? 0x3 : 0x1);
                 for (int64_t tt = 0; ok && tt < my_tiles; ++tt) {
                     if (!wait_bar(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, ctl, status)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + (uint32_t)(acc * kNOut);
                     for (int kb = 0; kb < nkb; ++kb) {
-                        if (!wait_bar(smem_u32(&ctl->ofull[o]), oph, ctl, status)) { ok = false; break; }
+                        if (!wait_bar(smem_u32(&ctl->cfull[s]), sph, ctl, status)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t a_hi = op_addr + (uint32_t)o * OP_BYTES;
+                        const uint32_t a_hi = slot_addr + (uint32_t)s * SLOT_BYTES;
                         const uint32_t m_hi = img_addr + (uint32_t)kb * kb_img_bytes;
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
@@ -247,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
                             tc_mma_cg<PAIR, T::kTf32>(d_tmem, sw128_desc(a_hi + koff), sw128_desc(m_hi + koff),
                                                       IDESC, accum);
                             if constexpr (T::kSplit) {
-                                const uint32_t a_lo = a_hi + kKBlockBytes;
+                                const uint32_t a_lo = a_hi + kBoxBytes;
                                 const uint32_t m_lo = m_hi + (uint32_t)nkb * kb_img_bytes;
                                 tc_mma_cg<PAIR, false>(d_tmem, sw128_desc(a_lo + koff), sw128_desc(m_hi + koff),
                                                        IDESC, 1u);
@@ -255,12 +308,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
                                                        IDESC, 1u);
                             }
                         }
-                        // operand buffer o is free again in both CTAs once these MMAs finish
-                        tc_commit_mc<PAIR>(smem_u32(&ctl->oempty[o]), (uint16_t)(PAIR == 2 ? 0x3 : 0x1));
-                        if (++o == T::kOp) { o = 0; oph ^= 1u; }
+                        // slot s is free again in both CTAs once these MMAs finish
+                        tc_commit_mc<PAIR>(smem_u32(&ctl->sempty[s]), both);
+                        if (++s == NS) { s = 0; sph ^= 1u; }
                     }
                     if (!ok) break;
-                    tc_commit_mc<PAIR>(smem_u32(&ctl->tfull[acc]), (uint16_t)(PAIR == 2 ? 0x3 : 0x1));
+                    tc_commit_mc<PAIR>(smem_u32(&ctl->tfull[acc]), both);
                     acc ^= 1;
                     if (acc == 0) acc_phase ^= 1u;
                 }
@@ -268,60 +321,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
                 tc_commit_mc<PAIR>(smem_u32(&ctl->mdone), (uint16_t)0x1);
                 drain_bar(smem_u32(&ctl->mdone), 0, kWaitNs, status);
             }
-            // the last "operand buffer free" signals have landed in this CTA
-            if (ok) {
-                for (int q = 0; q < T::kOp; ++q) {
-                    const int64_t uses = kblocks / T::kOp + (q < kblocks % T::kOp ? 1 : 0);
-                    if (uses > 0) drain_bar(smem_u32(&ctl->oempty[q]), (uint32_t)((uses - 1) & 1), kWaitNs, status);
-                }
-            }
         }
         __syncwarp();
     } else if (warp >= kEpiWarps) {
-        // ---------------- converters: staged FP32 boxes -> operand K blocks
-        const int ctid = (warp - kEpiWarps) * 32 + lane;      // 0..255
-        int s = 0, o = 0;
-        uint32_t sph = 0, oph = 0;
-        bool ok = true;
-        for (int64_t u = 0; ok && u < kblocks; ++u) {
-            if (!wait_bar(smem_u32(&ctl->oempty[o]), oph ^ 1u, ctl, status)) break;
-            uint8_t* ob = opbuf + o * OP_BYTES;
-            for (int b = 0; b < BOXES; ++b) {
-                if (!wait_bar(smem_u32(&ctl->sfull[s]), sph, ctl, status)) { ok = false; break; }
-                const uint8_t* sb = stg + s * kBoxBytes;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t task = (uint32_t)(ctid + q * 256);       // 1024 = 128 rows x 8 chunks
-                    const uint32_t c = task & 7u, row = cvt_row(task >> 3);
-                    const float4 x = *reinterpret_cast<const float4*>(sb + sw128_offset(row, c * 16u));
-                    if constexpr (T::kTf32) {
-                        *reinterpret_cast<uint4*>(ob + sw128_offset(row, c * 16u)) =
-                            make_uint4(f32_to_tf32(x.x), f32_to_tf32(x.y), f32_to_tf32(x.z), f32_to_tf32(x.w));
-                    } else {
-                        const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y);
-                        const __nv_bfloat162 h23 = __floats2bfloat162_rn(x.z, x.w);
-                        const uint32_t off = sw128_offset(row, (uint32_t)b * 64u + c * 8u);
-                        *reinterpret_cast<uint2*>(ob + off) =
-                            make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
-                        if constexpr (T::kSplit) {
-                            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-                            const __nv_bfloat162 l01 = __floats2bfloat162_rn(x.x - f01.x, x.y - f01.y);
-                            const __nv_bfloat162 l23 = __floats2bfloat162_rn(x.z - f23.x, x.w - f23.y);
-                            *reinterpret_cast<uint2*>(ob + kKBlockBytes + off) =
-                                make_uint2(*reinterpret_cast<const uint32_t*>(&l01),
-                                           *reinterpret_cast<const uint32_t*>(&l23));
-                        }
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&ctl->sempty[s]));
-                if (++s == T::kStg) { s = 0; sph ^= 1u; }
-            }
-            if (!ok) break;
+        // ---------------- converters: each slot rounded in place, rows owned by warps
+        const int cw = warp - kEpiWarps;                      // 0..7
+        int s = 0;
+        uint32_t sph = 0;
+        for (int64_t u = 0; u < uses; ++u) {
+            if (!wait_bar(smem_u32(&ctl->sfull[s]), sph, ctl, status)) break;
+            convert_slot<F>(slots + s * SLOT_BYTES, cw, lane);
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) arrive_leader<PAIR>(smem_u32(&ctl->ofull[o]), me);
-            if (++o == T::kOp) { o = 0; oph ^= 1u; }
+            if (lane == 0) arrive_leader<PAIR>(smem_u32(&ctl->cfull[s]), me);
+            if (++s == NS) { s = 0; sph ^= 1u; }
         }
     } else {
         // ---------------- epilogue: TMEM lane = row of this CTA's 128
@@ -421,8 +434,7 @@ int run_final_tc(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t ld
     CUtensorMap tmA;
     if (!make_map_2d(&tmA, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, n, d, lda, 32, kTileRows))
         return handle_fail(LEV_ECUDA, "cuTensorMapEncodeTiled failed for the final pass");
-    const int op_bytes = kKBlockBytes * (T::kSplit ? 2 : 1);
-    const size_t smem = 1024 + (size_t)half_bytes + (size_t)T::kOp * op_bytes + (size_t)T::kStg * kBoxBytes +
+    const size_t smem = 1024 + (size_t)half_bytes + (size_t)T::kSlots * (T::kKbe / 32) * kBoxBytes +
                         sizeof(TcSmemCtl) + 64;
     e = cudaFuncSetAttribute(k_final_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
