@@ -302,13 +302,15 @@ def main():
             roof = {"kernel": f"k_final_tc<{f}>", "bound": "hbm", "achieved": final_bytes / t / 1e9,
                     "peak": hbm_peak, "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})",
                     "algorithmic": final_bytes}
-            # the tensor pipe: executed MMA flops (Mfull carries d - r zero rows) per form
+            # the tensor pipe: executed MMA flops per form (Mfull is padded to 256 x 256; the split
+            # form runs three products hi*hi + lo*hi + hi*lo)
             mult = {"bf16": 1, "tf32": 1, "bf16x3": 3}[f]
             peak_tc = float(peaks.get("bf16_tflops", 1900.0)) * (0.5 if f == "tf32" else 1.0)
-            exec_flops = mult * 2.0 * n * d * cfg["k"]
+            exec_flops = mult * 2.0 * n * 256 * 256
             roof["tensor"] = {"achieved": exec_flops / t / 1e12, "peak": peak_tc, "unit": "TFLOP/s",
-                              "frac": exec_flops / t / 1e12 / peak_tc,
-                              "peak_source": "bf16_tflops (measured)" + (" x 1/2 (TF32 nominal ratio)" if f == "tf32" else "")}
+                              "frac": exec_flops / t / 1e12 / peak_tc, "executed_flops": exec_flops,
+                              "peak_source": "bf16_tflops burst (measured)"
+                              + (" x 1/2 (TF32 nominal ratio)" if f == "tf32" else "")}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = None
         roof["ms"] = final_ms[f]
@@ -316,8 +318,8 @@ def main():
 
     rooflines = {"final": final_roof(args.final_prec)}
     sk_bytes = n * d * 4 + cfg["s"] * d * 4
-    rooflines["sketch"] = {"kernels": "k_countsketch_dense_v4 + k_gauss_tc (or k_sgemm_splitk) + permutation",
-                           "bound": "mixed", "ms": stages["sketch"],
+    rooflines["sketch"] = {"kernels": "k_countsketch_dense_v4 + k_gauss_tc + permutation", "bound": "mixed",
+                           "ms": stages["sketch"],
                            "countsketch_bytes": sk_bytes, "gemm_flops": 2.0 * cfg["m"] * cfg["s"] * d}
     qf = qr_flops(cfg["m"], d, r)
     fp64_peak = 1.19   # TFLOP/s, FP64 FMA rate measured on this GB300 (dependent-chain probe)
@@ -326,176 +328,9 @@ def main():
                          "achieved_tflops": qf / (stages["rrqr"] * 1e-3) / 1e12, "fp64_peak_tflops": fp64_peak,
                          "note": f"{r} sequential pivot steps; one L2 round trip per step"}
     dominant = max(stages, key=stages.get)
-    # the final pass is the largest single kernel (tied with the pivoted Cholesky in the launch
-    # list) and the one the metric's HBM GB/s refers to
+    # the roofline line is the final pass: the largest kernel that moves the workload's bytes
+    # (the pivoted Cholesky is latency-bound on an m x d problem independent of n)
     roof = rooflines["final"]
-
-    out = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "n": cfg["n"], "d": cfg["d"], "s": cfg["s"], "m": cfg["m"],
-                      "k": cfg["k"], "parallelism": "replicas"},
-           "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cpu_threads(), "kind": "oracle",
-                            "sample": desc},
-           "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(out), flush=True)
-
-
-def qr_flops(m, d, r):
-    """FP64 flops of the pivoted Householder QR that stops at rank r (norm recompute included)."""
-    f = 0.0
-    for j in range(r):
-        rows, cols = m - j, d - j - 1
-        f += 6.0 * rows * cols + 2.0 * rows
-    return f
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--sketch-prec", default="bf16x3")
-    ap.add_argument("--final-prec", default="bf16x3")
-    ap.add_argument("--forms", default="fp32,tf32,bf16,bf16x3",
-                    help="whole-path forms timed and checked: fp32 = FP32 SIMT sketch and final pass; "
-                         "tf32 / bf16 / bf16x3 = split-BF16 tensor-core sketch with that final-pass form")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-backward", action="store_true")
-    ap.add_argument("--no-csr", action="store_true", help="skip the CSR 8e6 x 1024 measurement")
-    ap.add_argument("--csr-large", action="store_true", help="also measure the CSR 8e7 x 1024 (~1e9 nnz) workload")
-    args = ap.parse_args()
-    args.warmup = max(3, args.warmup)
-    cfg = W.CONFIGS[WORKLOAD]
-    if args.impl == "reference":
-        run_reference(args, cfg)
-        return
-
-    import torch
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    import paper_2105_11004_gb300 as L
-
-    n, d = cfg["n"], cfg["d"]
-    A_np = make_input(cfg)
-    A_host = torch.from_numpy(A_np).pin_memory()
-    A = A_host.cuda()
-    h = L.Handle(local)
-
-    def params(final_prec):
-        return L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
-                             sketch_prec=args.sketch_prec, final_prec=final_prec)
-
-    p = params(args.final_prec)
-    theta = torch.empty(n, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    kernels_per_step = 11 if args.final_prec == "fp32" else 12
-
-    rank_found = L.lev_estimate_dense(h, A, p, theta)          # also generates and caches G
-    for _ in range(args.warmup):
-        L.lev_estimate_dense(h, A, p, theta, want_rank=False)
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    time.sleep(0.3)
-    barrier(world)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_wall0 = time.time()
-    e0.record(stream)
-    for _ in range(args.steps):
-        L.lev_estimate_dense(h, A, p, theta, want_rank=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_wall1 = time.time()
-    barrier(world)
-    ms = allmax(world, e0.elapsed_time(e1) / args.steps)
-    clocks = sampler.summary(t_wall0, t_wall1)
-    sampler.stop()
-
-    def time_steps(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
-    reps = max(3, min(args.steps, 20))
-    # every final-pass form: whole-step time and theta~ for the accuracy check
-    forms = {}
-    form_theta = {}
-    for f in [x for x in args.forms.split(",") if x]:
-        pf = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
-                           sketch_prec="fp32" if f == "fp32" else "bf16x3", final_prec=f)
-        tf = torch.empty(n, dtype=torch.float32, device="cuda")
-        L.lev_estimate_dense(h, A, pf, tf)
-        form_theta[f] = tf.cpu().numpy()
-        t_ms = time_steps(lambda: L.lev_estimate_dense(h, A, pf, tf, want_rank=False), reps)
-        forms[f] = {"ms_per_step": t_ms, "rows_per_s": n / (t_ms * 1e-3),
-                    "sketch_prec": "fp32" if f == "fp32" else "bf16x3", "final_prec": f}
-
-    # per-stage times (same inputs, same stream) for the rooflines
-    At = torch.empty((cfg["m"], d), dtype=torch.float32, device="cuda")
-    perm = torch.empty(d, dtype=torch.int32, device="cuda")
-    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
-    Mf = torch.empty((d, cfg["k"]), dtype=torch.float32, device="cuda")
-    L.lev_sketch_dense(h, A, p, At)
-    r = L.lev_rrqr(h, At, cfg["tau"], perm, R)
-    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
-    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
-    stages = {
-        "sketch": time_steps(lambda: L.lev_sketch_dense(h, A, p, At), reps),
-        "rrqr": time_steps(lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R), reps),
-        "omega": time_steps(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf), reps),
-    }
-    final_ms = {f: time_steps(lambda f=f: L.lev_final_dense(h, A, Mf, f, theta), reps)
-                for f in sorted(set(list(forms) + [args.final_prec]))}
-    stages["final"] = final_ms[args.final_prec]
-
-    peaks, peak_src = load_peaks()
-    hbm_peak = float(peaks["hbm_gbs"])
-    fp32_peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    final_bytes = n * d * 4 + n * 4 + d * cfg["k"] * 4
-    final_flops = 2.0 * n * r * cfg["k"]
-
-    def final_roof(f):
-        t = final_ms[f] * 1e-3
-        if f == "fp32":
-            roof = {"kernel": "k_final_dense_fp32", "bound": "alu", "achieved": final_flops / t / 1e12,
-                    "peak": fp32_peak, "unit": "TFLOP/s",
-                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock",
-                    "algorithmic": final_flops}
-        else:
-            roof = {"kernel": f"k_final_tc<{f}>", "bound": "hbm", "achieved": final_bytes / t / 1e9,
-                    "peak": hbm_peak, "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})",
-                    "algorithmic": final_bytes}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = None
-        roof["ms"] = final_ms[f]
-        return roof
-
-    rooflines = {"final": final_roof(args.final_prec)}
-    sk_bytes = n * d * 4 + cfg["s"] * d * 4
-    rooflines["sketch"] = {"kernels": "k_countsketch_dense_v4 + k_sgemm_splitk + permutation", "bound": "mixed",
-                           "ms": stages["sketch"],
-                           "countsketch_bytes": sk_bytes, "gemm_flops": 2.0 * cfg["m"] * cfg["s"] * d}
-    qf = qr_flops(cfg["m"], d, r)
-    rooflines["rrqr"] = {"kernel": "k_pivoted_qr", "bound": "latency", "ms": stages["rrqr"], "fp64_flops": qf,
-                         "achieved_tflops": qf / (stages["rrqr"] * 1e-3) / 1e12,
-                         "note": f"{r} sequential steps, one grid barrier each"}
-    dominant = max(stages, key=stages.get)
-    roof = rooflines["final"] if dominant == "final" else dict(rooflines[dominant])
-    if dominant != "final":
-        roof.setdefault("frac", None)
-        roof.setdefault("achieved", None)
-        roof.setdefault("peak", None)
-        roof.setdefault("unit", None)
-        roof.setdefault("traffic", None)
 
     out = {"metric": METRIC, "value": n * world / (ms * 1e-3), "unit": "rows/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

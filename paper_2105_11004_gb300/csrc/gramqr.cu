@@ -16,11 +16,11 @@
 //     CTAs keep a replicated Schur diagonal and take the same pivot p_j (largest
 //     diagonal, ties to the lowest column) and the same rank decision
 //     S_pp <= tau^2 S_00 without exchanging them; the owner of each pivot
-//     publishes its row of R as soon as its column is up to date, and the
-//     others wait for that row only (one flag, no grid barrier per step).
+//     publishes its updated column, unscaled, as soon as it is up to date, and
+//     the others wait for that row only (no flag, no grid barrier per step).
 //
 // The Gram route resolves |R_jj| / |R_00| down to about sqrt(m u) ~ 1e-7; the
-// caller uses the Householder kernel when tau is below 1e-6 or d > 512.
+// caller uses the Householder kernel when tau is below 1e-6 or d > 1024.
 #include <climits>
 
 #include "lev_common.cuh"
@@ -110,13 +110,20 @@ __device__ __forceinline__ uint64_t gtimer() {
 // CTA per SM). CTA c owns the columns l = c mod gridDim and keeps them in shared
 // memory. Every CTA keeps a replicated copy of the Schur diagonal, updated with
 // the same FMAs as the owners' columns, so all CTAs take the same pivots and the
-// same rank decisions without exchanging them. Row j of R (the scaled pivot
-// column, in original column order) is written to global memory by the owner
-// of the pivot as soon as its column is up to date; every other CTA reads each
-// entry once it no longer holds the "unwritten" pattern (bounded spin). Rows of
-// R are written once, so a slow reader never races a fast writer.
-// Rows of R start as a signalling-NaN pattern that arithmetic never produces; an
-// entry is final once it holds anything else (8-byte stores are single-copy atomic).
+// same rank decisions without exchanging them.
+//
+// Step j with pivot p (Schur diagonal s_pp): row j of R is u / sqrt(s_pp), u the
+// pivot column of the Schur complement. The owner of p publishes u UNSCALED in
+// row j of U as soon as its column is up to date, so no square root or division
+// sits between its update and its stores; every CTA has already computed
+// 1 / sqrt(s_pp) from its own copy of the diagonal while it waited. A reader
+// takes each entry of the row once it no longer holds the "unwritten" pattern
+// (bounded spin); rows of U are written once, so a slow reader never races a
+// fast writer. Thread t handles the indices i = t, t + 256, ... in every phase
+// (read, scale, diagonal update, local argmax, column updates), which leaves two
+// block barriers per step: one for the argmax, one after the column updates.
+// The owner writes row j of R (scaled, original column order) to Rorig off the
+// critical path; nothing reads Rorig before the kernel ends.
 constexpr unsigned long long kUnwritten = 0xFFF40000DEADBEEFull;
 __device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -133,22 +140,27 @@ __global__ void k_fill_unwritten(unsigned long long* R, int64_t count) {
         R[e] = kUnwritten;
 }
 
+// The Schur diagonal is compared through its bit pattern (int64 order = double order
+// for non-negative values; any positive value beats every non-positive one).
+__device__ __forceinline__ bool positive_finite(long long b) { return b > 0 && b < 0x7FF0000000000000LL; }
+
 __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict__ Gm, int d, int m, double tau,
                                                        const int32_t* __restrict__ forced, int forced_rank,
-                                                       double* __restrict__ Rorig, int32_t* __restrict__ piv,
-                                                       int64_t* __restrict__ rank_out, int32_t* status) {
+                                                       double* __restrict__ U, double* __restrict__ Rorig,
+                                                       int32_t* __restrict__ piv, int64_t* __restrict__ rank_out,
+                                                       int32_t* status) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int G = gridDim.x, me = blockIdx.x;
     const int ncl = (d - me + G - 1) / G;                        // columns me, me + G, ...
     double* S = reinterpret_cast<double*>(smem);                  // ncl x d (own columns)
-    double* rbufs = S + (size_t)ncl * d;                          // 2 x d: row j of R in rbufs[j & 1]
-    double* diag = rbufs + 2 * (size_t)d;                         // d: replicated Schur diagonal
+    double* ubuf = S + (size_t)ncl * d;                           // d: unscaled row (owner's own entries)
+    double* rbuf = ubuf + d;                                      // d: row j of R
+    double* diag = rbuf + d;                                      // d: replicated Schur diagonal
     int* active = reinterpret_cast<int*>(diag + d);               // d
     __shared__ long long red_b[8];
     __shared__ int red_i[8];
-    __shared__ int s_next, s_stop;
     __shared__ volatile int s_abort;
-    __shared__ double s_rjj;
+    __shared__ double s_inv, s_rjj;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int lc = 0; lc < ncl; ++lc) {
         const double* src = Gm + (int64_t)(lc * G + me) * d;     // column = row (symmetric)
@@ -160,9 +172,11 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     }
     if (tid == 0) s_abort = 0;
     __syncthreads();
+    // largest active diagonal entry, ties to the lowest index; one barrier, then every
+    // thread reduces the eight warp results itself
     auto pick = [&]() -> int {
         long long bb = LLONG_MIN;
-        int bi = 0x7fffffff;
+        int bi = INT_MAX;
         for (int i = tid; i < d; i += 256)
             if (active[i]) {
                 const long long v = __double_as_longlong(diag[i]);
@@ -176,67 +190,64 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         }
         if (lane == 0) { red_b[wid] = bb; red_i[wid] = bi; }
         __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < 8; ++w)
-                if (red_b[w] > bb || (red_b[w] == bb && red_i[w] < bi)) { bb = red_b[w]; bi = red_i[w]; }
-            s_next = bi;
-        }
-        __syncthreads();
-        return s_next;
+        bb = red_b[0];
+        bi = red_i[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w)
+            if (red_b[w] > bb || (red_b[w] == bb && red_i[w] < bi)) { bb = red_b[w]; bi = red_i[w]; }
+        return bi;
     };
-    // rank test on the pivot's squared trailing norm (thread 0; identical in every CTA)
-    double s00 = 0.0;
-    auto test = [&](int j, int p) -> bool {
-        if (tid == 0) {
-            const double bv = diag[p];
-            if (j == 0) s00 = bv;
-            int stop = !(bv > 0.0);
-            if (!forced && bv <= tau * tau * s00) stop = 1;
-            s_stop = stop;
-            if (!stop) s_rjj = sqrt(bv);
-        }
-        __syncthreads();
-        return s_stop == 0;
-    };
-    // owner of pivot p at step j: row j of R from its up-to-date column, into the
-    // local copy and (one 8-byte store per entry) into the global row that the
-    // other CTAs are spinning on
-    auto publish = [&](int j, int p) {
-        const int lc = p / G;
-        const double rjj = s_rjj, inv = 1.0 / rjj;
-        double* row = Rorig + (int64_t)j * d;
-        double* rbuf = rbufs + (size_t)(j & 1) * d;          // step j's buffer; step j-1's stays intact
-        for (int i = tid; i < d; i += 256)
-            if (active[i]) {
-                const double v = (i == p) ? rjj : S[(size_t)lc * d + i] * inv;
-                rbuf[i] = v;
-                st_relaxed_gpu_f64(row + i, v);
-            }
+    // rank test on the pivot's squared trailing norm: stop at a non-positive pivot, or
+    // (unforced) at s_pp <= tau^2 s_00; evaluated identically by every thread
+    long long thr = 0;
+    auto stops = [&](int j, int p) -> bool {
+        const double bv = diag[p];
+        const long long b = __double_as_longlong(bv);
+        if (!positive_finite(b)) return true;
+        if (j == 0) thr = __double_as_longlong(tau * tau * bv);
+        return !forced && b <= thr;
     };
     const int steps = forced ? min(forced_rank, min(m, d)) : min(m, d);
     int j = 0;
-    int p = forced ? (steps > 0 ? forced[0] : -1) : pick();
-    bool have = false;                                            // row j of R already known (published here)
-    if (p >= 0 && p < d && steps > 0 && test(0, p)) {
-        if (p % G == me) publish(0, p);
-        __syncthreads();
-        have = true;
+    int p = -1;
+    bool go = false;
+    if (steps > 0) {
+        p = forced ? forced[0] : pick();
+        go = p >= 0 && p < d && !stops(0, p);
     }
-    for (; have && j < steps; ++j) {
-        // 1. row j of R: the owner already holds it; the others read each entry from
-        //    global memory once it no longer holds the sentinel (bounded wait)
-        double* rbuf = rbufs + (size_t)(j & 1) * d;
-        const int own = p % G;
-        if (own != me) {
-            const unsigned long long* row = reinterpret_cast<const unsigned long long*>(Rorig + (int64_t)j * d);
-            for (int i = tid; i < d; i += 256) {
-                double v = 0.0;
-                if (active[i] && i != p) {
-                    unsigned long long bits = ld_relaxed_gpu_u64(row + i);
+    if (go) {
+        if (p % G == me) {
+            const double* col = S + (size_t)(p / G) * d;
+            for (int i = tid; i < d; i += 256)
+                if (i != p) {
+                    ubuf[i] = col[i];
+                    st_relaxed_gpu_f64(U + i, col[i]);
+                }
+        }
+        if (tid == 0) {
+            s_inv = rsqrt(diag[p]);
+            s_rjj = sqrt(diag[p]);
+        }
+        __syncthreads();
+    }
+    for (; go && j < steps; ++j) {
+        const double inv = s_inv;
+        const bool owner = (p % G) == me;
+        // 1. row j of R: unscaled entries (own copy or the published row, bounded spin), scaled,
+        //    and the replicated diagonal updated, index by index
+        const unsigned long long* urow = reinterpret_cast<const unsigned long long*>(U + (int64_t)j * d);
+        for (int i = tid; i < d; i += 256) {
+            double r = 0.0;
+            if (active[i] && i != p) {
+                double u;
+                if (owner) {
+                    u = ubuf[i];
+                } else {
+                    unsigned long long bits = ld_relaxed_gpu_u64(urow + i);
                     if (bits == kUnwritten) {
                         const uint64_t t0 = gtimer();
                         for (uint32_t it = 0;; ++it) {
-                            bits = ld_relaxed_gpu_u64(row + i);
+                            bits = ld_relaxed_gpu_u64(urow + i);
                             if (bits != kUnwritten) break;
                             if ((it & 15u) == 15u && (s_abort || gtimer() - t0 > kClusterWaitNs)) {
                                 if (!s_abort) atomicExch(status, kStatusClusterTimeout);
@@ -245,38 +256,55 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
                             }
                         }
                     }
-                    v = __longlong_as_double((long long)bits);
+                    u = __longlong_as_double((long long)bits);
                 }
-                rbuf[i] = v;
+                r = u * inv;
+                diag[i] = fma(-r, r, diag[i]);
             }
+            if (i == p) active[i] = 0;
+            rbuf[i] = r;
+        }
+        if (owner) {
+            double* row = Rorig + (int64_t)j * d;
+            const double rjj = s_rjj;
+            for (int i = tid; i < d; i += 256)
+                if (i == p)
+                    row[i] = rjj;
+                else if (active[i])
+                    row[i] = rbuf[i];
+        }
+        if (me == 0 && tid == 0) piv[j] = p;
+        // 2. the next pivot and its rank test (one barrier)
+        int pn;
+        if (forced) {
+            pn = j + 1 < steps ? forced[j + 1] : -1;
             __syncthreads();
-            if (s_abort) break;
         } else {
-            if (tid == 0) rbuf[p] = 0.0;
-            __syncthreads();
+            pn = pick();
         }
-        if (tid == 0) {
-            active[p] = 0;
-            if (me == 0) piv[j] = p;
-        }
-        __syncthreads();
-        // 2. replicated diagonal update and the next pivot
-        for (int i = tid; i < d; i += 256)
-            if (active[i]) diag[i] = fma(-rbuf[i], rbuf[i], diag[i]);
-        __syncthreads();
-        const int pn = forced ? (j + 1 < steps ? forced[j + 1] : -1) : pick();
-        const bool valid_next = j + 1 < steps && pn >= 0 && pn < d && active[pn];
-        const bool go_on = valid_next && test(j + 1, pn);
-        // 3. own columns: the next pivot's column first and its row of R published, then the rest
+        if (s_abort) break;
+        const bool go_on = j + 1 < steps && pn >= 0 && pn < d && active[pn] && !stops(j + 1, pn);
+        // 3. owner of the next pivot: its column first, published unscaled entry by entry
         if (go_on && pn % G == me) {
             double* col = S + (size_t)(pn / G) * d;
             const double rc = rbuf[pn];
+            double* urow_n = U + (int64_t)(j + 1) * d;
             for (int i = tid; i < d; i += 256)
-                if (active[i]) col[i] = fma(-rbuf[i], rc, col[i]);
-            __syncthreads();
-            publish(j + 1, pn);
-            __syncthreads();
+                if (active[i]) {
+                    const double v = fma(-rbuf[i], rc, col[i]);
+                    col[i] = v;
+                    if (i != pn) {
+                        ubuf[i] = v;
+                        st_relaxed_gpu_f64(urow_n + i, v);
+                    }
+                }
         }
+        // 4. the next step's scale factors (every CTA, while the row travels)
+        if (go_on && tid == 0) {
+            s_inv = rsqrt(diag[pn]);
+            s_rjj = sqrt(diag[pn]);
+        }
+        // 5. the other own columns
         for (int lc = 0; lc < ncl; ++lc) {
             const int c = lc * G + me;
             if (c == pn || !active[c]) continue;
@@ -328,11 +356,12 @@ cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t
     const size_t smem = sizeof(double) * (ncl * d + 3 * (size_t)d) + sizeof(int) * (size_t)d + 64;
     if ((e = cudaFuncSetAttribute(k_pchol_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    k_fill_unwritten<<<152 * 4, 256, 0, st>>>(reinterpret_cast<unsigned long long*>(q.Rorig), d * d);
+    k_fill_unwritten<<<152 * 4, 256, 0, st>>>(reinterpret_cast<unsigned long long*>(q.U), d * d);
     const double* S = q.G;
     const int32_t* fp = forced;
     int fr = (int)forced_rank, di = (int)d, mi = (int)m;
-    void* kargs[] = {&S, &di, &mi, &tau, &fp, &fr, (void*)&q.Rorig, (void*)&q.piv, (void*)&q.rank, &status};
+    void* kargs[] = {&S, &di, &mi, &tau, &fp, &fr, (void*)&q.U, (void*)&q.Rorig, (void*)&q.piv, (void*)&q.rank,
+                     &status};
     e = cudaLaunchCooperativeKernel((const void*)k_pchol_grid, dim3((unsigned)pgrid), dim3(256), kargs, smem, st);
     return e;
 }

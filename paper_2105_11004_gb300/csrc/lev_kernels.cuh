@@ -51,11 +51,11 @@ struct QrScratch {
     unsigned* barrier;  // 1 uint32 grid-barrier counter
     double* G;        // d x d FP64 Gram matrix (Gram route)
     double* Gp;       // split partials of the Gram matrix (Gram route)
-    unsigned* flags;  // per-CTA progress flags of the grid pivoted Cholesky (Gram route, d > 512)
+    double* U;        // d x d FP64: unscaled pivot rows exchanged by the grid pivoted Cholesky (Gram route)
 };
 
 // Gram route of the pivoted QR (gramqr.cu): G = A~^T A~ in FP64, then a
-// pivoted Cholesky on one thread-block cluster; fills Rorig, piv and rank.
+// pivoted Cholesky on one cooperative grid; fills Rorig, piv and rank.
 int gram_splits(int64_t m, int64_t d);
 size_t gram_partial_doubles(int64_t m, int64_t d);
 cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t d, double tau,

@@ -273,9 +273,8 @@ __global__ void k_omega_factor(const double* __restrict__ R, const int32_t* __re
 
 }  // namespace
 
-// The Gram route serves d <= kGramMaxD (one 16-CTA cluster up to d = 512, a
-// cooperative grid over the SMs above) and thresholds tau >= kGramMinTau (above
-// its noise floor of about sqrt(m u)).
+// The Gram route (one cooperative grid over the SMs) serves d <= kGramMaxD and
+// thresholds tau >= kGramMinTau (above its noise floor of about sqrt(m u)).
 constexpr int64_t kGramMaxD = 1024;
 constexpr double kGramMinTau = 1e-6;
 
@@ -296,7 +295,7 @@ static size_t qr_layout(int64_t m, int64_t d, char* base, QrScratch* q) {
     const bool gram = d <= kGramMaxD;
     char* G = gram ? take(sizeof(double) * (size_t)(d * d)) : nullptr;
     char* Gp = gram ? take(sizeof(double) * gram_partial_doubles(m, d)) : nullptr;
-    char* flags = gram ? take(sizeof(unsigned) * 1024) : nullptr;
+    char* U = gram ? take(sizeof(double) * (size_t)(d * d)) : nullptr;
     if (q) {
         q->W = reinterpret_cast<double*>(W);
         q->norms = reinterpret_cast<double*>(norms);
@@ -306,7 +305,7 @@ static size_t qr_layout(int64_t m, int64_t d, char* base, QrScratch* q) {
         q->barrier = reinterpret_cast<unsigned*>(barrier);
         q->G = reinterpret_cast<double*>(G);
         q->Gp = reinterpret_cast<double*>(Gp);
-        q->flags = reinterpret_cast<unsigned*>(flags);
+        q->U = reinterpret_cast<double*>(U);
     }
     return off;
 }
