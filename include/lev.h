@@ -67,6 +67,7 @@ extern "C" {
 #define LEV_OMEGA_IDENTITY  1u  /* Omega = I_r, k = r (the Pi_2-free mode of Sec. 6.4) */
 #define LEV_SKETCH_IDENTITY 2u  /* S = I, G = I, A~ = A (tests; needs n <= 65536) */
 #define LEV_FORCE_PIVOTS    4u  /* take perm_in[0..rank_in) as the pivots, no rank test */
+#define LEV_HOST_ASYNC      8u  /* lev_estimate_dense with host buffers and rank == NULL: enqueue only */
 
 typedef struct lev_handle lev_handle;
 
@@ -167,10 +168,18 @@ int lev_final_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
 
 /* The whole estimator (Alg. 10) on dense A: sketch, rrqr, omega_factor and the
  * final pass on one stream. A and theta may be device pointers or host
- * pointers (pageable or pinned); host buffers are staged through handle scratch
- * with cudaMemcpyAsync on `stream` and theta is copied back before return.
- * rank: host, may be NULL (then the call does not synchronise unless buffers
- * are on the host). perm: device d int32, may be NULL. Errors: any of the above. */
+ * pointers (pageable or pinned). A host A is copied by the handle's own copy
+ * stream into one of two device stage buffers that alternate between calls;
+ * `stream` waits for that copy, and the copy of the next call waits only for
+ * the kernels of the call that last used its buffer, so with pinned buffers
+ * the copy of call i+1 overlaps the kernels of call i. A host theta is
+ * copied back on `stream`. rank: host, may be NULL. The call synchronises
+ * `stream` before it returns when rank is non-NULL, or when a buffer is on the
+ * host, unless p->flags has LEV_HOST_ASYNC and rank is NULL: then it only
+ * enqueues the work, the host A must stay unchanged and theta is valid once
+ * `stream` has been synchronised, and a device-side timeout is reported by
+ * lev_device_status instead of the return code. perm: device d int32, may be
+ * NULL. Errors: any of the above. */
 int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
                        const lev_params* p, float* theta, int64_t* rank, int32_t* perm,
                        void* stream);

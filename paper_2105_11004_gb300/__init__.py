@@ -17,7 +17,7 @@ from .build import LIB_PATH, build as build_library  # noqa: F401
 
 LEV_OK, LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0 = 0, 1, 2, 3, 4, 5
 LEV_FP32, LEV_TF32, LEV_BF16, LEV_BF16X3 = 0, 1, 2, 3
-LEV_OMEGA_IDENTITY, LEV_SKETCH_IDENTITY, LEV_FORCE_PIVOTS = 1, 2, 4
+LEV_OMEGA_IDENTITY, LEV_SKETCH_IDENTITY, LEV_FORCE_PIVOTS, LEV_HOST_ASYNC = 1, 2, 4, 8
 PRECISIONS = {"fp32": LEV_FP32, "tf32": LEV_TF32, "bf16": LEV_BF16, "bf16x3": LEV_BF16X3}
 
 # Every symbol include/lev.h declares, with (restype, argtypes).
@@ -131,7 +131,7 @@ def default_handle(device: int = 0) -> Handle:
 
 def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec="fp32", eps=0.5,
                 delta=1.0 / 3.0, gamma=2.0, omega_identity=False, sketch_identity=False,
-                perm_in=None, rank_in=0) -> lev_params:
+                perm_in=None, rank_in=0, host_async=False) -> lev_params:
     p = lev_params()
     _check(lib.lev_params_init(ctypes.byref(p)))
     p.eps, p.delta, p.gamma = eps, delta, gamma
@@ -143,6 +143,8 @@ def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec=
         flags |= LEV_OMEGA_IDENTITY
     if sketch_identity:
         flags |= LEV_SKETCH_IDENTITY
+    if host_async:
+        flags |= LEV_HOST_ASYNC
     if perm_in is not None:
         flags |= LEV_FORCE_PIVOTS
         p.perm_in = perm_in.data_ptr()

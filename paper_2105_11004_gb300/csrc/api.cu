@@ -61,9 +61,15 @@ struct lev_handle {
     int num_sms = 0;
     int32_t* status = nullptr;      // device status word
     int64_t* host_rank = nullptr;   // pinned
-    Buf count, off, tmp, perm_rows, B, partial, Atilde, qr, R, perm_d, Mfull, stageA, stageTheta,
+    Buf count, off, tmp, perm_rows, B, partial, Atilde, qr, R, perm_d, Mfull, stageTheta,
         tc_ws, tc_ws2, csr_rp, csr_col, csr_val, bwd;
     GCache g;
+    // host A of lev_estimate_dense: two stage buffers filled by a copy stream of the handle
+    Buf stageA[2];
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+    bool used_once[2] = {false, false};
+    int stage_next = 0;
 };
 
 namespace {
@@ -350,9 +356,14 @@ int lev_destroy(lev_handle* h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
-                  &h->R, &h->perm_d, &h->Mfull, &h->stageA, &h->stageTheta, &h->tc_ws, &h->tc_ws2, &h->bwd, &h->csr_rp,
-                  &h->csr_col, &h->csr_val};
+                  &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
+                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val};
     for (Buf* b : all) release(*b);
+    for (int i = 0; i < 2; ++i) {
+        if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+        if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
+    }
+    if (h->copy_st) cudaStreamDestroy(h->copy_st);
     if (h->g.ptr) cudaFree(h->g.ptr);
     if (h->status) cudaFree(h->status);
     if (h->host_rank) cudaFreeHost(h->host_rank);
@@ -452,6 +463,35 @@ static int estimate_tail(lev_handle* h, const Sizes& z, int64_t d, const lev_par
     return LEV_OK;
 }
 
+// Copy host A (n x d, lda) into the next of the handle's two stage buffers on the handle's copy
+// stream. The copy waits for the kernels of the call that last read that buffer (event ev_used),
+// and `st` waits for the copy; the caller records ev_used[*slot] on `st` after its last read.
+int stage_host_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, cudaStream_t st, int* slot,
+                     const float** dA) {
+    if (!h->copy_st) {
+        LEV_CUDA(cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            LEV_CUDA(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming));
+            LEV_CUDA(cudaEventCreateWithFlags(&h->ev_used[i], cudaEventDisableTiming));
+        }
+    }
+    const int k = h->stage_next;
+    LEV_TRY(ensure(h->stageA[k], sizeof(float) * (size_t)n * d));
+    if (h->used_once[k]) LEV_CUDA(cudaStreamWaitEvent(h->copy_st, h->ev_used[k], 0));
+    if (lda == d)
+        LEV_CUDA(cudaMemcpyAsync(h->stageA[k].ptr, A, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice,
+                                 h->copy_st));
+    else
+        LEV_CUDA(cudaMemcpy2DAsync(h->stageA[k].ptr, sizeof(float) * d, A, sizeof(float) * lda, sizeof(float) * d, n,
+                                   cudaMemcpyHostToDevice, h->copy_st));
+    LEV_CUDA(cudaEventRecord(h->ev_copied[k], h->copy_st));
+    LEV_CUDA(cudaStreamWaitEvent(st, h->ev_copied[k], 0));
+    h->stage_next ^= 1;
+    *slot = k;
+    *dA = (const float*)h->stageA[k].ptr;
+    return LEV_OK;
+}
+
 int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const lev_params* p,
                        float* theta, int64_t* rank, int32_t* perm, void* stream) {
     LEV_TRY(set_device(h));
@@ -463,30 +503,35 @@ int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
     LEV_TRY(check_prec(p->final_prec, "final"));
     cudaStream_t st = (cudaStream_t)stream;
     const bool hostA = is_host_pointer(A), hostT = is_host_pointer(theta);
-    const float* dA = A;
-    int64_t ldA = lda;
-    if (hostA) {
-        LEV_TRY(ensure(h->stageA, sizeof(float) * (size_t)n * d));
-        if (lda == d)
-            LEV_CUDA(cudaMemcpyAsync(h->stageA.ptr, A, sizeof(float) * (size_t)n * d, cudaMemcpyHostToDevice, st));
-        else
-            LEV_CUDA(cudaMemcpy2DAsync(h->stageA.ptr, sizeof(float) * d, A, sizeof(float) * lda, sizeof(float) * d,
-                                       n, cudaMemcpyHostToDevice, st));
-        dA = (const float*)h->stageA.ptr;
-        ldA = d;
-    }
     float* dT = theta;
     if (hostT) {
         LEV_TRY(ensure(h->stageTheta, sizeof(float) * (size_t)n));
         dT = (float*)h->stageTheta.ptr;
     }
     LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
-    LEV_TRY(sketch_common_dense(h, dA, n, d, ldA, p, z, (float*)h->Atilde.ptr, st));
+    const float* dA = A;
+    int64_t ldA = lda;
+    int slot = -1;
+    if (hostA) {
+        LEV_TRY(stage_host_dense(h, A, n, d, lda, st, &slot, &dA));
+        ldA = d;
+    }
     lev::QrScratch qs;
-    LEV_TRY(estimate_tail(h, z, d, p, perm, &qs, st));
-    LEV_TRY(final_dense(h, dA, n, d, ldA, (const float*)h->Mfull.ptr, z.k, p->final_prec, dT, st));
+    auto kernels = [&]() -> int {
+        LEV_TRY(sketch_common_dense(h, dA, n, d, ldA, p, z, (float*)h->Atilde.ptr, st));
+        LEV_TRY(estimate_tail(h, z, d, p, perm, &qs, st));
+        return final_dense(h, dA, n, d, ldA, (const float*)h->Mfull.ptr, z.k, p->final_prec, dT, st);
+    };
+    const int rc = kernels();
+    if (slot >= 0) {
+        // the stage buffer is free for a later copy once everything enqueued so far on `st` has run
+        LEV_CUDA(cudaEventRecord(h->ev_used[slot], st));
+        h->used_once[slot] = true;
+    }
+    LEV_TRY(rc);
     if (hostT) LEV_CUDA(cudaMemcpyAsync(theta, dT, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!rank && !hostA && !hostT) return LEV_OK;
+    if (!rank && (p->flags & LEV_HOST_ASYNC)) return LEV_OK;
     return finish(h, qs, rank, st);
 }
 

@@ -376,6 +376,37 @@ def test_host_buffers_match_device_path(L, h):
     assert torch.equal(th_dev.cpu(), th_host) and torch.equal(th_host, th_page)
 
 
+def test_host_async_pipelined_calls(L, h):
+    """LEV_HOST_ASYNC: three enqueued calls on different host inputs (the stage buffers alternate,
+    so the third copy must wait for the first call's kernels), then one synchronisation; each
+    theta equals the device path's bit for bit, and so does a synchronous call afterwards. The
+    host inputs are overwritten only after the synchronisation."""
+    import torch
+    As = [W.dense_gaussian(12000, 40, seed=20 + i).astype(np.float32) for i in range(3)]
+    As[1] *= np.exp(np.random.default_rng(5).standard_normal(40)).astype(np.float32)[None, :]
+    p_sync = L.make_params(s=4096, m=160, k=64, seed=9, sketch_prec="bf16x3", final_prec="bf16x3")
+    p_async = L.make_params(s=4096, m=160, k=64, seed=9, sketch_prec="bf16x3", final_prec="bf16x3",
+                            host_async=True)
+    want = []
+    for A in As:
+        t = torch.empty(12000, device="cuda")
+        assert L.lev_estimate_dense(h, to_dev(A), p_sync, t) == 40
+        want.append(t.cpu())
+    hosts = [torch.from_numpy(A).pin_memory() for A in As]
+    outs = [torch.full((12000,), float("nan")).pin_memory() for _ in As]
+    for Ah, th in zip(hosts, outs):
+        L.lev_estimate_dense(h, Ah, p_async, th, want_rank=False)
+    torch.cuda.synchronize()
+    assert L.lev_device_status(h) == 0
+    for th, w in zip(outs, want):
+        assert torch.equal(th, w)
+    for Ah in hosts:
+        Ah.zero_()
+    th = torch.empty(12000).pin_memory()
+    assert L.lev_estimate_dense(h, torch.from_numpy(As[2]).pin_memory(), p_sync, th) == 40
+    assert torch.equal(th, want[2])
+
+
 def test_fresh_handle_first_call(L):
     """First call on a new handle: every scratch buffer is freshly allocated."""
     A = W.dense_gaussian(2000, 20, seed=0).astype(np.float32)
