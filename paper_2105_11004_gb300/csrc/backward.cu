@@ -7,13 +7,18 @@
 //   N = R_11^{-1} K R_11^{-T};  T = G^T Xbar;
 //   dg/dA_i = Z_i M^T + sigma_i T[h(i), :] on the columns of K, 0 elsewhere.
 // Working over all d columns with Mfull (zero rows off K) and Xbar scattered
-// into an m x d matrix (zero columns off K) makes both big passes plain dense
-// products, and the columns off K come out 0 by construction.
+// into an m x d matrix (zero columns off K) makes both big passes dense
+// products, and the columns off K come out 0 by construction. Both passes are
+// reassociated around the two d x d matrices H = A^T W A and P = Mfull Mfull^T:
+//   C = A^T Z = 2 (A^T W A) Mfull = 2 H Mfull,
+//   Z M^T = 2 W A Mfull Mfull^T = 2 W A P,
+// so the two passes over A cost 2 n d^2 flops each instead of 4 n d k.
 //
-// Kernels: pass 1 (Y recomputed per tile, C partials per row chunk), fixed-order
-// reduction of C in FP64, the small FP64 steps (C M^T, two blocked triangular
-// solves with R_11 and R_11^T, copyltu, Xbar), T = G^T Xbar (FP32), pass 2
-// (Y recomputed, Z M^T plus the CountSketch adjoint gathered by hash, no atomics).
+// Kernels: pass 1 (H partials per row chunk, 8 x 8 register blocks, the upper
+// 64 x 64 tiles only), fixed-order reduction of H, C = 2 H Mfull and P in FP64,
+// the small FP64 steps (C M^T, two blocked triangular solves with R_11 and
+// R_11^T, copyltu, Xbar), T = G^T Xbar (FP32), pass 2 (2 W A P plus the
+// CountSketch adjoint gathered by hash, 8 x 4 register blocks, no atomics).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -25,83 +30,136 @@ namespace lev {
 
 namespace {
 
-constexpr int P1_RT = 32, P1_DB = 64, P1_KB = 64;
+constexpr int HT = 64;          // H tile
+constexpr int H_RB = 32;        // rows staged per step of pass 1
 
-// C partial for (row chunk, d block, k block): C[a][q] = sum_i A[i][a] * 2 w_i (A_i Mfull)[q].
-__global__ void __launch_bounds__(256) k_bwd_pass1(const float* __restrict__ A, int64_t lda, int64_t n, int d,
-                                                   const float* __restrict__ Mf, int k, const float* __restrict__ w,
-                                                   int rows_per_chunk, float* __restrict__ Cp) {
-    extern __shared__ float sm[];
-    const int dpad = (d + 3) & ~3;
-    float* As = sm;                                 // P1_RT x dpad
-    float* Ms = As + P1_RT * dpad;                  // d x P1_KB  (Mfull[:, kb])
-    float* Zs = Ms + (size_t)d * P1_KB;             // P1_RT x P1_KB
-    const int t = threadIdx.x;
-    const int chunk = blockIdx.x, dbk = blockIdx.y, kbk = blockIdx.z;
-    const int q0 = kbk * P1_KB, a0 = dbk * P1_DB;
-    const int64_t r_begin = (int64_t)chunk * rows_per_chunk;
-    const int64_t r_end = min(n, r_begin + rows_per_chunk);
-    for (int e = t; e < d * P1_KB; e += 256) {
-        const int j = e / P1_KB, q = e % P1_KB;
-        Ms[e] = (q0 + q < k) ? Mf[(int64_t)j * k + q0 + q] : 0.f;
-    }
-    // thread tiles: Y: row ry = t / 8, columns qy .. qy+7; C: 4 x 4 at (ca, cq)
-    const int ry = t >> 3, qy = (t & 7) * 8;
-    const int ca = (t >> 4) * 4, cq = (t & 15) * 4;
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int64_t r0 = r_begin; r0 < r_end; r0 += P1_RT) {
-        __syncthreads();
-        for (int e = t; e < P1_RT * dpad; e += 256) {
-            const int r = e / dpad, j = e % dpad;
-            const int64_t row = r0 + r;
-            As[e] = (row < r_end && j < d) ? A[row * lda + j] : 0.f;
-        }
-        __syncthreads();
-        float y[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) y[u] = 0.f;
-        for (int j = 0; j < d; ++j) {
-            const float a = As[ry * dpad + j];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) y[u] = fmaf(a, Ms[j * P1_KB + qy + u], y[u]);
-        }
-        const int64_t row = r0 + ry;
-        const float tw = (row < r_end) ? 2.f * w[row] : 0.f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) Zs[ry * P1_KB + qy + u] = tw * y[u];
-        __syncthreads();
-        for (int r = 0; r < P1_RT; ++r) {
-            float av[4], zv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = (a0 + ca + i < d) ? As[r * dpad + a0 + ca + i] : 0.f;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) zv[j] = Zs[r * P1_KB + cq + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], zv[j], acc[i][j]);
-        }
-    }
-    float* out = Cp + (int64_t)chunk * d * k;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int a = a0 + ca + i, q = q0 + cq + j;
-            if (a < d && q < k) out[(int64_t)a * k + q] = acc[i][j];
-        }
+__host__ __device__ inline int h_tiles(int d) {
+    const int nt = (d + HT - 1) / HT;
+    return nt * (nt + 1) / 2;
 }
 
-__global__ void k_bwd_reduce_c(const float* __restrict__ Cp, int chunks, int d, int k, double* __restrict__ C) {
-    const int64_t total = (int64_t)d * k;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int z = 0; z < chunks; ++z) s += (double)Cp[(int64_t)z * total + e];
-        C[e] = s;
+__device__ inline void h_tile_coords(int t, int nt, int& bi, int& bj) {
+    bi = 0;
+    while (t >= nt - bi) { t -= nt - bi; ++bi; }
+    bj = bi + t;
+}
+
+// Pass 1: partial H = sum_i w_i A_i^T A_i over one row chunk, for the upper 64 x 64 tile
+// (bi, bj) of H. Four groups of 64 threads take every fourth staged row; thread (ti, tj) of a
+// group owns the 8 x 8 block (bi*64 + 8 ti .. , bj*64 + 8 tj ..). The groups' blocks are summed
+// in shared memory and the CTA writes one 64 x 64 FP32 partial.
+__global__ void __launch_bounds__(256) k_bwd_wgram(const float* __restrict__ A, int64_t lda, int64_t n, int d,
+                                                   int vecA, const float* __restrict__ w, int rows_per_chunk,
+                                                   float* __restrict__ Hp) {
+    extern __shared__ __align__(16) float sm[];
+    float* Ai = sm;                         // H_RB x 64: columns bi*64 ..
+    float* Aj = Ai + H_RB * HT;             // H_RB x 64: columns bj*64 ..
+    float* ws = Aj + H_RB * HT;             // H_RB
+    const int nt = (d + HT - 1) / HT;
+    int bi, bj;
+    h_tile_coords(blockIdx.y, nt, bi, bj);
+    const int t = threadIdx.x, g = t >> 6, tt = t & 63, ti = tt >> 3, tj = tt & 7;
+    const int64_t r_begin = (int64_t)blockIdx.x * rows_per_chunk;
+    const int64_t r_end = min(n, r_begin + rows_per_chunk);
+    float acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+    for (int64_t r0 = r_begin; r0 < r_end; r0 += H_RB) {
+        __syncthreads();
+        // 32 rows x 64 columns per side; float4 loads when A is 16-byte aligned and lda % 4 == 0
+        for (int e = t; e < H_RB * (HT / 4); e += 256) {
+            const int r = e / (HT / 4), c4 = (e % (HT / 4)) * 4;
+            const int64_t row = r0 + r;
+            float4 vi = make_float4(0.f, 0.f, 0.f, 0.f), vj = vi;
+            if (row < r_end) {
+                const float* src = A + row * lda;
+                const int ci = bi * HT + c4, cj = bj * HT + c4;
+                if (vecA && ci + 3 < d) vi = *reinterpret_cast<const float4*>(src + ci);
+                else {
+                    vi.x = ci < d ? src[ci] : 0.f; vi.y = ci + 1 < d ? src[ci + 1] : 0.f;
+                    vi.z = ci + 2 < d ? src[ci + 2] : 0.f; vi.w = ci + 3 < d ? src[ci + 3] : 0.f;
+                }
+                if (vecA && cj + 3 < d) vj = *reinterpret_cast<const float4*>(src + cj);
+                else {
+                    vj.x = cj < d ? src[cj] : 0.f; vj.y = cj + 1 < d ? src[cj + 1] : 0.f;
+                    vj.z = cj + 2 < d ? src[cj + 2] : 0.f; vj.w = cj + 3 < d ? src[cj + 3] : 0.f;
+                }
+            }
+            *reinterpret_cast<float4*>(Ai + r * HT + c4) = vi;
+            *reinterpret_cast<float4*>(Aj + r * HT + c4) = vj;
+        }
+        for (int r = t; r < H_RB; r += 256) ws[r] = (r0 + r < r_end) ? w[r0 + r] : 0.f;
+        __syncthreads();
+#pragma unroll 2
+        for (int r = g; r < H_RB; r += 4) {
+            const float wr = ws[r];
+            const float4 a0 = *reinterpret_cast<const float4*>(Ai + r * HT + ti * 8);
+            const float4 a1 = *reinterpret_cast<const float4*>(Ai + r * HT + ti * 8 + 4);
+            const float4 b0 = *reinterpret_cast<const float4*>(Aj + r * HT + tj * 8);
+            const float4 b1 = *reinterpret_cast<const float4*>(Aj + r * HT + tj * 8 + 4);
+            const float av[8] = {wr * a0.x, wr * a0.y, wr * a0.z, wr * a0.w, wr * a1.x, wr * a1.y, wr * a1.z, wr * a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+    }
+    // the four groups' blocks, summed in a fixed order
+    __syncthreads();
+    float* red = sm;                        // 4 x 64 x 64 (reuses the staging space)
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) red[(g * HT + ti * 8 + u) * HT + tj * 8 + v] = acc[u][v];
+    __syncthreads();
+    float* out = Hp + ((int64_t)blockIdx.x * gridDim.y + blockIdx.y) * (HT * HT);
+    for (int e = t; e < HT * HT; e += 256)
+        out[e] = ((red[e] + red[HT * HT + e]) + red[2 * HT * HT + e]) + red[3 * HT * HT + e];
+}
+
+// H (d x d FP64, both triangles) = sum over chunks of the partials, in chunk order.
+__global__ void k_bwd_reduce_h(const float* __restrict__ Hp, int chunks, int d, double* __restrict__ H) {
+    const int nt = (d + HT - 1) / HT;
+    const int T = nt * (nt + 1) / 2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)T * HT * HT;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int tile = (int)(e / (HT * HT)), x = (int)(e % (HT * HT));
+        int bi, bj;
+        h_tile_coords(tile, nt, bi, bj);
+        const int a = bi * HT + x / HT, b = bj * HT + x % HT;
+        // one writer per symmetric pair: in a diagonal tile the (a, b) and (b, a) partials
+        // round differently ((w a_a) a_b against (w a_b) a_a), so only a <= b is summed
+        if (a >= d || b >= d || a > b) continue;
+        double sum = 0.0;
+        for (int c = 0; c < chunks; ++c) sum += (double)Hp[((int64_t)c * T + tile) * (HT * HT) + x];
+        H[(int64_t)a * d + b] = sum;
+        H[(int64_t)b * d + a] = sum;
+    }
+}
+
+// C (d x k FP64) = 2 H Mfull.
+__global__ void k_bwd_hm(const double* __restrict__ H, const float* __restrict__ Mf, int d, int k,
+                         double* __restrict__ C) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)d * k;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / k), q = (int)(e % k);
+        double acc = 0.0;
+        for (int b = 0; b < d; ++b) acc = fma(H[(int64_t)a * d + b], (double)Mf[(int64_t)b * k + q], acc);
+        C[e] = 2.0 * acc;
+    }
+}
+
+// P (d x d FP32, row stride ldp = d rounded up to 4) = Mfull Mfull^T, accumulated in FP64.
+__global__ void k_bwd_pmat(const float* __restrict__ Mf, int d, int k, int ldp, float* __restrict__ P) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)d * d;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(e / d), c = (int)(e % d);
+        double acc = 0.0;
+        for (int q = 0; q < k; ++q) acc = fma((double)Mf[(int64_t)a * k + q], (double)Mf[(int64_t)c * k + q], acc);
+        P[(int64_t)a * ldp + c] = (float)acc;
     }
 }
 
@@ -266,81 +324,93 @@ __global__ void __launch_bounds__(256) k_gt_x(const float* __restrict__ G32, con
         }
 }
 
-// Pass 2: gradA[i][c] = sum_q Z_iq Mfull[c][q] + sigma_i T[h(i)][c], Z_i = 2 w_i A_i Mfull.
-// 32 rows per CTA. Phase A: Z (32 x k) from A (32 x d) and 64-column chunks of
-// Mfull staged in shared memory; phase B: 64 x 64 chunks of Mfull^T staged
-// (padded rows), 8 output columns per thread.
-constexpr int P2_RT = 32, P2_QC = 64, P2_CC = 64;
+// Pass 2: gradA[i][c] = 2 w_i (A_i P)[c] + sigma_i T[h(i)][c] for a tile of 128 rows x 64
+// columns. Thread (tr, tc) owns rows 8 tr .. 8 tr + 7 and columns 4 tc .. 4 tc + 3; A rows and
+// P rows are staged 64 columns of A at a time; each step of 4 j's takes eight float4 of A
+// and four of P for 128 FMAs.
+constexpr int P2_R = 128, P2_C = 64, P2_J = 64, P2_AS = P2_J + 4;
 __global__ void __launch_bounds__(256) k_bwd_pass2(const float* __restrict__ A, int64_t lda, int64_t n, int d,
-                                                   const float* __restrict__ Mf, int k, const float* __restrict__ w,
+                                                   int vecA, const float* __restrict__ P, int ldp,
+                                                   const float* __restrict__ w,
                                                    const float* __restrict__ T, uint64_t key, uint32_t s,
                                                    int identity, float* __restrict__ gA) {
-    extern __shared__ float sm[];
-    const int dpad = (d + 3) & ~3, kz = ((k + P2_QC - 1) / P2_QC) * P2_QC + 4;
-    float* As = sm;                       // P2_RT x dpad
-    float* Zs = As + P2_RT * dpad;        // P2_RT x kz
-    float* Ms = Zs + P2_RT * kz;          // phase A: d x P2_QC; phase B: P2_QC x (P2_CC + 4)
-    const int t = threadIdx.x;
-    const int64_t r0 = (int64_t)blockIdx.x * P2_RT;
-    for (int e = t; e < P2_RT * dpad; e += 256) {
-        const int r = e / dpad, j = e % dpad;
-        const int64_t row = r0 + r;
-        As[e] = (row < n && j < d) ? A[row * lda + j] : 0.f;
-    }
-    const int ry = t >> 3, g8 = (t & 7) * 8;
-    const int64_t row = r0 + ry;
-    const float tw = (row < n) ? 2.f * w[row] : 0.f;
-    for (int q0 = 0; q0 < k; q0 += P2_QC) {
+    extern __shared__ __align__(16) float sm[];
+    float* As = sm;                          // P2_R x P2_AS
+    float* Ps = As + P2_R * P2_AS;           // P2_J x P2_C
+    const int t = threadIdx.x, tr = t >> 4, tc = t & 15;
+    const int64_t r0 = (int64_t)blockIdx.x * P2_R;
+    const int c0 = blockIdx.y * P2_C;
+    float acc[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    for (int j0 = 0; j0 < d; j0 += P2_J) {
         __syncthreads();
-        for (int e = t; e < d * P2_QC; e += 256) {
-            const int j = e / P2_QC, q = e % P2_QC;
-            Ms[e] = (q0 + q < k) ? Mf[(int64_t)j * k + q0 + q] : 0.f;
+        for (int e = t; e < P2_R * (P2_J / 4); e += 256) {
+            const int r = e / (P2_J / 4), j4 = (e % (P2_J / 4)) * 4;
+            const int64_t row = r0 + r;
+            const int j = j0 + j4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < n) {
+                const float* src = A + row * lda;
+                if (vecA && j + 3 < d) v = *reinterpret_cast<const float4*>(src + j);
+                else {
+                    v.x = j < d ? src[j] : 0.f; v.y = j + 1 < d ? src[j + 1] : 0.f;
+                    v.z = j + 2 < d ? src[j + 2] : 0.f; v.w = j + 3 < d ? src[j + 3] : 0.f;
+                }
+            }
+            *reinterpret_cast<float4*>(As + r * P2_AS + j4) = v;
+        }
+        for (int e = t; e < P2_J * (P2_C / 4); e += 256) {
+            const int j = e / (P2_C / 4), c4 = (e % (P2_C / 4)) * 4;
+            const int jj = j0 + j, c = c0 + c4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (jj < d) {
+                const float* src = P + (int64_t)jj * ldp;          // ldp % 4 == 0, P 256-byte aligned
+                if (c + 3 < d) v = *reinterpret_cast<const float4*>(src + c);
+                else {
+                    v.x = c < d ? src[c] : 0.f; v.y = c + 1 < d ? src[c + 1] : 0.f;
+                    v.z = c + 2 < d ? src[c + 2] : 0.f; v.w = 0.f;
+                }
+            }
+            *reinterpret_cast<float4*>(Ps + j * P2_C + c4) = v;
         }
         __syncthreads();
-        float y[8];
+#pragma unroll 2
+        for (int j = 0; j < P2_J; j += 4) {
+            float4 a[8], p[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) y[u] = 0.f;
-        for (int j = 0; j < d; ++j) {
-            const float a = As[ry * dpad + j];
-            const float4 m0 = *reinterpret_cast<const float4*>(&Ms[j * P2_QC + g8]);
-            const float4 m1 = *reinterpret_cast<const float4*>(&Ms[j * P2_QC + g8 + 4]);
-            y[0] = fmaf(a, m0.x, y[0]); y[1] = fmaf(a, m0.y, y[1]); y[2] = fmaf(a, m0.z, y[2]); y[3] = fmaf(a, m0.w, y[3]);
-            y[4] = fmaf(a, m1.x, y[4]); y[5] = fmaf(a, m1.y, y[5]); y[6] = fmaf(a, m1.z, y[6]); y[7] = fmaf(a, m1.w, y[7]);
-        }
+            for (int u = 0; u < 8; ++u) a[u] = *reinterpret_cast<const float4*>(As + (tr * 8 + u) * P2_AS + j);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) Zs[ry * kz + q0 + g8 + u] = tw * y[u];
-    }
-    const uint64_t x = splitmix64(key, (uint64_t)row);
-    const int64_t bucket = identity ? row : (int64_t)bucket_of(x, s);     // S = I: row i is bucket i
-    const float sg = identity ? 1.f : sign_of(x);
-    constexpr int MT = P2_CC + 4;
-    for (int c0 = 0; c0 < d; c0 += P2_CC) {
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = 0.f;
-        for (int q0 = 0; q0 < k; q0 += P2_QC) {
-            __syncthreads();
-            for (int e = t; e < P2_QC * P2_CC; e += 256) {
-                const int c = e / P2_QC, q = e % P2_QC;             // coalesced over q of Mfull row c
-                Ms[q * MT + c] = (c0 + c < d && q0 + q < k) ? Mf[(int64_t)(c0 + c) * k + q0 + q] : 0.f;
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int q = 0; q < P2_QC; ++q) {
-                const float z = Zs[ry * kz + q0 + q];
-                const float4 m0 = *reinterpret_cast<const float4*>(&Ms[q * MT + g8]);
-                const float4 m1 = *reinterpret_cast<const float4*>(&Ms[q * MT + g8 + 4]);
-                v[0] = fmaf(z, m0.x, v[0]); v[1] = fmaf(z, m0.y, v[1]); v[2] = fmaf(z, m0.z, v[2]); v[3] = fmaf(z, m0.w, v[3]);
-                v[4] = fmaf(z, m1.x, v[4]); v[5] = fmaf(z, m1.y, v[5]); v[6] = fmaf(z, m1.z, v[6]); v[7] = fmaf(z, m1.w, v[7]);
-            }
-        }
-        if (row < n) {
+            for (int jj = 0; jj < 4; ++jj) p[jj] = *reinterpret_cast<const float4*>(Ps + (j + jj) * P2_C + tc * 4);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int c = c0 + g8 + u;
-                if (c < d) gA[row * d + c] = v[u] + sg * T[bucket * d + c];
+                const float av[4] = {a[u].x, a[u].y, a[u].z, a[u].w};
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    acc[u][0] = fmaf(av[jj], p[jj].x, acc[u][0]);
+                    acc[u][1] = fmaf(av[jj], p[jj].y, acc[u][1]);
+                    acc[u][2] = fmaf(av[jj], p[jj].z, acc[u][2]);
+                    acc[u][3] = fmaf(av[jj], p[jj].w, acc[u][3]);
+                }
             }
         }
+    }
+    const int c = c0 + tc * 4;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int64_t row = r0 + tr * 8 + u;
+        if (row >= n) break;
+        const uint64_t x = splitmix64(key, (uint64_t)row);
+        const int64_t bucket = identity ? row : (int64_t)bucket_of(x, s);     // S = I: row i is bucket i
+        const float sg = identity ? 1.f : sign_of(x);
+        const float tw = 2.f * w[row];
+        const float* trow = T + bucket * d;
+        float* out = gA + row * d;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if (c + v < d) out[c + v] = fmaf(tw, acc[u][v], sg * trow[c + v]);
     }
 }
 
@@ -355,18 +425,20 @@ int grid_cap(int64_t work, int block, int cap) {
 
 size_t backward_scratch_bytes(int64_t n, int64_t d, int64_t k, int64_t s, int64_t m, int chunks) {
     size_t b = 0;
-    b += sizeof(float) * (size_t)chunks * d * k;     // C partials
+    b += sizeof(float) * (size_t)chunks * h_tiles((int)d) * HT * HT;   // H partials
+    b += sizeof(double) * (size_t)d * d;            // H
     b += sizeof(double) * (size_t)d * k;            // C
-    b += 4 * sizeof(double) * (size_t)d * d;        // CMt/Rbar, K/V/N, spare
+    b += sizeof(float) * (size_t)d * ((d + 3) & ~3);   // P (row stride rounded up to 4)
+    b += 2 * sizeof(double) * (size_t)d * d;        // CMt/Rbar, K/V/N
     b += sizeof(float) * (size_t)m * d;             // Xbar_full
     b += sizeof(float) * (size_t)s * d;             // T (unused in the identity-sketch mode)
-    return b + 8 * 256;
+    return b + 10 * 256;
 }
 
-int backward_chunks(int64_t n, int64_t d, int64_t k) {
-    const int64_t dbk = (d + P1_DB - 1) / P1_DB, kbk = (k + P1_KB - 1) / P1_KB;
-    int64_t c = (2 * 152 + dbk * kbk - 1) / (dbk * kbk);
-    const int64_t max_c = (n + P1_RT - 1) / P1_RT;
+int backward_chunks(int64_t n, int64_t d, int64_t /*k*/) {
+    const int64_t tiles = h_tiles((int)d);
+    int64_t c = (2 * 152 + tiles - 1) / tiles;
+    const int64_t max_c = (n + H_RB - 1) / H_RB;
     if (c > max_c) c = max_c;
     if (c < 1) c = 1;
     return (int)c;
@@ -379,23 +451,28 @@ cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_
                                   void* scratch, int chunks, float* gradA, cudaStream_t st) {
     char* p = static_cast<char*>(scratch);
     auto take = [&](size_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return r; };
-    float* Cp = reinterpret_cast<float*>(take(sizeof(float) * (size_t)chunks * d * k));
+    const int ht = h_tiles((int)d);
+    float* Hp = reinterpret_cast<float*>(take(sizeof(float) * (size_t)chunks * ht * HT * HT));
+    double* H = reinterpret_cast<double*>(take(sizeof(double) * (size_t)d * d));
     double* C = reinterpret_cast<double*>(take(sizeof(double) * (size_t)d * k));
+    const int ldp = (int)((d + 3) & ~3);
+    float* P = reinterpret_cast<float*>(take(sizeof(float) * (size_t)d * ldp));
+    const int vecA = ((reinterpret_cast<uintptr_t>(A) & 15u) == 0 && (lda & 3) == 0) ? 1 : 0;
     double* B1 = reinterpret_cast<double*>(take(sizeof(double) * (size_t)d * d));
     double* B2 = reinterpret_cast<double*>(take(sizeof(double) * (size_t)d * d));
     float* Xf = reinterpret_cast<float*>(take(sizeof(float) * (size_t)m * d));
     float* T = reinterpret_cast<float*>(take(sizeof(float) * (size_t)s * d));
     cudaError_t e;
-    // pass 1
-    const int rows_per_chunk = (int)(((n + chunks - 1) / chunks + P1_RT - 1) / P1_RT * P1_RT);
-    const int dpad = (int)((d + 3) & ~3);
-    const size_t sm1 = sizeof(float) * ((size_t)P1_RT * dpad + (size_t)d * P1_KB + (size_t)P1_RT * P1_KB);
-    if (sm1 > 48 * 1024)
-        if ((e = cudaFuncSetAttribute(k_bwd_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) != cudaSuccess)
-            return e;
-    dim3 g1((unsigned)chunks, (unsigned)((d + P1_DB - 1) / P1_DB), (unsigned)((k + P1_KB - 1) / P1_KB));
-    k_bwd_pass1<<<g1, 256, sm1, st>>>(A, lda, n, (int)d, Mfull, (int)k, w, rows_per_chunk, Cp);
-    k_bwd_reduce_c<<<grid_cap(d * k, 256, 1024), 256, 0, st>>>(Cp, chunks, (int)d, (int)k, C);
+    // pass 1: H = A^T W A, then C = 2 H Mfull and P = Mfull Mfull^T
+    const int rows_per_chunk = (int)(((n + chunks - 1) / chunks + H_RB - 1) / H_RB * H_RB);
+    const size_t sm1 = sizeof(float) * (size_t)4 * HT * HT;     // staging (2 x 32 x 64 + 32) fits inside
+    if ((e = cudaFuncSetAttribute(k_bwd_wgram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) != cudaSuccess)
+        return e;
+    k_bwd_wgram<<<dim3((unsigned)chunks, (unsigned)ht), 256, sm1, st>>>(A, lda, n, (int)d, vecA, w, rows_per_chunk,
+                                                                        Hp);
+    k_bwd_reduce_h<<<grid_cap((int64_t)ht * HT * HT, 256, 1024), 256, 0, st>>>(Hp, chunks, (int)d, H);
+    k_bwd_hm<<<grid_cap(d * k, 128, 1024), 128, 0, st>>>(H, Mfull, (int)d, (int)k, C);
+    k_bwd_pmat<<<grid_cap(d * d, 128, 1024), 128, 0, st>>>(Mfull, (int)d, (int)k, ldp, P);
     // small FP64 steps
     k_bwd_cmt<<<grid_cap(d * d, 256, 1024), 256, 0, st>>>(C, Mfull, perm, d_rank, (int)d, (int)k, B1);
     // Rbar = -R^{-T} (C M^T): columns of CMt, in place in B1
@@ -415,15 +492,12 @@ cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_
     else
         k_gt_x<false><<<gt, 256, 0, st>>>(G32, nullptr, nullptr, ldg, (int)m, s, Xf, (int)d, T);
     // pass 2
-    const int kz = (int)((k + P2_QC - 1) / P2_QC * P2_QC + 4);
-    const size_t ms2 = std::max((size_t)d * P2_QC, (size_t)P2_QC * (P2_CC + 4));
-    const size_t sm2 = sizeof(float) * ((size_t)P2_RT * dpad + (size_t)P2_RT * kz + ms2);
-    if (sm2 > 48 * 1024)
-        if ((e = cudaFuncSetAttribute(k_bwd_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)
-            return e;
-    k_bwd_pass2<<<(unsigned)((n + P2_RT - 1) / P2_RT), 256, sm2, st>>>(A, lda, n, (int)d, Mfull, (int)k, w, T,
-                                                                       stream_key(seed, kStreamHash), (uint32_t)s,
-                                                                       identity ? 1 : 0, gradA);
+    const size_t sm2 = sizeof(float) * ((size_t)P2_R * P2_AS + (size_t)P2_J * P2_C);
+    if ((e = cudaFuncSetAttribute(k_bwd_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)
+        return e;
+    dim3 g2((unsigned)((n + P2_R - 1) / P2_R), (unsigned)((d + P2_C - 1) / P2_C));
+    k_bwd_pass2<<<g2, 256, sm2, st>>>(A, lda, n, (int)d, vecA, P, ldp, w, T, stream_key(seed, kStreamHash),
+                                      (uint32_t)s, identity ? 1 : 0, gradA);
     return cudaGetLastError();
 }
 
