@@ -144,6 +144,29 @@ __global__ void k_fill_unwritten(unsigned long long* R, int64_t count) {
 // for non-negative values; any positive value beats every non-positive one).
 __device__ __forceinline__ bool positive_finite(long long b) { return b > 0 && b < 0x7FF0000000000000LL; }
 
+// Order-preserving unsigned key of a double (larger value, larger key); 0 is below every value
+// and marks inactive entries.
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// 1/sqrt(x) for a positive finite x: an FP32 estimate of the exponent-reduced argument, then two
+// Newton-Raphson steps y <- y (3 - x y^2) / 2 in FP64 (the error squares each step: ~2^-22 to
+// ~2^-44 to FP64 rounding). Subnormal x takes CUDA's rsqrt.
+__device__ __forceinline__ double inv_sqrt_pos(double x) {
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF) - 1023;
+    if (E == -1023) return rsqrt(x);
+    const int h = E >> 1;                                               // x = m 2^(2h), m in [1, 4)
+    const double m = __longlong_as_double(b - ((long long)(2 * h) << 52));
+    double y = (double)rsqrtf((float)m);
+    y = __longlong_as_double(__double_as_longlong(y) - ((long long)h << 52));   // y ~ 1/sqrt(x)
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    y = y * fma(-0.5 * x, y * y, 1.5);
+    return y;
+}
+
 __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict__ Gm, int d, int m, double tau,
                                                        const int32_t* __restrict__ forced, int forced_rank,
                                                        double* __restrict__ U, double* __restrict__ Rorig,
@@ -157,10 +180,14 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     double* rbuf = ubuf + d;                                      // d: row j of R
     double* diag = rbuf + d;                                      // d: replicated Schur diagonal
     int* active = reinterpret_cast<int*>(diag + d);               // d
-    __shared__ long long red_b[8];
+    __shared__ unsigned long long red_k[8];
     __shared__ int red_i[8];
     __shared__ volatile int s_abort;
-    __shared__ double s_inv, s_rjj;
+    __shared__ double s_inv;
+    // steps whose pivot this CTA owns, by local column: the step and the pivot's Schur diagonal
+    // (the diagonal entries of R, sqrt of those, are written after the loop)
+    __shared__ int own_j[32];
+    __shared__ double own_bv[32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     for (int lc = 0; lc < ncl; ++lc) {
         const double* src = Gm + (int64_t)(lc * G + me) * d;     // column = row (symmetric)
@@ -170,32 +197,32 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         active[i] = 1;
         diag[i] = Gm[(int64_t)i * d + i];
     }
+    for (int lc = tid; lc < 32; lc += 256) own_j[lc] = -1;
     if (tid == 0) s_abort = 0;
     __syncthreads();
-    // largest active diagonal entry, ties to the lowest index; one barrier, then every
-    // thread reduces the eight warp results itself
+    // largest active diagonal entry, ties to the lowest index: per thread over its own indices,
+    // per warp by three redux operations (max of the key's high and low words, min index among
+    // the maxima), one barrier, then every thread reduces the eight warp results itself
     auto pick = [&]() -> int {
-        long long bb = LLONG_MIN;
+        unsigned long long bk = 0;
         int bi = INT_MAX;
         for (int i = tid; i < d; i += 256)
             if (active[i]) {
-                const long long v = __double_as_longlong(diag[i]);
-                if (v > bb || (v == bb && i < bi)) { bb = v; bi = i; }
+                const unsigned long long k = order_key(diag[i]);
+                if (k > bk) { bk = k; bi = i; }                       // i increases: ties keep the lowest
             }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long ov = __shfl_xor_sync(0xffffffffu, bb, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > bb || (ov == bb && oi < bi)) { bb = ov; bi = oi; }
-        }
-        if (lane == 0) { red_b[wid] = bb; red_i[wid] = bi; }
+        const unsigned hi = (unsigned)(bk >> 32), lo = (unsigned)bk;
+        const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+        const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+        const unsigned mi = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? (unsigned)bi : 0xffffffffu);
+        if (lane == 0) { red_k[wid] = ((unsigned long long)mh << 32) | ml; red_i[wid] = (int)mi; }
         __syncthreads();
-        bb = red_b[0];
+        bk = red_k[0];
         bi = red_i[0];
 #pragma unroll
         for (int w = 1; w < 8; ++w)
-            if (red_b[w] > bb || (red_b[w] == bb && red_i[w] < bi)) { bb = red_b[w]; bi = red_i[w]; }
-        return bi;
+            if (red_k[w] > bk || (red_k[w] == bk && red_i[w] < bi)) { bk = red_k[w]; bi = red_i[w]; }
+        return bk == 0 ? INT_MAX : bi;
     };
     // rank test on the pivot's squared trailing norm: stop at a non-positive pivot, or
     // (unforced) at s_pp <= tau^2 s_00; evaluated identically by every thread
@@ -224,10 +251,8 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
                     st_relaxed_gpu_f64(U + i, col[i]);
                 }
         }
-        if (tid == 0) {
-            s_inv = rsqrt(diag[p]);
-            s_rjj = sqrt(diag[p]);
-        }
+        if (tid == 0) s_inv = inv_sqrt_pos(diag[p]);
+        if (tid == 0 && p % G == me) { own_j[p / G] = 0; own_bv[p / G] = diag[p]; }
         __syncthreads();
     }
     for (; go && j < steps; ++j) {
@@ -266,12 +291,8 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         }
         if (owner) {
             double* row = Rorig + (int64_t)j * d;
-            const double rjj = s_rjj;
             for (int i = tid; i < d; i += 256)
-                if (i == p)
-                    row[i] = rjj;
-                else if (active[i])
-                    row[i] = rbuf[i];
+                if (i != p && active[i]) row[i] = rbuf[i];
         }
         if (me == 0 && tid == 0) piv[j] = p;
         // 2. the next pivot and its rank test (one barrier)
@@ -299,10 +320,10 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
                     }
                 }
         }
-        // 4. the next step's scale factors (every CTA, while the row travels)
+        // 4. the next step's scale factor (every CTA, while the row travels)
         if (go_on && tid == 0) {
-            s_inv = rsqrt(diag[pn]);
-            s_rjj = sqrt(diag[pn]);
+            s_inv = inv_sqrt_pos(diag[pn]);
+            if (pn % G == me) { own_j[pn / G] = j + 1; own_bv[pn / G] = diag[pn]; }
         }
         // 5. the other own columns
         for (int lc = 0; lc < ncl; ++lc) {
@@ -317,6 +338,10 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         if (!go_on) { ++j; break; }
         p = pn;
     }
+    // R_jj = sqrt(s_pp) for the steps this CTA owned (steps at or beyond the rank were never taken)
+    __syncthreads();
+    for (int lc = tid; lc < ncl; lc += 256)
+        if (own_j[lc] >= 0 && own_j[lc] < j) Rorig[(int64_t)own_j[lc] * d + lc * G + me] = sqrt(own_bv[lc]);
     if (me == 0 && tid == 0) *rank_out = j;
 }
 
@@ -353,6 +378,7 @@ cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int pgrid = sms < (int)d ? sms : (int)d;
     const size_t ncl = ((size_t)d + pgrid - 1) / pgrid;
+    if (ncl > 32) return cudaErrorInvalidConfiguration;          // per-CTA bookkeeping holds 32 columns
     const size_t smem = sizeof(double) * (ncl * d + 3 * (size_t)d) + sizeof(int) * (size_t)d + 64;
     if ((e = cudaFuncSetAttribute(k_pchol_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
