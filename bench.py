@@ -219,7 +219,12 @@ def main():
     p = params(args.final_prec)
     theta = torch.empty(n, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    kernels_per_step = 11 if args.final_prec == "fp32" else 12
+    # kernels of one lev_estimate_dense step with the bucket permutation, G and Omega cached:
+    # CountSketch, then the Gaussian stage (split-K SGEMM + reduce, or operand transpose + tcgen05
+    # GEMM + reduce), Gram + reduce + row fill + pivoted Cholesky + two assembly kernels, the scaled
+    # transpose and the solve of the omega factor, and the final pass (plus its operand packing)
+    kernels_per_step = (1 + (2 if args.sketch_prec == "fp32" else 3) + 6 + 2
+                        + (1 if args.final_prec == "fp32" else 2))
 
     rank_found = L.lev_estimate_dense(h, A, p, theta)          # also generates and caches G
     for _ in range(args.warmup):

@@ -16,8 +16,9 @@
  *    failing call on the calling thread.
  *  - Ownership: every array is owned by the caller. Device pointers are plain
  *    CUDA device pointers. The handle owns its scratch memory (grown on demand
- *    with cudaMalloc) and a cache of the Gaussian sketch matrix G per
- *    (seed, m, s, precision).
+ *    with cudaMalloc), a cache of the Gaussian sketch matrix G per
+ *    (seed, m, s, precision) and of the CountSketch bucket permutation per
+ *    (seed, n, s).
  *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream). Work is enqueued on it; a call returns before the work finishes
  *    unless it writes a host-side result (rank), in which case it synchronises

@@ -64,6 +64,16 @@ struct lev_handle {
     Buf count, off, tmp, perm_rows, B, partial, Atilde, qr, R, perm_d, Mfull, stageTheta,
         tc_ws, tc_ws2, csr_rp, csr_col, csr_val, bwd;
     GCache g;
+    // the CountSketch bucket permutation (off, perm_rows) of the last (seed, n, s), and an event
+    // recorded after it was built so that a call on another stream waits for it
+    uint64_t perm_seed = 0;
+    int64_t perm_n = -1, perm_s = -1;
+    cudaEvent_t ev_perm = nullptr;
+    // Omega (d x k FP64) of the last (seed, d, k), with its event, and the R_11 scratch of the solve
+    Buf omega, omega_rs;
+    uint64_t omega_seed = 0;
+    int64_t omega_d = -1, omega_k = -1;
+    cudaEvent_t ev_omega = nullptr;
     // host A of lev_estimate_dense: two stage buffers filled by a copy stream of the handle
     Buf stageA[2];
     cudaStream_t copy_st = nullptr;
@@ -216,19 +226,68 @@ int gaussian_stage(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t 
     return lev::tc_gaussian_stage(h, B, m, s, d, seed, prec, Atilde, st);
 }
 
+// The rows of each bucket in increasing order (off: s+1 bucket offsets, perm_rows: n rows). It
+// depends on (seed, n, s) only, so the handle keeps the last one and rebuilds it only when one of
+// those (or the buffers) changes.
+int bucket_perm(lev_handle* h, int64_t n, int64_t s, uint64_t seed, cudaStream_t st) {
+    const void* off0 = h->off.ptr;
+    const void* perm0 = h->perm_rows.ptr;
+    LEV_TRY(ensure(h->count, sizeof(int) * (size_t)(s + 1)));
+    LEV_TRY(ensure(h->off, sizeof(int) * (size_t)(s + 1)));
+    LEV_TRY(ensure(h->tmp, sizeof(uint32_t) * (size_t)n));
+    LEV_TRY(ensure(h->perm_rows, sizeof(uint32_t) * (size_t)n));
+    if (!h->ev_perm) LEV_CUDA(cudaEventCreateWithFlags(&h->ev_perm, cudaEventDisableTiming));
+    if (h->perm_n == n && h->perm_s == s && h->perm_seed == seed && h->off.ptr == off0 && h->perm_rows.ptr == perm0) {
+        LEV_CUDA(cudaStreamWaitEvent(st, h->ev_perm, 0));
+        return LEV_OK;
+    }
+    h->perm_n = -1;
+    LEV_CUDA(lev::launch_bucket_perm(n, s, seed, (int*)h->count.ptr, (int*)h->off.ptr, (uint32_t*)h->tmp.ptr,
+                                     (uint32_t*)h->perm_rows.ptr, st));
+    LEV_CUDA(cudaEventRecord(h->ev_perm, st));
+    h->perm_seed = seed;
+    h->perm_n = n;
+    h->perm_s = s;
+    return LEV_OK;
+}
+
+// M = R_11^{-1} Omega into Mfull through the handle's Omega cache (drawn once per (seed, d, k)).
+int omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int64_t* d_rank, int64_t d, int64_t k,
+                 uint64_t seed, bool identity, float* Mfull, cudaStream_t st) {
+    const double* Om = nullptr;
+    if (!identity && d <= 1024) {
+        const void* p0 = h->omega.ptr;
+        LEV_TRY(ensure(h->omega, sizeof(double) * (size_t)d * k));
+        if (!h->ev_omega) LEV_CUDA(cudaEventCreateWithFlags(&h->ev_omega, cudaEventDisableTiming));
+        if (h->omega_seed == seed && h->omega_d == d && h->omega_k == k && h->omega.ptr == p0) {
+            LEV_CUDA(cudaStreamWaitEvent(st, h->ev_omega, 0));
+        } else {
+            h->omega_d = -1;
+            LEV_CUDA(lev::launch_gen_omega(seed, d, k, (double*)h->omega.ptr, st));
+            LEV_CUDA(cudaEventRecord(h->ev_omega, st));
+            h->omega_seed = seed;
+            h->omega_d = d;
+            h->omega_k = k;
+        }
+        Om = (const double*)h->omega.ptr;
+    }
+    double* Rs = nullptr;
+    if (d <= 1024) {
+        LEV_TRY(ensure(h->omega_rs, sizeof(double) * (size_t)d * d));
+        Rs = (double*)h->omega_rs.ptr;
+    }
+    LEV_CUDA(lev::launch_omega_factor(R, perm, d_rank, d, k, seed, identity, Om, Rs, Mfull, st));
+    return LEV_OK;
+}
+
 int sketch_common_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
                         const lev_params* p, const Sizes& z, float* Atilde, cudaStream_t st) {
     if (p->flags & LEV_SKETCH_IDENTITY) {
         LEV_CUDA(lev::launch_copy_dense(A, lda, n, d, Atilde, st));
         return LEV_OK;
     }
-    LEV_TRY(ensure(h->count, sizeof(int) * (size_t)(z.s + 1)));
-    LEV_TRY(ensure(h->off, sizeof(int) * (size_t)(z.s + 1)));
-    LEV_TRY(ensure(h->tmp, sizeof(uint32_t) * (size_t)n));
-    LEV_TRY(ensure(h->perm_rows, sizeof(uint32_t) * (size_t)n));
+    LEV_TRY(bucket_perm(h, n, z.s, p->seed, st));
     LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
-    LEV_CUDA(lev::launch_bucket_perm(n, z.s, p->seed, (int*)h->count.ptr, (int*)h->off.ptr,
-                                     (uint32_t*)h->tmp.ptr, (uint32_t*)h->perm_rows.ptr, st));
     LEV_CUDA(lev::launch_countsketch_dense(A, lda, d, z.s, (const int*)h->off.ptr,
                                            (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));
     return gaussian_stage(h, (const float*)h->B.ptr, z.m, z.s, d, p->seed, p->sketch_prec, Atilde, st);
@@ -238,13 +297,8 @@ int sketch_common_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col,
                       int64_t n, int64_t d, const lev_params* p, const Sizes& z, float* Atilde,
                       cudaStream_t st) {
     if (p->flags & LEV_SKETCH_IDENTITY) return fail(LEV_EINVAL, "LEV_SKETCH_IDENTITY is for dense A only");
-    LEV_TRY(ensure(h->count, sizeof(int) * (size_t)(z.s + 1)));
-    LEV_TRY(ensure(h->off, sizeof(int) * (size_t)(z.s + 1)));
-    LEV_TRY(ensure(h->tmp, sizeof(uint32_t) * (size_t)n));
-    LEV_TRY(ensure(h->perm_rows, sizeof(uint32_t) * (size_t)n));
+    LEV_TRY(bucket_perm(h, n, z.s, p->seed, st));
     LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
-    LEV_CUDA(lev::launch_bucket_perm(n, z.s, p->seed, (int*)h->count.ptr, (int*)h->off.ptr,
-                                     (uint32_t*)h->tmp.ptr, (uint32_t*)h->perm_rows.ptr, st));
     LEV_CUDA(lev::launch_countsketch_csr(row_ptr, col, val, d, z.s, (const int*)h->off.ptr,
                                          (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));
     return gaussian_stage(h, (const float*)h->B.ptr, z.m, z.s, d, p->seed, p->sketch_prec, Atilde, st);
@@ -357,13 +411,15 @@ int lev_destroy(lev_handle* h) {
     cudaDeviceSynchronize();
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
                   &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
-                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val};
+                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs};
     for (Buf* b : all) release(*b);
     for (int i = 0; i < 2; ++i) {
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
         if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
     }
     if (h->copy_st) cudaStreamDestroy(h->copy_st);
+    if (h->ev_perm) cudaEventDestroy(h->ev_perm);
+    if (h->ev_omega) cudaEventDestroy(h->ev_omega);
     if (h->g.ptr) cudaFree(h->g.ptr);
     if (h->status) cudaFree(h->status);
     if (h->host_rank) cudaFreeHost(h->host_rank);
@@ -418,9 +474,8 @@ int lev_omega_factor(lev_handle* h, const double* R, const int32_t* perm, const 
     LEV_TRY(set_device(h));
     if (!R || !perm || !d_rank || !Mfull) return fail(LEV_EINVAL, "NULL array");
     if (d < 1 || d > 4096 || k < 1 || k > 4096) return fail(LEV_EINVAL, "bad shape d=%lld k=%lld", (long long)d, (long long)k);
-    LEV_CUDA(lev::launch_omega_factor(R, perm, d_rank, d, k, seed, (flags & LEV_OMEGA_IDENTITY) != 0, nullptr,
-                                      Mfull, (cudaStream_t)stream));
-    return LEV_OK;
+    return omega_factor(h, R, perm, d_rank, d, k, seed, (flags & LEV_OMEGA_IDENTITY) != 0, Mfull,
+                        (cudaStream_t)stream);
 }
 
 int lev_final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const float* Mfull,
@@ -458,8 +513,8 @@ static int estimate_tail(lev_handle* h, const Sizes& z, int64_t d, const lev_par
     if (perm != (int32_t*)h->perm_d.ptr)
         LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
     LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * z.k));
-    LEV_CUDA(lev::launch_omega_factor((const double*)h->R.ptr, perm, qs->rank, d, z.k, p->seed,
-                                      (p->flags & LEV_OMEGA_IDENTITY) != 0, nullptr, (float*)h->Mfull.ptr, st));
+    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, qs->rank, d, z.k, p->seed,
+                         (p->flags & LEV_OMEGA_IDENTITY) != 0, (float*)h->Mfull.ptr, st));
     return LEV_OK;
 }
 

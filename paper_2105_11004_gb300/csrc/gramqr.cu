@@ -347,13 +347,33 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
 
 }  // namespace
 
+// Row splits of the Gram product. The FP64 pipe of an SM is shared by its resident CTAs, so the
+// SM with the most CTAs sets the time: take the split count whose CTA total fills its last wave
+// over the SMs best (the largest such count within 1%), with the FP64 partials held to 4 MB.
 int gram_splits(int64_t m, int64_t d) {
-    const int T = gram_tiles((int)d);
-    const int64_t blocks = (m + GT - 1) / GT;
-    int64_t s = (2 * 152 + T - 1) / T;
-    if (s > blocks) s = blocks;
-    if (s < 1) s = 1;
-    return (int)s;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms < 1)
+            sms = 152;
+    }
+    const int64_t T = gram_tiles((int)d);
+    const int64_t blocks = (m + 15) / 16;
+    int64_t cap = ((int64_t)4 << 20) / (T * GT * GT * (int64_t)sizeof(double));
+    if (cap > blocks) cap = blocks;
+    if (cap < 1) cap = 1;
+    int64_t best = 1;
+    double best_eff = -1.0;
+    for (int64_t sp = 1; sp <= cap; ++sp) {
+        const int64_t ctas = T * sp, waves = (ctas + sms - 1) / sms;
+        const double eff = (double)ctas / ((double)sms * (double)waves);
+        if (eff > best_eff + 0.01 || eff >= best_eff - 0.01) {
+            if (eff > best_eff) best_eff = eff;
+            best = sp;
+        }
+    }
+    return (int)best;
 }
 
 size_t gram_partial_doubles(int64_t m, int64_t d) {
@@ -364,8 +384,7 @@ cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t
                                          const int32_t* forced, int64_t forced_rank, const QrScratch& q,
                                          int32_t* status, cudaStream_t st) {
     const int splits = gram_splits(m, d);
-    int64_t blocks_rows = (m + GT - 1) / GT;
-    const int rows_per_split = (int)(((blocks_rows + splits - 1) / splits) * GT);
+    const int rows_per_split = (int)(((m + splits - 1) / splits + 15) / 16 * 16);
     dim3 grid((unsigned)gram_tiles((int)d), (unsigned)splits);
     k_gram_fp64<<<grid, 256, 0, st>>>(Atilde, (int)m, (int)d, rows_per_split, q.Gp);
     k_gram_reduce<<<152 * 4, 256, 0, st>>>(q.Gp, (int)d, splits, q.G);

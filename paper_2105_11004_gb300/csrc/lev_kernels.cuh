@@ -71,10 +71,14 @@ cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double 
                               const QrScratch& q, int32_t* perm, double* R, int32_t* status,
                               int num_sms, cudaStream_t st);
 
-// Mfull (d x k FP32) = scatter of R_11^{-1} Omega by perm; reads r from d_rank.
+// Mfull (d x k FP32) = scatter of R_11^{-1} Omega by perm; reads r from d_rank. Omega: d x k FP64
+// from launch_gen_omega (unused with omega_identity); Rs: d x d FP64 scratch. With d > 1024 or
+// without Rs the one-warp-per-column kernel runs and draws Omega itself.
 cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int64_t* d_rank,
                                 int64_t d, int64_t k, uint64_t seed, bool omega_identity,
-                                double* Mscratch, float* Mfull, cudaStream_t st);
+                                const double* Omega, double* Rs, float* Mfull, cudaStream_t st);
+// Omega (d x k FP64) of stream 3 of seed, every pivot position p < d.
+cudaError_t launch_gen_omega(uint64_t seed, int64_t d, int64_t k, double* Omega, cudaStream_t st);
 
 // ---- backward.cu: gradient of sum_i w_i theta~_i ----
 

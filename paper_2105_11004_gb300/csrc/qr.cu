@@ -271,6 +271,64 @@ __global__ void k_omega_factor(const double* __restrict__ R, const int32_t* __re
     for (int p = lane; p < r; p += 32) Mfull[(int64_t)perm[p] * k + q] = (float)Ms[p];
 }
 
+// Omega (d x k FP64): entry (p, q) = N(0,1)/sqrt(k) from stream 3 at counter p k + q, for every pivot
+// position p < d (a call with rank r uses rows 0..r-1). Grid-wide; the handle caches the result.
+__global__ void k_gen_omega(uint64_t key, int d, int k, double inv_sqrt_k, double* __restrict__ Om) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)d * k;
+         e += (int64_t)gridDim.x * blockDim.x)
+        Om[e] = box_muller(key, (uint64_t)e) * inv_sqrt_k;
+}
+
+// Rs (d x d FP64): Rs[j][i] = R[i][j] / R[i][i] for i < j < r, the strictly upper part of R_11
+// scaled to a unit diagonal and transposed, so that step j of the substitution reads row j.
+__global__ void k_scaled_transpose(const double* __restrict__ R, const int64_t* __restrict__ d_rank, int d,
+                                   double* __restrict__ Rs) {
+    const int r = (int)min(max(*d_rank, (int64_t)0), (int64_t)d);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)r * r;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / r), i = (int)(e % r);
+        if (i < j) Rs[(int64_t)j * d + i] = R[(int64_t)i * d + j] / R[(int64_t)i * d + i];
+    }
+}
+
+// M = R_11^{-1} Omega column by column, one CTA per column q and one thread per row i (r <= 1024):
+// with the unit-diagonal form x_i = w_i / R_ii - sum_{j > i} (R_ij / R_ii) x_j, step j (from the
+// bottom) publishes x_j through shared memory (double-buffered by step parity, one barrier per
+// step) and every thread i < j subtracts Rs[j][i] x_j. The coefficients of the next four steps
+// are loaded ahead. Row i of M goes to row perm[i] of Mfull.
+constexpr int OMEGA_PF = 4;
+__global__ void __launch_bounds__(1024) k_omega_solve(const double* __restrict__ R, const double* __restrict__ Rs,
+                                                      const double* __restrict__ Om, const int32_t* __restrict__ perm,
+                                                      const int64_t* __restrict__ d_rank, int d, int k, int identity,
+                                                      float* __restrict__ Mfull) {
+    __shared__ double xs[2];
+    const int q = blockIdx.x, i = threadIdx.x;
+    const int r = (int)min(max(*d_rank, (int64_t)0), (int64_t)d);
+    double x = 0.0;
+    if (i < r) {
+        const double w = identity ? (i == q ? 1.0 : 0.0) : Om[(int64_t)i * k + q];
+        x = w / R[(int64_t)i * d + i];
+    }
+    // ring of coefficients: c[t] holds Rs[j - t][i] for the current step j
+    double c[OMEGA_PF];
+#pragma unroll
+    for (int t = 0; t < OMEGA_PF; ++t) {
+        const int j = r - 1 - t;
+        c[t] = (j > i) ? Rs[(int64_t)j * d + i] : 0.0;
+    }
+    for (int j = r - 1; j >= 0; --j) {
+        const double cj = c[0];
+#pragma unroll
+        for (int t = 0; t + 1 < OMEGA_PF; ++t) c[t] = c[t + 1];
+        const int jn = j - OMEGA_PF;
+        c[OMEGA_PF - 1] = (jn > i) ? Rs[(int64_t)jn * d + i] : 0.0;
+        if (i == j) xs[j & 1] = x;
+        __syncthreads();
+        if (i < j) x = fma(-cj, xs[j & 1], x);
+    }
+    if (i < r) Mfull[(int64_t)perm[i] * k + q] = (float)x;
+}
+
 }  // namespace
 
 // The Gram route (one cooperative grid over the SMs) serves d <= kGramMaxD and
@@ -344,11 +402,29 @@ cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double 
     return cudaGetLastError();
 }
 
+cudaError_t launch_gen_omega(uint64_t seed, int64_t d, int64_t k, double* Omega, cudaStream_t st) {
+    const int64_t total = d * k;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 8) grid = 152 * 8;
+    if (grid < 1) grid = 1;
+    k_gen_omega<<<grid, 256, 0, st>>>(stream_key(seed, kStreamOmega), (int)d, (int)k, 1.0 / sqrt((double)k), Omega);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int64_t* d_rank,
                                 int64_t d, int64_t k, uint64_t seed, bool omega_identity,
-                                double* /*Mscratch*/, float* Mfull, cudaStream_t st) {
+                                const double* Omega, double* Rs, float* Mfull, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(Mfull, 0, sizeof(float) * (size_t)(d * k), st);
     if (e != cudaSuccess) return e;
+    if (d <= 1024 && Rs && (Omega || omega_identity)) {
+        int grid = (int)((d * d + 255) / 256);
+        if (grid > 152 * 8) grid = 152 * 8;
+        k_scaled_transpose<<<grid, 256, 0, st>>>(R, d_rank, (int)d, Rs);
+        const int threads = (int)((d + 31) / 32 * 32);
+        k_omega_solve<<<(unsigned)k, threads, 0, st>>>(R, Rs, Omega, perm, d_rank, (int)d, (int)k,
+                                                       omega_identity ? 1 : 0, Mfull);
+        return cudaGetLastError();
+    }
     const int warps = 1;                              // spread the FP64 work over the SMs
     const size_t smem = sizeof(double) * (size_t)d * warps;
     if (smem > 48 * 1024) {
@@ -360,7 +436,6 @@ cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int6
                                                    1.0 / sqrt((double)k), omega_identity ? 1 : 0, Mfull);
     return cudaGetLastError();
 }
-
 
 // ---------------------------------------------------------------------------
 // lev_rrqr_noalloc: the same pivoted QR with its scratch in a fixed device array.

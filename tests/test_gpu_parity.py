@@ -188,6 +188,42 @@ def test_omega_factor_parity(L, h, k, identity):
     assert np.all(got[gp[rank:]] == 0)
 
 
+@pytest.mark.parametrize("d,r,k", [(1024, 1000, 24), (1100, 1050, 8)])
+def test_omega_factor_wide(L, h, d, r, k):
+    """d = 1024 (the row-parallel solve at its 1024-thread limit) and d > 1024 (the one-warp-per-
+    column kernel): a synthetic upper-triangular R with a dominant diagonal, a random pivot order."""
+    import torch
+    rs = np.random.default_rng(d)
+    R = np.triu(rs.standard_normal((d, d)) * 0.05) + np.diag(1.0 + rs.random(d))
+    gp = rs.permutation(d).astype(np.int32)
+    Mf = torch.empty((d, k), dtype=torch.float32, device="cuda")
+    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
+    L.lev_omega_factor(h, to_dev(R), to_dev(gp), d_rank, d, k, 21, 0, Mf)
+    torch.cuda.synchronize()
+    want = E.m_full(E.omega_factor(R[:r, :r], k, 21), gp, d)
+    got = to_np(Mf).astype(np.float64)
+    assert np.max(np.abs(got - want)) <= 1e-6 * np.max(np.abs(want))
+    assert np.all(got[gp[r:]] == 0)
+
+
+def test_omega_cache_follows_seed_and_shape(L, h):
+    """The handle's Omega cache is keyed by (seed, d, k): alternating seeds and k give the oracle's
+    M every time."""
+    import torch
+    rs = np.random.default_rng(3)
+    d, r = 48, 40
+    R = np.triu(rs.standard_normal((d, d)) * 0.1) + np.diag(1.0 + rs.random(d))
+    gp = np.arange(d, dtype=np.int32)
+    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
+    for seed, k in [(13, 16), (14, 16), (13, 16), (13, 24)]:
+        Mf = torch.empty((d, k), dtype=torch.float32, device="cuda")
+        L.lev_omega_factor(h, to_dev(R), to_dev(gp), d_rank, d, k, seed, 0, Mf)
+        torch.cuda.synchronize()
+        want = E.m_full(E.omega_factor(R[:r, :r], k, seed), gp, d)
+        got = to_np(Mf).astype(np.float64)
+        assert np.max(np.abs(got - want)) <= 1e-6 * np.max(np.abs(want))
+
+
 # ---------------------------------------------------------------- final pass
 
 @pytest.mark.parametrize("n,d,k,lda", [(10007, 256, 256, 256), (999, 37, 100, 37), (5000, 64, 512, 80),
