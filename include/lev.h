@@ -228,6 +228,17 @@ int lev_device_status(lev_handle* h, int32_t* status);
  * so calls that overlap on the GPU (different streams, or different host
  * threads) race and give wrong results. Errors: LEV_EINVAL, LEV_ECUDA,
  * LEV_ETIMEOUT, LEV_ERANK0. */
+/* Diagnostics (no counterpart in the paper). With timing on (enable != 0) every pivoted QR of
+ * the handle (lev_rrqr and the rrqr stage of lev_estimate_*) records CUDA events on its stream
+ * before the factorisation, after the Gram product with its reduction (Gram route; nothing
+ * runs before the factorisation kernel on the Householder route) and after the factorisation
+ * kernel (the grid pivoted Cholesky, or the Householder kernel). lev_rrqr_timing waits for the
+ * events of the last such call and returns the two durations in milliseconds; either output
+ * pointer may be NULL. Errors: LEV_EINVAL (timing off, or no QR since it was enabled),
+ * LEV_ECUDA. */
+int lev_set_timing(lev_handle* h, int enable);
+int lev_rrqr_timing(lev_handle* h, float* gram_ms, float* factor_ms);
+
 int lev_rrqr_noalloc(const float* Atilde, int64_t m, int64_t d, double tau,
                      int32_t* perm, double* R, int64_t* rank, void* stream);
 

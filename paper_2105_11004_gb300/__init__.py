@@ -60,6 +60,8 @@ SIGNATURES = {
                                           _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p, _c_void_p,
                                           _c_void_p]),
     "lev_device_status": (ctypes.c_int, [_c_void_p, _P(_i32)]),
+    "lev_set_timing": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
+    "lev_rrqr_timing": (ctypes.c_int, [_c_void_p, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
 }
 
@@ -230,6 +232,17 @@ def lev_rrqr_noalloc(Atilde, tau, perm, R, stream=None) -> int:
     rc = _check(lib.lev_rrqr_noalloc(_ptr(Atilde), m, d, float(tau), _ptr(perm), _ptr(R), ctypes.byref(r),
                                      _stream(stream)), allow=(LEV_ERANK0,))
     return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_set_timing(h: Handle, enable: bool = True):
+    _check(lib.lev_set_timing(h.ptr, 1 if enable else 0))
+
+
+def lev_rrqr_timing(h: Handle):
+    """(gram_ms, factor_ms) of the last pivoted QR on h since lev_set_timing(h, True)."""
+    g, f = ctypes.c_float(), ctypes.c_float()
+    _check(lib.lev_rrqr_timing(h.ptr, ctypes.byref(g), ctypes.byref(f)))
+    return g.value, f.value
 
 
 def lev_device_status(h: Handle) -> int:

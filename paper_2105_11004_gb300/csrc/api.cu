@@ -66,6 +66,9 @@ struct lev_handle {
     GCache g;
     // the CountSketch bucket permutation (off, perm_rows) of the last (seed, n, s), and an event
     // recorded after it was built so that a call on another stream waits for it
+    // diagnostics: events around the Gram product and the factorisation of the last rrqr
+    bool timing = false, timed_once = false;
+    cudaEvent_t tmark[3] = {nullptr, nullptr, nullptr};
     uint64_t perm_seed = 0;
     int64_t perm_n = -1, perm_s = -1;
     cudaEvent_t ev_perm = nullptr;
@@ -310,7 +313,8 @@ int rrqr_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double
     LEV_TRY(ensure(h->qr, lev::qr_scratch_bytes(m, d)));
     lev::qr_scratch_carve(h->qr.ptr, m, d, qs);
     LEV_CUDA(lev::launch_pivoted_qr(Atilde, m, d, tau, forced, forced_rank, *qs, perm, R, h->status,
-                                    h->num_sms, st));
+                                    h->num_sms, st, h->timing ? h->tmark : nullptr));
+    if (h->timing) h->timed_once = true;
     return LEV_OK;
 }
 
@@ -419,11 +423,34 @@ int lev_destroy(lev_handle* h) {
     }
     if (h->copy_st) cudaStreamDestroy(h->copy_st);
     if (h->ev_perm) cudaEventDestroy(h->ev_perm);
+    for (int i = 0; i < 3; ++i)
+        if (h->tmark[i]) cudaEventDestroy(h->tmark[i]);
     if (h->ev_omega) cudaEventDestroy(h->ev_omega);
     if (h->g.ptr) cudaFree(h->g.ptr);
     if (h->status) cudaFree(h->status);
     if (h->host_rank) cudaFreeHost(h->host_rank);
     delete h;
+    return LEV_OK;
+}
+
+int lev_set_timing(lev_handle* h, int enable) {
+    LEV_TRY(set_device(h));
+    if (enable && !h->tmark[0])
+        for (int i = 0; i < 3; ++i) LEV_CUDA(cudaEventCreate(&h->tmark[i]));
+    h->timing = enable != 0;
+    h->timed_once = false;
+    return LEV_OK;
+}
+
+int lev_rrqr_timing(lev_handle* h, float* gram_ms, float* factor_ms) {
+    LEV_TRY(set_device(h));
+    if (!h->timing || !h->timed_once) return fail(LEV_EINVAL, "timing is off or no rrqr ran since it was enabled");
+    LEV_CUDA(cudaEventSynchronize(h->tmark[2]));
+    float a = 0.f, b = 0.f;
+    LEV_CUDA(cudaEventElapsedTime(&a, h->tmark[0], h->tmark[1]));
+    LEV_CUDA(cudaEventElapsedTime(&b, h->tmark[1], h->tmark[2]));
+    if (gram_ms) *gram_ms = a;
+    if (factor_ms) *factor_ms = b;
     return LEV_OK;
 }
 

@@ -382,7 +382,7 @@ size_t gram_partial_doubles(int64_t m, int64_t d) {
 
 cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t d, double tau,
                                          const int32_t* forced, int64_t forced_rank, const QrScratch& q,
-                                         int32_t* status, cudaStream_t st) {
+                                         int32_t* status, cudaStream_t st, cudaEvent_t after_gram) {
     const int splits = gram_splits(m, d);
     const int rows_per_split = (int)(((m + splits - 1) / splits + 15) / 16 * 16);
     dim3 grid((unsigned)gram_tiles((int)d), (unsigned)splits);
@@ -390,6 +390,7 @@ cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t
     k_gram_reduce<<<152 * 4, 256, 0, st>>>(q.Gp, (int)d, splits, q.G);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (after_gram && (e = cudaEventRecord(after_gram, st)) != cudaSuccess) return e;
 
     // cooperative grid over the SMs (one CTA per SM), own columns in shared memory
     int sms = 0, dev = 0;

@@ -60,16 +60,19 @@ int gram_splits(int64_t m, int64_t d);
 size_t gram_partial_doubles(int64_t m, int64_t d);
 cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t d, double tau,
                                          const int32_t* forced, int64_t forced_rank, const QrScratch& q,
-                                         int32_t* status, cudaStream_t st);
+                                         int32_t* status, cudaStream_t st, cudaEvent_t after_gram = nullptr);
 size_t qr_scratch_bytes(int64_t m, int64_t d);
 void qr_scratch_carve(void* base, int64_t m, int64_t d, QrScratch* q);
 
-// Pivoted QR of Atilde (m x d FP32 row-major). forced_perm may be null.
+// Pivoted QR of Atilde (m x d FP32 row-major). forced_perm may be null. marks (optional, three
+// events): recorded before the factorisation, after the Gram product (Gram route; at the start
+// on the Householder route) and after the factorisation kernel.
 // Writes perm (d), R (d x d row-major), d_rank. status: device status word.
 cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double tau,
                               const int32_t* forced_perm, int64_t forced_rank,
                               const QrScratch& q, int32_t* perm, double* R, int32_t* status,
-                              int num_sms, cudaStream_t st);
+                              int num_sms, cudaStream_t st,
+                              const cudaEvent_t* marks = nullptr);
 
 // Mfull (d x k FP32) = scatter of R_11^{-1} Omega by perm; reads r from d_rank. Omega: d x k FP64
 // from launch_gen_omega (unused with omega_identity); Rs: d x d FP64 scratch. With d > 1024 or

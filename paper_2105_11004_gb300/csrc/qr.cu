@@ -377,14 +377,17 @@ void qr_scratch_carve(void* base, int64_t m, int64_t d, QrScratch* q) {
 cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double tau,
                               const int32_t* forced_perm, int64_t forced_rank,
                               const QrScratch& q, int32_t* perm, double* R, int32_t* status,
-                              int num_sms, cudaStream_t st) {
+                              int num_sms, cudaStream_t st, const cudaEvent_t* marks) {
     cudaError_t e;
+    if (marks && (e = cudaEventRecord(marks[0], st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(q.barrier, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(q.Rorig, 0, sizeof(double) * (size_t)(d * d), st)) != cudaSuccess) return e;
     if (d <= kGramMaxD && (forced_perm || tau >= kGramMinTau)) {
-        e = launch_gram_pivoted_cholesky(Atilde, m, d, tau, forced_perm, forced_rank, q, status, st);
+        e = launch_gram_pivoted_cholesky(Atilde, m, d, tau, forced_perm, forced_rank, q, status, st,
+                                         marks ? marks[1] : nullptr);
         if (e != cudaSuccess) return e;
     } else {
+        if (marks && (e = cudaEventRecord(marks[1], st)) != cudaSuccess) return e;
         int occ = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pivoted_qr, QR_THREADS, 0)) != cudaSuccess)
             return e;
@@ -397,6 +400,7 @@ cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double 
                                         kargs, 0, st);
         if (e != cudaSuccess) return e;
     }
+    if (marks && (e = cudaEventRecord(marks[2], st)) != cudaSuccess) return e;
     k_assemble_perm<<<1, 1024, sizeof(int) * (size_t)d, st>>>(q, (int)d, perm);
     k_assemble_r<<<(unsigned)d, 256, 0, st>>>(q, (int)d, perm, R);
     return cudaGetLastError();

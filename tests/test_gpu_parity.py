@@ -443,6 +443,30 @@ def test_host_async_pipelined_calls(L, h):
     assert torch.equal(th, want[2])
 
 
+def test_rrqr_timing_diagnostics(L, h):
+    """lev_set_timing / lev_rrqr_timing: positive durations for both kernels of the Gram route,
+    gram 0-width on the Householder route, EINVAL when timing is off."""
+    import torch
+    At = to_dev(_rank_deficient_sketch(300, 64, 40, seed=1))
+    perm = torch.empty(64, dtype=torch.int32, device="cuda")
+    R = torch.empty((64, 64), dtype=torch.float64, device="cuda")
+    L.lev_set_timing(h, True)
+    try:
+        with pytest.raises(L.LevError):
+            L.lev_rrqr_timing(h)                          # no QR since timing was enabled
+        assert L.lev_rrqr(h, At, 1e-5, perm, R) == 40
+        g_ms, f_ms = L.lev_rrqr_timing(h)
+        assert g_ms > 0 and f_ms > 0
+        assert L.lev_rrqr(h, At, 1e-9, perm, R) >= 40     # tau < 1e-6: Householder route (FP32 noise ranks)
+        g_ms, f_ms = L.lev_rrqr_timing(h)
+        assert g_ms >= 0 and f_ms > 0
+    finally:
+        L.lev_set_timing(h, False)
+    with pytest.raises(L.LevError) as e:
+        L.lev_rrqr_timing(h)
+    assert e.value.code == L.LEV_EINVAL
+
+
 def test_fresh_handle_first_call(L):
     """First call on a new handle: every scratch buffer is freshly allocated."""
     A = W.dense_gaussian(2000, 20, seed=0).astype(np.float32)
