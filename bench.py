@@ -47,7 +47,7 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms in a thread."""
+    """nvidia-smi clocks and throttle reasons sampled every 25 ms in a thread."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -57,7 +57,7 @@ class ClockSampler:
         self.proc = None
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "25",
                  "-i", str(device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -80,9 +80,9 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self, t0, t1):
-        sel = [p for (t, p) in self.samples if t0 - 0.25 <= t <= t1 + 0.25]
+        sel = [p for (t, p) in self.samples if t0 <= t <= t1]
         if not sel:
-            sel = [p for (_, p) in self.samples[-5:]]
+            sel = [p for (t, p) in self.samples if t0 - 0.1 <= t <= t1 + 0.1]
         if not sel:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         def num(x):
@@ -181,7 +181,7 @@ def qr_flops(m, d, r):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sketch-prec", default="bf16x3")
@@ -194,6 +194,9 @@ def main():
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR 8e6 x 1024 measurement")
     ap.add_argument("--csr-large", action="store_true", help="also measure the CSR 8e7 x 1024 (~1e9 nnz) workload")
+    ap.add_argument("--streams", type=int, default=3,
+                    help="batches in flight: step i runs on stream i mod S with its own handle, so one batch's "
+                         "latency-bound pivoted Cholesky overlaps another batch's HBM- and tensor-bound kernels")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     cfg = W.CONFIGS[WORKLOAD]
@@ -227,8 +230,17 @@ def main():
                         + (1 if args.final_prec == "fp32" else 2))
 
     rank_found = L.lev_estimate_dense(h, A, p, theta)          # also generates and caches G
-    for _ in range(args.warmup):
-        L.lev_estimate_dense(h, A, p, theta, want_rank=False)
+    # S batches in flight: handle i and stream i take steps i, i + S, ... (each handle holds its own
+    # scratch and caches; every step is the whole path on the whole batch)
+    S = max(1, args.streams)
+    hs = [h] + [L.Handle(local) for _ in range(S - 1)]
+    sts = [torch.cuda.Stream() for _ in range(S)]
+    ths = [theta] + [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(S - 1)]
+    for i in range(S):
+        L.lev_estimate_dense(hs[i], A, p, ths[i], stream=sts[i])   # caches of every handle
+    torch.cuda.synchronize()
+    for t in range(args.warmup):
+        L.lev_estimate_dense(hs[t % S], A, p, ths[t % S], want_rank=False, stream=sts[t % S])
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     time.sleep(0.3)
@@ -237,8 +249,12 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_wall0 = time.time()
     e0.record(stream)
-    for _ in range(args.steps):
-        L.lev_estimate_dense(h, A, p, theta, want_rank=False)
+    for st_ in sts:
+        st_.wait_stream(stream)
+    for t in range(args.steps):
+        L.lev_estimate_dense(hs[t % S], A, p, ths[t % S], want_rank=False, stream=sts[t % S])
+    for st_ in sts:
+        stream.wait_stream(st_)
     e1.record(stream)
     torch.cuda.synchronize()
     t_wall1 = time.time()
@@ -246,6 +262,7 @@ def main():
     ms = allmax(world, e0.elapsed_time(e1) / args.steps)
     clocks = sampler.summary(t_wall0, t_wall1)
     sampler.stop()
+    same_theta = all(torch.equal(ths[0], t_) for t_ in ths[1:])
 
     def time_steps(fn, reps):
         fn()
@@ -369,8 +386,12 @@ def main():
                       "k": cfg["k"], "tau": cfg["tau"], "sketch_prec": args.sketch_prec,
                       "final_prec": args.final_prec, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (A is 1.02 GB), no flush",
-                      "cached": "G (m x s) generated once per seed in the handle; all other stages every step"},
+                      "cached": "per handle: G (m x s) per seed, the bucket permutation per (seed, n, s), Omega "
+                                "per (seed, d, k); every stage of the path runs every step",
+                      "batches_in_flight": S},
            "rank_found": rank_found, "stages_ms": stages, "final_ms_by_form": final_ms, "forms": forms,
+           "ms_per_step_one_batch_in_flight": forms.get(args.final_prec, {}).get("ms_per_step"),
+           "theta_equal_across_streams": same_theta,
            "roofline": roof, "dominant_stage": dominant, "dominant_kernel": dominant_kernel,
            "kernel_ms": kernel_ms, "rooflines": rooflines,
            "roofline_final_pass": rooflines["final"],
