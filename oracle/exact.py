@@ -12,6 +12,10 @@ Two routes:
 * ``exact_leverage_gram``: Alg. 5 (Gram matrix A^T A formed as a sum of row
   outer products, Lemma 3; symmetric eigendecomposition; keep eigenvalues
   lambda_j > tau^2 lambda_max; theta_i = ||A_i V_k Lambda_k^{-1/2}||^2).
+
+And Alg. 7 (LS-HRN-exact), ``ls_hrn_exact``: the columns K and the rank k come
+from the pivoted QR of the CountGauss sketch (Alg. 4), then the exact scores of
+A_K by its Gram matrix (steps 4-6).
 """
 from __future__ import annotations
 
@@ -19,6 +23,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .linalg import pivoted_qr
+from .estimator import sketch
 
 
 def exact_leverage_qr(A: np.ndarray, tau: float):
@@ -63,3 +68,37 @@ def exact_leverage_gram(A, tau: float, block: int = 1 << 16):
         Y = (blk @ X) if sp.issparse(blk) else np.asarray(blk, dtype=np.float64) @ X
         theta[r0:r0 + block] = np.sum(np.asarray(Y) ** 2, axis=1)
     return theta, k
+
+
+def ls_hrn_exact(A, s: int, m: int, tau: float, seed: int, *, sketch_identity: bool = False,
+                 block: int = 1 << 16):
+    """Alg. 7 (LS-HRN-exact), FP64. Returns (theta, rank, perm).
+
+    Steps 1-3: K and k from the column-pivoted QR of the sketch A~ = G S A (Alg. 3 and 4, the
+    GEQP3-style pivoting and rank rule of Sec. 6; A~ = A when ``sketch_identity``); A_K = A P_k.
+    Step 4: B = A_K^T A_K as a sum of row outer products (Lemma 3).
+    Step 5: B = V Sigma^2 V^T (B is symmetric positive definite when the k columns are linearly
+    independent, so its SVD is its eigendecomposition).
+    Step 6: theta_i = ||e_i^T A_K V Sigma^{-1}||^2.
+    """
+    n, d = A.shape
+    if sketch_identity:
+        At = A.toarray() if sp.issparse(A) else np.array(A, dtype=np.float64)
+        At = At.astype(np.float64)
+    else:
+        At = sketch(A, s, m, seed)
+    qr = pivoted_qr(At, tau)
+    k = qr.rank
+    if k == 0:
+        return np.zeros(n), 0, qr.perm
+    K = np.asarray(qr.perm[:k])
+    A_K = A.tocsc()[:, K].tocsr() if sp.issparse(A) else np.asarray(A, dtype=np.float64)[:, K]
+    B = gram(A_K, block)
+    lam, V = np.linalg.eigh(B)
+    X = V / np.sqrt(lam)[None, :]
+    theta = np.empty(n)
+    for r0 in range(0, n, block):
+        blk = A_K[r0:r0 + block]
+        Y = (blk @ X) if sp.issparse(blk) else np.asarray(blk, dtype=np.float64) @ X
+        theta[r0:r0 + block] = np.sum(np.asarray(Y) ** 2, axis=1)
+    return theta, k, qr.perm
