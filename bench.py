@@ -192,6 +192,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-exact", action="store_true", help="skip the Alg. 7 (LS-HRN-exact) measurement")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR 8e6 x 1024 measurement")
     ap.add_argument("--csr-large", action="store_true", help="also measure the CSR 8e7 x 1024 (~1e9 nnz) workload")
     ap.add_argument("--streams", type=int, default=3,
@@ -396,6 +397,27 @@ def main():
            "kernel_ms": kernel_ms, "rooflines": rooflines,
            "roofline_final_pass": rooflines["final"],
            "clocks": clocks, "gpu_launches": kernels_per_step * args.steps}
+
+    # Alg. 7 (LS-HRN-exact) on the same batch: the sketch's QR selects K, the FP64 Gram matrix of A
+    # (2.1e10 FMA at n = 1e6, d = 256) gives B = A_K^T A_K, then its Cholesky and the final pass
+    if not args.no_exact:
+        pe = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
+                           sketch_prec=args.sketch_prec, final_prec=args.final_prec)
+        th_e = torch.empty(n, dtype=torch.float32, device="cuda")
+        r_e = L.lev_exact_dense(h, A, pe, th_e)
+        ex_ms = time_steps(lambda: L.lev_exact_dense(h, A, pe, th_e), 3)
+        # the Gram product of A alone: the QR of A itself runs it (timing marks of the library)
+        L.lev_set_timing(h, True)
+        pa = torch.empty(d, dtype=torch.int32, device="cuda")
+        Ra = torch.empty((d, d), dtype=torch.float64, device="cuda")
+        L.lev_rrqr(h, A, cfg["tau"], pa, Ra)
+        g_ms, _ = L.lev_rrqr_timing(h)
+        L.lev_set_timing(h, False)
+        gram_fma = n * d * (d + 32) / 2.0            # upper 32 x 32 tiles, diagonal tiles in full
+        out["exact"] = {"algorithm": "Alg. 7 (LS-HRN-exact), lev_exact_dense", "rank": r_e, "ms_per_call": ex_ms,
+                        "rows_per_s": n / (ex_ms * 1e-3), "gram_ms": g_ms,
+                        "gram_fp64_tflops": 2.0 * gram_fma / (g_ms * 1e-3) / 1e12, "fp64_peak_tflops": fp64_peak,
+                        "sketch_prec": args.sketch_prec, "final_prec": args.final_prec}
 
     # backward workload: dense 200,000 x 64, s = 16,384, m = 256, k = 128; forward = the four stages
     if not args.no_backward:

@@ -185,6 +185,22 @@ int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
                        const lev_params* p, float* theta, int64_t* rank, int32_t* perm,
                        void* stream);
 
+/* Alg. 7 (LS-HRN-exact) on dense A: the columns K and the rank k come from the
+ * pivoted QR of the CountGauss sketch (as in lev_estimate_dense, with p's sizes,
+ * tau, seed and sketch_prec); then B = A_K^T A_K in FP64 (Lemma 3: the Gram
+ * matrix of A, products of the FP32 entries exact, sums in FP64, restricted to K
+ * in pivot order), its Cholesky factor B = R^T R (step 5 asks for the SVD
+ * B = V Sigma^2 V^T; both give theta_i = a_K B^{-1} a_K^T, B being positive
+ * definite), and theta_i = ||A_{i,K} R^{-1}||^2 with the final pass of
+ * p->final_prec (tensor-core forms need d <= 256); d <= 1024. If the Cholesky meets a
+ * non-positive pivot before k steps, *rank is the number of steps taken.
+ * A, theta: device. perm: device d int32 or NULL (the pivots of the sketch's QR).
+ * rank: host, may be NULL; the call synchronises `stream` twice (after each
+ * factorisation). Errors: as lev_estimate_dense; LEV_ERANK0 sets theta to 0. */
+int lev_exact_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
+                    const lev_params* p, float* theta, int64_t* rank, int32_t* perm,
+                    void* stream);
+
 /* The whole estimator on CSR A (arrays as lev_sketch_csr, device or host). */
 int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
                      int64_t n, int64_t d, int64_t nnz, const lev_params* p,

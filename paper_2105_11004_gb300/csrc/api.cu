@@ -79,6 +79,8 @@ struct lev_handle {
     cudaEvent_t ev_omega = nullptr;
     // host A of lev_estimate_dense: two stage buffers filled by a copy stream of the handle
     Buf stageA[2];
+    Buf exact_gp;  // split partials of the Gram matrix of A (LS-HRN-exact)
+    Buf tc_pad;   // A copied with a 16-byte row stride when the caller's cannot feed TMA
     cudaStream_t copy_st = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
     bool used_once[2] = {false, false};
@@ -350,7 +352,7 @@ int final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda
 // ---------------------------------------------------------------------------
 namespace lev {
 int handle_scratch(lev_handle* h, int which, size_t bytes, void** out) {
-    Buf* b = which == 0 ? &h->tc_ws : (which == 1 ? &h->partial : &h->tc_ws2);
+    Buf* b = which == 0 ? &h->tc_ws : (which == 1 ? &h->partial : (which == 2 ? &h->tc_ws2 : &h->tc_pad));
     LEV_TRY(ensure(*b, bytes));
     *out = b->ptr;
     return LEV_OK;
@@ -415,7 +417,8 @@ int lev_destroy(lev_handle* h) {
     cudaDeviceSynchronize();
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
                   &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
-                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs};
+                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->tc_pad,
+                  &h->exact_gp};
     for (Buf* b : all) release(*b);
     for (int i = 0; i < 2; ++i) {
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
@@ -571,6 +574,64 @@ int stage_host_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_
     h->stage_next ^= 1;
     *slot = k;
     *dA = (const float*)h->stageA[k].ptr;
+    return LEV_OK;
+}
+
+int lev_exact_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const lev_params* p,
+                    float* theta, int64_t* rank, int32_t* perm_out, void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!A || !theta) return fail(LEV_EINVAL, "NULL array");
+    if (lda < d) return fail(LEV_EINVAL, "lda < d");
+    if (is_host_pointer(A) || is_host_pointer(theta)) return fail(LEV_EINVAL, "lev_exact_dense takes device arrays");
+    if (p->flags & (LEV_FORCE_PIVOTS | LEV_OMEGA_IDENTITY))
+        return fail(LEV_EINVAL, "lev_exact_dense takes neither forced pivots nor LEV_OMEGA_IDENTITY");
+    if (d > 1024) return fail(LEV_EINVAL, "lev_exact_dense needs d <= 1024 (the Gram route of the QR)");
+    if (p->final_prec != LEV_FP32 && d > 256)
+        return fail(LEV_EINVAL, "tensor-core final pass of lev_exact_dense needs d <= 256");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    LEV_TRY(check_prec(p->final_prec, "final"));
+    cudaStream_t st = (cudaStream_t)stream;
+    // steps 1-3 (Alg. 7): the columns K and the rank k from the pivoted QR of the CountGauss sketch
+    LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
+    LEV_TRY(sketch_common_dense(h, A, n, d, lda, p, z, (float*)h->Atilde.ptr, st));
+    LEV_TRY(ensure(h->R, sizeof(double) * (size_t)d * d));
+    LEV_TRY(ensure(h->perm_d, sizeof(int32_t) * (size_t)d));
+    int32_t* perm = perm_out ? perm_out : (int32_t*)h->perm_d.ptr;
+    lev::QrScratch qs;
+    LEV_TRY(rrqr_common(h, (const float*)h->Atilde.ptr, z.m, d, tau_of(p), nullptr, 0, perm, (double*)h->R.ptr, &qs,
+                        st));
+    int64_t k = 0;
+    int rc = finish(h, qs, &k, st);
+    if (rc == LEV_ERANK0) {
+        LEV_CUDA(cudaMemsetAsync(theta, 0, sizeof(float) * (size_t)n, st));
+        if (rank) *rank = 0;
+        return rc;
+    }
+    LEV_TRY(rc);
+    // step 4: B = A_K^T A_K, the Gram matrix of A in FP64 restricted to K in pivot order; step 5
+    // by its Cholesky factor B = R^T R (the pivoted Cholesky with the pivots of step 2 forced)
+    LEV_TRY(ensure(h->exact_gp, sizeof(double) * lev::gram_partial_doubles(n, d)));
+    lev::QrScratch q2 = qs;
+    q2.Gp = (double*)h->exact_gp.ptr;
+    LEV_CUDA(lev::launch_gram_fp64(A, lda, n, d, q2.Gp, q2.G, st));
+    LEV_CUDA(lev::launch_factor_gram(n, d, tau_of(p), perm, k, q2, perm, (double*)h->R.ptr, h->status, st));
+    int64_t k2 = 0;
+    rc = finish(h, q2, &k2, st);
+    if (rc == LEV_ERANK0) {
+        LEV_CUDA(cudaMemsetAsync(theta, 0, sizeof(float) * (size_t)n, st));
+        if (rank) *rank = 0;
+        return rc;
+    }
+    LEV_TRY(rc);
+    // step 6: theta_i = ||A_{i,K} R^{-1}||^2: M = R^{-1} (Omega = I) scattered into Mfull (d x d)
+    LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * d));
+    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, q2.rank, d, d, p->seed, true, (float*)h->Mfull.ptr, st));
+    if (perm != (int32_t*)h->perm_d.ptr)
+        LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
+    LEV_TRY(final_dense(h, A, n, d, lda, (const float*)h->Mfull.ptr, d, p->final_prec, theta, st));
+    if (rank) *rank = k2;
     return LEV_OK;
 }
 

@@ -45,7 +45,8 @@ __device__ inline void tile_coords(int t, int nt, int& bi, int& bj) {
     bj = bi + t;
 }
 
-__global__ void __launch_bounds__(256) k_gram_fp64(const float* __restrict__ At, int m, int d, int rows_per_split,
+__global__ void __launch_bounds__(256) k_gram_fp64(const float* __restrict__ At, int64_t lda, int m, int d,
+                                                   int rows_per_split,
                                                    double* __restrict__ Gp) {
     // 16 rows of the two column panels per stage, converted to FP64 once when staged
     __shared__ double As[16][GT];
@@ -64,8 +65,8 @@ __global__ void __launch_bounds__(256) k_gram_fp64(const float* __restrict__ At,
             const int r = e / GT, c = e % GT;
             const int row = r0 + r;
             const bool rok = row < r_end;
-            As[r][c] = (rok && bi * GT + c < d) ? (double)At[(int64_t)row * d + bi * GT + c] : 0.0;
-            Bs[r][c] = (rok && bj * GT + c < d) ? (double)At[(int64_t)row * d + bj * GT + c] : 0.0;
+            As[r][c] = (rok && bi * GT + c < d) ? (double)At[(int64_t)row * lda + bi * GT + c] : 0.0;
+            Bs[r][c] = (rok && bj * GT + c < d) ? (double)At[(int64_t)row * lda + bj * GT + c] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -380,18 +381,28 @@ size_t gram_partial_doubles(int64_t m, int64_t d) {
     return (size_t)gram_splits(m, d) * gram_tiles((int)d) * GT * GT;
 }
 
-cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t d, double tau,
-                                         const int32_t* forced, int64_t forced_rank, const QrScratch& q,
-                                         int32_t* status, cudaStream_t st, cudaEvent_t after_gram) {
+cudaError_t launch_gram_fp64(const float* A, int64_t lda, int64_t m, int64_t d, double* Gp, double* G,
+                             cudaStream_t st) {
     const int splits = gram_splits(m, d);
     const int rows_per_split = (int)(((m + splits - 1) / splits + 15) / 16 * 16);
     dim3 grid((unsigned)gram_tiles((int)d), (unsigned)splits);
-    k_gram_fp64<<<grid, 256, 0, st>>>(Atilde, (int)m, (int)d, rows_per_split, q.Gp);
-    k_gram_reduce<<<152 * 4, 256, 0, st>>>(q.Gp, (int)d, splits, q.G);
-    cudaError_t e = cudaGetLastError();
+    k_gram_fp64<<<grid, 256, 0, st>>>(A, lda, (int)m, (int)d, rows_per_split, Gp);
+    k_gram_reduce<<<152 * 4, 256, 0, st>>>(Gp, (int)d, splits, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t d, double tau,
+                                         const int32_t* forced, int64_t forced_rank, const QrScratch& q,
+                                         int32_t* status, cudaStream_t st, cudaEvent_t after_gram) {
+    cudaError_t e = launch_gram_fp64(Atilde, d, m, d, q.Gp, q.G, st);
     if (e != cudaSuccess) return e;
     if (after_gram && (e = cudaEventRecord(after_gram, st)) != cudaSuccess) return e;
+    return launch_pivoted_cholesky(m, d, tau, forced, forced_rank, q, status, st);
+}
 
+cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,
+                                    const QrScratch& q, int32_t* status, cudaStream_t st) {
+    cudaError_t e;
     // cooperative grid over the SMs (one CTA per SM), own columns in shared memory
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);

@@ -58,6 +58,18 @@ struct QrScratch {
 // pivoted Cholesky on one cooperative grid; fills Rorig, piv and rank.
 int gram_splits(int64_t m, int64_t d);
 size_t gram_partial_doubles(int64_t m, int64_t d);
+// G (d x d FP64, both triangles) = A^T A for A (m x d FP32, leading dimension lda); Gp holds
+// gram_partial_doubles(m, d) doubles of split partials.
+cudaError_t launch_gram_fp64(const float* A, int64_t lda, int64_t m, int64_t d, double* Gp, double* G,
+                             cudaStream_t st);
+// The grid pivoted Cholesky of q.G (rank test as lev_rrqr's with min(m, d) steps; forced pivots
+// optional): fills q.Rorig, q.piv, q.rank.
+cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,
+                                    const QrScratch& q, int32_t* status, cudaStream_t st);
+// R (d x d FP64, pivoted order) and perm of a pivoted Cholesky of the Gram matrix already in q.G
+// (forced pivots optional); the output conventions of launch_pivoted_qr.
+cudaError_t launch_factor_gram(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,
+                               const QrScratch& q, int32_t* perm, double* R, int32_t* status, cudaStream_t st);
 cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t d, double tau,
                                          const int32_t* forced, int64_t forced_rank, const QrScratch& q,
                                          int32_t* status, cudaStream_t st, cudaEvent_t after_gram = nullptr);

@@ -9,7 +9,8 @@ struct lev_handle;
 
 namespace lev {
 
-// Handle services used by the tensor-core module (defined in api.cu).
+// Handle services used by the tensor-core module (defined in api.cu). Scratch slots: 0 operand
+// image of the final pass, 1 split-K partials, 2 operand B^T of the Gaussian stage, 3 padded A.
 int handle_scratch(lev_handle* h, int which, size_t bytes, void** out);
 int handle_num_sms(lev_handle* h);
 int32_t* handle_status(lev_handle* h);

@@ -415,6 +415,16 @@ cudaError_t launch_gen_omega(uint64_t seed, int64_t d, int64_t k, double* Omega,
     return cudaGetLastError();
 }
 
+cudaError_t launch_factor_gram(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,
+                               const QrScratch& q, int32_t* perm, double* R, int32_t* status, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(q.Rorig, 0, sizeof(double) * (size_t)(d * d), st)) != cudaSuccess) return e;
+    if ((e = launch_pivoted_cholesky(m, d, tau, forced, forced_rank, q, status, st)) != cudaSuccess) return e;
+    k_assemble_perm<<<1, 1024, sizeof(int) * (size_t)d, st>>>(q, (int)d, perm);
+    k_assemble_r<<<(unsigned)d, 256, 0, st>>>(q, (int)d, perm, R);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int64_t* d_rank,
                                 int64_t d, int64_t k, uint64_t seed, bool omega_identity,
                                 const double* Omega, double* Rs, float* Mfull, cudaStream_t st) {

@@ -475,15 +475,35 @@ int run_final_tc(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t ld
     return LEV_OK;
 }
 
+// out (n x ldo) = A (n x d, lda); the columns d..ldo-1 of out are never read (TMA clips at d).
+__global__ void k_copy_rows(const float* __restrict__ A, int64_t lda, int64_t n, int d, float* __restrict__ out,
+                            int64_t ldo) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * d; e += (int64_t)gridDim.x * blockDim.x)
+        out[(e / d) * ldo + (e % d)] = A[(e / d) * lda + (e % d)];
+}
+
 }  // namespace
 
 int tc_final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const float* Mfull, int64_t k,
                    int32_t prec, float* theta, cudaStream_t st) {
-    if ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || (lda & 3) != 0 || (d & 3) != 0)
-        return handle_fail(LEV_EINVAL, "tensor-core final pass needs A 16-byte aligned, lda and d multiples of 4");
     if (d > 256 || k > 256)
         return handle_fail(LEV_EINVAL, "tensor-core final pass needs d <= 256 and k <= 256");
     if (n == 0) return LEV_OK;
+    // TMA reads rows at a 16-byte aligned base with a row stride that is a multiple of 16 bytes;
+    // any other A is first copied to a padded buffer of the handle
+    if ((reinterpret_cast<uintptr_t>(A) & 15u) != 0 || (lda & 3) != 0) {
+        const int64_t ldo = (d + 3) & ~int64_t(3);
+        void* buf = nullptr;
+        int rc = handle_scratch(h, 3, sizeof(float) * (size_t)n * ldo, &buf);
+        if (rc != LEV_OK) return rc;
+        int grid = (int)((n * d + 255) / 256);
+        if (grid > 152 * 16) grid = 152 * 16;
+        k_copy_rows<<<grid, 256, 0, st>>>(A, lda, n, (int)d, static_cast<float*>(buf), ldo);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
+        A = static_cast<const float*>(buf);
+        lda = ldo;
+    }
     int32_t* status = handle_status(h);
     switch (prec) {
         case LEV_BF16: return run_final_tc<kBF16>(h, A, n, d, lda, Mfull, k, theta, status, st);

@@ -247,9 +247,11 @@ TC_TOL = {"bf16": 1e-2, "tf32": 2e-3, "bf16x3": 5e-5}
 
 @pytest.mark.parametrize("prec", ["bf16", "tf32", "bf16x3"])
 @pytest.mark.parametrize("n,d,k,lda", [(10007, 256, 256, 256), (999, 36, 100, 36), (5000, 64, 200, 80),
-                                       (1, 4, 4, 4), (300, 256, 17, 256), (129, 128, 256, 132)])
+                                       (1, 4, 4, 4), (300, 256, 17, 256), (129, 128, 256, 132),
+                                       (777, 37, 64, 40), (999, 37, 100, 37), (500, 250, 33, 251)])
 def test_final_dense_tensor_core_parity(L, h, prec, n, d, k, lda):
-    """tcgen05 forms of the final pass against the FP64 product of the same FP32 inputs."""
+    """tcgen05 forms of the final pass against the FP64 product of the same FP32 inputs; d need not
+    be a multiple of 4, and a row stride that TMA cannot take (lda % 4 != 0) goes through a padded copy."""
     import torch
     rs = np.random.default_rng(n + d + k)
     A = rs.standard_normal((n, lda)).astype(np.float32)
