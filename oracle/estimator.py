@@ -66,9 +66,40 @@ def gaussian_stage(B: np.ndarray, m: int, seed: int, block: int = 1 << 14) -> np
     return At
 
 
-def sketch(A, s: int, m: int, seed: int) -> np.ndarray:
-    """CountGauss sketch A~ = G (S A) of Alg. 3 (FP64)."""
-    return gaussian_stage(count_sketch(A, s, seed), m, seed)
+def fwht(X: np.ndarray) -> np.ndarray:
+    """Unnormalised Walsh-Hadamard transform along axis 0 (length a power of two): butterflies
+    (x_i, x_{i+h}) -> (x_i + x_{i+h}, x_i - x_{i+h}) within blocks of 2h, h = 1, 2, 4, ...; the
+    result is H X with H_{ij} = (-1)^{popcount(i & j)} (Sylvester order)."""
+    X = np.array(X, dtype=np.float64)
+    n = X.shape[0]
+    assert n & (n - 1) == 0
+    tail = X.shape[1:]
+    h = 1
+    while h < n:
+        Y = X.reshape((n // (2 * h), 2, h) + tail)
+        a = Y[:, 0].copy()
+        Y[:, 0] += Y[:, 1]
+        Y[:, 1] = a - Y[:, 1]
+        X = Y.reshape((n,) + tail)
+        h *= 2
+    return X
+
+
+def srht(B: np.ndarray, t: int, seed: int) -> np.ndarray:
+    """C = F B with the SRHT F = sqrt(s/t) P H D of Sec. 2.3.2 (t x s): D the signs of stream 4,
+    H the Walsh-Hadamard matrix scaled by 1/sqrt(s), P t uniform row draws (stream 5)."""
+    s = B.shape[0]
+    X = fwht(rng.srht_signs(s, seed)[:, None] * B)
+    return X[rng.srht_rows(t, s, seed)] / np.sqrt(t)
+
+
+def sketch(A, s: int, m: int, seed: int, srht_t: int = 0) -> np.ndarray:
+    """CountGauss sketch A~ = G (S A) of Alg. 3 (FP64); with srht_t > 0 the CountSketch is
+    followed by an SRHT to t rows (S~ = F S, Sec. 3.1) and G is m x t."""
+    B = count_sketch(A, s, seed)
+    if srht_t:
+        B = srht(B, srht_t, seed)
+    return gaussian_stage(B, m, seed)
 
 
 def omega_factor(R11: np.ndarray, k: int, seed: int, omega_identity: bool = False) -> np.ndarray:
@@ -109,7 +140,7 @@ class Estimate:
 
 def estimate(A, s: int, m: int, k: int, tau: float, seed: int, *,
              sketch_identity: bool = False, omega_identity: bool = False,
-             forced_perm=None, forced_rank=None, Atilde=None) -> Estimate:
+             forced_perm=None, forced_rank=None, Atilde=None, srht_t: int = 0) -> Estimate:
     """Alg. 10 end to end: returns theta (n), rank, perm (d), Atilde, R (r x d), M (r x k).
 
     ``Atilde`` may be passed in to run steps 4-7 on a given sketch.
@@ -120,7 +151,7 @@ def estimate(A, s: int, m: int, k: int, tau: float, seed: int, *,
             Atilde = _as_float64(A)
             Atilde = Atilde.toarray() if sp.issparse(Atilde) else np.array(Atilde)
         else:
-            Atilde = sketch(A, s, m, seed)
+            Atilde = sketch(A, s, m, seed, srht_t)
     qr = pivoted_qr(Atilde, tau, forced_perm=forced_perm, forced_rank=forced_rank)
     r = qr.rank
     if r == 0:

@@ -71,7 +71,7 @@ def exact_leverage_gram(A, tau: float, block: int = 1 << 16):
 
 
 def ls_hrn_exact(A, s: int, m: int, tau: float, seed: int, *, sketch_identity: bool = False,
-                 block: int = 1 << 16):
+                 block: int = 1 << 16, srht_t: int = 0):
     """Alg. 7 (LS-HRN-exact), FP64. Returns (theta, rank, perm).
 
     Steps 1-3: K and k from the column-pivoted QR of the sketch A~ = G S A (Alg. 3 and 4, the
@@ -86,7 +86,7 @@ def ls_hrn_exact(A, s: int, m: int, tau: float, seed: int, *, sketch_identity: b
         At = A.toarray() if sp.issparse(A) else np.array(A, dtype=np.float64)
         At = At.astype(np.float64)
     else:
-        At = sketch(A, s, m, seed)
+        At = sketch(A, s, m, seed, srht_t)
     qr = pivoted_qr(At, tau)
     k = qr.rank
     if k == 0:

@@ -35,6 +35,7 @@ _MUL1 = np.uint64(0xBF58476D1CE4E5B9)
 _MUL2 = np.uint64(0x94D049BB133111EB)
 _STREAM_MUL = 0xD1B54A32D192ED03
 STREAM_HASH, STREAM_G, STREAM_OMEGA = 1, 2, 3
+STREAM_SRHT_SIGN, STREAM_SRHT_ROWS = 4, 5
 _MASK64 = (1 << 64) - 1
 
 
@@ -61,6 +62,19 @@ def bucket_and_sign(n: int, s: int, seed: int, start: int = 0):
     b = ((x >> np.uint64(32)) * np.uint64(s)) >> np.uint64(32)
     sign = np.where((x & np.uint64(1)) == 0, 1.0, -1.0)
     return b.astype(np.int64), sign
+
+
+def srht_signs(s: int, seed: int) -> np.ndarray:
+    """Diagonal of D of the SRHT (Sec. 2.3.2): +1 / -1 from bit 0 of stream 4 at counters 0..s-1."""
+    x = splitmix64(stream_key(seed, STREAM_SRHT_SIGN), np.arange(s, dtype=np.uint64))
+    return np.where((x & np.uint64(1)) == 0, 1.0, -1.0)
+
+
+def srht_rows(t: int, s: int, seed: int) -> np.ndarray:
+    """Rows of P of the SRHT: t independent uniform draws from [0, s), multiply-shift of the high
+    word of stream 5 at counters 0..t-1."""
+    x = splitmix64(stream_key(seed, STREAM_SRHT_ROWS), np.arange(t, dtype=np.uint64))
+    return (((x >> np.uint64(32)) * np.uint64(s)) >> np.uint64(32)).astype(np.int64)
 
 
 def gaussian(seed: int, stream: int, counters) -> np.ndarray:
