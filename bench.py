@@ -516,9 +516,20 @@ def csr_timing(L, h, name, reps):
               "omega": timed(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf), reps),
               "final": timed(lambda: L.lev_final_csr(h, rp, cl, vl, n, d, Mf, "fp32", theta), reps)}
     csr_bytes = C.nnz * 8 + (n + 1) * 8
-    return {"n": n, "d": d, "nnz": C.nnz, "rank": r, "ms_per_step": ms, "rows_per_s": n / (ms * 1e-3),
-            "csr_gbs_two_passes": 2 * csr_bytes / (ms * 1e-3) / 1e9, "stages_ms": stages,
-            "sketch_prec": "bf16x3", "final_prec": "fp32", "generation_s": gen_s}
+    out = {"n": n, "d": d, "nnz": C.nnz, "rank": r, "ms_per_step": ms, "rows_per_s": n / (ms * 1e-3),
+           "csr_gbs_two_passes": 2 * csr_bytes / (ms * 1e-3) / 1e9, "stages_ms": stages,
+           "sketch_prec": "bf16x3", "final_prec": "fp32", "generation_s": gen_s}
+    # the same estimate with an SRHT after the CountSketch (Sec. 3.1): t from the quoted SRHT
+    # theorem, 4 (sqrt(d) + sqrt(ln(s d)))^2 ln d, rounded up to a multiple of 64
+    t = int(np.ceil(4 * (np.sqrt(d) + np.sqrt(np.log(cfg["s"] * d))) ** 2 * np.log(d) / 64.0) * 64)
+    ps = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3",
+                       srht_t=t)
+    r_s = L.lev_estimate_csr(h, rp, cl, vl, n, d, ps, theta)
+    ms_s = timed(lambda: L.lev_estimate_csr(h, rp, cl, vl, n, d, ps, theta, want_rank=False), reps)
+    sk_s = timed(lambda: L.lev_sketch_csr(h, rp, cl, vl, n, d, ps, At), reps)
+    out["srht"] = {"t": t, "rank": r_s, "ms_per_step": ms_s, "rows_per_s": n / (ms_s * 1e-3), "sketch_ms": sk_s,
+                   "gaussian_stage_flops": 2.0 * cfg["m"] * t * d, "note": "A~ = G (F (S A)), G m x t"}
+    return out
 
 
 def backward_timing(L, h, reps):

@@ -69,6 +69,7 @@ extern "C" {
 #define LEV_SKETCH_IDENTITY 2u  /* S = I, G = I, A~ = A (tests; needs n <= 65536) */
 #define LEV_FORCE_PIVOTS    4u  /* take perm_in[0..rank_in) as the pivots, no rank test */
 #define LEV_HOST_ASYNC      8u  /* lev_estimate_dense with host buffers and rank == NULL: enqueue only */
+#define LEV_SKETCH_SRHT    16u  /* A~ = G F S A: an SRHT F (t = srht_t rows) after the CountSketch (Sec. 3.1) */
 
 typedef struct lev_handle lev_handle;
 
@@ -84,7 +85,7 @@ typedef struct lev_params {
     int32_t  sketch_prec;  /* LEV_FP32 | LEV_TF32 | LEV_BF16 | LEV_BF16X3 for A~ = G B */
     int32_t  final_prec;   /* same set for theta~ = ||A M_full||^2 */
     uint32_t flags;        /* LEV_* flags above */
-    int32_t  reserved;
+    int32_t  srht_t;       /* rows t of the SRHT with LEV_SKETCH_SRHT (1 <= t <= s; s a power of two) */
     const int32_t* perm_in;  /* device, d entries; read with LEV_FORCE_PIVOTS */
     int64_t  rank_in;        /* number of forced pivots; read with LEV_FORCE_PIVOTS */
 } lev_params;
@@ -114,7 +115,11 @@ int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d,
 
 /* CountGauss sketch of dense A (Alg. 3): Atilde (m x d, row-major, ld = d,
  * FP32, device) = G (S A). A: device, n x d FP32, leading dimension lda >= d.
- * p->sketch_prec selects the arithmetic of the product G B.
+ * p->sketch_prec selects the arithmetic of the product G B. With LEV_SKETCH_SRHT
+ * the CountSketch is followed by the SRHT F = sqrt(s/t) P H D of Sec. 2.3.2 (D:
+ * signs of stream 4; H: Walsh-Hadamard / sqrt(s); P: t uniform row draws of
+ * stream 5, multiply-shift of the high word), S~ = F S (Sec. 3.1), and G is
+ * m x t: A~ = G (F (S A)). s must be a power of two, at most 2^24.
  * Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA. */
 int lev_sketch_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
                      const lev_params* p, float* Atilde, void* stream);

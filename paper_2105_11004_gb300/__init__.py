@@ -17,7 +17,7 @@ from .build import LIB_PATH, build as build_library  # noqa: F401
 
 LEV_OK, LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0 = 0, 1, 2, 3, 4, 5
 LEV_FP32, LEV_TF32, LEV_BF16, LEV_BF16X3 = 0, 1, 2, 3
-LEV_OMEGA_IDENTITY, LEV_SKETCH_IDENTITY, LEV_FORCE_PIVOTS, LEV_HOST_ASYNC = 1, 2, 4, 8
+LEV_OMEGA_IDENTITY, LEV_SKETCH_IDENTITY, LEV_FORCE_PIVOTS, LEV_HOST_ASYNC, LEV_SKETCH_SRHT = 1, 2, 4, 8, 16
 PRECISIONS = {"fp32": LEV_FP32, "tf32": LEV_TF32, "bf16": LEV_BF16, "bf16x3": LEV_BF16X3}
 
 # Every symbol include/lev.h declares, with (restype, argtypes).
@@ -30,7 +30,7 @@ class lev_params(ctypes.Structure):
         ("eps", _dbl), ("delta", _dbl), ("gamma", _dbl),
         ("s", _i64), ("m", _i64), ("k", _i64),
         ("tau", _dbl), ("seed", _u64),
-        ("sketch_prec", _i32), ("final_prec", _i32), ("flags", _u32), ("reserved", _i32),
+        ("sketch_prec", _i32), ("final_prec", _i32), ("flags", _u32), ("srht_t", _i32),
         ("perm_in", _c_void_p), ("rank_in", _i64),
     ]
 
@@ -135,7 +135,7 @@ def default_handle(device: int = 0) -> Handle:
 
 def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec="fp32", eps=0.5,
                 delta=1.0 / 3.0, gamma=2.0, omega_identity=False, sketch_identity=False,
-                perm_in=None, rank_in=0, host_async=False) -> lev_params:
+                perm_in=None, rank_in=0, host_async=False, srht_t=0) -> lev_params:
     p = lev_params()
     _check(lib.lev_params_init(ctypes.byref(p)))
     p.eps, p.delta, p.gamma = eps, delta, gamma
@@ -149,6 +149,9 @@ def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec=
         flags |= LEV_SKETCH_IDENTITY
     if host_async:
         flags |= LEV_HOST_ASYNC
+    if srht_t:
+        flags |= LEV_SKETCH_SRHT
+        p.srht_t = int(srht_t)
     if perm_in is not None:
         flags |= LEV_FORCE_PIVOTS
         p.perm_in = perm_in.data_ptr()
@@ -265,12 +268,12 @@ def lev_device_status(h: Handle) -> int:
 # ---- convenience ----
 
 def estimate(A, *, s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec="fp32",
-             omega_identity=False, sketch_identity=False, handle: Handle | None = None):
+             omega_identity=False, sketch_identity=False, srht_t=0, handle: Handle | None = None):
     """theta~ (n, FP32), rank, perm (d, int32) for dense FP32 A (torch, on a CUDA device)."""
     import torch
     h = handle or default_handle(A.device.index or 0)
     p = make_params(s=s, m=m, k=k, tau=tau, seed=seed, sketch_prec=sketch_prec, final_prec=final_prec,
-                    omega_identity=omega_identity, sketch_identity=sketch_identity)
+                    omega_identity=omega_identity, sketch_identity=sketch_identity, srht_t=srht_t)
     theta = torch.empty(A.shape[0], dtype=torch.float32, device=A.device)
     perm = torch.empty(A.shape[1], dtype=torch.int32, device=A.device)
     r = lev_estimate_dense(h, A, p, theta, perm)

@@ -80,6 +80,7 @@ struct lev_handle {
     // host A of lev_estimate_dense: two stage buffers filled by a copy stream of the handle
     Buf stageA[2];
     Buf exact_gp;  // split partials of the Gram matrix of A (LS-HRN-exact)
+    Buf srht_c;    // F (S A), t x d (LEV_SKETCH_SRHT)
     Buf tc_pad;   // A copied with a 16-byte row stride when the caller's cannot feed TMA
     cudaStream_t copy_st = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
@@ -285,6 +286,21 @@ int omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int6
     return LEV_OK;
 }
 
+// The stages after B = S A (in h->B): A~ = G B, or with LEV_SKETCH_SRHT A~ = G (F B), F the
+// SRHT to t = p->srht_t rows (B is transformed in place) and G m x t.
+int gaussian_after_countsketch(lev_handle* h, const lev_params* p, const Sizes& z, int64_t d, float* Atilde,
+                               cudaStream_t st) {
+    if (!(p->flags & LEV_SKETCH_SRHT))
+        return gaussian_stage(h, (const float*)h->B.ptr, z.m, z.s, d, p->seed, p->sketch_prec, Atilde, st);
+    const int64_t t = p->srht_t;
+    if ((z.s & (z.s - 1)) != 0 || z.s > (int64_t(1) << 24))
+        return fail(LEV_EINVAL, "LEV_SKETCH_SRHT needs s a power of two <= 2^24 (s = %lld)", (long long)z.s);
+    if (t < 1 || t > z.s) return fail(LEV_EINVAL, "LEV_SKETCH_SRHT needs 1 <= srht_t <= s");
+    LEV_TRY(ensure(h->srht_c, sizeof(float) * (size_t)t * d));
+    LEV_CUDA(lev::launch_srht((float*)h->B.ptr, z.s, d, t, p->seed, (float*)h->srht_c.ptr, st));
+    return gaussian_stage(h, (const float*)h->srht_c.ptr, z.m, t, d, p->seed, p->sketch_prec, Atilde, st);
+}
+
 int sketch_common_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
                         const lev_params* p, const Sizes& z, float* Atilde, cudaStream_t st) {
     if (p->flags & LEV_SKETCH_IDENTITY) {
@@ -295,7 +311,7 @@ int sketch_common_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int
     LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
     LEV_CUDA(lev::launch_countsketch_dense(A, lda, d, z.s, (const int*)h->off.ptr,
                                            (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));
-    return gaussian_stage(h, (const float*)h->B.ptr, z.m, z.s, d, p->seed, p->sketch_prec, Atilde, st);
+    return gaussian_after_countsketch(h, p, z, d, Atilde, st);
 }
 
 int sketch_common_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
@@ -306,7 +322,7 @@ int sketch_common_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col,
     LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
     LEV_CUDA(lev::launch_countsketch_csr(row_ptr, col, val, d, z.s, (const int*)h->off.ptr,
                                          (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));
-    return gaussian_stage(h, (const float*)h->B.ptr, z.m, z.s, d, p->seed, p->sketch_prec, Atilde, st);
+    return gaussian_after_countsketch(h, p, z, d, Atilde, st);
 }
 
 int rrqr_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double tau,
@@ -418,7 +434,7 @@ int lev_destroy(lev_handle* h) {
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
                   &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
                   &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->tc_pad,
-                  &h->exact_gp};
+                  &h->exact_gp, &h->srht_c};
     for (Buf* b : all) release(*b);
     for (int i = 0; i < 2; ++i) {
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
@@ -730,6 +746,7 @@ int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
     if (!A || !Atilde || !perm || !d_rank || !R || !Mfull || !w || !gradA) return fail(LEV_EINVAL, "NULL array");
     if (lda < d) return fail(LEV_EINVAL, "lda < d");
     if (d > 256 || z.k > 256) return fail(LEV_EINVAL, "lev_backward_dense needs d <= 256 and k <= 256");
+    if (p->flags & LEV_SKETCH_SRHT) return fail(LEV_EINVAL, "lev_backward_dense has no adjoint of the SRHT sketch");
     LEV_TRY(check_prec(p->sketch_prec, "sketch"));
     cudaStream_t st = (cudaStream_t)stream;
     const bool identity = (p->flags & LEV_SKETCH_IDENTITY) != 0;

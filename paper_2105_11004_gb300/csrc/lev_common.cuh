@@ -15,7 +15,7 @@ namespace lev {
 // ---------------------------------------------------------------------------
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kStreamMul = 0xD1B54A32D192ED03ull;
-constexpr int kStreamHash = 1, kStreamG = 2, kStreamOmega = 3;
+constexpr int kStreamHash = 1, kStreamG = 2, kStreamOmega = 3, kStreamSrhtSign = 4, kStreamSrhtRows = 5;
 
 __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t key, uint64_t c) {
     uint64_t z = key + (c + 1ull) * kGolden;

@@ -54,6 +54,10 @@ struct QrScratch {
     double* U;        // d x d FP64: unscaled pivot rows exchanged by the grid pivoted Cholesky (Gram route)
 };
 
+// C (t x d) = F B with the SRHT F = sqrt(s/t) P H D (srht.cu); B (s x d, s a power of two) is
+// overwritten with H' D B, H' the unscaled Walsh-Hadamard matrix.
+cudaError_t launch_srht(float* B, int64_t s, int64_t d, int64_t t, uint64_t seed, float* C, cudaStream_t st);
+
 // Gram route of the pivoted QR (gramqr.cu): G = A~^T A~ in FP64, then a
 // pivoted Cholesky on one cooperative grid; fills Rorig, piv and rank.
 int gram_splits(int64_t m, int64_t d);

@@ -144,6 +144,30 @@ def test_csr_8e6x1024(L, h):
     assert max_rel(theta[rows], _rows_theta(C, rows, Mf)) <= 1e-5
 
 
+def test_csr_8e6x1024_srht(L, h):
+    """The CSR 8e6 x 1024 workload with the SRHT after the CountSketch (t = 36,864 rows, the
+    size of the quoted SRHT theorem at d = 1024, s = 262,144): full rank, sampled theta~ from the
+    GPU's Mfull, and sum theta~ against its expectation r m / (m - r - 1)."""
+    import torch
+    cfg = W.CONFIGS["csr_8e6x1024"]
+    n, d, s, m, k = cfg["n"], cfg["d"], cfg["s"], cfg["m"], cfg["k"]
+    C = W.csr_uniform(n, d, seed=cfg["data_seed"])
+    rp, cl, vl = to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val)
+    p = L.make_params(s=s, m=m, k=k, tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3", srht_t=36864)
+    theta_t = torch.empty(n, device="cuda")
+    At, perm, R, r, Mf, _ = _run_stages(
+        L, h, p, lambda out: L.lev_sketch_csr(h, rp, cl, vl, n, d, p, out),
+        lambda Mf_: (L.lev_final_csr(h, rp, cl, vl, n, d, Mf_, "fp32", theta_t), to_np(theta_t))[1], d, m, k)
+    theta = to_np(theta_t)
+    assert r == d
+    rs = np.random.default_rng(2)
+    _check_qr(At, perm, R, r, rs)
+    rows = rs.integers(0, n, 2000)
+    assert max_rel(theta[rows], _rows_theta(C, rows, Mf)) <= 1e-5
+    want_sum = r * m / (m - r - 1)
+    assert abs(float(theta.astype(np.float64).sum()) / want_sum - 1) < 0.03
+
+
 def test_csr_8e7x1024_rank1014(L, h):
     """CSR 8e7 x 1024, ~12 nnz/row (~1e9 nnz), column j + 512 = 2 x column j for j < 10:
     rank exactly 1014, no dependent pair both selected, sampled sketch entries and theta~."""
