@@ -194,7 +194,12 @@ __global__ void __launch_bounds__(256) k_countsketch_dense_scalar(
 
 // CSR: warp per bucket, dense accumulator row of d floats in shared memory.
 // Rows of a bucket are added one after the other (__syncwarp between rows),
-// so a column's sum runs in row order.
+// so a column's sum runs in row order. The bounds of up to 32 rows are fetched
+// at once (lane r holds row r's), and the first 32 entries of four rows are
+// loaded before any of them is added, so the dependent global loads of a
+// bucket overlap instead of running one row at a time; entries past the 32nd
+// of a row (the heavy rows) follow in that row's turn.
+constexpr int CS_PF = 4;
 __global__ void __launch_bounds__(128) k_countsketch_csr(
         const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
         const float* __restrict__ val, int d, const int* __restrict__ off,
@@ -209,16 +214,48 @@ __global__ void __launch_bounds__(128) k_countsketch_csr(
         for (int c = lane; c < d; c += 32) sacc[c] = 0.f;
         __syncwarp();
         const int t0 = off[b], t1 = off[b + 1];
-        for (int t = t0; t < t1; ++t) {
-            const uint32_t e = perm[t];
-            const float sg = (e & kSignBit) ? -1.f : 1.f;
-            const int64_t row = e & ~kSignBit;
-            const int64_t p0 = row_ptr[row], p1 = row_ptr[row + 1];
-            for (int64_t p = p0 + lane; p < p1; p += 32) {
-                const int c = col[p];
-                if ((unsigned)c < (unsigned)d) atomicAdd(&sacc[c], sg * val[p]);
+        for (int tb = t0; tb < t1; tb += 32) {
+            const int nr = min(32, t1 - tb);
+            int64_t my_p0 = 0, my_p1 = 0;
+            float my_sg = 0.f;
+            if (lane < nr) {
+                const uint32_t e = perm[tb + lane];
+                const int64_t row = e & ~kSignBit;
+                my_sg = (e & kSignBit) ? -1.f : 1.f;
+                my_p0 = row_ptr[row];
+                my_p1 = row_ptr[row + 1];
             }
-            __syncwarp();
+            for (int r0 = 0; r0 < nr; r0 += CS_PF) {
+                int cc[CS_PF];
+                float vv[CS_PF];
+#pragma unroll
+                for (int u = 0; u < CS_PF; ++u) {            // loads of four rows in flight together
+                    const int r = r0 + u;
+                    const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, r & 31);
+                    const int64_t p1 = __shfl_sync(0xffffffffu, my_p1, r & 31);
+                    cc[u] = -1;
+                    vv[u] = 0.f;
+                    if (r < nr && p0 + lane < p1) {
+                        cc[u] = col[p0 + lane];
+                        vv[u] = val[p0 + lane];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < CS_PF; ++u) {            // rows added in order
+                    const int r = r0 + u;
+                    const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, r & 31);
+                    const int64_t p1 = __shfl_sync(0xffffffffu, my_p1, r & 31);
+                    const float sg = __shfl_sync(0xffffffffu, my_sg, r & 31);
+                    if (r < nr) {
+                        if ((unsigned)cc[u] < (unsigned)d) atomicAdd(&sacc[cc[u]], sg * vv[u]);
+                        for (int64_t p = p0 + 32 + lane; p < p1; p += 32) {
+                            const int c = col[p];
+                            if ((unsigned)c < (unsigned)d) atomicAdd(&sacc[c], sg * val[p]);
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
         }
         float* out = B + (int64_t)b * d;
         for (int c = lane; c < d; c += 32) out[c] = sacc[c];
