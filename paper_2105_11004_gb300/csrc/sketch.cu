@@ -195,11 +195,11 @@ __global__ void __launch_bounds__(256) k_countsketch_dense_scalar(
 // CSR: warp per bucket, dense accumulator row of d floats in shared memory.
 // Rows of a bucket are added one after the other (__syncwarp between rows),
 // so a column's sum runs in row order. The bounds of up to 32 rows are fetched
-// at once (lane r holds row r's), and the first 32 entries of four rows are
+// at once (lane r holds row r's), and the first 32 entries of eight rows are
 // loaded before any of them is added, so the dependent global loads of a
 // bucket overlap instead of running one row at a time; entries past the 32nd
 // of a row (the heavy rows) follow in that row's turn.
-constexpr int CS_PF = 4;
+constexpr int CS_PF = 8;
 __global__ void __launch_bounds__(128) k_countsketch_csr(
         const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
         const float* __restrict__ val, int d, const int* __restrict__ off,
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(128) k_countsketch_csr(
                 int cc[CS_PF];
                 float vv[CS_PF];
 #pragma unroll
-                for (int u = 0; u < CS_PF; ++u) {            // loads of four rows in flight together
+                for (int u = 0; u < CS_PF; ++u) {            // loads of CS_PF rows in flight together
                     const int r = r0 + u;
                     const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, r & 31);
                     const int64_t p1 = __shfl_sync(0xffffffffu, my_p1, r & 31);
