@@ -88,6 +88,10 @@ typedef struct lev_params {
     int32_t  srht_t;       /* rows t of the SRHT with LEV_SKETCH_SRHT (1 <= t <= s; s a power of two) */
     const int32_t* perm_in;  /* device, d entries; read with LEV_FORCE_PIVOTS */
     int64_t  rank_in;        /* number of forced pivots; read with LEV_FORCE_PIVOTS */
+    int64_t  row0;           /* row shard: global index of local row 0 (hash and sign of row i use
+                                row0 + i); read by lev_sketch_* and lev_resolve_sizes, 0 elsewhere */
+    int64_t  n_total;        /* row shard: rows of the whole matrix (k = 0 is derived from it);
+                                0 = the call's n; same entry points as row0 */
 } lev_params;
 
 /* Create a handle on CUDA device `device` (the device is made current for every
@@ -112,6 +116,15 @@ int lev_params_init(lev_params* p);
  * each unless set explicitly in p. Any output pointer may be NULL. */
 int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d,
                       int64_t* s, int64_t* m, int64_t* k);
+
+/* Row shards. S A = sum_p S_{:,P_p} A_{P_p,:} for any partition of the rows into blocks P_p
+ * (block matrix product), and G and the SRHT act linearly on S A, so the sketch of a matrix
+ * whose rows are split across processes is the SUM of the sketches of its row blocks when each
+ * block hashes its rows by their global index: call lev_sketch_* on each block with
+ * p->row0 = the block's first global row and p->n_total = the rows of the whole matrix, sum the
+ * m x d results (one all-reduce), then lev_rrqr and lev_omega_factor on the sum (the same on
+ * every process) and lev_final_* on each block. Every other entry point sums over the rows of
+ * its own A and rejects row0 != 0 or n_total != 0 with LEV_EINVAL. */
 
 /* CountGauss sketch of dense A (Alg. 3): Atilde (m x d, row-major, ld = d,
  * FP32, device) = G (S A). A: device, n x d FP32, leading dimension lda >= d.

@@ -42,13 +42,16 @@ def _as_float64(A):
     return np.asarray(A, dtype=np.float64)
 
 
-def count_sketch(A, s: int, seed: int, block: int = 1 << 18) -> np.ndarray:
-    """B = S A (s x d), S the CountSketch of rows 0..n-1 (Sec. 2.3.3), FP64 sums."""
+def count_sketch(A, s: int, seed: int, block: int = 1 << 18, row0: int = 0) -> np.ndarray:
+    """B = S A (s x d), S the CountSketch of rows 0..n-1 (Sec. 2.3.3), FP64 sums.
+
+    With row0 > 0, A is the block of rows row0..row0+n-1 of a larger matrix and the result is
+    S_{:,row0:row0+n} A: each row is hashed by its global index (block matrix product)."""
     n, d = A.shape
     B = np.zeros((s, d))
     for r0 in range(0, n, block):
         r1 = min(n, r0 + block)
-        b, sign = rng.bucket_and_sign(r1 - r0, s, seed, start=r0)
+        b, sign = rng.bucket_and_sign(r1 - r0, s, seed, start=row0 + r0)
         S = sp.csr_matrix((sign, (b, np.arange(r1 - r0))), shape=(s, r1 - r0))
         blk = _as_float64(A[r0:r1])
         prod = S @ blk
@@ -93,10 +96,11 @@ def srht(B: np.ndarray, t: int, seed: int) -> np.ndarray:
     return X[rng.srht_rows(t, s, seed)] / np.sqrt(t)
 
 
-def sketch(A, s: int, m: int, seed: int, srht_t: int = 0) -> np.ndarray:
+def sketch(A, s: int, m: int, seed: int, srht_t: int = 0, row0: int = 0) -> np.ndarray:
     """CountGauss sketch A~ = G (S A) of Alg. 3 (FP64); with srht_t > 0 the CountSketch is
-    followed by an SRHT to t rows (S~ = F S, Sec. 3.1) and G is m x t."""
-    B = count_sketch(A, s, seed)
+    followed by an SRHT to t rows (S~ = F S, Sec. 3.1) and G is m x t. With row0 > 0, A is a
+    block of rows starting at global row row0 (see count_sketch)."""
+    B = count_sketch(A, s, seed, row0=row0)
     if srht_t:
         B = srht(B, srht_t, seed)
     return gaussian_stage(B, m, seed)

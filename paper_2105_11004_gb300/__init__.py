@@ -32,6 +32,7 @@ class lev_params(ctypes.Structure):
         ("tau", _dbl), ("seed", _u64),
         ("sketch_prec", _i32), ("final_prec", _i32), ("flags", _u32), ("srht_t", _i32),
         ("perm_in", _c_void_p), ("rank_in", _i64),
+        ("row0", _i64), ("n_total", _i64),
     ]
 
 
@@ -135,7 +136,7 @@ def default_handle(device: int = 0) -> Handle:
 
 def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec="fp32", eps=0.5,
                 delta=1.0 / 3.0, gamma=2.0, omega_identity=False, sketch_identity=False,
-                perm_in=None, rank_in=0, host_async=False, srht_t=0) -> lev_params:
+                perm_in=None, rank_in=0, host_async=False, srht_t=0, row0=0, n_total=0) -> lev_params:
     p = lev_params()
     _check(lib.lev_params_init(ctypes.byref(p)))
     p.eps, p.delta, p.gamma = eps, delta, gamma
@@ -157,6 +158,7 @@ def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec=
         p.perm_in = perm_in.data_ptr()
         p.rank_in = int(rank_in)
     p.flags = flags
+    p.row0, p.n_total = int(row0), int(n_total)
     return p
 
 
@@ -278,6 +280,92 @@ def estimate(A, *, s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_pr
     perm = torch.empty(A.shape[1], dtype=torch.int32, device=A.device)
     r = lev_estimate_dense(h, A, p, theta, perm)
     return theta, r, perm
+
+
+# ---- row shards (rows of one matrix split across processes; see include/lev.h) ----
+
+def row_shard(n: int, world_size: int, rank: int):
+    """(row0, rows) of block `rank` when n rows are cut into world_size contiguous blocks whose
+    sizes differ by at most one (the first n mod world_size blocks take the extra row)."""
+    if world_size < 1 or not 0 <= rank < world_size or n < world_size:
+        raise ValueError(f"cannot cut {n} rows into {world_size} blocks (rank {rank})")
+    q, rem = divmod(n, world_size)
+    return rank * q + min(rank, rem), q + (1 if rank < rem else 0)
+
+
+def _shard_params(p: lev_params, row0: int, n_total: int) -> lev_params:
+    q = lev_params()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(lev_params))
+    q.row0, q.n_total = int(row0), int(n_total)
+    return q
+
+
+def sketch_shard(h: Handle, A_local, p: lev_params, row0: int, n_total: int, Atilde, csr=None, stream=None):
+    """This block's part G (S_{:,block} A_block) of the sketch (rows hashed by global index)."""
+    q = _shard_params(p, row0, n_total)
+    if csr is None:
+        lev_sketch_dense(h, A_local, q, Atilde, stream)
+    else:
+        row_ptr, col, val, n, d = csr
+        lev_sketch_csr(h, row_ptr, col, val, n, d, q, Atilde, stream)
+
+
+def allreduce_sketch(Atilde, group=None):
+    """Sum the blocks' partial sketches in place on every process: the one exchange of the
+    sharded path (m x d FP32). A no-op without an initialised process group of size > 1."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1:
+        if Atilde.is_cuda and dist.get_backend(group) == "gloo":    # gloo reduces host memory
+            host = Atilde.cpu()
+            dist.all_reduce(host, op=dist.ReduceOp.SUM, group=group)
+            Atilde.copy_(host)
+        else:
+            dist.all_reduce(Atilde, op=dist.ReduceOp.SUM, group=group)
+    return Atilde
+
+
+def finish_shard(h: Handle, A_local, p: lev_params, Atilde, k: int, csr=None, stream=None):
+    """Pivoted QR of the summed sketch, M = R_11^{-1} Omega and the final pass over this block:
+    (theta~ of the block's rows, rank, perm). Every process gets the same (perm, rank, Mfull)
+    from the same summed sketch."""
+    import torch
+    dev = Atilde.device
+    d = Atilde.shape[1]
+    perm = torch.empty(d, dtype=torch.int32, device=dev)
+    R = torch.empty((d, d), dtype=torch.float64, device=dev)
+    r = lev_rrqr(h, Atilde, p.tau, perm, R, stream)
+    n_local = A_local.shape[0] if csr is None else csr[3]
+    theta = torch.zeros(n_local, dtype=torch.float32, device=dev)
+    if r == 0:
+        return theta, 0, perm
+    d_rank = torch.tensor([r], dtype=torch.int64, device=dev)
+    Mfull = torch.empty((d, k), dtype=torch.float32, device=dev)
+    lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, p.flags, Mfull, stream)
+    if csr is None:
+        lev_final_dense(h, A_local, Mfull, p.final_prec, theta, stream)
+    else:
+        row_ptr, col, val, n, _ = csr
+        lev_final_csr(h, row_ptr, col, val, n, d, Mfull, p.final_prec, theta, stream)
+    return theta, r, perm
+
+
+def estimate_sharded(A_local, p: lev_params, row0: int, n_total: int, *, csr=None, group=None,
+                     handle: Handle | None = None):
+    """Alg. 10 on a matrix whose rows [row0, row0 + rows) live on this process: the partial
+    sketch, one all-reduce of it, then the QR, M and the final pass. Returns (theta~ of the
+    local rows, rank, perm); rank and perm are the same on every process.
+
+    Dense: A_local is the block (FP32, CUDA). CSR: csr = (row_ptr, col, val, rows, d) of the block
+    and A_local is None."""
+    import torch
+    dev = (A_local if csr is None else csr[0]).device
+    h = handle or default_handle(dev.index or 0)
+    n_local, d = (A_local.shape if csr is None else (csr[3], csr[4]))
+    _, m, k = lev_resolve_sizes(_shard_params(p, row0, n_total), n_local, d)
+    Atilde = torch.empty((m, d), dtype=torch.float32, device=dev)
+    sketch_shard(h, A_local, p, row0, n_total, Atilde, csr)
+    allreduce_sketch(Atilde, group)
+    return finish_shard(h, A_local, p, Atilde, k, csr)
 
 
 def forward_state(A, p: lev_params, handle: Handle | None = None):

@@ -70,7 +70,7 @@ struct lev_handle {
     bool timing = false, timed_once = false;
     cudaEvent_t tmark[3] = {nullptr, nullptr, nullptr};
     uint64_t perm_seed = 0;
-    int64_t perm_n = -1, perm_s = -1;
+    int64_t perm_n = -1, perm_s = -1, perm_row0 = 0;
     cudaEvent_t ev_perm = nullptr;
     // Omega (d x k FP64) of the last (seed, d, k), with its event, and the R_11 scratch of the solve
     Buf omega, omega_rs;
@@ -133,12 +133,24 @@ bool is_host_pointer(const void* p) {
 
 struct Sizes {
     int64_t s, m, k;
+    int64_t row0;  // global index of local row 0 (hash and sign of a row shard)
 };
 
-int resolve(const lev_params* p, int64_t n, int64_t d, Sizes* z) {
+// Sizes of a call with (p, n, d). Only the sketch entry points take a row shard (row0, n_total):
+// every other entry point sums over all rows of A itself, so it rejects them.
+int resolve(const lev_params* p, int64_t n, int64_t d, Sizes* z, bool shard_ok = false) {
     if (!p) return fail(LEV_EINVAL, "params is NULL");
     if (n < 1 || n >= (int64_t)1 << 31) return fail(LEV_EINVAL, "n = %lld out of range [1, 2^31)", (long long)n);
     if (d < 1 || d > 4096) return fail(LEV_EINVAL, "d = %lld out of range [1, 4096]", (long long)d);
+    if ((p->row0 != 0 || p->n_total != 0) && !shard_ok)
+        return fail(LEV_EINVAL, "row0 / n_total (a row shard) are read by lev_sketch_* and lev_resolve_sizes only");
+    if (p->row0 < 0 || p->n_total < 0 || p->n_total >= (int64_t)1 << 62 ||
+        (p->n_total != 0 && p->row0 > p->n_total - n))
+        return fail(LEV_EINVAL, "row shard [%lld, %lld) outside n_total = %lld", (long long)p->row0,
+                    (long long)(p->row0 + n), (long long)p->n_total);
+    if ((p->flags & LEV_SKETCH_IDENTITY) && (p->row0 != 0 || p->n_total != 0))
+        return fail(LEV_EINVAL, "LEV_SKETCH_IDENTITY takes no row shard");
+    const int64_t n_all = p->n_total != 0 ? p->n_total : n;   // k from the rows of the whole matrix
     const double eps = p->eps, delta = p->delta;
     int64_t s = p->s, m = p->m, k = p->k;
     if (s == 0) {
@@ -152,7 +164,7 @@ int resolve(const lev_params* p, int64_t n, int64_t d, Sizes* z) {
     }
     if (k == 0) {
         if (!(eps > 0 && eps < 1)) return fail(LEV_EINVAL, "eps must be in (0,1)");
-        k = (int64_t)std::ceil(4.0 * std::log((double)(n > 1 ? n : 2)) / (eps * eps / 2 - eps * eps * eps / 3));
+        k = (int64_t)std::ceil(4.0 * std::log((double)(n_all > 1 ? n_all : 2)) / (eps * eps / 2 - eps * eps * eps / 3));
     }
     if (p->flags & LEV_SKETCH_IDENTITY) {
         s = n;
@@ -167,6 +179,7 @@ int resolve(const lev_params* p, int64_t n, int64_t d, Sizes* z) {
     z->s = s;
     z->m = m;
     z->k = k;
+    z->row0 = p->row0;
     return LEV_OK;
 }
 
@@ -232,10 +245,10 @@ int gaussian_stage(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t 
     return lev::tc_gaussian_stage(h, B, m, s, d, seed, prec, Atilde, st);
 }
 
-// The rows of each bucket in increasing order (off: s+1 bucket offsets, perm_rows: n rows). It
-// depends on (seed, n, s) only, so the handle keeps the last one and rebuilds it only when one of
-// those (or the buffers) changes.
-int bucket_perm(lev_handle* h, int64_t n, int64_t s, uint64_t seed, cudaStream_t st) {
+// The rows of each bucket in increasing order (off: s+1 bucket offsets, perm_rows: n local rows,
+// hashed by their global index row0 + i). It depends on (seed, n, s, row0) only, so the handle
+// keeps the last one and rebuilds it only when one of those (or the buffers) changes.
+int bucket_perm(lev_handle* h, int64_t n, int64_t s, uint64_t seed, int64_t row0, cudaStream_t st) {
     const void* off0 = h->off.ptr;
     const void* perm0 = h->perm_rows.ptr;
     LEV_TRY(ensure(h->count, sizeof(int) * (size_t)(s + 1)));
@@ -243,15 +256,17 @@ int bucket_perm(lev_handle* h, int64_t n, int64_t s, uint64_t seed, cudaStream_t
     LEV_TRY(ensure(h->tmp, sizeof(uint32_t) * (size_t)n));
     LEV_TRY(ensure(h->perm_rows, sizeof(uint32_t) * (size_t)n));
     if (!h->ev_perm) LEV_CUDA(cudaEventCreateWithFlags(&h->ev_perm, cudaEventDisableTiming));
-    if (h->perm_n == n && h->perm_s == s && h->perm_seed == seed && h->off.ptr == off0 && h->perm_rows.ptr == perm0) {
+    if (h->perm_n == n && h->perm_s == s && h->perm_seed == seed && h->perm_row0 == row0 && h->off.ptr == off0 &&
+        h->perm_rows.ptr == perm0) {
         LEV_CUDA(cudaStreamWaitEvent(st, h->ev_perm, 0));
         return LEV_OK;
     }
     h->perm_n = -1;
-    LEV_CUDA(lev::launch_bucket_perm(n, s, seed, (int*)h->count.ptr, (int*)h->off.ptr, (uint32_t*)h->tmp.ptr,
+    LEV_CUDA(lev::launch_bucket_perm(n, s, seed, row0, (int*)h->count.ptr, (int*)h->off.ptr, (uint32_t*)h->tmp.ptr,
                                      (uint32_t*)h->perm_rows.ptr, st));
     LEV_CUDA(cudaEventRecord(h->ev_perm, st));
     h->perm_seed = seed;
+    h->perm_row0 = row0;
     h->perm_n = n;
     h->perm_s = s;
     return LEV_OK;
@@ -307,7 +322,7 @@ int sketch_common_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int
         LEV_CUDA(lev::launch_copy_dense(A, lda, n, d, Atilde, st));
         return LEV_OK;
     }
-    LEV_TRY(bucket_perm(h, n, z.s, p->seed, st));
+    LEV_TRY(bucket_perm(h, n, z.s, p->seed, z.row0, st));
     LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
     LEV_CUDA(lev::launch_countsketch_dense(A, lda, d, z.s, (const int*)h->off.ptr,
                                            (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));
@@ -318,7 +333,7 @@ int sketch_common_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col,
                       int64_t n, int64_t d, const lev_params* p, const Sizes& z, float* Atilde,
                       cudaStream_t st) {
     if (p->flags & LEV_SKETCH_IDENTITY) return fail(LEV_EINVAL, "LEV_SKETCH_IDENTITY is for dense A only");
-    LEV_TRY(bucket_perm(h, n, z.s, p->seed, st));
+    LEV_TRY(bucket_perm(h, n, z.s, p->seed, z.row0, st));
     LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
     LEV_CUDA(lev::launch_countsketch_csr(row_ptr, col, val, d, z.s, (const int*)h->off.ptr,
                                          (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));
@@ -400,7 +415,7 @@ int lev_params_init(lev_params* p) {
 
 int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d, int64_t* s, int64_t* m, int64_t* k) {
     Sizes z;
-    LEV_TRY(resolve(p, n, d, &z));
+    LEV_TRY(resolve(p, n, d, &z, true));
     if (s) *s = z.s;
     if (m) *m = z.m;
     if (k) *k = z.k;
@@ -484,7 +499,7 @@ int lev_sketch_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_
                      const lev_params* p, float* Atilde, void* stream) {
     LEV_TRY(set_device(h));
     Sizes z;
-    LEV_TRY(resolve(p, n, d, &z));
+    LEV_TRY(resolve(p, n, d, &z, true));
     if (!A || !Atilde) return fail(LEV_EINVAL, "NULL array");
     if (lda < d) return fail(LEV_EINVAL, "lda < d");
     LEV_TRY(check_prec(p->sketch_prec, "sketch"));
@@ -495,7 +510,7 @@ int lev_sketch_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, co
                    int64_t n, int64_t d, int64_t nnz, const lev_params* p, float* Atilde, void* stream) {
     LEV_TRY(set_device(h));
     Sizes z;
-    LEV_TRY(resolve(p, n, d, &z));
+    LEV_TRY(resolve(p, n, d, &z, true));
     if (!row_ptr || (nnz > 0 && (!col || !val)) || !Atilde) return fail(LEV_EINVAL, "NULL array");
     if (nnz < 0) return fail(LEV_EINVAL, "nnz < 0");
     LEV_TRY(check_prec(p->sketch_prec, "sketch"));

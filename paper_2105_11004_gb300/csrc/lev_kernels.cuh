@@ -12,7 +12,7 @@ namespace lev {
 // Bucket permutation of rows 0..n-1 (counting sort by h(i), rows ascending in
 // each bucket). count: s+1 ints (scratch), off: s+1 ints (out), tmp and perm:
 // n uint32 each (perm out). A perm entry is row | (sign < 0) << 31.
-cudaError_t launch_bucket_perm(int64_t n, int64_t s, uint64_t seed, int* count, int* off,
+cudaError_t launch_bucket_perm(int64_t n, int64_t s, uint64_t seed, int64_t row0, int* count, int* off,
                                uint32_t* tmp, uint32_t* perm, cudaStream_t st);
 
 // B (s x d, ld = d, FP32) = S A for dense A (n x d, lda).

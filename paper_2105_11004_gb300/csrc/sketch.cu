@@ -19,11 +19,13 @@ namespace {
 
 constexpr uint32_t kSignBit = 0x80000000u;
 
-__global__ void k_bucket_hist(int64_t n, uint32_t s, uint64_t key, int* count) {
+// Local row i of a row shard is hashed by its global index row0 + i, so the shards' sketches
+// are column blocks of one S and add up to the sketch of the whole matrix.
+__global__ void k_bucket_hist(int64_t n, int64_t row0, uint32_t s, uint64_t key, int* count) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (; i < n; i += stride) {
-        uint64_t x = splitmix64(key, (uint64_t)i);
+        uint64_t x = splitmix64(key, (uint64_t)(row0 + i));
         atomicAdd(&count[bucket_of(x, s)], 1);
     }
 }
@@ -75,12 +77,12 @@ __global__ void __launch_bounds__(1024) k_scan_offsets(const int* count, int* of
     if (t == 0) off[s] = carry_s;
 }
 
-__global__ void k_bucket_scatter(int64_t n, uint32_t s, uint64_t key, const int* off,
+__global__ void k_bucket_scatter(int64_t n, int64_t row0, uint32_t s, uint64_t key, const int* off,
                                  int* cursor, uint32_t* out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (; i < n; i += stride) {
-        uint64_t x = splitmix64(key, (uint64_t)i);
+        uint64_t x = splitmix64(key, (uint64_t)(row0 + i));
         uint32_t b = bucket_of(x, s);
         int pos = off[b] + atomicAdd(&cursor[b], 1);
         out[pos] = (uint32_t)i | ((x & 1ull) ? kSignBit : 0u);
@@ -407,16 +409,16 @@ int grid_for(int64_t work, int block, int cap = 1 << 20) {
 
 }  // namespace
 
-cudaError_t launch_bucket_perm(int64_t n, int64_t s, uint64_t seed, int* count, int* off,
+cudaError_t launch_bucket_perm(int64_t n, int64_t s, uint64_t seed, int64_t row0, int* count, int* off,
                                uint32_t* tmp, uint32_t* perm, cudaStream_t st) {
     const uint64_t key = stream_key(seed, kStreamHash);
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(s + 1), st);
     if (e != cudaSuccess) return e;
-    k_bucket_hist<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, (uint32_t)s, key, count);
+    k_bucket_hist<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, row0, (uint32_t)s, key, count);
     k_scan_offsets<<<1, 1024, 0, st>>>(count, off, (int)s);
     e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(s + 1), st);
     if (e != cudaSuccess) return e;
-    k_bucket_scatter<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, (uint32_t)s, key, off, count, tmp);
+    k_bucket_scatter<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, row0, (uint32_t)s, key, off, count, tmp);
     k_segment_sort<<<grid_for(s * 32, 256), 256, 0, st>>>(off, (int)s, tmp, perm);
     return cudaGetLastError();
 }

@@ -23,10 +23,11 @@ def to_np(t):
     return t.detach().cpu().numpy()
 
 
-def sketch_abs_scale(A64, s, m, seed):
-    """|G| (|S| |A|): the scale that bounds the rounding error of each entry of G S A."""
+def sketch_abs_scale(A64, s, m, seed, row0=0):
+    """|G| (|S| |A|): the scale that bounds the rounding error of each entry of G S A (A the
+    block of rows from global row row0)."""
     n, d = A64.shape
-    b, _ = orng.bucket_and_sign(n, s, seed)
+    b, _ = orng.bucket_and_sign(n, s, seed, start=row0)
     Babs = np.zeros((s, d))
     np.add.at(Babs, b, np.abs(A64))
     out = np.zeros((m, d))

@@ -38,9 +38,21 @@ def test_library_exports_every_declared_symbol(lev):
         assert name in lev.SIGNATURES
 
 
-def test_params_struct_layout_matches_header(lev):
-    # eps, delta, gamma (3 doubles), s, m, k (3 int64), tau, seed, 4 x int32, perm_in, rank_in
-    assert ctypes.sizeof(lev.lev_params) == 3 * 8 + 3 * 8 + 8 + 8 + 4 * 4 + 8 + 8
+def test_params_struct_layout_matches_header(lev, tmp_path):
+    """Every field of the ctypes mirror sits at the offset the C compiler gives it in lev.h."""
+    fields = [f for f, _ in lev.lev_params._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "lev.h"\nint main(void) {\n'
+                   '  printf("size %zu\\n", sizeof(lev_params));\n'
+                   + "".join(f'  printf("{f} %zu\\n", offsetof(lev_params, {f}));\n' for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(lev.lev_params)
+    for f in fields:
+        assert int(got[f]) == getattr(lev.lev_params, f).offset, f
     p = lev.make_params()
     assert p.eps == 0.5 and abs(p.delta - 1 / 3) < 1e-15 and p.gamma == 2.0 and p.tau == 1e-5
 
