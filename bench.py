@@ -529,6 +529,14 @@ def csr_timing(L, h, name, reps):
     sk_s = timed(lambda: L.lev_sketch_csr(h, rp, cl, vl, n, d, ps, At), reps)
     out["srht"] = {"t": t, "rank": r_s, "ms_per_step": ms_s, "rows_per_s": n / (ms_s * 1e-3), "sketch_ms": sk_s,
                    "gaussian_stage_flops": 2.0 * cfg["m"] * t * d, "note": "A~ = G (F (S A)), G m x t"}
+    # Alg. 7 (LS-HRN-exact) on the same matrix: B = A_K^T A_K from the rows' outer products
+    # (Lemma 3, FP64), its forced-pivot Cholesky, theta = ||A_K R^{-1}||^2 (k = d)
+    r_e = L.lev_exact_csr(h, rp, cl, vl, n, d, p, theta)
+    ms_e = timed(lambda: L.lev_exact_csr(h, rp, cl, vl, n, d, p, theta), max(1, reps // 2))
+    lens = np.diff(C.row_ptr).astype(np.float64)
+    out["exact"] = {"algorithm": "Alg. 7 (LS-HRN-exact), lev_exact_csr", "rank": r_e, "ms_per_call": ms_e,
+                    "rows_per_s": n / (ms_e * 1e-3), "gram_pairs": float(np.sum(lens * (lens + 1) / 2)),
+                    "note": "two host synchronisations per call (after each factorisation)"}
     return out
 
 

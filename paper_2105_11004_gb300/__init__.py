@@ -63,6 +63,8 @@ SIGNATURES = {
     "lev_device_status": (ctypes.c_int, [_c_void_p, _P(_i32)]),
     "lev_exact_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p, _P(_i64),
                                        _c_void_p, _c_void_p]),
+    "lev_exact_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params),
+                                     _c_void_p, _P(_i64), _c_void_p, _c_void_p]),
     "lev_set_timing": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "lev_rrqr_timing": (ctypes.c_int, [_c_void_p, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
@@ -223,6 +225,14 @@ def lev_exact_dense(h: Handle, A, p: lev_params, theta, perm=None, stream=None) 
     r = _i64(-1)
     rc = _check(lib.lev_exact_dense(h.ptr, _ptr(A), n, d, A.stride(0), ctypes.byref(p), _ptr(theta),
                                     ctypes.byref(r), _ptr(perm), _stream(stream)), allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_exact_csr(h: Handle, row_ptr, col, val, n, d, p: lev_params, theta, perm=None, stream=None) -> int:
+    """Alg. 7 (LS-HRN-exact) on a device CSR matrix; returns the rank."""
+    r = _i64(-1)
+    rc = _check(lib.lev_exact_csr(h.ptr, _ptr(row_ptr), _ptr(col), _ptr(val), n, d, col.numel(), ctypes.byref(p),
+                                  _ptr(theta), ctypes.byref(r), _ptr(perm), _stream(stream)), allow=(LEV_ERANK0,))
     return 0 if rc == LEV_ERANK0 else r.value
 
 

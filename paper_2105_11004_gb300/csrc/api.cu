@@ -666,6 +666,62 @@ int lev_exact_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t
     return LEV_OK;
 }
 
+int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n, int64_t d,
+                  int64_t nnz, const lev_params* p, float* theta, int64_t* rank, int32_t* perm_out, void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!row_ptr || (nnz > 0 && (!col || !val)) || !theta) return fail(LEV_EINVAL, "NULL array");
+    if (nnz < 0) return fail(LEV_EINVAL, "nnz < 0");
+    if (is_host_pointer(row_ptr) || (nnz > 0 && (is_host_pointer(col) || is_host_pointer(val))) ||
+        is_host_pointer(theta))
+        return fail(LEV_EINVAL, "lev_exact_csr takes device arrays");
+    if (p->flags & (LEV_FORCE_PIVOTS | LEV_OMEGA_IDENTITY))
+        return fail(LEV_EINVAL, "lev_exact_csr takes neither forced pivots nor LEV_OMEGA_IDENTITY");
+    if (d > 1024) return fail(LEV_EINVAL, "lev_exact_csr needs d <= 1024 (the Gram route of the QR)");
+    if (p->final_prec != LEV_FP32) return fail(LEV_EINVAL, "the CSR final pass supports LEV_FP32 only");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    cudaStream_t st = (cudaStream_t)stream;
+    // steps 1-3 (Alg. 7): K and the rank k from the pivoted QR of the CountGauss sketch
+    LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
+    LEV_TRY(sketch_common_csr(h, row_ptr, col, val, n, d, p, z, (float*)h->Atilde.ptr, st));
+    LEV_TRY(ensure(h->R, sizeof(double) * (size_t)d * d));
+    LEV_TRY(ensure(h->perm_d, sizeof(int32_t) * (size_t)d));
+    int32_t* perm = perm_out ? perm_out : (int32_t*)h->perm_d.ptr;
+    lev::QrScratch qs;
+    LEV_TRY(rrqr_common(h, (const float*)h->Atilde.ptr, z.m, d, tau_of(p), nullptr, 0, perm, (double*)h->R.ptr, &qs,
+                        st));
+    int64_t k = 0;
+    int rc = finish(h, qs, &k, st);
+    if (rc == LEV_ERANK0) {
+        LEV_CUDA(cudaMemsetAsync(theta, 0, sizeof(float) * (size_t)n, st));
+        if (rank) *rank = 0;
+        return rc;
+    }
+    LEV_TRY(rc);
+    // step 4: B = A_K^T A_K from the rows' outer products (Lemma 3), FP64 (all of A^T A, read
+    // at K in pivot order); step 5 by the Cholesky factor B = R^T R with the pivots of step 2
+    // forced
+    LEV_CUDA(lev::launch_gram_csr_fp64(row_ptr, col, val, n, d, qs.G, st));
+    LEV_CUDA(lev::launch_factor_gram(n, d, tau_of(p), perm, k, qs, perm, (double*)h->R.ptr, h->status, st));
+    int64_t k2 = 0;
+    rc = finish(h, qs, &k2, st);
+    if (rc == LEV_ERANK0) {
+        LEV_CUDA(cudaMemsetAsync(theta, 0, sizeof(float) * (size_t)n, st));
+        if (rank) *rank = 0;
+        return rc;
+    }
+    LEV_TRY(rc);
+    // step 6: theta_i = ||A_{i,K} R^{-1}||^2 with M = R^{-1} (Omega = I) scattered into Mfull
+    LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * d));
+    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, qs.rank, d, d, p->seed, true, (float*)h->Mfull.ptr, st));
+    if (perm != (int32_t*)h->perm_d.ptr)
+        LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
+    LEV_CUDA(lev::launch_final_csr_fp32(row_ptr, col, val, n, d, (const float*)h->Mfull.ptr, d, theta, st));
+    if (rank) *rank = k2;
+    return LEV_OK;
+}
+
 int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const lev_params* p,
                        float* theta, int64_t* rank, int32_t* perm, void* stream) {
     LEV_TRY(set_device(h));

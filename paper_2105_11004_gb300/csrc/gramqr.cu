@@ -99,6 +99,56 @@ __global__ void k_gram_reduce(const double* __restrict__ Gp, int d, int splits, 
     }
 }
 
+// B = A^T A of a CSR matrix as the sum of its rows' outer products (Lemma 3), FP64, into the
+// upper triangle of G (d x d, zeroed by the caller). One warp per row: the first 32 entries of a
+// chunk are held one per lane and broadcast in turn as entry p; the lanes take the entries q >= p
+// of the row. A product of two FP32 values is exact in FP64; the sums are FP64 atomics in L2, so
+// their order (and the last bits of G) varies between runs. Duplicate columns of a row add up
+// (the pair p != q on one cell counts twice, once for each order); columns outside [0, d) are
+// skipped.
+__global__ void __launch_bounds__(256) k_gram_csr_fp64(const int64_t* __restrict__ row_ptr,
+                                                       const int32_t* __restrict__ col,
+                                                       const float* __restrict__ val, int64_t n, int d,
+                                                       double* __restrict__ G) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+        for (int64_t pb = p0; pb < p1; pb += 32) {
+            const int cnt = (int)min((int64_t)32, p1 - pb);
+            int my_c = -1;
+            float my_v = 0.f;
+            if (lane < cnt) {
+                my_c = col[pb + lane];
+                my_v = val[pb + lane];
+            }
+            for (int u = 0; u < cnt; ++u) {
+                const int cp = __shfl_sync(0xffffffffu, my_c, u);
+                const double vp = (double)__shfl_sync(0xffffffffu, my_v, u);
+                if ((unsigned)cp >= (unsigned)d) continue;                  // uniform over the warp
+                for (int64_t q = pb + u + lane; q < p1; q += 32) {
+                    const int cq = col[q];
+                    if ((unsigned)cq >= (unsigned)d) continue;
+                    double x = vp * (double)val[q];
+                    if (cq == cp && q != pb + u) x *= 2.0;
+                    const int a = cp < cq ? cp : cq, b = cp < cq ? cq : cp;
+                    atomicAdd(&G[(int64_t)a * d + b], x);
+                }
+            }
+        }
+    }
+}
+
+// G[j][i] = G[i][j] for i < j.
+__global__ void k_mirror_upper(double* __restrict__ G, int d) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)d * d;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / d), j = (int)(e % d);
+        if (i > j) G[e] = G[(int64_t)j * d + i];
+    }
+}
+
 // ---------------------------------------------------------------- helpers
 
 __device__ __forceinline__ uint64_t gtimer() {
@@ -388,6 +438,18 @@ cudaError_t launch_gram_fp64(const float* A, int64_t lda, int64_t m, int64_t d, 
     dim3 grid((unsigned)gram_tiles((int)d), (unsigned)splits);
     k_gram_fp64<<<grid, 256, 0, st>>>(A, lda, (int)m, (int)d, rows_per_split, Gp);
     k_gram_reduce<<<152 * 4, 256, 0, st>>>(Gp, (int)d, splits, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_csr_fp64(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                                 int64_t d, double* G, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * (size_t)(d * d), st);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (n * 32 + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    k_gram_csr_fp64<<<(unsigned)grid, 256, 0, st>>>(row_ptr, col, val, n, (int)d, G);
+    k_mirror_upper<<<152 * 4, 256, 0, st>>>(G, (int)d);
     return cudaGetLastError();
 }
 

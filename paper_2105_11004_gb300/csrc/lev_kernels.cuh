@@ -66,6 +66,10 @@ size_t gram_partial_doubles(int64_t m, int64_t d);
 // gram_partial_doubles(m, d) doubles of split partials.
 cudaError_t launch_gram_fp64(const float* A, int64_t lda, int64_t m, int64_t d, double* Gp, double* G,
                              cudaStream_t st);
+// G (d x d FP64, both triangles) = A^T A for CSR A (n rows) by the rows' outer products, FP64
+// atomics (the order of the sums varies between runs).
+cudaError_t launch_gram_csr_fp64(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                                 int64_t d, double* G, cudaStream_t st);
 // The grid pivoted Cholesky of q.G (rank test as lev_rrqr's with min(m, d) steps; forced pivots
 // optional): fills q.Rorig, q.piv, q.rank.
 cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,

@@ -168,6 +168,37 @@ def test_csr_8e6x1024_srht(L, h):
     assert abs(float(theta.astype(np.float64).sum()) / want_sum - 1) < 0.03
 
 
+def test_csr_8e6x1024_exact(L, h):
+    """Alg. 7 on the CSR 8e6 x 1024 workload (lev_exact_csr): full rank, the scores sum to the
+    rank (trace of the hat matrix), 0 <= theta <= 1, and 2,000 sampled rows against
+    a_K B^{-1} a_K^T with B = A^T A formed on the host in FP64 (rows with more than 32 entries
+    densified through a BLAS product, the others as a scipy sparse product)."""
+    import scipy.linalg as sla
+    import torch
+    cfg = W.CONFIGS["csr_8e6x1024"]
+    n, d, s, m, k = cfg["n"], cfg["d"], cfg["s"], cfg["m"], cfg["k"]
+    C = W.csr_uniform(n, d, seed=cfg["data_seed"])
+    p = L.make_params(s=s, m=m, k=k, tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3")
+    theta_t = torch.empty(n, device="cuda")
+    perm_t = torch.empty(d, dtype=torch.int32, device="cuda")
+    r = L.lev_exact_csr(h, to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val), n, d, p, theta_t, perm_t)
+    theta = to_np(theta_t).astype(np.float64)
+    assert r == d
+    assert abs(theta.sum() - d) < 1e-4 * d
+    assert theta.min() >= 0 and theta.max() <= 1 + 1e-5
+    A = sp.csr_matrix((C.val.astype(np.float64), C.col, C.row_ptr), shape=(n, d))
+    heavy = np.diff(C.row_ptr) > 32
+    Ah = A[np.flatnonzero(heavy)].toarray()
+    Al = A[np.flatnonzero(~heavy)]
+    B = Ah.T @ Ah + (Al.T @ Al).toarray()
+    cf = sla.cho_factor(B)
+    rows = np.random.default_rng(4).integers(0, n, 2000)
+    Ar = A[rows].toarray()
+    want = np.einsum("ij,ij->i", Ar, sla.cho_solve(cf, Ar.T).T)
+    assert max_rel(theta[rows], want) <= 1e-5
+    assert L.lev_device_status(h) == 0
+
+
 def test_csr_8e7x1024_rank1014(L, h):
     """CSR 8e7 x 1024, ~12 nnz/row (~1e9 nnz), column j + 512 = 2 x column j for j < 10:
     rank exactly 1014, no dependent pair both selected, sampled sketch entries and theta~."""

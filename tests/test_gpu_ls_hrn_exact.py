@@ -87,3 +87,75 @@ def test_rejects_unsupported(L, h):
     with pytest.raises(L.LevError) as e:
         L.lev_exact_dense(h, torch.zeros((10, 4), device="cuda"), p, torch.empty(10, device="cuda"))
     assert e.value.code == L.LEV_EINVAL
+
+
+# ---- CSR A (lev_exact_csr): B = A_K^T A_K by the rows' outer products (Lemma 3) ----
+
+def _run_csr(L, h, C, **cfg):
+    import torch
+    n, d = C.shape
+    p = L.make_params(sketch_prec="bf16x3", final_prec="fp32", **cfg)
+    theta = torch.full((n,), float("nan"), device="cuda")
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    r = L.lev_exact_csr(h, to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val), n, d, p, theta, perm)
+    torch.cuda.synchronize()
+    return to_np(theta).astype(np.float64), r, to_np(perm)
+
+
+def _scipy(C):
+    import scipy.sparse as sp
+    return sp.csr_matrix((C.val.astype(np.float64), C.col, C.row_ptr), shape=C.shape)
+
+
+@pytest.mark.parametrize("n,d,heavy", [(60000, 96, 64), (7001, 33, 33)])
+def test_csr_matches_oracle(L, h, n, d, heavy):
+    C = W.csr_uniform(n, d, nnz_per_row=6, heavy_frac=0.02, heavy_nnz=heavy, seed=n % 97)
+    cfg = dict(s=8192, m=4 * d, k=64, tau=1e-6, seed=5)
+    th, r, perm = _run_csr(L, h, C, **cfg)
+    want, k, operm = X.ls_hrn_exact(_scipy(C), cfg["s"], cfg["m"], cfg["tau"], cfg["seed"])
+    assert r == k == d
+    assert np.array_equal(perm[:r], operm[:k])
+    assert max_rel(th, want) <= 1e-5
+    assert abs(th.sum() - d) < 1e-5 * d                 # sum of exact leverage scores = rank
+    assert L.lev_device_status(h) == 0
+
+
+def test_csr_rank_deficient(L, h):
+    n, d = 50000, 64
+    C = W.csr_dup_columns(n, d, nnz_per_row=8, pairs=5, seed=8)
+    cfg = dict(s=8192, m=256, k=64, tau=1e-5, seed=6)
+    th, r, perm = _run_csr(L, h, C, **cfg)
+    want, k, operm = X.ls_hrn_exact(_scipy(C), cfg["s"], cfg["m"], cfg["tau"], cfg["seed"])
+    assert r == k == d - 5
+    assert np.array_equal(perm[:r], operm[:k])
+    assert max_rel(th, want) <= 1e-5
+    assert abs(th.sum() - (d - 5)) < 1e-3
+
+
+def test_csr_unsorted_duplicate_and_empty_rows(L, h):
+    """Columns in any order, repeated columns (they add up), rows with no entries (theta = 0)."""
+    rs = np.random.default_rng(12)
+    n, d = 20000, 24
+    lens = rs.integers(0, 9, size=n)
+    lens[::97] = 0
+    row_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    col = rs.integers(0, d, size=row_ptr[-1]).astype(np.int32)           # unsorted, repeats
+    val = rs.standard_normal(row_ptr[-1]).astype(np.float32)
+    C = W.CSR(row_ptr, col, val, (n, d))
+    cfg = dict(s=4096, m=96, k=32, tau=1e-6, seed=9)
+    th, r, perm = _run_csr(L, h, C, **cfg)
+    want, k, operm = X.ls_hrn_exact(_scipy(C), cfg["s"], cfg["m"], cfg["tau"], cfg["seed"])
+    assert r == k == d
+    assert np.array_equal(perm[:r], operm[:k])
+    assert np.all(th[lens == 0] == 0)
+    assert max_rel(th, want) <= 1e-5
+
+
+def test_csr_repeat_runs_agree(L, h):
+    """The FP64 atomic sums of B may round in another order each run: theta agrees to ~1e-12."""
+    C = W.csr_uniform(30000, 48, nnz_per_row=6, heavy_frac=0.02, heavy_nnz=48, seed=3)
+    cfg = dict(s=4096, m=192, k=32, tau=1e-6, seed=2)
+    a, ra, pa = _run_csr(L, h, C, **cfg)
+    b, rb, pb = _run_csr(L, h, C, **cfg)
+    assert ra == rb and np.array_equal(pa, pb)
+    assert max_rel(a, b) <= 1e-6
