@@ -144,10 +144,14 @@ class Estimate:
 
 def estimate(A, s: int, m: int, k: int, tau: float, seed: int, *,
              sketch_identity: bool = False, omega_identity: bool = False,
-             forced_perm=None, forced_rank=None, Atilde=None, srht_t: int = 0) -> Estimate:
+             forced_perm=None, forced_rank=None, Atilde=None, srht_t: int = 0,
+             rank_rule: str = "diag", srrqr_phi: float = 0.0) -> Estimate:
     """Alg. 10 end to end: returns theta (n), rank, perm (d), Atilde, R (r x d), M (r x k).
 
-    ``Atilde`` may be passed in to run steps 4-7 on a given sketch.
+    ``Atilde`` may be passed in to run steps 4-7 on a given sketch. ``rank_rule="svd"`` takes
+    the rank from the singular values of the sketch (Alg. 11 step 3, Sec. 6.2) and the columns
+    from its pivoted QR run to the end; ``srrqr_phi >= 1`` then improves the selected columns by
+    strong-RRQR swaps at that rank (oracle/rank.py).
     """
     n, d = A.shape
     if Atilde is None:
@@ -156,6 +160,18 @@ def estimate(A, s: int, m: int, k: int, tau: float, seed: int, *,
             Atilde = Atilde.toarray() if sp.issparse(Atilde) else np.array(Atilde)
         else:
             Atilde = sketch(A, s, m, seed, srht_t)
+    if forced_perm is None and (rank_rule != "diag" or srrqr_phi):
+        from . import rank as rank_mod
+        if rank_rule == "svd":
+            forced_perm = pivoted_qr(Atilde, 0.0).perm
+            forced_rank = rank_mod.rank_svd(rank_mod.singular_values(Atilde), tau)
+        elif rank_rule == "diag":
+            qr0 = pivoted_qr(Atilde, tau)
+            forced_perm, forced_rank = qr0.perm, qr0.rank
+        else:
+            raise ValueError(f"unknown rank rule {rank_rule}")
+        if srrqr_phi:
+            forced_perm = rank_mod.srrqr(Atilde, forced_rank, srrqr_phi, forced_perm)[0]
     qr = pivoted_qr(Atilde, tau, forced_perm=forced_perm, forced_rank=forced_rank)
     r = qr.rank
     if r == 0:
