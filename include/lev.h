@@ -70,6 +70,10 @@ extern "C" {
 #define LEV_FORCE_PIVOTS    4u  /* take perm_in[0..rank_in) as the pivots, no rank test */
 #define LEV_HOST_ASYNC      8u  /* lev_estimate_dense with host buffers and rank == NULL: enqueue only */
 #define LEV_SKETCH_SRHT    16u  /* A~ = G F S A: an SRHT F (t = srht_t rows) after the CountSketch (Sec. 3.1) */
+#define LEV_RANK_SVD       32u  /* rank = #{sigma_j(A~) > tau sigma_1(A~)} (Alg. 11 step 3, Sec. 6.2); columns
+                                   from the pivoted QR run to the end; d <= 1024 */
+#define LEV_SRRQR          64u  /* after the rank: strong-RRQR swaps at that rank until every
+                                   rho_ij <= phi (Alg. 2); d <= 1024 */
 
 typedef struct lev_handle lev_handle;
 
@@ -92,6 +96,7 @@ typedef struct lev_params {
                                 row0 + i); read by lev_sketch_* and lev_resolve_sizes, 0 elsewhere */
     int64_t  n_total;        /* row shard: rows of the whole matrix (k = 0 is derived from it);
                                 0 = the call's n; same entry points as row0 */
+    double   phi;            /* strong-RRQR bound (LEV_SRRQR), >= 1; 0 means 2 */
 } lev_params;
 
 /* Create a handle on CUDA device `device` (the device is made current for every
@@ -158,6 +163,23 @@ int lev_sketch_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, co
  * LEV_ETIMEOUT, LEV_ERANK0 (rank 0; perm = identity, R = 0). */
 int lev_rrqr(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double tau,
              int32_t* perm, double* R, int64_t* rank, void* stream);
+
+/* The pivoted QR of A~ (as lev_rrqr) with the rank rule of p->flags, tau = p->tau:
+ *  - no flag: the diagonal test of lev_rrqr;
+ *  - LEV_RANK_SVD: the QR runs to the end (column order only) and the rank is the number of
+ *    singular values of A~ above tau sigma_1 (Alg. 11 step 3; Sec. 6.2 advises the singular
+ *    values where the diagonal of R misses a small gap), from a one-sided Jacobi SVD of R;
+ *  - LEV_SRRQR: then strong-RRQR swaps at that rank (Alg. 2, Gu and Eisenstat): while the
+ *    largest rho_ij = sqrt((R11^{-1} R12)_ij^2 + (gamma_j(R22) ||e_i^T R11^{-1}||)^2) exceeds
+ *    p->phi (0 means 2), selected column i and unselected column j trade places; each swap
+ *    re-factors through the Gram matrix of A~ and synchronises `stream` once.
+ * perm, R, rank: as lev_rrqr (R rows < rank for the final columns). sigma: device, d doubles or
+ * NULL: the singular values of A~, descending (LEV_RANK_SVD only). swaps: host or NULL: the
+ * number of swaps. d <= 1024 with either flag. Errors: LEV_EINVAL (shapes, phi < 1, no
+ * settling within 64 d swaps), LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0. */
+int lev_rrqr_select(lev_handle* h, const float* Atilde, int64_t m, int64_t d, const lev_params* p,
+                    int32_t* perm, double* R, int64_t* rank, double* sigma, int64_t* swaps,
+                    void* stream);
 
 /* The small factor of the final pass (Alg. 8 step 4 with the QR
  * orthogonaliser): M = R_11^{-1} Omega (r x k) by FP64 back-substitution, with

@@ -18,6 +18,7 @@ from .build import LIB_PATH, build as build_library  # noqa: F401
 LEV_OK, LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0 = 0, 1, 2, 3, 4, 5
 LEV_FP32, LEV_TF32, LEV_BF16, LEV_BF16X3 = 0, 1, 2, 3
 LEV_OMEGA_IDENTITY, LEV_SKETCH_IDENTITY, LEV_FORCE_PIVOTS, LEV_HOST_ASYNC, LEV_SKETCH_SRHT = 1, 2, 4, 8, 16
+LEV_RANK_SVD, LEV_SRRQR = 32, 64
 PRECISIONS = {"fp32": LEV_FP32, "tf32": LEV_TF32, "bf16": LEV_BF16, "bf16x3": LEV_BF16X3}
 
 # Every symbol include/lev.h declares, with (restype, argtypes).
@@ -32,7 +33,7 @@ class lev_params(ctypes.Structure):
         ("tau", _dbl), ("seed", _u64),
         ("sketch_prec", _i32), ("final_prec", _i32), ("flags", _u32), ("srht_t", _i32),
         ("perm_in", _c_void_p), ("rank_in", _i64),
-        ("row0", _i64), ("n_total", _i64),
+        ("row0", _i64), ("n_total", _i64), ("phi", _dbl),
     ]
 
 
@@ -65,6 +66,8 @@ SIGNATURES = {
                                        _c_void_p, _c_void_p]),
     "lev_exact_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params),
                                      _c_void_p, _P(_i64), _c_void_p, _c_void_p]),
+    "lev_rrqr_select": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _P(lev_params), _c_void_p, _c_void_p,
+                                       _P(_i64), _c_void_p, _P(_i64), _c_void_p]),
     "lev_set_timing": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "lev_rrqr_timing": (ctypes.c_int, [_c_void_p, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
@@ -138,7 +141,8 @@ def default_handle(device: int = 0) -> Handle:
 
 def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec="fp32", eps=0.5,
                 delta=1.0 / 3.0, gamma=2.0, omega_identity=False, sketch_identity=False,
-                perm_in=None, rank_in=0, host_async=False, srht_t=0, row0=0, n_total=0) -> lev_params:
+                perm_in=None, rank_in=0, host_async=False, srht_t=0, row0=0, n_total=0, rank_svd=False,
+                srrqr_phi=0.0) -> lev_params:
     p = lev_params()
     _check(lib.lev_params_init(ctypes.byref(p)))
     p.eps, p.delta, p.gamma = eps, delta, gamma
@@ -159,6 +163,11 @@ def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec=
         flags |= LEV_FORCE_PIVOTS
         p.perm_in = perm_in.data_ptr()
         p.rank_in = int(rank_in)
+    if rank_svd:
+        flags |= LEV_RANK_SVD
+    if srrqr_phi:
+        flags |= LEV_SRRQR
+        p.phi = float(srrqr_phi)
     p.flags = flags
     p.row0, p.n_total = int(row0), int(n_total)
     return p
@@ -188,6 +197,15 @@ def lev_rrqr(h: Handle, Atilde, tau, perm, R, stream=None) -> int:
     rc = _check(lib.lev_rrqr(h.ptr, _ptr(Atilde), m, d, float(tau), _ptr(perm), _ptr(R), ctypes.byref(r),
                              _stream(stream)), allow=(LEV_ERANK0,))
     return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_rrqr_select(h: Handle, Atilde, p: lev_params, perm, R, sigma=None, stream=None):
+    """Pivoted QR with p's rank rule (LEV_RANK_SVD, LEV_SRRQR): returns (rank, swaps)."""
+    m, d = Atilde.shape
+    r, sw = _i64(), _i64()
+    rc = _check(lib.lev_rrqr_select(h.ptr, _ptr(Atilde), m, d, ctypes.byref(p), _ptr(perm), _ptr(R), ctypes.byref(r),
+                                    _ptr(sigma), ctypes.byref(sw), _stream(stream)), allow=(LEV_ERANK0,))
+    return (0 if rc == LEV_ERANK0 else r.value), sw.value
 
 
 def lev_omega_factor(h: Handle, R, perm, d_rank, d, k, seed, flags, Mfull, stream=None):

@@ -81,6 +81,8 @@ struct lev_handle {
     Buf stageA[2];
     Buf exact_gp;  // split partials of the Gram matrix of A (LS-HRN-exact)
     Buf srht_c;    // F (S A), t x d (LEV_SKETCH_SRHT)
+    Buf rank_ws;   // Jacobi copy of R, strong-RRQR Z, norms and argmax partials (LEV_RANK_SVD, LEV_SRRQR)
+    int64_t last_swaps = 0;
     Buf tc_pad;   // A copied with a 16-byte row stride when the caller's cannot feed TMA
     cudaStream_t copy_st = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
@@ -352,6 +354,7 @@ int rrqr_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double
 }
 
 // Synchronise, read the rank and the device status word.
+
 int finish(lev_handle* h, const lev::QrScratch& qs, int64_t* rank, cudaStream_t st) {
     LEV_CUDA(cudaMemcpyAsync(h->host_rank, qs.rank, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     int32_t status = 0;
@@ -364,6 +367,69 @@ int finish(lev_handle* h, const lev::QrScratch& qs, int64_t* rank, cudaStream_t 
     }
     if (rank) *rank = h->host_rank[0];
     if (h->host_rank[0] == 0) return fail(LEV_ERANK0, "numerical rank is 0");
+    return LEV_OK;
+}
+
+// The pivoted QR of A~ with the rank rule of p: the diagonal test of rrqr_common by default;
+// with LEV_RANK_SVD the QR runs to the end and the rank is the count of singular values of A~
+// above tau sigma_1 (sigma: optional device output, d doubles, descending); with LEV_SRRQR
+// strong-RRQR swaps at that rank follow, each step a forced-pivot Cholesky of the Gram matrix of
+// A~ for the current columns, then the largest rho, until rho <= phi. Leaves perm, R (rows < rank,
+// pivot order) and qs->rank like rrqr_common; h->last_swaps counts the swaps. Synchronises `st`
+// once per strong-RRQR step.
+int select_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, const lev_params* p, int32_t* perm,
+                  double* R, lev::QrScratch* qs, double* sigma_out, cudaStream_t st) {
+    const bool svd = (p->flags & LEV_RANK_SVD) != 0, sr = (p->flags & LEV_SRRQR) != 0;
+    h->last_swaps = 0;
+    if (!svd && !sr) {
+        if (sigma_out) return fail(LEV_EINVAL, "sigma is computed with LEV_RANK_SVD only");
+        return rrqr_common(h, Atilde, m, d, tau_of(p), nullptr, 0, perm, R, qs, st);
+    }
+    if (d > 1024) return fail(LEV_EINVAL, "LEV_RANK_SVD and LEV_SRRQR need d <= 1024");
+    if (p->flags & LEV_FORCE_PIVOTS) return fail(LEV_EINVAL, "forced pivots take no rank rule");
+    const double phi = p->phi == 0 ? 2.0 : p->phi;
+    if (sr && !(phi >= 1.0)) return fail(LEV_EINVAL, "phi must be >= 1 (got %g)", phi);
+    LEV_TRY(ensure(h->rank_ws, sizeof(double) * lev::rank_scratch_doubles(d)));
+    double* ws = (double*)h->rank_ws.ptr;
+    double* Y = ws;                                   // d x d (Jacobi) or Z (strong RRQR)
+    double* sig = ws + d * d;                         // d
+    double* wn = sig + d;                             // d
+    double* g2 = wn + d;                              // d
+    double* out = g2 + d;                             // 4
+    double* part_v = out + 16;                        // 1024
+    long long* part_e = reinterpret_cast<long long*>(part_v + 1024);   // 1024
+    unsigned* work = reinterpret_cast<unsigned*>(part_e + 1024);     // 64 (barrier, rotation counts)
+    int32_t* order = reinterpret_cast<int32_t*>(work + 64);
+    int32_t* sweeps = order + d;
+    if (svd) {
+        LEV_TRY(rrqr_common(h, Atilde, m, d, 0.0, nullptr, 0, perm, R, qs, st));      // every step
+        LEV_CUDA(lev::launch_svd_rank(R, qs->rank, d, tau_of(p), Y, work, sigma_out ? sigma_out : sig, order,
+                                      qs->rank, sweeps, h->status, h->num_sms, st));
+    } else {
+        LEV_TRY(rrqr_common(h, Atilde, m, d, tau_of(p), nullptr, 0, perm, R, qs, st));
+    }
+    if (!sr) return LEV_OK;
+    int64_t k = 0;
+    LEV_TRY(finish(h, *qs, &k, st));
+    if (k >= d) return LEV_OK;
+    LEV_TRY(ensure(h->omega_rs, sizeof(double) * (size_t)d * d));
+    double* Rs = (double*)h->omega_rs.ptr;
+    LEV_CUDA(lev::launch_gram_fp64(Atilde, d, m, d, qs->Gp, qs->G, st));
+    const int64_t max_swaps = 64 * d;
+    double* host_out = reinterpret_cast<double*>(h->host_rank + 2);
+    for (int64_t it = 0;; ++it) {
+        LEV_CUDA(lev::launch_factor_gram(m, d, tau_of(p), perm, k, *qs, perm, R, h->status, st));
+        LEV_CUDA(lev::launch_scaled_transpose(R, qs->rank, d, Rs, st));
+        LEV_CUDA(lev::launch_srrqr_step(R, Rs, qs->G, perm, d, k, phi, Y, wn, g2, part_v, part_e, out, st));
+        LEV_CUDA(cudaMemcpyAsync(host_out, out, sizeof(double), cudaMemcpyDeviceToHost, st));
+        int64_t k2 = 0;
+        LEV_TRY(finish(h, *qs, &k2, st));
+        if (k2 != k) return fail(LEV_EINVAL, "strong RRQR: the forced factor stopped at %lld of %lld columns",
+                                 (long long)k2, (long long)k);
+        if (!(*host_out > phi * phi)) break;
+        h->last_swaps = it + 1;
+        if (it + 1 >= max_swaps) return fail(LEV_EINVAL, "strong RRQR did not settle in %lld swaps", (long long)max_swaps);
+    }
     return LEV_OK;
 }
 
@@ -530,6 +596,20 @@ int lev_rrqr(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double ta
     return finish(h, qs, rank, st);
 }
 
+int lev_rrqr_select(lev_handle* h, const float* Atilde, int64_t m, int64_t d, const lev_params* p, int32_t* perm,
+                    double* R, int64_t* rank, double* sigma, int64_t* swaps, void* stream) {
+    LEV_TRY(set_device(h));
+    if (!Atilde || !perm || !R || !p) return fail(LEV_EINVAL, "NULL array");
+    if (m < 1 || d < 1 || d > 4096 || m > (1 << 20)) return fail(LEV_EINVAL, "bad shape m=%lld d=%lld", (long long)m, (long long)d);
+    if (p->flags & LEV_FORCE_PIVOTS) return fail(LEV_EINVAL, "lev_rrqr_select takes no forced pivots");
+    cudaStream_t st = (cudaStream_t)stream;
+    lev::QrScratch qs;
+    LEV_TRY(select_common(h, Atilde, m, d, p, perm, R, &qs, sigma, st));
+    if (swaps) *swaps = h->last_swaps;
+    if (!rank) return LEV_OK;
+    return finish(h, qs, rank, st);
+}
+
 int lev_omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int64_t* d_rank,
                      int64_t d, int64_t k, uint64_t seed, uint32_t flags, float* Mfull, void* stream) {
     LEV_TRY(set_device(h));
@@ -569,8 +649,11 @@ static int estimate_tail(lev_handle* h, const Sizes& z, int64_t d, const lev_par
     const bool forced = (p->flags & LEV_FORCE_PIVOTS) != 0;
     if (forced && (!p->perm_in || p->rank_in < 0 || p->rank_in > d))
         return fail(LEV_EINVAL, "LEV_FORCE_PIVOTS needs perm_in and 0 <= rank_in <= d");
-    LEV_TRY(rrqr_common(h, (const float*)h->Atilde.ptr, z.m, d, tau_of(p), forced ? p->perm_in : nullptr,
-                        forced ? p->rank_in : 0, perm, (double*)h->R.ptr, qs, st));
+    if (forced)
+        LEV_TRY(rrqr_common(h, (const float*)h->Atilde.ptr, z.m, d, tau_of(p), p->perm_in, p->rank_in, perm,
+                            (double*)h->R.ptr, qs, st));
+    else
+        LEV_TRY(select_common(h, (const float*)h->Atilde.ptr, z.m, d, p, perm, (double*)h->R.ptr, qs, nullptr, st));
     if (perm != (int32_t*)h->perm_d.ptr)
         LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
     LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * z.k));
@@ -631,8 +714,7 @@ int lev_exact_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t
     LEV_TRY(ensure(h->perm_d, sizeof(int32_t) * (size_t)d));
     int32_t* perm = perm_out ? perm_out : (int32_t*)h->perm_d.ptr;
     lev::QrScratch qs;
-    LEV_TRY(rrqr_common(h, (const float*)h->Atilde.ptr, z.m, d, tau_of(p), nullptr, 0, perm, (double*)h->R.ptr, &qs,
-                        st));
+    LEV_TRY(select_common(h, (const float*)h->Atilde.ptr, z.m, d, p, perm, (double*)h->R.ptr, &qs, nullptr, st));
     int64_t k = 0;
     int rc = finish(h, qs, &k, st);
     if (rc == LEV_ERANK0) {
@@ -689,8 +771,7 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     LEV_TRY(ensure(h->perm_d, sizeof(int32_t) * (size_t)d));
     int32_t* perm = perm_out ? perm_out : (int32_t*)h->perm_d.ptr;
     lev::QrScratch qs;
-    LEV_TRY(rrqr_common(h, (const float*)h->Atilde.ptr, z.m, d, tau_of(p), nullptr, 0, perm, (double*)h->R.ptr, &qs,
-                        st));
+    LEV_TRY(select_common(h, (const float*)h->Atilde.ptr, z.m, d, p, perm, (double*)h->R.ptr, &qs, nullptr, st));
     int64_t k = 0;
     int rc = finish(h, qs, &k, st);
     if (rc == LEV_ERANK0) {

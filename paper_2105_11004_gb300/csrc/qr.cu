@@ -406,6 +406,13 @@ cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double 
     return cudaGetLastError();
 }
 
+cudaError_t launch_scaled_transpose(const double* R, const int64_t* d_rank, int64_t d, double* Rs, cudaStream_t st) {
+    int grid = (int)((d * d + 255) / 256);
+    if (grid > 152 * 8) grid = 152 * 8;
+    k_scaled_transpose<<<grid, 256, 0, st>>>(R, d_rank, (int)d, Rs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gen_omega(uint64_t seed, int64_t d, int64_t k, double* Omega, cudaStream_t st) {
     const int64_t total = d * k;
     int grid = (int)((total + 255) / 256);
