@@ -181,6 +181,35 @@ int lev_rrqr_select(lev_handle* h, const float* Atilde, int64_t m, int64_t d, co
                     int32_t* perm, double* R, int64_t* rank, double* sigma, int64_t* swaps,
                     void* stream);
 
+/* Alg. 11 (CountGaussPrecondition) on dense A (device, n x d FP32, lda >= d): the CountGauss
+ * sketch A~ = G S A with p's sizes, seed and sketch_prec, its SVD (the LEV_RANK_SVD path of
+ * lev_rrqr_select), k = #{sigma_j > p->tau sigma_1}, and N = V_k Sigma_k^{-1} written to N (device,
+ * d x d FP64, row-major; columns >= k are zero). By the GSA preconditioning theorem (Sec. 5.2)
+ * kappa(A N) <= xi eta with high probability, whatever kappa(A) is. rank: host, may be NULL.
+ * sigma: device d doubles or NULL (the sketch's singular values, descending). d <= 1024.
+ * Synchronises `stream`. Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0. */
+int lev_precondition_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
+                           const lev_params* p, double* N, int64_t* rank, double* sigma,
+                           void* stream);
+
+/* The same on CSR A (device arrays, the conventions of lev_sketch_csr). */
+int lev_precondition_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
+                         int64_t n, int64_t d, int64_t nnz, const lev_params* p, double* N,
+                         int64_t* rank, double* sigma, void* stream);
+
+/* LSQR (Paige and Saunders) on min_y ||A N y - b|| with A dense (device, n x d FP32, lda >= d), N
+ * (device, d x d FP64 row-major, first k columns used, e.g. from lev_precondition_dense) and b
+ * (device, n FP32); x = N y (device, d FP64), the minimum-norm least-squares solution A^+ b when N
+ * comes from Alg. 11. Each iteration is one pass over A (A (N v) and A^T u' together) plus FP64
+ * steps on d-vectors; the passes compute in FP32 with FP64 partial sums, so atol and btol much
+ * below 1e-6 are not reached. Stops when ||(AN)^T r|| <= atol ||AN||_F ||r||, ||r|| <= btol ||b||,
+ * or after max_iter iterations (atol, btol <= 0 mean 1e-6). iters, rnorm (host, may be NULL):
+ * iterations run and the residual norm estimate. d <= 1024. Synchronises `stream` every 16
+ * iterations. Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA. */
+int lev_lsqr_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const double* N,
+                   int64_t k, const float* b, double* x, int32_t max_iter, double atol, double btol,
+                   int32_t* iters, double* rnorm, void* stream);
+
 /* The small factor of the final pass (Alg. 8 step 4 with the QR
  * orthogonaliser): M = R_11^{-1} Omega (r x k) by FP64 back-substitution, with
  * Omega drawn from stream 3 of `seed` (or I_r with LEV_OMEGA_IDENTITY, k = r),

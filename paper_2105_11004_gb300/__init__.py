@@ -68,6 +68,12 @@ SIGNATURES = {
                                      _c_void_p, _P(_i64), _c_void_p, _c_void_p]),
     "lev_rrqr_select": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _P(lev_params), _c_void_p, _c_void_p,
                                        _P(_i64), _c_void_p, _P(_i64), _c_void_p]),
+    "lev_precondition_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p,
+                                              _P(_i64), _c_void_p, _c_void_p]),
+    "lev_precondition_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64,
+                                            _P(lev_params), _c_void_p, _P(_i64), _c_void_p, _c_void_p]),
+    "lev_lsqr_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _c_void_p, _i64, _c_void_p, _c_void_p,
+                                      _i32, _dbl, _dbl, _P(_i32), _P(_dbl), _c_void_p]),
     "lev_set_timing": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "lev_rrqr_timing": (ctypes.c_int, [_c_void_p, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
@@ -206,6 +212,49 @@ def lev_rrqr_select(h: Handle, Atilde, p: lev_params, perm, R, sigma=None, strea
     rc = _check(lib.lev_rrqr_select(h.ptr, _ptr(Atilde), m, d, ctypes.byref(p), _ptr(perm), _ptr(R), ctypes.byref(r),
                                     _ptr(sigma), ctypes.byref(sw), _stream(stream)), allow=(LEV_ERANK0,))
     return (0 if rc == LEV_ERANK0 else r.value), sw.value
+
+
+def lev_precondition_dense(h: Handle, A, p: lev_params, N, sigma=None, stream=None) -> int:
+    """Alg. 11: N (d x d FP64, device; first k columns) = V_k Sigma_k^{-1} of the sketch; returns k."""
+    n, d = A.shape
+    r = _i64()
+    rc = _check(lib.lev_precondition_dense(h.ptr, _ptr(A), n, d, A.stride(0), ctypes.byref(p), _ptr(N),
+                                           ctypes.byref(r), _ptr(sigma), _stream(stream)), allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_precondition_csr(h: Handle, row_ptr, col, val, n, d, p: lev_params, N, sigma=None, stream=None) -> int:
+    r = _i64()
+    rc = _check(lib.lev_precondition_csr(h.ptr, _ptr(row_ptr), _ptr(col), _ptr(val), n, d, col.numel(),
+                                         ctypes.byref(p), _ptr(N), ctypes.byref(r), _ptr(sigma), _stream(stream)),
+                allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_lsqr_dense(h: Handle, A, N, k, b, x, max_iter=200, atol=1e-6, btol=1e-6, stream=None):
+    """LSQR on min ||A N y - b||, x = N y (device FP64); returns (iterations, residual norm estimate)."""
+    n, d = A.shape
+    it, rn = _i32(), _dbl()
+    _check(lib.lev_lsqr_dense(h.ptr, _ptr(A), n, d, A.stride(0), _ptr(N), int(k), _ptr(b), _ptr(x), int(max_iter),
+                              float(atol), float(btol), ctypes.byref(it), ctypes.byref(rn), _stream(stream)))
+    return it.value, rn.value
+
+
+def lstsq(A, b, *, s=0, m=0, tau=1e-10, seed=0, sketch_prec="bf16x3", max_iter=200, atol=1e-6, btol=1e-6,
+          handle: Handle | None = None):
+    """min ||A x - b|| (dense FP32 A and b on a CUDA device): Alg. 11, then LSQR on A N.
+    Returns (x FP64, rank, iterations, residual norm estimate)."""
+    import torch
+    h = handle or default_handle(A.device.index or 0)
+    n, d = A.shape
+    p = make_params(s=s, m=m, k=8, tau=tau, seed=seed, sketch_prec=sketch_prec)
+    N = torch.empty((d, d), dtype=torch.float64, device=A.device)
+    k = lev_precondition_dense(h, A, p, N)
+    x = torch.zeros(d, dtype=torch.float64, device=A.device)
+    if k == 0:                                          # A~ = 0: x = 0
+        return x, 0, 0, None
+    it, rn = lev_lsqr_dense(h, A, N, k, b, x, max_iter=max_iter, atol=atol, btol=btol)
+    return x, k, it, rn
 
 
 def lev_omega_factor(h: Handle, R, perm, d_rank, d, k, seed, flags, Mfull, stream=None):

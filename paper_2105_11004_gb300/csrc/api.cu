@@ -83,6 +83,9 @@ struct lev_handle {
     Buf srht_c;    // F (S A), t x d (LEV_SKETCH_SRHT)
     Buf rank_ws;   // Jacobi copy of R, strong-RRQR Z, norms and argmax partials (LEV_RANK_SVD, LEV_SRRQR)
     int64_t last_swaps = 0;
+    Buf lsqr_u;    // LSQR: the unnormalised left vector u (n FP32)
+    Buf lsqr_ws;   // LSQR: state, short vectors, pass partials, N^T
+    double* host_lsqr = nullptr;   // pinned LSQR state read back by the host
     Buf tc_pad;   // A copied with a 16-byte row stride when the caller's cannot feed TMA
     cudaStream_t copy_st = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
@@ -370,6 +373,31 @@ int finish(lev_handle* h, const lev::QrScratch& qs, int64_t* rank, cudaStream_t 
     return LEV_OK;
 }
 
+// Pieces of the handle's rank workspace: Y or Z (d x d), sigma, wn, g2 (d each), out (16),
+// argmax partials (1024 values, 1024 indices), 64 uint32 of barrier and rotation counts, order (d
+// int32), the sweep count.
+struct RankWs {
+    double *Y, *sig, *wn, *g2, *out, *part_v;
+    long long* part_e;
+    unsigned* work;
+    int32_t *order, *sweeps;
+};
+int rank_ws(lev_handle* h, int64_t d, RankWs* w) {
+    LEV_TRY(ensure(h->rank_ws, sizeof(double) * lev::rank_scratch_doubles(d)));
+    double* ws = (double*)h->rank_ws.ptr;
+    w->Y = ws;
+    w->sig = ws + d * d;
+    w->wn = w->sig + d;
+    w->g2 = w->wn + d;
+    w->out = w->g2 + d;
+    w->part_v = w->out + 16;
+    w->part_e = reinterpret_cast<long long*>(w->part_v + 1024);
+    w->work = reinterpret_cast<unsigned*>(w->part_e + 1024);
+    w->order = reinterpret_cast<int32_t*>(w->work + 64);
+    w->sweeps = w->order + d;
+    return LEV_OK;
+}
+
 // The pivoted QR of A~ with the rank rule of p: the diagonal test of rrqr_common by default;
 // with LEV_RANK_SVD the QR runs to the end and the rank is the count of singular values of A~
 // above tau sigma_1 (sigma: optional device output, d doubles, descending); with LEV_SRRQR
@@ -389,18 +417,12 @@ int select_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, cons
     if (p->flags & LEV_FORCE_PIVOTS) return fail(LEV_EINVAL, "forced pivots take no rank rule");
     const double phi = p->phi == 0 ? 2.0 : p->phi;
     if (sr && !(phi >= 1.0)) return fail(LEV_EINVAL, "phi must be >= 1 (got %g)", phi);
-    LEV_TRY(ensure(h->rank_ws, sizeof(double) * lev::rank_scratch_doubles(d)));
-    double* ws = (double*)h->rank_ws.ptr;
-    double* Y = ws;                                   // d x d (Jacobi) or Z (strong RRQR)
-    double* sig = ws + d * d;                         // d
-    double* wn = sig + d;                             // d
-    double* g2 = wn + d;                              // d
-    double* out = g2 + d;                             // 4
-    double* part_v = out + 16;                        // 1024
-    long long* part_e = reinterpret_cast<long long*>(part_v + 1024);   // 1024
-    unsigned* work = reinterpret_cast<unsigned*>(part_e + 1024);     // 64 (barrier, rotation counts)
-    int32_t* order = reinterpret_cast<int32_t*>(work + 64);
-    int32_t* sweeps = order + d;
+    RankWs rw;
+    LEV_TRY(rank_ws(h, d, &rw));
+    double *Y = rw.Y, *sig = rw.sig, *wn = rw.wn, *g2 = rw.g2, *out = rw.out, *part_v = rw.part_v;
+    long long* part_e = rw.part_e;
+    unsigned* work = rw.work;
+    int32_t *order = rw.order, *sweeps = rw.sweeps;
     if (svd) {
         LEV_TRY(rrqr_common(h, Atilde, m, d, 0.0, nullptr, 0, perm, R, qs, st));      // every step
         LEV_CUDA(lev::launch_svd_rank(R, qs->rank, d, tau_of(p), Y, work, sigma_out ? sigma_out : sig, order,
@@ -515,7 +537,7 @@ int lev_destroy(lev_handle* h) {
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
                   &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
                   &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->tc_pad,
-                  &h->exact_gp, &h->srht_c};
+                  &h->exact_gp, &h->srht_c, &h->rank_ws, &h->lsqr_u, &h->lsqr_ws};
     for (Buf* b : all) release(*b);
     for (int i = 0; i < 2; ++i) {
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
@@ -529,6 +551,7 @@ int lev_destroy(lev_handle* h) {
     if (h->g.ptr) cudaFree(h->g.ptr);
     if (h->status) cudaFree(h->status);
     if (h->host_rank) cudaFreeHost(h->host_rank);
+    if (h->host_lsqr) cudaFreeHost(h->host_lsqr);
     delete h;
     return LEV_OK;
 }
@@ -608,6 +631,82 @@ int lev_rrqr_select(lev_handle* h, const float* Atilde, int64_t m, int64_t d, co
     if (swaps) *swaps = h->last_swaps;
     if (!rank) return LEV_OK;
     return finish(h, qs, rank, st);
+}
+
+// Alg. 11 after the sketch in h->Atilde: the SVD rank rule, then N = V_k Sigma_k^{-1}.
+static int precondition_tail(lev_handle* h, const Sizes& z, int64_t d, const lev_params* p, double* N,
+                             int64_t* rank, double* sigma, cudaStream_t st) {
+    if (d > 1024) return fail(LEV_EINVAL, "lev_precondition_* needs d <= 1024");
+    lev_params q = *p;
+    q.flags = (p->flags & ~(uint32_t)(LEV_SRRQR | LEV_FORCE_PIVOTS)) | LEV_RANK_SVD;
+    LEV_TRY(ensure(h->R, sizeof(double) * (size_t)d * d));
+    LEV_TRY(ensure(h->perm_d, sizeof(int32_t) * (size_t)d));
+    lev::QrScratch qs;
+    LEV_TRY(select_common(h, (const float*)h->Atilde.ptr, z.m, d, &q, (int32_t*)h->perm_d.ptr, (double*)h->R.ptr,
+                          &qs, sigma, st));
+    RankWs rw;
+    LEV_TRY(rank_ws(h, d, &rw));
+    LEV_CUDA(lev::launch_precond_n(rw.Y, rw.order, sigma ? sigma : rw.sig, (const int32_t*)h->perm_d.ptr, qs.rank, d,
+                                   N, st));
+    return finish(h, qs, rank, st);
+}
+
+int lev_precondition_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const lev_params* p,
+                           double* N, int64_t* rank, double* sigma, void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!A || !N) return fail(LEV_EINVAL, "NULL array");
+    if (lda < d) return fail(LEV_EINVAL, "lda < d");
+    if (is_host_pointer(A) || is_host_pointer(N)) return fail(LEV_EINVAL, "lev_precondition_dense takes device arrays");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    cudaStream_t st = (cudaStream_t)stream;
+    LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
+    LEV_TRY(sketch_common_dense(h, A, n, d, lda, p, z, (float*)h->Atilde.ptr, st));
+    return precondition_tail(h, z, d, p, N, rank, sigma, st);
+}
+
+int lev_precondition_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                         int64_t d, int64_t nnz, const lev_params* p, double* N, int64_t* rank, double* sigma,
+                         void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z));
+    if (!row_ptr || (nnz > 0 && (!col || !val)) || !N) return fail(LEV_EINVAL, "NULL array");
+    if (nnz < 0) return fail(LEV_EINVAL, "nnz < 0");
+    if (is_host_pointer(row_ptr) || is_host_pointer(N)) return fail(LEV_EINVAL, "lev_precondition_csr takes device arrays");
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    cudaStream_t st = (cudaStream_t)stream;
+    LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
+    LEV_TRY(sketch_common_csr(h, row_ptr, col, val, n, d, p, z, (float*)h->Atilde.ptr, st));
+    return precondition_tail(h, z, d, p, N, rank, sigma, st);
+}
+
+int lev_lsqr_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const double* N, int64_t k,
+                   const float* b, double* x, int32_t max_iter, double atol, double btol, int32_t* iters,
+                   double* rnorm, void* stream) {
+    LEV_TRY(set_device(h));
+    if (!A || !N || !b || !x) return fail(LEV_EINVAL, "NULL array");
+    if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > 1024 || lda < d)
+        return fail(LEV_EINVAL, "bad shape n=%lld d=%lld lda=%lld", (long long)n, (long long)d, (long long)lda);
+    if (k < 1 || k > d) return fail(LEV_EINVAL, "k = %lld outside [1, d]", (long long)k);
+    if (max_iter < 0) return fail(LEV_EINVAL, "max_iter < 0");
+    if (is_host_pointer(A) || is_host_pointer(N) || is_host_pointer(b) || is_host_pointer(x))
+        return fail(LEV_EINVAL, "lev_lsqr_dense takes device arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int parts = lev::lsqr_parts(h->num_sms);
+    LEV_TRY(ensure(h->lsqr_u, sizeof(float) * (size_t)n));
+    LEV_TRY(ensure(h->lsqr_ws, sizeof(double) * lev::lsqr_scratch_doubles(d, parts)));
+    if (!h->host_lsqr && cudaMallocHost(&h->host_lsqr, 256) != cudaSuccess)
+        return fail(LEV_ENOMEM, "pinned host buffer");
+    LEV_CUDA(cudaMemcpyAsync(h->lsqr_u.ptr, b, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    int it = 0;
+    double rn = 0.0;
+    LEV_CUDA(lev::launch_lsqr(A, lda, n, d, N, k, (float*)h->lsqr_u.ptr, x, max_iter, atol > 0 ? atol : 1e-6,
+                              btol > 0 ? btol : 1e-6, (double*)h->lsqr_ws.ptr, parts, h->host_lsqr, &it, &rn, st));
+    if (iters) *iters = it;
+    if (rnorm) *rnorm = rn;
+    return LEV_OK;
 }
 
 int lev_omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int64_t* d_rank,

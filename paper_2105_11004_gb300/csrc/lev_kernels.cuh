@@ -97,6 +97,19 @@ cudaError_t launch_srrqr_step(const double* R, const double* Rs, const double* G
                               double phi, double* Z, double* wn, double* g2, double* part_v, long long* part_e,
                               double* out, cudaStream_t st);
 cudaError_t launch_scaled_transpose(const double* R, const int64_t* d_rank, int64_t d, double* Rs, cudaStream_t st);
+
+// Preconditioning and LSQR (lsqr.cu). launch_precond_n: N (d x d FP64, row-major; columns >= k
+// zero) = V_k Sigma_k^{-1} from the Jacobi rows Y, order and sigma of launch_svd_rank and the
+// pivots perm. launch_lsqr: LSQR on min ||A N y - b|| with u holding b on entry (overwritten), x =
+// N y (d FP64); ws: lsqr_scratch_doubles(d, parts) doubles; host_state: pinned, lsqr_state_doubles().
+size_t lsqr_scratch_doubles(int64_t d, int parts);
+int lsqr_parts(int num_sms);
+int lsqr_state_doubles();
+cudaError_t launch_precond_n(const double* Y, const int32_t* order, const double* sigma, const int32_t* perm,
+                             const int64_t* d_rank, int64_t d, double* N, cudaStream_t st);
+cudaError_t launch_lsqr(const float* A, int64_t lda, int64_t n, int64_t d, const double* N, int64_t k, float* u,
+                        double* x, int max_iter, double atol, double btol, double* ws, int parts, double* host_state,
+                        int* iters_out, double* rnorm_out, cudaStream_t st);
 void qr_scratch_carve(void* base, int64_t m, int64_t d, QrScratch* q);
 
 // Pivoted QR of Atilde (m x d FP32 row-major). forced_perm may be null. marks (optional, three
