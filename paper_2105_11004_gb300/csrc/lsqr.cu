@@ -76,8 +76,10 @@ __device__ __forceinline__ void fold4(double* z, int col, int d, float4& a) {
 }
 
 // One fused pass (see the header). zpart: gridDim.x x d FP64; npart: gridDim.x FP64 (sum x_r^2).
-// Lane l holds columns c*128 + 4l .. +3 for c < NC. VEC: A 16-byte aligned with lda % 4 == 0.
-template <int NC, bool VEC>
+// Lane l holds columns c*128 + 4l .. +3 for c < NC; a warp takes U rows at a time, all their loads
+// (and the U values of u, one per lane) issued before any is used. VEC: A 16-byte aligned with
+// lda % 4 == 0.
+template <int NC, int U, bool VEC>
 __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_pass(const float* __restrict__ A, int64_t lda, int64_t n,
                                                                int d, const float* __restrict__ t,
                                                                const double* __restrict__ state,
@@ -100,34 +102,56 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_pass(const float* __re
     int since = 0;
     double* zw = zs + w * d;
     const int64_t wid = (int64_t)blockIdx.x * kPassWarps + w, nw = (int64_t)gridDim.x * kPassWarps;
-    for (int64_t r = wid; r < n; r += nw) {
-        float4 a[NC];
-        const float* row = A + r * lda;
-        float dot = 0.f;
+    for (int64_t r0 = wid * U; r0 < n; r0 += nw * U) {
+        float4 a[U][NC];
+        const int64_t rq = r0 + (lane < U ? lane : 0);
+        const float uq = (lane < U && rq < n) ? u[rq] : 0.f;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            a[c] = load4<VEC>(row, c * 128 + lane * 4, d);
-            dot = fmaf(a[c].x, tr[c].x, dot);
-            dot = fmaf(a[c].y, tr[c].y, dot);
-            dot = fmaf(a[c].z, tr[c].z, dot);
-            dot = fmaf(a[c].w, tr[c].w, dot);
-        }
-        dot = warp_sum(dot);
-        float x = 0.f;
-        if (lane == 0) {
-            x = fmaf(gamma, u[r], dot);
-            u[r] = x;
-        }
-        x = __shfl_sync(0xffffffffu, x, 0);
-        if (lane == 0) nrm = fma((double)x, (double)x, nrm);
+        for (int q = 0; q < U; ++q) {
+            const bool ok = r0 + q < n;
+            const float* row = A + (r0 + q) * lda;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            acc[c].x = fmaf(a[c].x, x, acc[c].x);
-            acc[c].y = fmaf(a[c].y, x, acc[c].y);
-            acc[c].z = fmaf(a[c].z, x, acc[c].z);
-            acc[c].w = fmaf(a[c].w, x, acc[c].w);
+            for (int c = 0; c < NC; ++c)
+                a[q][c] = ok ? load4<VEC>(row, c * 128 + lane * 4, d) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (++since == kFold) {
+        float dot[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            float s = 0.f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                s = fmaf(a[q][c].x, tr[c].x, s);
+                s = fmaf(a[q][c].y, tr[c].y, s);
+                s = fmaf(a[q][c].z, tr[c].z, s);
+                s = fmaf(a[q][c].w, tr[c].w, s);
+            }
+            dot[q] = s;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < U; ++q) dot[q] += __shfl_xor_sync(0xffffffffu, dot[q], o);
+        float mine = 0.f;                                   // lane q < U: x of row r0 + q
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (lane == q) mine = fmaf(gamma, uq, dot[q]);
+        if (lane < U && rq < n && r0 + lane < n) {
+            u[rq] = mine;
+            nrm = fma((double)mine, (double)mine, nrm);
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const float x = __shfl_sync(0xffffffffu, mine, q);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                acc[c].x = fmaf(a[q][c].x, x, acc[c].x);
+                acc[c].y = fmaf(a[q][c].y, x, acc[c].y);
+                acc[c].z = fmaf(a[q][c].z, x, acc[c].z);
+                acc[c].w = fmaf(a[q][c].w, x, acc[c].w);
+            }
+        }
+        since += U;
+        if (since >= kFold) {
             since = 0;
 #pragma unroll
             for (int c = 0; c < NC; ++c) fold4(zw, c * 128 + lane * 4, d, acc[c]);
@@ -135,6 +159,7 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_pass(const float* __re
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) fold4(zw, c * 128 + lane * 4, d, acc[c]);
+    nrm = warp_sum(nrm);
     if (lane == 0) ns[w] = nrm;
     __syncthreads();
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
@@ -149,24 +174,34 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_pass(const float* __re
     }
 }
 
-// z[j] = sum over CTAs of zpart (fixed order); the last CTA (blockIdx.x == gridDim.x - 1) sums npart
-// into beta = sqrt(.) and the scale of the stored u (1 / beta).
-__global__ void k_lsqr_reduce(const double* __restrict__ zpart, const double* __restrict__ npart, int parts, int d,
-                              double* __restrict__ z, double* __restrict__ state) {
+// z[j] = sum over CTAs of zpart and beta = sqrt(sum of npart), in a fixed order: block b < gridDim.x
+// - 1 takes columns 32b .. 32b + 31 (lane = column), warp w the partials w, w + 8, ..., then the
+// warps' sums are added in warp order; the last block does the same for npart.
+__global__ void __launch_bounds__(256) k_lsqr_reduce(const double* __restrict__ zpart, const double* __restrict__ npart,
+                                                     int parts, int d, double* __restrict__ z,
+                                                     double* __restrict__ state) {
+    __shared__ double ws[8][32];
     if (state[S_DONE] != 0.0) return;
-    if (blockIdx.x == gridDim.x - 1) {
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int c = 0; c < parts; ++c) s += npart[c];
-            state[S_BETA] = sqrt(s);
-        }
-        return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool last = blockIdx.x == gridDim.x - 1;
+    const int j = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (last) {
+        for (int c = w * 32 + lane; c < parts; c += 256) s += npart[c];
+        s = warp_sum(s);
+    } else if (j < d) {
+        for (int c = w; c < parts; c += 8) s += zpart[(int64_t)c * d + j];
     }
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < d) {
-        double s = 0.0;
-        for (int c = 0; c < parts; ++c) s += zpart[(int64_t)c * d + j];
-        z[j] = s;
+    ws[w][lane] = s;
+    __syncthreads();
+    if (w == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += ws[q][lane];
+        if (last) {
+            if (lane == 0) state[S_BETA] = sqrt(t);
+        } else if (j < d) {
+            z[j] = t;
+        }
     }
 }
 
@@ -303,19 +338,21 @@ cudaError_t launch_precond_n(const double* Y, const int32_t* order, const double
     return cudaGetLastError();
 }
 
-template <int NC>
+template <int NC, int U>
 static cudaError_t lsqr_pass(bool vec, int parts, size_t smem, cudaStream_t st, const float* A, int64_t lda, int64_t n,
                              int d, const float* t, const double* state, float* u, double* zpart, double* npart) {
     cudaError_t e;
     const int mx = (int)(sizeof(double) * kPassWarps * 1024);
     if (vec) {
-        if ((e = cudaFuncSetAttribute(k_lsqr_pass<NC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_lsqr_pass<NC, U, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+            cudaSuccess)
             return e;
-        k_lsqr_pass<NC, true><<<parts, 32 * kPassWarps, smem, st>>>(A, lda, n, d, t, state, u, zpart, npart);
+        k_lsqr_pass<NC, U, true><<<parts, 32 * kPassWarps, smem, st>>>(A, lda, n, d, t, state, u, zpart, npart);
     } else {
-        if ((e = cudaFuncSetAttribute(k_lsqr_pass<NC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_lsqr_pass<NC, U, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) !=
+            cudaSuccess)
             return e;
-        k_lsqr_pass<NC, false><<<parts, 32 * kPassWarps, smem, st>>>(A, lda, n, d, t, state, u, zpart, npart);
+        k_lsqr_pass<NC, U, false><<<parts, 32 * kPassWarps, smem, st>>>(A, lda, n, d, t, state, u, zpart, npart);
     }
     return cudaGetLastError();
 }
@@ -339,16 +376,16 @@ cudaError_t launch_lsqr(const float* A, int64_t lda, int64_t n, int64_t d, const
     const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
     const size_t smem = sizeof(double) * (size_t)kPassWarps * d;
     auto pass = [&]() -> cudaError_t {
-        if (nc == 1) return lsqr_pass<1>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
-        if (nc == 2) return lsqr_pass<2>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
-        if (nc <= 4) return lsqr_pass<4>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
-        return lsqr_pass<8>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
+        if (nc == 1) return lsqr_pass<1, 8>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
+        if (nc == 2) return lsqr_pass<2, 4>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
+        if (nc <= 4) return lsqr_pass<4, 2>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
+        return lsqr_pass<8, 1>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
     };
     int tg = (int)((k * d + 255) / 256);
     if (tg > 152 * 8) tg = 152 * 8;
     k_transpose_n<<<tg, 256, 0, st>>>(N, (int)d, (int)k, Nt);
     const int warps_k = (int)((k * 32 + 255) / 256), warps_d = (int)((d * 32 + 255) / 256);
-    const int red_grid = (int)((d + 255) / 256) + 1;
+    const int red_grid = (int)((d + 31) / 32) + 1;
     k_lsqr_init_state<<<1, 32, 0, st>>>(state, atol, btol);
     if ((e = cudaMemsetAsync(t, 0, sizeof(float) * (size_t)d, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(v, 0, sizeof(double) * (size_t)d, st)) != cudaSuccess) return e;
