@@ -193,6 +193,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-exact", action="store_true", help="skip the Alg. 7 (LS-HRN-exact) measurement")
+    ap.add_argument("--no-extras", action="store_true", help="skip the rank-rule and least-squares measurements")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR 8e6 x 1024 measurement")
     ap.add_argument("--csr-large", action="store_true", help="also measure the CSR 8e7 x 1024 (~1e9 nnz) workload")
     ap.add_argument("--streams", type=int, default=3,
@@ -419,6 +420,25 @@ def main():
                         "gram_fp64_tflops": 2.0 * gram_fma / (g_ms * 1e-3) / 1e12, "fp64_peak_tflops": fp64_peak,
                         "sketch_prec": args.sketch_prec, "final_prec": args.final_prec}
 
+    # rank rules on the same batch's sketch (lev_rrqr_select): the diagonal test, the singular values
+    # of the sketch (Alg. 11 step 3), strong-RRQR swaps (Alg. 2)
+    if not args.no_extras:
+        ps = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
+                           sketch_prec=args.sketch_prec)
+        At_r = torch.empty((cfg["m"], d), dtype=torch.float32, device="cuda")
+        L.lev_sketch_dense(h, A, ps, At_r)
+        pr = torch.empty(d, dtype=torch.int32, device="cuda")
+        Rr = torch.empty((d, d), dtype=torch.float64, device="cuda")
+        rules = {}
+        for name, kw in [("diag", {}), ("svd", dict(rank_svd=True)), ("srrqr_phi2", dict(srrqr_phi=2.0)),
+                         ("svd_srrqr_phi1.05", dict(rank_svd=True, srrqr_phi=1.05))]:
+            pk = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"], **kw)
+            rk, sw = L.lev_rrqr_select(h, At_r, pk, pr, Rr)
+            rules[name] = {"rank": rk, "swaps": sw,
+                           "ms": time_steps(lambda: L.lev_rrqr_select(h, At_r, pk, pr, Rr), 3)}
+        out["rank_rules"] = {"sketch": f"{cfg['m']} x {d}", "rules": rules}
+        out["lstsq"] = lstsq_timing(L, h, n, d, time_steps)
+
     # backward workload: dense 200,000 x 64, s = 16,384, m = 256, k = 128; forward = the four stages
     if not args.no_backward:
         out["backward"] = backward_timing(L, h, reps)
@@ -538,6 +558,29 @@ def csr_timing(L, h, name, reps):
                     "rows_per_s": n / (ms_e * 1e-3), "gram_pairs": float(np.sum(lens * (lens + 1) / 2)),
                     "note": "two host synchronisations per call (after each factorisation)"}
     return out
+
+
+def lstsq_timing(L, h, n, d, time_steps):
+    """Alg. 11 (CountGauss preconditioner) and LSQR on A N for a dense n x d least-squares problem:
+    A with lognormal row scales (the batch's distribution at full rank), b ~ N(0, 1)."""
+    import torch
+    rs = np.random.default_rng(0)
+    A = torch.from_numpy(W.dense_lowrank_skewed(n, d, d, seed=1)).cuda()
+    b = torch.from_numpy(rs.standard_normal(n).astype(np.float32)).cuda()
+    p = L.make_params(s=65536, m=4 * d, k=8, tau=1e-10, seed=3, sketch_prec="bf16x3")
+    N = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    k = L.lev_precondition_dense(h, A, p, N)
+    pre_ms = time_steps(lambda: L.lev_precondition_dense(h, A, p, N), 3)
+    x = torch.zeros(d, dtype=torch.float64, device="cuda")
+    it, rn = L.lev_lsqr_dense(h, A, N, k, b, x, max_iter=200, atol=1e-6, btol=1e-6)
+    ls_ms = time_steps(lambda: L.lev_lsqr_dense(h, A, N, k, b, x, max_iter=200, atol=1e-6, btol=1e-6), 5)
+    passes = it + 1
+    pass_bytes = n * d * 4 + 2 * n * 4                 # A once, u read and written
+    return {"problem": f"dense {n} x {d}, lognormal row scales, b ~ N(0,1)", "rank": k, "iterations": it,
+            "precondition_ms": pre_ms, "lsqr_ms": ls_ms, "residual": rn,
+            "lsqr_gbs_per_pass": passes * pass_bytes / (ls_ms * 1e-3) / 1e9,
+            "note": "one fused pass over A per iteration (A N v and A^T u' together); GB/s counts the whole "
+                    "solve including the small FP64 steps and one host check per 16 iterations"}
 
 
 def backward_timing(L, h, reps):

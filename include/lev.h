@@ -181,6 +181,11 @@ int lev_rrqr_select(lev_handle* h, const float* Atilde, int64_t m, int64_t d, co
                     int32_t* perm, double* R, int64_t* rank, double* sigma, int64_t* swaps,
                     void* stream);
 
+/* Diagnostics of the last lev_rrqr_select / LEV_RANK_SVD / LEV_SRRQR call on h: the strong-RRQR
+ * swaps and the Jacobi sweeps (41 when the last of 40 sweeps still rotated). Synchronises the
+ * device. Either pointer may be NULL. */
+int lev_rank_stats(lev_handle* h, int64_t* swaps, int32_t* jacobi_sweeps);
+
 /* Alg. 11 (CountGaussPrecondition) on dense A (device, n x d FP32, lda >= d): the CountGauss
  * sketch A~ = G S A with p's sizes, seed and sketch_prec, its SVD (the LEV_RANK_SVD path of
  * lev_rrqr_select), k = #{sigma_j > p->tau sigma_1}, and N = V_k Sigma_k^{-1} written to N (device,

@@ -74,6 +74,7 @@ SIGNATURES = {
                                             _P(lev_params), _c_void_p, _P(_i64), _c_void_p, _c_void_p]),
     "lev_lsqr_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _c_void_p, _i64, _c_void_p, _c_void_p,
                                       _i32, _dbl, _dbl, _P(_i32), _P(_dbl), _c_void_p]),
+    "lev_rank_stats": (ctypes.c_int, [_c_void_p, _P(_i64), _P(_i32)]),
     "lev_set_timing": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "lev_rrqr_timing": (ctypes.c_int, [_c_void_p, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
@@ -255,6 +256,13 @@ def lstsq(A, b, *, s=0, m=0, tau=1e-10, seed=0, sketch_prec="bf16x3", max_iter=2
         return x, 0, 0, None
     it, rn = lev_lsqr_dense(h, A, N, k, b, x, max_iter=max_iter, atol=atol, btol=btol)
     return x, k, it, rn
+
+
+def lev_rank_stats(h: Handle):
+    """(swaps, Jacobi sweeps) of the last rank-rule call on h."""
+    sw, js = _i64(), _i32()
+    _check(lib.lev_rank_stats(h.ptr, ctypes.byref(sw), ctypes.byref(js)))
+    return sw.value, js.value
 
 
 def lev_omega_factor(h: Handle, R, perm, d_rank, d, k, seed, flags, Mfull, stream=None):

@@ -83,6 +83,7 @@ struct lev_handle {
     Buf srht_c;    // F (S A), t x d (LEV_SKETCH_SRHT)
     Buf rank_ws;   // Jacobi copy of R, strong-RRQR Z, norms and argmax partials (LEV_RANK_SVD, LEV_SRRQR)
     int64_t last_swaps = 0;
+    int64_t rank_ws_d = 0;   // d of the last carve of rank_ws
     Buf lsqr_u;    // LSQR: the unnormalised left vector u (n FP32)
     Buf lsqr_ws;   // LSQR: state, short vectors, pass partials, N^T
     double* host_lsqr = nullptr;   // pinned LSQR state read back by the host
@@ -381,9 +382,11 @@ struct RankWs {
     long long* part_e;
     unsigned* work;
     int32_t *order, *sweeps;
+    unsigned* version;
 };
 int rank_ws(lev_handle* h, int64_t d, RankWs* w) {
     LEV_TRY(ensure(h->rank_ws, sizeof(double) * lev::rank_scratch_doubles(d)));
+    h->rank_ws_d = d;
     double* ws = (double*)h->rank_ws.ptr;
     w->Y = ws;
     w->sig = ws + d * d;
@@ -395,6 +398,7 @@ int rank_ws(lev_handle* h, int64_t d, RankWs* w) {
     w->work = reinterpret_cast<unsigned*>(w->part_e + 1024);
     w->order = reinterpret_cast<int32_t*>(w->work + 64);
     w->sweeps = w->order + d;
+    w->version = reinterpret_cast<unsigned*>(w->sweeps + 2);
     return LEV_OK;
 }
 
@@ -426,7 +430,7 @@ int select_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, cons
     if (svd) {
         LEV_TRY(rrqr_common(h, Atilde, m, d, 0.0, nullptr, 0, perm, R, qs, st));      // every step
         LEV_CUDA(lev::launch_svd_rank(R, qs->rank, d, tau_of(p), Y, work, sigma_out ? sigma_out : sig, order,
-                                      qs->rank, sweeps, h->status, h->num_sms, st));
+                                      qs->rank, sweeps, rw.version, h->status, h->num_sms, st));
     } else {
         LEV_TRY(rrqr_common(h, Atilde, m, d, tau_of(p), nullptr, 0, perm, R, qs, st));
     }
@@ -706,6 +710,21 @@ int lev_lsqr_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t 
                               btol > 0 ? btol : 1e-6, (double*)h->lsqr_ws.ptr, parts, h->host_lsqr, &it, &rn, st));
     if (iters) *iters = it;
     if (rnorm) *rnorm = rn;
+    return LEV_OK;
+}
+
+int lev_rank_stats(lev_handle* h, int64_t* swaps, int32_t* jacobi_sweeps) {
+    LEV_TRY(set_device(h));
+    if (swaps) *swaps = h->last_swaps;
+    if (jacobi_sweeps) {
+        *jacobi_sweeps = 0;
+        if (h->rank_ws.ptr) {
+            RankWs rw;
+            LEV_TRY(rank_ws(h, h->rank_ws_d, &rw));
+            LEV_CUDA(cudaDeviceSynchronize());
+            LEV_CUDA(cudaMemcpy(jacobi_sweeps, rw.sweeps, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+    }
     return LEV_OK;
 }
 

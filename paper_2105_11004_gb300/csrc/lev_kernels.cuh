@@ -92,7 +92,7 @@ size_t qr_scratch_bytes(int64_t m, int64_t d);
 size_t rank_scratch_doubles(int64_t d);
 cudaError_t launch_svd_rank(const double* R, const int64_t* d_rows, int64_t d, double tau, double* Y,
                             unsigned* work, double* sigma, int32_t* order, int64_t* rank_out, int32_t* sweeps_out,
-                            int32_t* status, int num_sms, cudaStream_t st);
+                            unsigned* version, int32_t* status, int num_sms, cudaStream_t st);
 cudaError_t launch_srrqr_step(const double* R, const double* Rs, const double* G, int32_t* perm, int64_t d, int64_t k,
                               double phi, double* Z, double* wn, double* g2, double* part_v, long long* part_e,
                               double* out, cudaStream_t st);

@@ -30,13 +30,22 @@ __device__ __forceinline__ void round_pair(int n, int t, int i, int& p, int& q) 
     }
 }
 
-// Y: rows 0..r-1 (r read from *d_rows, at most d), row-major, ld = d. rotated[s] counts the
-// rotations of sweep s (zeroed by the caller); *sweeps_out = sweeps run (max_sweeps + 1 when the
-// last sweep still rotated).
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Y: rows 0..r-1 (r read from *d_rows, at most d), row-major, ld = d. Rounds are ordered by rows,
+// not by a grid barrier: version[p] (zeroed by the caller) counts the rounds applied to row p, and
+// the CTA that holds pair (p, q) in global round T waits (bounded) until both rows reached version
+// T, rotates them and publishes T + 1. Every CTA takes its pairs in round order and all CTAs are
+// resident (cooperative launch), so the earliest unfinished pair always has its rows ready. A grid
+// barrier ends each sweep; rotated[s] counts the rotations of sweep s (zeroed by the caller) and
+// the sweeps stop after one without any. *sweeps_out = sweeps run (max_sweeps + 1 when the last
+// sweep still rotated).
 __global__ void __launch_bounds__(256) k_jacobi_rows(double* __restrict__ Y, const int64_t* __restrict__ d_rows,
                                                      int d, int max_sweeps, unsigned* __restrict__ rotated,
-                                                     unsigned* __restrict__ barrier, int32_t* __restrict__ status,
-                                                     int32_t* __restrict__ sweeps_out) {
+                                                     unsigned* __restrict__ barrier, unsigned* __restrict__ version,
+                                                     int32_t* __restrict__ status, int32_t* __restrict__ sweeps_out) {
     __shared__ double part[3][8];
     __shared__ double tot[3];
     const int r = (int)min(max(*d_rows, (int64_t)0), (int64_t)d);
@@ -49,52 +58,73 @@ __global__ void __launch_bounds__(256) k_jacobi_rows(double* __restrict__ Y, con
     }
     for (int s = 0; s < max_sweeps; ++s) {
         for (int t = 0; t < n - 1; ++t) {
+            const unsigned T = (unsigned)s * (unsigned)(n - 1) + (unsigned)t;
             for (int i = blockIdx.x; i < n / 2; i += gridDim.x) {
                 int p, q;
                 round_pair(n, t, i, p, q);
-                if (p >= r || q >= r) continue;                                   // the padding row
-                double* yp = Y + (int64_t)p * d;
-                double* yq = Y + (int64_t)q * d;
-                double a = 0.0, b = 0.0, c = 0.0;
-                for (int j = threadIdx.x; j < d; j += blockDim.x) {
-                    const double x = yp[j], y = yq[j];
-                    a = fma(x, x, a);
-                    b = fma(y, y, b);
-                    c = fma(x, y, c);
-                }
-                a = warp_sum(a);
-                b = warp_sum(b);
-                c = warp_sum(c);
-                if (lane == 0) {
-                    part[0][w] = a;
-                    part[1][w] = b;
-                    part[2][w] = c;
+                const bool pv = p < r, qv = q < r;                       // q may be the padding row
+                if (threadIdx.x == 0) {
+                    long long spins = 0;
+                    while ((pv && ld_acquire_gpu(version + p) < T) || (qv && ld_acquire_gpu(version + q) < T)) {
+                        if (ld_volatile(status) != 0) break;
+                        if (++spins > kSpinLimit) {
+                            atomicExch(status, kStatusTimeoutBarrier);
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
                 }
                 __syncthreads();
-                if (threadIdx.x < 3) {
-                    double v = 0.0;
-                    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) v += part[threadIdx.x][u];
-                    tot[threadIdx.x] = v;
-                }
-                __syncthreads();
-                a = tot[0];
-                b = tot[1];
-                c = tot[2];
-                __syncthreads();                                               // tot is reused
-                if (a > 0.0 && b > 0.0 && fabs(c) > kJacobiTol * sqrt(a) * sqrt(b)) {
-                    const double zeta = (b - a) / (2.0 * c);
-                    const double tr = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double cs = 1.0 / sqrt(1.0 + tr * tr), sn = cs * tr;
+                if (ld_volatile(status) != 0) return;
+                if (pv && qv) {
+                    double* yp = Y + (int64_t)p * d;
+                    double* yq = Y + (int64_t)q * d;
+                    double a = 0.0, b = 0.0, c = 0.0;
                     for (int j = threadIdx.x; j < d; j += blockDim.x) {
                         const double x = yp[j], y = yq[j];
-                        yp[j] = cs * x - sn * y;
-                        yq[j] = sn * x + cs * y;
+                        a = fma(x, x, a);
+                        b = fma(y, y, b);
+                        c = fma(x, y, c);
                     }
-                    if (threadIdx.x == 0) atomicAdd(&rotated[s], 1u);
+                    a = warp_sum(a);
+                    b = warp_sum(b);
+                    c = warp_sum(c);
+                    if (lane == 0) {
+                        part[0][w] = a;
+                        part[1][w] = b;
+                        part[2][w] = c;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < 3) {
+                        double v = 0.0;
+                        for (int u = 0; u < (int)(blockDim.x >> 5); ++u) v += part[threadIdx.x][u];
+                        tot[threadIdx.x] = v;
+                    }
+                    __syncthreads();
+                    a = tot[0];
+                    b = tot[1];
+                    c = tot[2];
+                    if (a > 0.0 && b > 0.0 && fabs(c) > kJacobiTol * sqrt(a) * sqrt(b)) {
+                        const double zeta = (b - a) / (2.0 * c);
+                        const double tr = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        const double cs = 1.0 / sqrt(1.0 + tr * tr), sn = cs * tr;
+                        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+                            const double x = yp[j], y = yq[j];
+                            yp[j] = cs * x - sn * y;
+                            yq[j] = sn * x + cs * y;
+                        }
+                        if (threadIdx.x == 0) atomicAdd(&rotated[s], 1u);
+                    }
+                }
+                __syncthreads();                                             // rows written, tot read
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    if (pv) st_release_gpu(version + p, T + 1);
+                    if (qv) st_release_gpu(version + q, T + 1);
                 }
             }
-            if (!grid_barrier(barrier, epoch, status)) return;
         }
+        if (!grid_barrier(barrier, epoch, status)) return;
         if (*(volatile unsigned*)&rotated[s] == 0u) {
             if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = s + 1;
             return;
@@ -274,12 +304,13 @@ __global__ void k_srrqr_swap(const double* __restrict__ out, double phi2, int32_
 }  // namespace
 
 // Y or Z (d x d), sigma, wn, g2 (d each), out (16), argmax partials (1024 values + 1024 indices),
-// then 64 uint32 of barrier and rotation counts, order (d int32) and the sweep count.
-size_t rank_scratch_doubles(int64_t d) { return (size_t)(d * d + 3 * d + 16 + 2 * 1024 + 32 + d + 8); }
+// then 64 uint32 of barrier and rotation counts, order (d int32), the sweep count, the row versions
+// of the Jacobi (d uint32, from the sweep count + 2).
+size_t rank_scratch_doubles(int64_t d) { return (size_t)(d * d + 3 * d + 16 + 2 * 1024 + 32 + d + 8 + d); }
 
 cudaError_t launch_svd_rank(const double* R, const int64_t* d_rows, int64_t d, double tau, double* Y,
                             unsigned* work, double* sigma, int32_t* order, int64_t* rank_out, int32_t* sweeps_out,
-                            int32_t* status, int num_sms, cudaStream_t st) {
+                            unsigned* version, int32_t* status, int num_sms, cudaStream_t st) {
     cudaError_t e;
     constexpr int kMaxSweeps = 40;
     if (d > 1024) return cudaErrorInvalidValue;
@@ -288,11 +319,12 @@ cudaError_t launch_svd_rank(const double* R, const int64_t* d_rows, int64_t d, d
     unsigned* barrier = work;
     unsigned* rotated = work + 1;
     if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned) * (1 + kMaxSweeps), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(version, 0, sizeof(unsigned) * (size_t)d, st)) != cudaSuccess) return e;
     int grid = (int)((d + 1) / 2);
     if (grid > num_sms) grid = num_sms;
     if (grid < 1) grid = 1;
     int di = (int)d, ms = kMaxSweeps;
-    void* kargs[] = {&Y, (void*)&d_rows, &di, &ms, &rotated, &barrier, &status, &sweeps_out};
+    void* kargs[] = {&Y, (void*)&d_rows, &di, &ms, &rotated, &barrier, &version, &status, &sweeps_out};
     if ((e = cudaLaunchCooperativeKernel((const void*)k_jacobi_rows, dim3((unsigned)grid), dim3(256), kargs, 0, st)) !=
         cudaSuccess)
         return e;
