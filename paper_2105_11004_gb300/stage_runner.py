@@ -4,6 +4,9 @@
     python -m paper_2105_11004_gb300.stage_runner rrqr --m 1024 --d 256 --rank 200 --tau 1e-4
     python -m paper_2105_11004_gb300.stage_runner sketch --n 262144 --d 256 --s 65536 --m 1024
     python -m paper_2105_11004_gb300.stage_runner backward --n 200000 --d 64 --k 128
+    python -m paper_2105_11004_gb300.stage_runner lsqr --n 262144 --d 256
+    python -m paper_2105_11004_gb300.stage_runner svd --m 1024 --d 256 --rank 200
+    python -m paper_2105_11004_gb300.stage_runner exact_csr --n 1000000 --d 1024
 
 Inputs are seeded and synthetic (the generators of the ``workloads`` module); every stage runs
 through the C ABI exactly as ``lev_estimate_dense`` runs it. The script prints the CUDA-event time
@@ -18,7 +21,7 @@ import sys
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("stage", choices=["final", "rrqr", "sketch", "backward"])
+    ap.add_argument("stage", choices=["final", "rrqr", "sketch", "backward", "lsqr", "svd", "exact_csr"])
     ap.add_argument("--n", type=int, default=262144)
     ap.add_argument("--d", type=int, default=256)
     ap.add_argument("--k", type=int, default=256)
@@ -70,6 +73,29 @@ def main(argv=None):
         perm = torch.empty(a.d, dtype=torch.int32, device="cuda")
         R = torch.empty((a.d, a.d), dtype=torch.float64, device="cuda")
         ms = timed(lambda: L.lev_rrqr(h, At, a.tau, perm, R))
+    elif a.stage == "lsqr":
+        # Alg. 11 once, then LSQR on A N (each iteration one fused pass over A)
+        b = torch.from_numpy(np.random.default_rng(a.seed).standard_normal(a.n).astype(np.float32)).cuda()
+        A = torch.from_numpy(W.dense_lowrank_skewed(a.n, a.d, a.d, seed=a.seed)).cuda()
+        p = L.make_params(s=a.s, m=4 * a.d, k=8, tau=1e-10, seed=a.seed, sketch_prec="bf16x3")
+        N = torch.empty((a.d, a.d), dtype=torch.float64, device="cuda")
+        k = L.lev_precondition_dense(h, A, p, N)
+        x = torch.zeros(a.d, dtype=torch.float64, device="cuda")
+        ms = timed(lambda: L.lev_lsqr_dense(h, A, N, k, b, x, max_iter=200, atol=1e-6, btol=1e-6))
+    elif a.stage == "svd":
+        rs = np.random.default_rng(a.seed)
+        X = rs.standard_normal((a.m, a.rank)) @ rs.standard_normal((a.rank, a.d))
+        At = torch.from_numpy(X.astype(np.float32)).cuda()
+        p = L.make_params(s=64, m=a.m, k=8, tau=a.tau, seed=a.seed, rank_svd=True)
+        perm = torch.empty(a.d, dtype=torch.int32, device="cuda")
+        R = torch.empty((a.d, a.d), dtype=torch.float64, device="cuda")
+        ms = timed(lambda: L.lev_rrqr_select(h, At, p, perm, R))
+    elif a.stage == "exact_csr":
+        C = W.csr_uniform(a.n, a.d, seed=a.seed)
+        rp, cl, vl = (torch.from_numpy(v).cuda() for v in (C.row_ptr, C.col, C.val))
+        p = L.make_params(s=262144, m=4096, k=256, tau=1e-5, seed=a.seed, sketch_prec="bf16x3")
+        theta = torch.empty(a.n, device="cuda")
+        ms = timed(lambda: L.lev_exact_csr(h, rp, cl, vl, a.n, a.d, p, theta))
     else:
         p = L.make_params(s=a.s, m=a.m, k=a.k, tau=a.tau, seed=a.seed, sketch_prec="bf16x3", final_prec="bf16x3")
         w = torch.rand(a.n, device="cuda")
