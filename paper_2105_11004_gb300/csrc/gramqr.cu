@@ -8,9 +8,17 @@
 // rate is low, this moves the m d^2 FP64 work into one embarrassingly parallel
 // product and leaves only d^3/3 of sequential work on a d x d matrix:
 //
-//   k_gram_fp64 / k_gram_reduce: G = A~^T A~, FP64 products of the FP32 sketch
-//     entries (exact) accumulated in FP64, upper 32 x 32 tiles split over rows,
-//     split partials reduced in a fixed order and mirrored;
+//   k_gram_dot2 / k_gram_reduce: G = A~^T A~ with FP64-grade sums from FP32
+//     arithmetic (FP64 runs at 1/64 of the FP32 rate on this GPU): each product
+//     of two FP32 entries is split exactly into p + e (p = a b rounded,
+//     e = fma(a, b, -p)); the products of 32 rows are summed error-free
+//     (TwoSum, s + q = s_old + p exactly), their rounding errors q and e
+//     gathered in an FP32 correction c, and every 32 rows s + c is added into
+//     FP64 (the compensated dot product of Ogita, Rump and Oishi, with an FP64
+//     outer sum). Error: about 64 u_32^2 sum |a b| per block (2e-13) plus the
+//     FP64 sum over blocks, below the m u_64 sum |a b| of an FP64 FMA chain.
+//     Upper 32 x 32 tiles split over rows, split partials reduced in a fixed
+//     order and mirrored;
 //   k_pchol_grid: one cooperative grid (one CTA per SM); CTA c owns the
 //     columns l = c mod gridDim of the Schur complement in shared memory. All
 //     CTAs keep a replicated Schur diagonal and take the same pivot p_j (largest
@@ -45,12 +53,12 @@ __device__ inline void tile_coords(int t, int nt, int& bi, int& bj) {
     bj = bi + t;
 }
 
-__global__ void __launch_bounds__(256) k_gram_fp64(const float* __restrict__ At, int64_t lda, int m, int d,
-                                                   int rows_per_split,
-                                                   double* __restrict__ Gp) {
-    // 16 rows of the two column panels per stage, converted to FP64 once when staged
-    __shared__ double As[16][GT];
-    __shared__ double Bs[16][GT];
+constexpr int kDot2Rows = 32;          // rows per error-free block before the FP64 add
+
+__global__ void __launch_bounds__(256) k_gram_dot2(const float* __restrict__ At, int64_t lda, int m, int d,
+                                                   int rows_per_split, double* __restrict__ Gp) {
+    __shared__ __align__(16) float As[kDot2Rows][GT];
+    __shared__ __align__(16) float Bs[kDot2Rows][GT];
     const int nt = (d + GT - 1) / GT;
     const int T = nt * (nt + 1) / 2;
     int bi, bj;
@@ -60,21 +68,34 @@ __global__ void __launch_bounds__(256) k_gram_fp64(const float* __restrict__ At,
     const int t = threadIdx.x;
     const int ty = t >> 3, tx = t & 7;           // 32 x 8 threads -> outputs (ty, tx*4 .. tx*4+3)
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int r0 = r_begin; r0 < r_end; r0 += 16) {
-        for (int e = t; e < 16 * GT; e += 256) {
+    for (int r0 = r_begin; r0 < r_end; r0 += kDot2Rows) {
+        for (int e = t; e < kDot2Rows * GT; e += 256) {
             const int r = e / GT, c = e % GT;
             const int row = r0 + r;
             const bool rok = row < r_end;
-            As[r][c] = (rok && bi * GT + c < d) ? (double)At[(int64_t)row * lda + bi * GT + c] : 0.0;
-            Bs[r][c] = (rok && bj * GT + c < d) ? (double)At[(int64_t)row * lda + bj * GT + c] : 0.0;
+            As[r][c] = (rok && bi * GT + c < d) ? At[(int64_t)row * lda + bi * GT + c] : 0.f;
+            Bs[r][c] = (rok && bj * GT + c < d) ? At[(int64_t)row * lda + bj * GT + c] : 0.f;
         }
         __syncthreads();
+        float sm[4] = {0.f, 0.f, 0.f, 0.f}, cm[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int r = 0; r < kDot2Rows; ++r) {
+            const float a = As[r][ty];
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[r][tx * 4]);
+            const float bq[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const double a = As[r][ty];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fma(a, Bs[r][tx * 4 + q], acc[q]);
+            for (int q = 0; q < 4; ++q) {
+                const float p = __fmul_rn(a, bq[q]);
+                const float ep = __fmaf_rn(a, bq[q], -p);          // a b = p + ep exactly
+                const float s1 = __fadd_rn(sm[q], p);
+                const float z = __fsub_rn(s1, sm[q]);
+                const float es = __fadd_rn(__fsub_rn(sm[q], __fsub_rn(s1, z)), __fsub_rn(p, z));  // s + p = s1 + es
+                sm[q] = s1;
+                cm[q] = __fadd_rn(cm[q], __fadd_rn(es, ep));
+            }
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += (double)sm[q] + (double)cm[q];
         __syncthreads();
     }
     double* out = Gp + ((int64_t)split * T + blockIdx.x) * (GT * GT);
@@ -434,9 +455,9 @@ size_t gram_partial_doubles(int64_t m, int64_t d) {
 cudaError_t launch_gram_fp64(const float* A, int64_t lda, int64_t m, int64_t d, double* Gp, double* G,
                              cudaStream_t st) {
     const int splits = gram_splits(m, d);
-    const int rows_per_split = (int)(((m + splits - 1) / splits + 15) / 16 * 16);
+    const int rows_per_split = (int)(((m + splits - 1) / splits + kDot2Rows - 1) / kDot2Rows * kDot2Rows);
     dim3 grid((unsigned)gram_tiles((int)d), (unsigned)splits);
-    k_gram_fp64<<<grid, 256, 0, st>>>(A, lda, (int)m, (int)d, rows_per_split, Gp);
+    k_gram_dot2<<<grid, 256, 0, st>>>(A, lda, (int)m, (int)d, rows_per_split, Gp);
     k_gram_reduce<<<152 * 4, 256, 0, st>>>(Gp, (int)d, splits, G);
     return cudaGetLastError();
 }
