@@ -84,6 +84,7 @@ struct lev_handle {
     Buf rank_ws;   // Jacobi copy of R, strong-RRQR Z, norms and argmax partials (LEV_RANK_SVD, LEV_SRRQR)
     int64_t last_swaps = 0;
     int64_t rank_ws_d = 0;   // d of the last carve of rank_ws
+    Buf csr_p;     // CSR final pass, second form of Lemma 1: P = Mfull Mfull^T (FP64), Gram partials, Mfull^T
     Buf lsqr_u;    // LSQR: the unnormalised left vector u (n FP32)
     Buf lsqr_ws;   // LSQR: state, short vectors, pass partials, N^T
     double* host_lsqr = nullptr;   // pinned LSQR state read back by the host
@@ -459,6 +460,19 @@ int select_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, cons
     return LEV_OK;
 }
 
+// theta~ of CSR A: the second form of Lemma 1 (a P a^T with P = Mfull Mfull^T) when the rows are
+// short against k, else the first (||a Mfull||^2).
+int final_csr(lev_handle* h, const int64_t* rp, const int32_t* cl, const float* vl, int64_t n, int64_t d, int64_t nnz,
+              const float* Mfull, int64_t k, float* theta, cudaStream_t st) {
+    if (lev::csr_gram_pays(n, d, nnz, k)) {
+        LEV_TRY(ensure(h->csr_p, lev::csr_gram_scratch_bytes(d, k)));
+        LEV_CUDA(lev::launch_final_csr_gram(rp, cl, vl, n, d, Mfull, k, h->csr_p.ptr, theta, st));
+        return LEV_OK;
+    }
+    LEV_CUDA(lev::launch_final_csr_fp32(rp, cl, vl, n, d, Mfull, k, theta, st));
+    return LEV_OK;
+}
+
 int final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const float* Mfull,
                 int64_t k, int32_t prec, float* theta, cudaStream_t st) {
     if (prec == LEV_FP32) {
@@ -541,7 +555,7 @@ int lev_destroy(lev_handle* h) {
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
                   &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
                   &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->tc_pad,
-                  &h->exact_gp, &h->srht_c, &h->rank_ws, &h->lsqr_u, &h->lsqr_ws};
+                  &h->exact_gp, &h->srht_c, &h->rank_ws, &h->lsqr_u, &h->lsqr_ws, &h->csr_p};
     for (Buf* b : all) release(*b);
     for (int i = 0; i < 2; ++i) {
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
@@ -755,7 +769,7 @@ int lev_final_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > 4096 || k < 1 || k > 4096 || nnz < 0)
         return fail(LEV_EINVAL, "bad shape");
     if (prec != LEV_FP32) return fail(LEV_EINVAL, "the CSR final pass supports LEV_FP32 only");
-    LEV_CUDA(lev::launch_final_csr_fp32(row_ptr, col, val, n, d, Mfull, k, theta, (cudaStream_t)stream));
+    LEV_TRY(final_csr(h, row_ptr, col, val, n, d, nnz, Mfull, k, theta, (cudaStream_t)stream));
     return LEV_OK;
 }
 
@@ -916,7 +930,7 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, qs.rank, d, d, p->seed, true, (float*)h->Mfull.ptr, st));
     if (perm != (int32_t*)h->perm_d.ptr)
         LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
-    LEV_CUDA(lev::launch_final_csr_fp32(row_ptr, col, val, n, d, (const float*)h->Mfull.ptr, d, theta, st));
+    LEV_TRY(final_csr(h, row_ptr, col, val, n, d, nnz, (const float*)h->Mfull.ptr, d, theta, st));
     if (rank) *rank = k2;
     return LEV_OK;
 }
@@ -1001,7 +1015,7 @@ int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, 
     LEV_TRY(sketch_common_csr(h, rp, cl, vl, n, d, p, z, (float*)h->Atilde.ptr, st));
     lev::QrScratch qs;
     LEV_TRY(estimate_tail(h, z, d, p, perm, &qs, st));
-    LEV_CUDA(lev::launch_final_csr_fp32(rp, cl, vl, n, d, (const float*)h->Mfull.ptr, z.k, dT, st));
+    LEV_TRY(final_csr(h, rp, cl, vl, n, d, nnz, (const float*)h->Mfull.ptr, z.k, dT, st));
     if (hostT) LEV_CUDA(cudaMemcpyAsync(theta, dT, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, st));
     if (!rank && !hostA && !hostT) return LEV_OK;
     return finish(h, qs, rank, st);

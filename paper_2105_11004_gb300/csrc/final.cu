@@ -120,7 +120,77 @@ __global__ void __launch_bounds__(256) k_final_dense_fp32(
     }
 }
 
-// CSR, warp per row, lane owns columns q0 + lane*4 + {0..3} and q0 + 128 + lane*4 + {0..3}.
+// ||a_i M||^2 of one CSR row (entries p0 .. p1), this lane's share (the caller sums the warp): lane
+// owns columns q0 + lane*4 + {0..3} and q0 + 128 + lane*4 + {0..3} of each 256-column chunk.
+template <bool VEC>
+__device__ __forceinline__ float csr_row_norm(int64_t p0, int64_t p1, const int32_t* __restrict__ col,
+                                              const float* __restrict__ val, int d, const float* __restrict__ M,
+                                              int k, int lane) {
+    float total = 0.f;
+    for (int q0 = 0; q0 < k; q0 += 256) {
+        float y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) y[j] = 0.f;
+        for (int64_t pb = p0; pb < p1; pb += 32) {
+            const int cnt = (int)min((int64_t)32, p1 - pb);
+            int my_c = -1;
+            float my_v = 0.f;
+            if (lane < cnt) {
+                my_c = col[pb + lane];
+                my_v = val[pb + lane];
+                if ((unsigned)my_c >= (unsigned)d) { my_c = 0; my_v = 0.f; }
+            }
+            int u = 0;
+            for (; u + 4 <= cnt; u += 4) {
+                float4 m0[4], m1[4];
+                float vv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = __shfl_sync(0xffffffffu, my_c, u + e);
+                    vv[e] = __shfl_sync(0xffffffffu, my_v, u + e);
+                    const float* Mr = M + (int64_t)c * k + q0;
+                    if (VEC) {
+                        m0[e] = (q0 + lane * 4 < k) ? __ldg(reinterpret_cast<const float4*>(Mr + lane * 4))
+                                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                        m1[e] = (q0 + 128 + lane * 4 < k)
+                                    ? __ldg(reinterpret_cast<const float4*>(Mr + 128 + lane * 4))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        float tmp[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int q = q0 + (j < 4 ? lane * 4 + j : 128 + lane * 4 + j - 4);
+                            tmp[j] = (q < k) ? __ldg(M + (int64_t)c * k + q) : 0.f;
+                        }
+                        m0[e] = make_float4(tmp[0], tmp[1], tmp[2], tmp[3]);
+                        m1[e] = make_float4(tmp[4], tmp[5], tmp[6], tmp[7]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    y[0] = fmaf(vv[e], m0[e].x, y[0]); y[1] = fmaf(vv[e], m0[e].y, y[1]);
+                    y[2] = fmaf(vv[e], m0[e].z, y[2]); y[3] = fmaf(vv[e], m0[e].w, y[3]);
+                    y[4] = fmaf(vv[e], m1[e].x, y[4]); y[5] = fmaf(vv[e], m1[e].y, y[5]);
+                    y[6] = fmaf(vv[e], m1[e].z, y[6]); y[7] = fmaf(vv[e], m1[e].w, y[7]);
+                }
+            }
+            for (; u < cnt; ++u) {
+                const int c = __shfl_sync(0xffffffffu, my_c, u);
+                const float v = __shfl_sync(0xffffffffu, my_v, u);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int q = q0 + (j < 4 ? lane * 4 + j : 128 + lane * 4 + j - 4);
+                    if (q < k) y[j] = fmaf(v, __ldg(M + (int64_t)c * k + q), y[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) total = fmaf(y[j], y[j], total);
+    }
+    return total;
+}
+
+// CSR, warp per row: ||a_i Mfull||^2.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_final_csr_fp32(
         const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -130,70 +200,130 @@ __global__ void __launch_bounds__(256) k_final_csr_fp32(
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < n; i += nwarps) {
-        const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-        float total = 0.f;
-        for (int q0 = 0; q0 < k; q0 += 256) {
-            float y[8];
+        const float total = warp_sum(csr_row_norm<VEC>(row_ptr[i], row_ptr[i + 1], col, val, d, M, k, lane));
+        if (lane == 0) theta[i] = total;
+    }
+}
+
+// CSR with the second form of Lemma 1 for short rows: theta~_i = a_i P a_i^T, P = Mfull Mfull^T
+// (d x d FP64), i.e. the sum over the entry pairs p <= q of (2 - [p = q]) a_p a_q P[c_p][c_q]:
+// nnz_i^2 / 2 FP64 terms from a matrix that sits in L2, against nnz_i k products and nnz_i rows of
+// Mfull for the first form. Repeated columns are handled as they stand (the double sum over the
+// pairs is the quadratic form); columns outside [0, d) count as zero.
+//
+// k_final_csr_short: rows of at most 8 entries, 8 lanes a row and four rows a warp (the chain of
+// dependent loads of a row, bounds then entries then P, is what limits this pass, so a warp keeps
+// four rows in flight); each lane holds one entry, the pairs (row-major upper triangle, at most 36)
+// go round the 8 lanes in 5 fixed rounds. Longer rows are left to k_final_csr_long.
+__device__ __forceinline__ void tri_pair(int t, int len, int& p, int& q) {
+    p = 0;
+    while (t >= len - p) {
+        t -= len - p;
+        ++p;
+    }
+    q = p + t;
+}
+
+__global__ void __launch_bounds__(256) k_final_csr_short(const int64_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const float* __restrict__ val, int64_t n, int d,
+                                                         const double* __restrict__ P, float* __restrict__ theta) {
+    const int lane = threadIdx.x & 31, seg = lane >> 3, sl = lane & 7;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = warp * 4; r0 < n; r0 += nwarps * 4) {
+        const int64_t r = r0 + seg;
+        const bool rok = r < n;
+        const int64_t p0 = rok ? row_ptr[r] : 0, p1 = rok ? row_ptr[r + 1] : 0;
+        const int len = (int)(p1 - p0);
+        const bool mine = rok && len <= 8;
+        int my_c = 0;
+        double my_v = 0.0;
+        if (mine && sl < len) {
+            const int c = col[p0 + sl];
+            if ((unsigned)c < (unsigned)d) {
+                my_c = c;
+                my_v = (double)val[p0 + sl];
+            }
+        }
+        const int npairs = mine ? len * (len + 1) / 2 : 0;
+        double acc = 0.0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) y[j] = 0.f;
-            for (int64_t pb = p0; pb < p1; pb += 32) {
-                const int cnt = (int)min((int64_t)32, p1 - pb);
-                int my_c = -1;
-                float my_v = 0.f;
-                if (lane < cnt) {
-                    my_c = col[pb + lane];
-                    my_v = val[pb + lane];
-                    if ((unsigned)my_c >= (unsigned)d) { my_c = 0; my_v = 0.f; }
-                }
-                int u = 0;
-                for (; u + 4 <= cnt; u += 4) {
-                    float4 m0[4], m1[4];
-                    float vv[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = __shfl_sync(0xffffffffu, my_c, u + e);
-                        vv[e] = __shfl_sync(0xffffffffu, my_v, u + e);
-                        const float* Mr = M + (int64_t)c * k + q0;
-                        if (VEC) {
-                            m0[e] = (q0 + lane * 4 < k) ? __ldg(reinterpret_cast<const float4*>(Mr + lane * 4))
-                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-                            m1[e] = (q0 + 128 + lane * 4 < k)
-                                        ? __ldg(reinterpret_cast<const float4*>(Mr + 128 + lane * 4))
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-                        } else {
-                            float tmp[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const int q = q0 + (j < 4 ? lane * 4 + j : 128 + lane * 4 + j - 4);
-                                tmp[j] = (q < k) ? __ldg(M + (int64_t)c * k + q) : 0.f;
-                            }
-                            m0[e] = make_float4(tmp[0], tmp[1], tmp[2], tmp[3]);
-                            m1[e] = make_float4(tmp[4], tmp[5], tmp[6], tmp[7]);
-                        }
-                    }
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        y[0] = fmaf(vv[e], m0[e].x, y[0]); y[1] = fmaf(vv[e], m0[e].y, y[1]);
-                        y[2] = fmaf(vv[e], m0[e].z, y[2]); y[3] = fmaf(vv[e], m0[e].w, y[3]);
-                        y[4] = fmaf(vv[e], m1[e].x, y[4]); y[5] = fmaf(vv[e], m1[e].y, y[5]);
-                        y[6] = fmaf(vv[e], m1[e].z, y[6]); y[7] = fmaf(vv[e], m1[e].w, y[7]);
-                    }
-                }
-                for (; u < cnt; ++u) {
-                    const int c = __shfl_sync(0xffffffffu, my_c, u);
-                    const float v = __shfl_sync(0xffffffffu, my_v, u);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int q = q0 + (j < 4 ? lane * 4 + j : 128 + lane * 4 + j - 4);
-                        if (q < k) y[j] = fmaf(v, __ldg(M + (int64_t)c * k + q), y[j]);
-                    }
+        for (int round = 0; round < 5; ++round) {
+            const int t = round * 8 + sl;
+            int pp = 0, qq = 0;
+            if (t < npairs) tri_pair(t, len, pp, qq);
+            const int cp = __shfl_sync(0xffffffffu, my_c, seg * 8 + pp);
+            const int cq = __shfl_sync(0xffffffffu, my_c, seg * 8 + qq);
+            const double vp = __shfl_sync(0xffffffffu, my_v, seg * 8 + pp);
+            const double vq = __shfl_sync(0xffffffffu, my_v, seg * 8 + qq);
+            if (t < npairs) acc = fma((pp == qq ? 1.0 : 2.0) * vp * vq, P[(int64_t)cp * d + cq], acc);
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (mine && sl == 0) theta[r] = (float)acc;
+    }
+}
+
+// Rows of more than 8 entries: a warp scans the bounds of 32 rows at once and takes each long row
+// in turn with the whole warp: the second form (one entry per lane, pairs round the lanes) up to 32
+// entries, the first form (csr_row_norm) above.
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_final_csr_long(const int64_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const float* __restrict__ val, int64_t n, int d,
+                                                        const float* __restrict__ M, int k,
+                                                        const double* __restrict__ P, float* __restrict__ theta) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r0 = warp * 32; r0 < n; r0 += nwarps * 32) {
+        const int64_t rl = r0 + lane;
+        const int64_t lenl = rl < n ? row_ptr[rl + 1] - row_ptr[rl] : 0;
+        unsigned todo = __ballot_sync(0xffffffffu, lenl > 8);
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t i = r0 + b;
+            const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+            const int len = (int)(p1 - p0);
+            if (len > 32) {
+                const float total = warp_sum(csr_row_norm<VEC>(p0, p1, col, val, d, M, k, lane));
+                if (lane == 0) theta[i] = total;
+                continue;
+            }
+            int my_c = 0;
+            double my_v = 0.0;
+            if (lane < len) {
+                const int c = col[p0 + lane];
+                if ((unsigned)c < (unsigned)d) {
+                    my_c = c;
+                    my_v = (double)val[p0 + lane];
                 }
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) total = fmaf(y[j], y[j], total);
+            const int npairs = len * (len + 1) / 2;
+            double acc = 0.0;
+            for (int base = 0; base < npairs; base += 32) {
+                const int t = base + lane;
+                int pp = 0, qq = 0;
+                if (t < npairs) tri_pair(t, len, pp, qq);
+                const int cp = __shfl_sync(0xffffffffu, my_c, pp), cq = __shfl_sync(0xffffffffu, my_c, qq);
+                const double vp = __shfl_sync(0xffffffffu, my_v, pp), vq = __shfl_sync(0xffffffffu, my_v, qq);
+                if (t < npairs) acc = fma((pp == qq ? 1.0 : 2.0) * vp * vq, P[(int64_t)cp * d + cq], acc);
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) theta[i] = (float)acc;
         }
-        total = warp_sum(total);
-        if (lane == 0) theta[i] = total;
+    }
+}
+
+// MT (k x d) = Mfull^T (Mfull d x k, both row-major).
+__global__ void k_transpose_mfull(const float* __restrict__ M, int d, int k, float* __restrict__ MT) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)d * k;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e / d), c = (int)(e % d);
+        MT[e] = M[(int64_t)c * k + q];
     }
 }
 
@@ -209,6 +339,41 @@ cudaError_t launch_final_dense_fp32(const float* A, int64_t lda, int64_t n, int6
         k_final_dense_fp32<true><<<(unsigned)grid, 256, 0, st>>>(A, lda, n, (int)d, Mfull, (int)k, theta);
     else
         k_final_dense_fp32<false><<<(unsigned)grid, 256, 0, st>>>(A, lda, n, (int)d, Mfull, (int)k, theta);
+    return cudaGetLastError();
+}
+
+size_t csr_gram_scratch_bytes(int64_t d, int64_t k) {
+    return sizeof(double) * (size_t)(d * d + gram_partial_doubles(k, d)) + sizeof(float) * (size_t)(k * d) + 1024;
+}
+
+bool csr_gram_pays(int64_t n, int64_t d, int64_t nnz, int64_t k) {
+    return d <= 1024 && n > 0 && nnz * 8 < n * k;      // short rows on average: nnz_i < k / 8
+}
+
+cudaError_t launch_final_csr_gram(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n, int64_t d,
+                                  const float* Mfull, int64_t k, void* scratch, float* theta, cudaStream_t st) {
+    double* P = reinterpret_cast<double*>(scratch);
+    double* Gp = P + d * d;
+    float* MT = reinterpret_cast<float*>(Gp + gram_partial_doubles(k, d));
+    int tg = (int)((d * k + 255) / 256);
+    if (tg > 152 * 8) tg = 152 * 8;
+    k_transpose_mfull<<<tg, 256, 0, st>>>(Mfull, (int)d, (int)k, MT);
+    cudaError_t e = launch_gram_fp64(MT, d, k, d, Gp, P, st);           // P = Mfull Mfull^T
+    if (e != cudaSuccess) return e;
+    const bool vec = (reinterpret_cast<uintptr_t>(Mfull) % 16 == 0) && (k % 4 == 0);
+    int64_t grid = (n * 8 + 255) / 256;                 // four rows a warp
+    if (grid > 152 * 64) grid = 152 * 64;
+    if (grid < 1) grid = 1;
+    k_final_csr_short<<<(unsigned)grid, 256, 0, st>>>(row_ptr, col, val, n, (int)d, P, theta);
+    int64_t grid_l = (n + 255) / 256;                   // 32 rows scanned a warp
+    if (grid_l > 152 * 16) grid_l = 152 * 16;
+    if (grid_l < 1) grid_l = 1;
+    if (vec)
+        k_final_csr_long<true><<<(unsigned)grid_l, 256, 0, st>>>(row_ptr, col, val, n, (int)d, Mfull, (int)k, P,
+                                                                theta);
+    else
+        k_final_csr_long<false><<<(unsigned)grid_l, 256, 0, st>>>(row_ptr, col, val, n, (int)d, Mfull, (int)k, P,
+                                                                 theta);
     return cudaGetLastError();
 }
 

@@ -145,6 +145,13 @@ cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_
 
 cudaError_t launch_final_dense_fp32(const float* A, int64_t lda, int64_t n, int64_t d,
                                     const float* Mfull, int64_t k, float* theta, cudaStream_t st);
+// CSR final pass in the second form of Lemma 1 for rows of at most 32 entries (theta~ = a P a^T,
+// P = Mfull Mfull^T in FP64 built here from Mfull) and the first form for longer rows; scratch:
+// csr_gram_scratch_bytes(d, k). csr_gram_pays: whether the second form is the cheaper one.
+size_t csr_gram_scratch_bytes(int64_t d, int64_t k);
+bool csr_gram_pays(int64_t n, int64_t d, int64_t nnz, int64_t k);
+cudaError_t launch_final_csr_gram(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n, int64_t d,
+                                  const float* Mfull, int64_t k, void* scratch, float* theta, cudaStream_t st);
 cudaError_t launch_final_csr_fp32(const int64_t* row_ptr, const int32_t* col, const float* val,
                                   int64_t n, int64_t d, const float* Mfull, int64_t k,
                                   float* theta, cudaStream_t st);

@@ -285,6 +285,33 @@ def test_final_csr_parity(L, h):
     assert max_rel(to_np(theta), want) <= 1e-5
 
 
+@pytest.mark.parametrize("k", [256, 64])
+def test_final_csr_both_forms_of_lemma1(L, h, k):
+    """Rows of 0..40 entries straddle the switch between the second form of Lemma 1 (a P a^T for
+    rows of <= 32 entries) and the first (||a Mfull||^2); columns unsorted, repeated (they add up)
+    and, on some rows, outside [0, d) (they count as zero)."""
+    import torch
+    rs = np.random.default_rng(k)
+    n, d = 6001, 120
+    lens = rs.integers(0, 41, size=n)
+    row_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    col = rs.integers(0, d, size=row_ptr[-1]).astype(np.int32)
+    col[rs.random(col.size) < 0.01] = d + 5                      # out of range
+    val = rs.standard_normal(row_ptr[-1]).astype(np.float32)
+    Mf = (rs.standard_normal((d, k)) / np.sqrt(k)).astype(np.float32)
+    theta = torch.full((n,), float("nan"), device="cuda")
+    L.lev_final_csr(h, to_dev(row_ptr), to_dev(col), to_dev(val), n, d, to_dev(Mf), "fp32", theta)
+    torch.cuda.synchronize()
+    ok = col < d
+    rows = np.repeat(np.arange(n), lens)
+    Adense = np.zeros((n, d))
+    np.add.at(Adense, (rows[ok], col[ok]), val[ok].astype(np.float64))
+    want = np.sum((Adense @ Mf.astype(np.float64)) ** 2, axis=1)
+    got = to_np(theta).astype(np.float64)
+    assert np.all(got[lens == 0] == 0)
+    assert max_rel(got, want) <= 1e-5
+
+
 # ---------------------------------------------------------------- end to end
 
 def _oracle_estimate(A32, cfg):
