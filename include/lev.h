@@ -215,6 +215,15 @@ int lev_lsqr_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t 
                    int64_t k, const float* b, double* x, int32_t max_iter, double atol, double btol,
                    int32_t* iters, double* rnorm, void* stream);
 
+/* The same on CSR A (device arrays, the conventions of lev_sketch_csr; columns outside [0, d) count
+ * as zero). Each pass takes the rows of at most 8 entries four to a warp and the others a warp
+ * each. A repeated column within a row adds through a shared-memory atomic, so its rounding order
+ * (and x's last bits) may vary between runs; otherwise the sums run in a fixed order. */
+int lev_lsqr_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
+                 int64_t n, int64_t d, int64_t nnz, const double* N, int64_t k, const float* b,
+                 double* x, int32_t max_iter, double atol, double btol, int32_t* iters,
+                 double* rnorm, void* stream);
+
 /* The small factor of the final pass (Alg. 8 step 4 with the QR
  * orthogonaliser): M = R_11^{-1} Omega (r x k) by FP64 back-substitution, with
  * Omega drawn from stream 3 of `seed` (or I_r with LEV_OMEGA_IDENTITY, k = r),

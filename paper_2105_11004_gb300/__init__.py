@@ -75,6 +75,8 @@ SIGNATURES = {
     "lev_lsqr_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _c_void_p, _i64, _c_void_p, _c_void_p,
                                       _i32, _dbl, _dbl, _P(_i32), _P(_dbl), _c_void_p]),
     "lev_rank_stats": (ctypes.c_int, [_c_void_p, _P(_i64), _P(_i32)]),
+    "lev_lsqr_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64, _c_void_p, _i64,
+                                    _c_void_p, _c_void_p, _i32, _dbl, _dbl, _P(_i32), _P(_dbl), _c_void_p]),
     "lev_set_timing": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "lev_rrqr_timing": (ctypes.c_int, [_c_void_p, _P(ctypes.c_float), _P(ctypes.c_float)]),
     "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
@@ -238,6 +240,15 @@ def lev_lsqr_dense(h: Handle, A, N, k, b, x, max_iter=200, atol=1e-6, btol=1e-6,
     it, rn = _i32(), _dbl()
     _check(lib.lev_lsqr_dense(h.ptr, _ptr(A), n, d, A.stride(0), _ptr(N), int(k), _ptr(b), _ptr(x), int(max_iter),
                               float(atol), float(btol), ctypes.byref(it), ctypes.byref(rn), _stream(stream)))
+    return it.value, rn.value
+
+
+def lev_lsqr_csr(h: Handle, row_ptr, col, val, n, d, N, k, b, x, max_iter=200, atol=1e-6, btol=1e-6, stream=None):
+    """LSQR on min ||A N y - b|| for CSR A, x = N y (device FP64); returns (iterations, residual estimate)."""
+    it, rn = _i32(), _dbl()
+    _check(lib.lev_lsqr_csr(h.ptr, _ptr(row_ptr), _ptr(col), _ptr(val), n, d, col.numel(), _ptr(N), int(k), _ptr(b),
+                            _ptr(x), int(max_iter), float(atol), float(btol), ctypes.byref(it), ctypes.byref(rn),
+                            _stream(stream)))
     return it.value, rn.value
 
 

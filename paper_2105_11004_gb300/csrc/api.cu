@@ -720,7 +720,8 @@ int lev_lsqr_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t 
     LEV_CUDA(cudaMemcpyAsync(h->lsqr_u.ptr, b, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     int it = 0;
     double rn = 0.0;
-    LEV_CUDA(lev::launch_lsqr(A, lda, n, d, N, k, (float*)h->lsqr_u.ptr, x, max_iter, atol > 0 ? atol : 1e-6,
+    LEV_CUDA(lev::launch_lsqr(A, lda, nullptr, nullptr, nullptr, n, d, N, k, (float*)h->lsqr_u.ptr, x, max_iter,
+                              atol > 0 ? atol : 1e-6,
                               btol > 0 ? btol : 1e-6, (double*)h->lsqr_ws.ptr, parts, h->host_lsqr, &it, &rn, st));
     if (iters) *iters = it;
     if (rnorm) *rnorm = rn;
@@ -739,6 +740,34 @@ int lev_rank_stats(lev_handle* h, int64_t* swaps, int32_t* jacobi_sweeps) {
             LEV_CUDA(cudaMemcpy(jacobi_sweeps, rw.sweeps, sizeof(int32_t), cudaMemcpyDeviceToHost));
         }
     }
+    return LEV_OK;
+}
+
+int lev_lsqr_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n, int64_t d,
+                 int64_t nnz, const double* N, int64_t k, const float* b, double* x, int32_t max_iter, double atol,
+                 double btol, int32_t* iters, double* rnorm, void* stream) {
+    LEV_TRY(set_device(h));
+    if (!row_ptr || (nnz > 0 && (!col || !val)) || !N || !b || !x) return fail(LEV_EINVAL, "NULL array");
+    if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > 1024 || nnz < 0)
+        return fail(LEV_EINVAL, "bad shape n=%lld d=%lld", (long long)n, (long long)d);
+    if (k < 1 || k > d) return fail(LEV_EINVAL, "k = %lld outside [1, d]", (long long)k);
+    if (max_iter < 0) return fail(LEV_EINVAL, "max_iter < 0");
+    if (is_host_pointer(row_ptr) || is_host_pointer(N) || is_host_pointer(b) || is_host_pointer(x))
+        return fail(LEV_EINVAL, "lev_lsqr_csr takes device arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int parts = lev::lsqr_parts(h->num_sms);
+    LEV_TRY(ensure(h->lsqr_u, sizeof(float) * (size_t)n));
+    LEV_TRY(ensure(h->lsqr_ws, sizeof(double) * lev::lsqr_scratch_doubles(d, parts)));
+    if (!h->host_lsqr && cudaMallocHost(&h->host_lsqr, 256) != cudaSuccess)
+        return fail(LEV_ENOMEM, "pinned host buffer");
+    LEV_CUDA(cudaMemcpyAsync(h->lsqr_u.ptr, b, sizeof(float) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    int it = 0;
+    double rn = 0.0;
+    LEV_CUDA(lev::launch_lsqr(nullptr, 0, row_ptr, col, val, n, d, N, k, (float*)h->lsqr_u.ptr, x, max_iter,
+                              atol > 0 ? atol : 1e-6, btol > 0 ? btol : 1e-6, (double*)h->lsqr_ws.ptr, parts,
+                              h->host_lsqr, &it, &rn, st));
+    if (iters) *iters = it;
+    if (rnorm) *rnorm = rn;
     return LEV_OK;
 }
 

@@ -107,7 +107,9 @@ int lsqr_parts(int num_sms);
 int lsqr_state_doubles();
 cudaError_t launch_precond_n(const double* Y, const int32_t* order, const double* sigma, const int32_t* perm,
                              const int64_t* d_rank, int64_t d, double* N, cudaStream_t st);
-cudaError_t launch_lsqr(const float* A, int64_t lda, int64_t n, int64_t d, const double* N, int64_t k, float* u,
+// A dense (A, lda) or CSR (row_ptr, col, val; A == nullptr).
+cudaError_t launch_lsqr(const float* A, int64_t lda, const int64_t* row_ptr, const int32_t* col, const float* val,
+                        int64_t n, int64_t d, const double* N, int64_t k, float* u,
                         double* x, int max_iter, double atol, double btol, double* ws, int parts, double* host_state,
                         int* iters_out, double* rnorm_out, cudaStream_t st);
 void qr_scratch_carve(void* base, int64_t m, int64_t d, QrScratch* q);

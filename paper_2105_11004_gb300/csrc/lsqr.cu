@@ -174,6 +174,129 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_pass(const float* __re
     }
 }
 
+// The same pass for CSR A. Each warp keeps z = A^T x of its rows in its own FP64 shared-memory
+// array (a repeated column in a row adds through a shared-memory atomic), written out as the CTA's
+// partial; t = N v sits in shared memory. k_lsqr_csr_short takes the rows of at most 8 entries, 8
+// lanes a row and four rows a warp (a row is a chain of dependent loads: bounds, entries, t);
+// k_lsqr_csr_long the others, a whole warp a row, found by scanning 32 row lengths at a time.
+// Columns outside [0, d) count as zero.
+__device__ __forceinline__ void csr_pass_finish(const double* zs, const double* ns, int d, double* zrow,
+                                                double* nout) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < kPassWarps; ++q) s += zs[q * d + j];
+        zrow[j] = s;
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < kPassWarps; ++q) s += ns[q];
+        *nout = s;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_csr_short(const int64_t* __restrict__ row_ptr,
+                                                                    const int32_t* __restrict__ col,
+                                                                    const float* __restrict__ val, int64_t n, int d,
+                                                                    const float* __restrict__ t,
+                                                                    const double* __restrict__ state,
+                                                                    float* __restrict__ u, double* __restrict__ zpart,
+                                                                    double* __restrict__ npart) {
+    extern __shared__ double zs[];                      // kPassWarps x d, then t (d floats)
+    __shared__ double ns[kPassWarps];
+    if (state[S_DONE] != 0.0) return;
+    float* ts = reinterpret_cast<float*>(zs + kPassWarps * d);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, seg = lane >> 3, sl = lane & 7;
+    const float gamma = (float)state[S_GAMMA];
+    for (int j = threadIdx.x; j < kPassWarps * d; j += blockDim.x) zs[j] = 0.0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) ts[j] = t[j];
+    __syncthreads();
+    double* zw = zs + w * d;
+    double nrm = 0.0;
+    const int64_t wid = (int64_t)blockIdx.x * kPassWarps + w, nw = (int64_t)gridDim.x * kPassWarps;
+    for (int64_t r0 = wid * 4; r0 < n; r0 += nw * 4) {
+        const int64_t r = r0 + seg;
+        const bool rok = r < n;
+        const int64_t p0 = rok ? row_ptr[r] : 0, p1 = rok ? row_ptr[r + 1] : 0;
+        const int len = (int)(p1 - p0);
+        const bool mine = rok && len <= 8;
+        int c = -1;
+        float a = 0.f;
+        if (mine && sl < len) {
+            c = col[p0 + sl];
+            a = val[p0 + sl];
+            if ((unsigned)c >= (unsigned)d) { c = -1; a = 0.f; }
+        }
+        float dot = c >= 0 ? a * ts[c] : 0.f;
+        dot += __shfl_xor_sync(0xffffffffu, dot, 4);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 2);
+        dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+        float x = 0.f;
+        if (mine && sl == 0) {
+            x = fmaf(gamma, u[r], dot);
+            u[r] = x;
+            nrm = fma((double)x, (double)x, nrm);
+        }
+        x = __shfl_sync(0xffffffffu, x, seg * 8);
+        if (c >= 0) atomicAdd(zw + c, (double)a * (double)x);
+    }
+    nrm = warp_sum(nrm);
+    if (lane == 0) ns[w] = nrm;
+    csr_pass_finish(zs, ns, d, zpart + (int64_t)blockIdx.x * d, npart + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_csr_long(const int64_t* __restrict__ row_ptr,
+                                                                   const int32_t* __restrict__ col,
+                                                                   const float* __restrict__ val, int64_t n, int d,
+                                                                   const float* __restrict__ t,
+                                                                   const double* __restrict__ state,
+                                                                   float* __restrict__ u, double* __restrict__ zpart,
+                                                                   double* __restrict__ npart) {
+    extern __shared__ double zs[];
+    __shared__ double ns[kPassWarps];
+    if (state[S_DONE] != 0.0) return;
+    float* ts = reinterpret_cast<float*>(zs + kPassWarps * d);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float gamma = (float)state[S_GAMMA];
+    for (int j = threadIdx.x; j < kPassWarps * d; j += blockDim.x) zs[j] = 0.0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) ts[j] = t[j];
+    __syncthreads();
+    double* zw = zs + w * d;
+    double nrm = 0.0;
+    const int64_t wid = (int64_t)blockIdx.x * kPassWarps + w, nw = (int64_t)gridDim.x * kPassWarps;
+    for (int64_t r0 = wid * 32; r0 < n; r0 += nw * 32) {
+        const int64_t rl = r0 + lane;
+        const int64_t lenl = rl < n ? row_ptr[rl + 1] - row_ptr[rl] : 0;
+        unsigned todo = __ballot_sync(0xffffffffu, lenl > 8);
+        while (todo) {
+            const int b = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t i = r0 + b;
+            const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+            float dot = 0.f;
+            for (int64_t e = p0 + lane; e < p1; e += 32) {
+                const int c = col[e];
+                if ((unsigned)c < (unsigned)d) dot = fmaf(val[e], ts[c], dot);
+            }
+            dot = warp_sum(dot);
+            float x = 0.f;
+            if (lane == 0) {
+                x = fmaf(gamma, u[i], dot);
+                u[i] = x;
+                nrm = fma((double)x, (double)x, nrm);
+            }
+            x = __shfl_sync(0xffffffffu, x, 0);
+            for (int64_t e = p0 + lane; e < p1; e += 32) {
+                const int c = col[e];
+                if ((unsigned)c < (unsigned)d) atomicAdd(zw + c, (double)val[e] * (double)x);
+            }
+        }
+    }
+    nrm = warp_sum(nrm);
+    if (lane == 0) ns[w] = nrm;
+    csr_pass_finish(zs, ns, d, zpart + (int64_t)blockIdx.x * d, npart + blockIdx.x);
+}
+
 // z[j] = sum over CTAs of zpart and beta = sqrt(sum of npart), in a fixed order: block b < gridDim.x
 // - 1 takes columns 32b .. 32b + 31 (lane = column), warp w the partials w, w + 8, ..., then the
 // warps' sums are added in warp order; the last block does the same for npart.
@@ -357,7 +480,8 @@ static cudaError_t lsqr_pass(bool vec, int parts, size_t smem, cudaStream_t st, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_lsqr(const float* A, int64_t lda, int64_t n, int64_t d, const double* N, int64_t k, float* u,
+cudaError_t launch_lsqr(const float* A, int64_t lda, const int64_t* row_ptr, const int32_t* col, const float* val,
+                        int64_t n, int64_t d, const double* N, int64_t k, float* u,
                         double* x, int max_iter, double atol, double btol, double* ws, int parts, double* host_state,
                         int* iters_out, double* rnorm_out, cudaStream_t st) {
     cudaError_t e;
@@ -373,9 +497,26 @@ cudaError_t launch_lsqr(const float* A, int64_t lda, int64_t n, int64_t d, const
     double* npart = zpart + (size_t)parts * d;
     double* Nt = npart + parts;
     const int nc = (int)((d + 127) / 128);
-    const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
+    const bool vec = A && (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
     const size_t smem = sizeof(double) * (size_t)kPassWarps * d;
+    const bool csr = row_ptr != nullptr;
+    const int parts_s = parts / 2, parts_l = parts - parts_s;
+    const size_t smem_csr = sizeof(double) * (size_t)kPassWarps * d + sizeof(float) * (size_t)d;
+    if (csr) {
+        const int mx = (int)(sizeof(double) * kPassWarps * 1024 + sizeof(float) * 1024);
+        if ((e = cudaFuncSetAttribute(k_lsqr_csr_short, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k_lsqr_csr_long, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+            return e;
+    }
     auto pass = [&]() -> cudaError_t {
+        if (csr) {
+            k_lsqr_csr_short<<<parts_s, 32 * kPassWarps, smem_csr, st>>>(row_ptr, col, val, n, (int)d, t, state, u,
+                                                                         zpart, npart);
+            k_lsqr_csr_long<<<parts_l, 32 * kPassWarps, smem_csr, st>>>(row_ptr, col, val, n, (int)d, t, state, u,
+                                                                        zpart + (size_t)parts_s * d, npart + parts_s);
+            return cudaGetLastError();
+        }
         if (nc == 1) return lsqr_pass<1, 8>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
         if (nc == 2) return lsqr_pass<2, 4>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);
         if (nc <= 4) return lsqr_pass<4, 2>(vec, parts, smem, st, A, lda, n, (int)d, t, state, u, zpart, npart);

@@ -136,3 +136,29 @@ def test_csr_preconditioner_bound(L, h):
     assert np.linalg.cond(Asp.toarray()) > 50
     sv = np.linalg.svd(Asp @ to_np(N), compute_uv=False)
     assert sv[0] / sv[-1] <= P.kappa_bound(d, 4 * d, alpha=0.3, eps=0.5)
+
+
+def test_lstsq_csr_matches_numpy(L, h):
+    """Alg. 11 and LSQR on CSR input: rows of 0..40 entries (both pass kernels), scaled columns."""
+    import torch
+    rs = np.random.default_rng(6)
+    n, d = 80000, 72
+    lens = np.where(rs.random(n) < 0.05, rs.integers(9, 41, size=n), rs.integers(0, 9, size=n))
+    row_ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    col = np.concatenate([rs.choice(d, size=l, replace=False) for l in lens]).astype(np.int32)
+    scale = np.exp(rs.standard_normal(d))
+    val = (rs.standard_normal(row_ptr[-1]) * scale[col]).astype(np.float32)
+    Ad = sp.csr_matrix((val.astype(np.float64), col, row_ptr), shape=(n, d)).toarray()
+    kappa = np.linalg.cond(Ad)
+    x0 = rs.standard_normal(d)
+    b = Ad @ x0
+    b = (b + 1e-3 * np.linalg.norm(b) / np.sqrt(n) * rs.standard_normal(n)).astype(np.float32)
+    dr, dc, dv = to_dev(row_ptr), to_dev(col), to_dev(val)
+    p = L.make_params(s=16384, m=4 * d, k=8, tau=1e-10, seed=2, sketch_prec="bf16x3")
+    N = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    k = L.lev_precondition_csr(h, dr, dc, dv, n, d, p, N)
+    assert k == d
+    x = torch.zeros(d, dtype=torch.float64, device="cuda")
+    it, rn = L.lev_lsqr_csr(h, dr, dc, dv, n, d, N, k, to_dev(b), x)
+    assert 0 < it < 60
+    _check_solution(Ad.astype(np.float32), b, to_np(x), kappa)
