@@ -549,6 +549,17 @@ def csr_timing(L, h, name, reps):
     sk_s = timed(lambda: L.lev_sketch_csr(h, rp, cl, vl, n, d, ps, At), reps)
     out["srht"] = {"t": t, "rank": r_s, "ms_per_step": ms_s, "rows_per_s": n / (ms_s * 1e-3), "sketch_ms": sk_s,
                    "gaussian_stage_flops": 2.0 * cfg["m"] * t * d, "note": "A~ = G (F (S A)), G m x t"}
+    # Alg. 11 and LSQR on the same matrix with b ~ N(0, 1): min ||A x - b|| for CSR A
+    b = torch.from_numpy(np.random.default_rng(0).standard_normal(n).astype(np.float32)).cuda()
+    pn = L.make_params(s=cfg["s"], m=cfg["m"], k=8, tau=1e-10, seed=cfg["seed"], sketch_prec="bf16x3")
+    Np = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    kp = L.lev_precondition_csr(h, rp, cl, vl, n, d, pn, Np)
+    pre_ms = timed(lambda: L.lev_precondition_csr(h, rp, cl, vl, n, d, pn, Np), 1)
+    xs = torch.zeros(d, dtype=torch.float64, device="cuda")
+    its, rns = L.lev_lsqr_csr(h, rp, cl, vl, n, d, Np, kp, b, xs)
+    ls_ms = timed(lambda: L.lev_lsqr_csr(h, rp, cl, vl, n, d, Np, kp, b, xs), 2)
+    out["lstsq"] = {"rank": kp, "precondition_ms": pre_ms, "iterations": its, "lsqr_ms": ls_ms,
+                    "csr_gbs_per_pass": (its + 1) * (csr_bytes + 8 * n) / (ls_ms * 1e-3) / 1e9}
     # Alg. 7 (LS-HRN-exact) on the same matrix: B = A_K^T A_K from the rows' outer products
     # (Lemma 3, FP64), its forced-pivot Cholesky, theta = ||A_K R^{-1}||^2 (k = d)
     r_e = L.lev_exact_csr(h, rp, cl, vl, n, d, p, theta)

@@ -231,20 +231,29 @@ __global__ void __launch_bounds__(256) k_final_csr_short(const int64_t* __restri
     const int lane = threadIdx.x & 31, seg = lane >> 3, sl = lane & 7;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // one-deep pipeline: the bounds of the next four rows load while this four runs
+    int64_t rn = warp * 4 + seg;
+    int64_t np0 = rn < n ? row_ptr[rn] : 0, np1 = rn < n ? row_ptr[rn + 1] : 0;
     for (int64_t r0 = warp * 4; r0 < n; r0 += nwarps * 4) {
         const int64_t r = r0 + seg;
         const bool rok = r < n;
-        const int64_t p0 = rok ? row_ptr[r] : 0, p1 = rok ? row_ptr[r + 1] : 0;
+        const int64_t p0 = np0, p1 = np1;
         const int len = (int)(p1 - p0);
         const bool mine = rok && len <= 8;
+        int c = -1;
+        float a = 0.f;
+        if (mine && sl < len) {
+            c = col[p0 + sl];
+            a = val[p0 + sl];
+        }
+        rn = r + nwarps * 4;
+        np0 = rn < n ? row_ptr[rn] : 0;
+        np1 = rn < n ? row_ptr[rn + 1] : 0;
         int my_c = 0;
         double my_v = 0.0;
-        if (mine && sl < len) {
-            const int c = col[p0 + sl];
-            if ((unsigned)c < (unsigned)d) {
-                my_c = c;
-                my_v = (double)val[p0 + sl];
-            }
+        if ((unsigned)c < (unsigned)d) {
+            my_c = c;
+            my_v = (double)a;
         }
         const int npairs = mine ? len * (len + 1) / 2 : 0;
         double acc = 0.0;

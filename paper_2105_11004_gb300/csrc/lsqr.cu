@@ -80,7 +80,7 @@ __device__ __forceinline__ void fold4(double* z, int col, int d, float4& a) {
 // (and the U values of u, one per lane) issued before any is used. VEC: A 16-byte aligned with
 // lda % 4 == 0.
 template <int NC, int U, bool VEC>
-__global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_pass(const float* __restrict__ A, int64_t lda, int64_t n,
+__global__ void __launch_bounds__(32 * kPassWarps, (NC <= 2 ? 3 : 1)) k_lsqr_pass(const float* __restrict__ A, int64_t lda, int64_t n,
                                                                int d, const float* __restrict__ t,
                                                                const double* __restrict__ state,
                                                                float* __restrict__ u, double* __restrict__ zpart,
@@ -174,18 +174,19 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_pass(const float* __re
     }
 }
 
-// The same pass for CSR A. Each warp keeps z = A^T x of its rows in its own FP64 shared-memory
-// array (a repeated column in a row adds through a shared-memory atomic), written out as the CTA's
-// partial; t = N v sits in shared memory. k_lsqr_csr_short takes the rows of at most 8 entries, 8
+// The same pass for CSR A. Each warp keeps z = A^T x of its rows in its own FP32 shared-memory
+// array (native shared-memory float atomics; a column of a sparse row gets few terms per warp, so
+// FP32 adds about u_32 sqrt(terms) to a sum that LSQR uses at the 1e-6 level), summed over the
+// warps in FP64 into the CTA's partial; t = N v sits in shared memory. k_lsqr_csr_short takes the rows of at most 8 entries, 8
 // lanes a row and four rows a warp (a row is a chain of dependent loads: bounds, entries, t);
 // k_lsqr_csr_long the others, a whole warp a row, found by scanning 32 row lengths at a time.
 // Columns outside [0, d) count as zero.
-__device__ __forceinline__ void csr_pass_finish(const double* zs, const double* ns, int d, double* zrow,
+__device__ __forceinline__ void csr_pass_finish(const float* zs, const double* ns, int d, double* zrow,
                                                 double* nout) {
     __syncthreads();
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
         double s = 0.0;
-        for (int q = 0; q < kPassWarps; ++q) s += zs[q * d + j];
+        for (int q = 0; q < kPassWarps; ++q) s += (double)zs[q * d + j];
         zrow[j] = s;
     }
     if (threadIdx.x == 0) {
@@ -202,22 +203,28 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_csr_short(const int64_
                                                                     const double* __restrict__ state,
                                                                     float* __restrict__ u, double* __restrict__ zpart,
                                                                     double* __restrict__ npart) {
-    extern __shared__ double zs[];                      // kPassWarps x d, then t (d floats)
+    extern __shared__ float zsf[];                      // kPassWarps x d, then t (d floats)
     __shared__ double ns[kPassWarps];
     if (state[S_DONE] != 0.0) return;
-    float* ts = reinterpret_cast<float*>(zs + kPassWarps * d);
+    float* zs = zsf;
+    float* ts = zsf + kPassWarps * d;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, seg = lane >> 3, sl = lane & 7;
     const float gamma = (float)state[S_GAMMA];
-    for (int j = threadIdx.x; j < kPassWarps * d; j += blockDim.x) zs[j] = 0.0;
+    for (int j = threadIdx.x; j < kPassWarps * d; j += blockDim.x) zs[j] = 0.f;
     for (int j = threadIdx.x; j < d; j += blockDim.x) ts[j] = t[j];
     __syncthreads();
-    double* zw = zs + w * d;
+    float* zw = zs + w * d;
     double nrm = 0.0;
     const int64_t wid = (int64_t)blockIdx.x * kPassWarps + w, nw = (int64_t)gridDim.x * kPassWarps;
+    // one-deep pipeline: the bounds and u of the next four rows load while this four runs
+    int64_t rn = wid * 4 + seg;
+    int64_t np0 = rn < n ? row_ptr[rn] : 0, np1 = rn < n ? row_ptr[rn + 1] : 0;
+    float nu = (rn < n && sl == 0) ? u[rn] : 0.f;
     for (int64_t r0 = wid * 4; r0 < n; r0 += nw * 4) {
         const int64_t r = r0 + seg;
         const bool rok = r < n;
-        const int64_t p0 = rok ? row_ptr[r] : 0, p1 = rok ? row_ptr[r + 1] : 0;
+        const int64_t p0 = np0, p1 = np1;
+        const float ur = nu;
         const int len = (int)(p1 - p0);
         const bool mine = rok && len <= 8;
         int c = -1;
@@ -225,20 +232,24 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_csr_short(const int64_
         if (mine && sl < len) {
             c = col[p0 + sl];
             a = val[p0 + sl];
-            if ((unsigned)c >= (unsigned)d) { c = -1; a = 0.f; }
         }
+        rn = r + nw * 4;
+        np0 = rn < n ? row_ptr[rn] : 0;
+        np1 = rn < n ? row_ptr[rn + 1] : 0;
+        nu = (rn < n && sl == 0) ? u[rn] : 0.f;
+        if ((unsigned)c >= (unsigned)d) { c = -1; a = 0.f; }
         float dot = c >= 0 ? a * ts[c] : 0.f;
         dot += __shfl_xor_sync(0xffffffffu, dot, 4);
         dot += __shfl_xor_sync(0xffffffffu, dot, 2);
         dot += __shfl_xor_sync(0xffffffffu, dot, 1);
         float x = 0.f;
         if (mine && sl == 0) {
-            x = fmaf(gamma, u[r], dot);
+            x = fmaf(gamma, ur, dot);
             u[r] = x;
             nrm = fma((double)x, (double)x, nrm);
         }
         x = __shfl_sync(0xffffffffu, x, seg * 8);
-        if (c >= 0) atomicAdd(zw + c, (double)a * (double)x);
+        if (c >= 0) atomicAdd(zw + c, a * x);
     }
     nrm = warp_sum(nrm);
     if (lane == 0) ns[w] = nrm;
@@ -252,16 +263,17 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_csr_long(const int64_t
                                                                    const double* __restrict__ state,
                                                                    float* __restrict__ u, double* __restrict__ zpart,
                                                                    double* __restrict__ npart) {
-    extern __shared__ double zs[];
+    extern __shared__ float zsf[];
     __shared__ double ns[kPassWarps];
     if (state[S_DONE] != 0.0) return;
-    float* ts = reinterpret_cast<float*>(zs + kPassWarps * d);
+    float* zs = zsf;
+    float* ts = zsf + kPassWarps * d;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float gamma = (float)state[S_GAMMA];
-    for (int j = threadIdx.x; j < kPassWarps * d; j += blockDim.x) zs[j] = 0.0;
+    for (int j = threadIdx.x; j < kPassWarps * d; j += blockDim.x) zs[j] = 0.f;
     for (int j = threadIdx.x; j < d; j += blockDim.x) ts[j] = t[j];
     __syncthreads();
-    double* zw = zs + w * d;
+    float* zw = zs + w * d;
     double nrm = 0.0;
     const int64_t wid = (int64_t)blockIdx.x * kPassWarps + w, nw = (int64_t)gridDim.x * kPassWarps;
     for (int64_t r0 = wid * 32; r0 < n; r0 += nw * 32) {
@@ -288,7 +300,7 @@ __global__ void __launch_bounds__(32 * kPassWarps) k_lsqr_csr_long(const int64_t
             x = __shfl_sync(0xffffffffu, x, 0);
             for (int64_t e = p0 + lane; e < p1; e += 32) {
                 const int c = col[e];
-                if ((unsigned)c < (unsigned)d) atomicAdd(zw + c, (double)val[e] * (double)x);
+                if ((unsigned)c < (unsigned)d) atomicAdd(zw + c, val[e] * x);
             }
         }
     }
@@ -449,7 +461,9 @@ size_t lsqr_scratch_doubles(int64_t d, int parts) {
     return (size_t)(S_COUNT + 8 + 5 * d + d / 2 + 2 + (size_t)parts * (d + 1) + (size_t)d * d);
 }
 
-int lsqr_parts(int num_sms) { return num_sms * 2; }
+// Partial rows of z: the CSR pass uses 8 per SM (6 for the short rows: many warps hide the chain of
+// dependent loads of a row), the dense pass 3 per SM; the workspace holds the larger count.
+int lsqr_parts(int num_sms) { return num_sms * 8; }
 
 int lsqr_state_doubles() { return S_COUNT; }
 
@@ -500,10 +514,11 @@ cudaError_t launch_lsqr(const float* A, int64_t lda, const int64_t* row_ptr, con
     const bool vec = A && (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0);
     const size_t smem = sizeof(double) * (size_t)kPassWarps * d;
     const bool csr = row_ptr != nullptr;
-    const int parts_s = parts / 2, parts_l = parts - parts_s;
-    const size_t smem_csr = sizeof(double) * (size_t)kPassWarps * d + sizeof(float) * (size_t)d;
+    const int parts_s = parts * 3 / 4, parts_l = parts - parts_s;
+    if (!csr) parts = parts * 3 / 8;                    // dense: 3 CTAs a SM
+    const size_t smem_csr = sizeof(float) * (size_t)(kPassWarps + 1) * d;
     if (csr) {
-        const int mx = (int)(sizeof(double) * kPassWarps * 1024 + sizeof(float) * 1024);
+        const int mx = (int)(sizeof(float) * (kPassWarps + 1) * 1024);
         if ((e = cudaFuncSetAttribute(k_lsqr_csr_short, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
             return e;
         if ((e = cudaFuncSetAttribute(k_lsqr_csr_long, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
