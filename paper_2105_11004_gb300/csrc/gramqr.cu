@@ -11,12 +11,13 @@
 //   k_gram_dot2 / k_gram_reduce: G = A~^T A~ with FP64-grade sums from FP32
 //     arithmetic (FP64 runs at 1/64 of the FP32 rate on this GPU): each product
 //     of two FP32 entries is split exactly into p + e (p = a b rounded,
-//     e = fma(a, b, -p)); the products of 32 rows are summed error-free
+//     e = fma(a, b, -p)); the products of 64 rows are summed error-free
 //     (TwoSum, s + q = s_old + p exactly), their rounding errors q and e
-//     gathered in an FP32 correction c, and every 32 rows s + c is added into
+//     gathered in an FP32 correction c, and every 64 rows s + c is added into
 //     FP64 (the compensated dot product of Ogita, Rump and Oishi, with an FP64
-//     outer sum). Error: about 64 u_32^2 sum |a b| per block (2e-13) plus the
-//     FP64 sum over blocks, below the m u_64 sum |a b| of an FP64 FMA chain.
+//     outer sum). Error: about 128 u_32^2 sum |a b| per block (4e-13) plus the
+//     FP64 sum over blocks, comparable to the m u_64 sum |a b| of an FP64 FMA
+//     chain at the sketch sizes (m = 1,024 to 4,096).
 //     Upper 32 x 32 tiles split over rows, split partials reduced in a fixed
 //     order and mirrored;
 //   k_pchol_grid: one cooperative grid (one CTA per SM); CTA c owns the
@@ -53,7 +54,7 @@ __device__ inline void tile_coords(int t, int nt, int& bi, int& bj) {
     bj = bi + t;
 }
 
-constexpr int kDot2Rows = 32;          // rows per error-free block before the FP64 add
+constexpr int kDot2Rows = 64;          // rows per error-free block before the FP64 add
 
 __global__ void __launch_bounds__(256) k_gram_dot2(const float* __restrict__ At, int64_t lda, int m, int d,
                                                    int rows_per_split, double* __restrict__ Gp) {
