@@ -46,7 +46,7 @@ def _sketch_entries(col_of, n, s, m, seed, js, cs):
                 g = Grows[ji]
             else:
                 idx = np.uint64(j) * np.uint64(s) + np.arange(s, dtype=np.uint64)
-                g = orng.gaussian(seed, orng.STREAM_G, idx) / np.sqrt(m)
+                g = orng.sketch_gaussian(seed, idx, m)
             out[ji, ci] = g @ Bc
     return out
 
@@ -59,7 +59,7 @@ def _abs_entries(col_of, n, s, m, seed, js, cs):
         np.add.at(Bc, b, np.abs(col_of(c)))
         for ji, j in enumerate(js):
             idx = np.uint64(j) * np.uint64(s) + np.arange(s, dtype=np.uint64)
-            out[ji, ci] = np.abs(orng.gaussian(seed, orng.STREAM_G, idx) / np.sqrt(m)) @ Bc
+            out[ji, ci] = np.abs(orng.sketch_gaussian(seed, idx, m)) @ Bc
     return out
 
 

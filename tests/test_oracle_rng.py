@@ -91,3 +91,41 @@ def test_gaussian_sketch_and_omega_scaling():
     assert abs(Om.var() * 40 - 1) < 0.1
     # Omega rows depend on the pivot position only, not on r
     assert np.array_equal(rng.omega(20, 40, 1), Om[:20])
+
+
+def test_bf16_round_matches_bitwise_definition():
+    """bf16_round against a per-value brute force: the nearest BF16 value of the FP32 rounding,
+    ties to the even significand (checked on random values, ties and powers of two)."""
+    rs = np.random.default_rng(5)
+    x = np.concatenate([rs.standard_normal(2000), rs.standard_normal(200) * 1e-30, [1.0, -2.0, 0.0, 3.0, 1e30]])
+    ties = np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8)])   # halfway: to even
+    x = np.concatenate([x, ties])
+    got = rng.bf16_round(x)
+    for xi, gi in zip(x, got):
+        f = np.float32(xi)
+        if f == 0:
+            assert gi == 0
+            continue
+        e = np.floor(np.log2(abs(float(f))))
+        ulp = 2.0 ** (e - 7)                      # 8-bit significand
+        lo = np.floor(float(f) / ulp) * ulp
+        hi = lo + ulp
+        d_lo, d_hi = float(f) - lo, hi - float(f)
+        if d_lo < d_hi:
+            want = lo
+        elif d_hi < d_lo:
+            want = hi
+        else:
+            want = lo if int(round(lo / ulp)) % 2 == 0 else hi
+        assert gi == want, (xi, gi, want)
+    assert rng.bf16_round(np.array(ties)).tolist() == [1.0, 1.0 + 4 * 2.0 ** -8, -1.0]
+
+
+def test_sketch_gaussian_entries_are_bf16_draws():
+    idx = np.arange(50_000, dtype=np.uint64)
+    g = rng.gaussian(4, rng.STREAM_G, idx)
+    z = rng.sketch_gaussian(4, idx, 64) * 8.0
+    assert np.all(np.abs(z - g) <= 2.0 ** -8 * np.abs(g))               # within half a BF16 ulp
+    bits = z.astype(np.float32).view(np.uint32)
+    assert np.all(bits & 0xFFFF == 0) and np.all(z.astype(np.float32) == z)
+    assert abs(z.mean()) < 0.02 and abs(z.var() - 1) < 0.02
