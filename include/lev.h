@@ -38,8 +38,9 @@
  *    (hi32(x) * s) >> 32, sign = +1 if bit 0 of x is 0 else -1;
  *  - N(0,1) number c of stream t: Box-Muller, cosine branch, with
  *    u1 = ((splitmix64(key_t, 2c) >> 11) + 1) 2^-53, u2 = (splitmix64(key_t, 2c+1) >> 11) 2^-53;
- *  - G[j, b] = N_{j*s + b} / sqrt(m) (Sec. 2.3.1 scaling); Omega[p, q] = N_{p*k + q} / sqrt(k),
- *    p the pivot position (0 <= p < r), q < k.
+ *  - G[j, b] = Z_{j*s + b} / sqrt(m) (Sec. 2.3.1 scaling) with Z_c the BF16 rounding (to nearest
+ *    even) of the FP32 rounding of N_c, so that G is exact in the tensor cores' 16-bit operand
+ *    type; Omega[p, q] = N_{p*k + q} / sqrt(k), p the pivot position (0 <= p < r), q < k.
  */
 #ifndef LEV_H
 #define LEV_H
@@ -62,7 +63,8 @@ extern "C" {
 #define LEV_FP32    0   /* FP32 SIMT FMA */
 #define LEV_TF32    1   /* tcgen05 kind::tf32, FP32 accumulate */
 #define LEV_BF16    2   /* tcgen05 kind::f16 with BF16 operands, FP32 accumulate */
-#define LEV_BF16X3  3   /* split hi+lo BF16: hi*hi + lo*hi + hi*lo, FP32 accumulate */
+#define LEV_BF16X3  3   /* split hi+lo BF16 of FP32 operands, FP32 accumulate: hi*hi + lo*hi + hi*lo in
+                           the final pass; Z*B_hi + Z*B_lo in the Gaussian stage (G exact in BF16) */
 
 /* Flags (lev_params.flags). */
 #define LEV_OMEGA_IDENTITY  1u  /* Omega = I_r, k = r (the Pi_2-free mode of Sec. 6.4) */

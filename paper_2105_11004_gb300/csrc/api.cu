@@ -202,11 +202,11 @@ double tau_of(const lev_params* p) { return p->tau > 0 ? p->tau : 1e-5; }
 // s rounded up to 64 (TMA rows of whole 128-byte lines). Kind 3: FP32 rounded
 // to TF32, same padded leading dimension.
 int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
-             const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo) {
+             const float** g32, const __nv_bfloat16** ghi) {
     GCache& g = h->g;
     const int64_t ld = kind == 0 ? s : (s + 63) / 64 * 64;
     const size_t elems = (size_t)m * (size_t)ld;
-    const size_t bytes = kind == 2 ? elems * 2 * sizeof(__nv_bfloat16) : elems * sizeof(float);
+    const size_t bytes = kind == 2 ? elems * sizeof(__nv_bfloat16) : elems * sizeof(float);
     if (!(g.ptr && g.seed == seed && g.m == m && g.s == s && g.kind == kind)) {
         if (g.bytes < bytes) {
             if (g.ptr) cudaFree(g.ptr);
@@ -222,10 +222,9 @@ int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaS
         }
         cudaError_t e;
         if (kind == 2)
-            e = lev::launch_gen_gaussian(m, s, ld, seed, nullptr, false, (__nv_bfloat16*)g.ptr,
-                                         (__nv_bfloat16*)g.ptr + elems, st);
+            e = lev::launch_gen_gaussian(m, s, ld, seed, nullptr, false, (__nv_bfloat16*)g.ptr, st);
         else
-            e = lev::launch_gen_gaussian(m, s, ld, seed, (float*)g.ptr, kind == 3, nullptr, nullptr, st);
+            e = lev::launch_gen_gaussian(m, s, ld, seed, (float*)g.ptr, kind == 3, nullptr, st);
         if (e != cudaSuccess) return fail(LEV_ECUDA, "G generation: %s", cudaGetErrorString(e));
         g.seed = seed;
         g.m = m;
@@ -234,7 +233,6 @@ int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaS
     }
     if (g32) *g32 = kind != 2 ? (const float*)g.ptr : nullptr;
     if (ghi) *ghi = kind == 2 ? (const __nv_bfloat16*)g.ptr : nullptr;
-    if (glo) *glo = kind == 2 ? (const __nv_bfloat16*)g.ptr + elems : nullptr;
     return LEV_OK;
 }
 
@@ -243,7 +241,7 @@ int gaussian_stage(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t 
                    int32_t prec, float* Atilde, cudaStream_t st) {
     if (prec == LEV_FP32) {
         const float* g32 = nullptr;
-        LEV_TRY(ensure_g(h, m, s, seed, 0, st, &g32, nullptr, nullptr));
+        LEV_TRY(ensure_g(h, m, s, seed, 0, st, &g32, nullptr));
         const int splits = lev::gaussian_stage_splits(m, d, s);
         LEV_TRY(ensure(h->partial, sizeof(float) * (size_t)splits * m * d));
         LEV_CUDA(lev::launch_gaussian_stage_fp32(g32, B, m, s, d, (float*)h->partial.ptr, splits, Atilde, st));
@@ -497,8 +495,8 @@ int handle_scratch(lev_handle* h, int which, size_t bytes, void** out) {
 int handle_num_sms(lev_handle* h) { return h->num_sms; }
 int32_t* handle_status(lev_handle* h) { return h->status; }
 int handle_gaussian(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
-                    const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo) {
-    return ensure_g(h, m, s, seed, kind, st, g32, ghi, glo);
+                    const float** g32, const __nv_bfloat16** ghi) {
+    return ensure_g(h, m, s, seed, kind, st, g32, ghi);
 }
 int handle_fail(int code, const char* msg) { return fail(code, "%s", msg); }
 }  // namespace lev
@@ -1064,19 +1062,20 @@ int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
     cudaStream_t st = (cudaStream_t)stream;
     const bool identity = (p->flags & LEV_SKETCH_IDENTITY) != 0;
     const float* g32 = nullptr;
-    const __nv_bfloat16 *ghi = nullptr, *glo = nullptr;
+    const __nv_bfloat16* ghi = nullptr;
     int64_t ldg = z.s;
     if (!identity) {
         // the G image the forward's sketch used (cached in the handle)
         const int kind = p->sketch_prec == LEV_FP32 ? 0 : (p->sketch_prec == LEV_TF32 ? 3 : 2);
-        LEV_TRY(ensure_g(h, z.m, z.s, p->seed, kind, st, &g32, &ghi, &glo));
+        LEV_TRY(ensure_g(h, z.m, z.s, p->seed, kind, st, &g32, &ghi));
         if (kind != 0) ldg = (z.s + 63) / 64 * 64;
-        if (p->sketch_prec == LEV_BF16) glo = nullptr;      // that form multiplies by the BF16 hi part only
     }
+    // the BF16 (kind 2) and TF32 (kind 3) images hold the unscaled Z; the FP32 image is Z / sqrt(m)
+    const float g_scale = (identity || p->sketch_prec == LEV_FP32) ? 1.f : (float)(1.0 / std::sqrt((double)z.m));
     const int chunks = lev::backward_chunks(n, d, z.k);
     LEV_TRY(ensure(h->bwd, lev::backward_scratch_bytes(n, d, z.k, z.s, z.m, chunks)));
     LEV_CUDA(lev::launch_backward_dense(A, lda, n, d, z.s, z.m, z.k, p->seed, Atilde, perm, d_rank, R, Mfull, w, g32,
-                                        ghi, glo, ldg, identity, h->bwd.ptr, chunks, gradA, st));
+                                        ghi, ldg, g_scale, identity, h->bwd.ptr, chunks, gradA, st));
     return LEV_OK;
 }
 

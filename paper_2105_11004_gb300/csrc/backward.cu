@@ -267,10 +267,11 @@ __global__ void k_xbar(const float* __restrict__ At, const double* __restrict__ 
     }
 }
 
-// T (s x d) = G^T Xbar_full, G (m x s, leading dimension ldg) as FP32 or BF16 hi + lo.
-template <bool SPLIT>
+// T (s x d) = G^T Xbar_full, G = g_scale * (the image: FP32, or BF16 when B16), m x s with leading
+// dimension ldg.
+template <bool B16>
 __global__ void __launch_bounds__(256) k_gt_x(const float* __restrict__ G32, const __nv_bfloat16* __restrict__ Ghi,
-                                              const __nv_bfloat16* __restrict__ Glo, int64_t ldg, int m, int64_t s,
+                                              int64_t ldg, int m, int64_t s, float g_scale,
                                               const float* __restrict__ Xf, int d, float* __restrict__ T) {
     __shared__ float Gs[16][64];
     __shared__ float Xs[16][64];
@@ -290,13 +291,7 @@ __global__ void __launch_bounds__(256) k_gt_x(const float* __restrict__ G32, con
             const int j = j0 + jj;
             const int64_t b = b0 + u;
             float g = 0.f;
-            if (j < m && b < s) {
-                if (SPLIT)
-                    g = __bfloat162float(Ghi[(int64_t)j * ldg + b]) +
-                        (Glo ? __bfloat162float(Glo[(int64_t)j * ldg + b]) : 0.f);
-                else
-                    g = G32[(int64_t)j * ldg + b];
-            }
+            if (j < m && b < s) g = B16 ? __bfloat162float(Ghi[(int64_t)j * ldg + b]) : G32[(int64_t)j * ldg + b];
             Gs[jj][u] = g;
             Xs[jj][u] = (j < m && c0 + u < d) ? Xf[(int64_t)j * d + c0 + u] : 0.f;
         }
@@ -320,7 +315,7 @@ __global__ void __launch_bounds__(256) k_gt_x(const float* __restrict__ G32, con
         for (int j = 0; j < 4; ++j) {
             const int64_t b = b0 + tb + i;
             const int c = c0 + tc + j;
-            if (b < s && c < d) T[b * d + c] = acc[i][j];
+            if (b < s && c < d) T[b * d + c] = acc[i][j] * g_scale;
         }
 }
 
@@ -447,7 +442,7 @@ int backward_chunks(int64_t n, int64_t d, int64_t /*k*/) {
 cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_t d, int64_t s, int64_t m, int64_t k,
                                   uint64_t seed, const float* Atilde, const int32_t* perm, const int64_t* d_rank,
                                   const double* R, const float* Mfull, const float* w, const float* G32,
-                                  const __nv_bfloat16* Ghi, const __nv_bfloat16* Glo, int64_t ldg, bool identity,
+                                  const __nv_bfloat16* Ghi, int64_t ldg, float g_scale, bool identity,
                                   void* scratch, int chunks, float* gradA, cudaStream_t st) {
     char* p = static_cast<char*>(scratch);
     auto take = [&](size_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return r; };
@@ -488,9 +483,9 @@ cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_
     if (identity)
         T = Xf;
     else if (Ghi)
-        k_gt_x<true><<<gt, 256, 0, st>>>(nullptr, Ghi, Glo, ldg, (int)m, s, Xf, (int)d, T);
+        k_gt_x<true><<<gt, 256, 0, st>>>(nullptr, Ghi, ldg, (int)m, s, g_scale, Xf, (int)d, T);
     else
-        k_gt_x<false><<<gt, 256, 0, st>>>(G32, nullptr, nullptr, ldg, (int)m, s, Xf, (int)d, T);
+        k_gt_x<false><<<gt, 256, 0, st>>>(G32, nullptr, ldg, (int)m, s, g_scale, Xf, (int)d, T);
     // pass 2
     const size_t sm2 = sizeof(float) * ((size_t)P2_R * P2_AS + (size_t)P2_J * P2_C);
     if ((e = cudaFuncSetAttribute(k_bwd_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)

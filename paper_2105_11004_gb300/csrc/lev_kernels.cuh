@@ -24,10 +24,11 @@ cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, c
                                    int64_t d, int64_t s, const int* off, const uint32_t* perm,
                                    float* B, cudaStream_t st);
 
-// G (m x s) with leading dimension ld >= s (columns s..ld zero): FP32 copy
-// (optionally TF32-rounded) and/or BF16 hi/lo copies (any pointer may be null).
-cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, bool tf32_round,
-                                __nv_bfloat16* ghi, __nv_bfloat16* glo, cudaStream_t st);
+// G = Z / sqrt(m) (m x s, Z the BF16 rounding of the counter draws) with leading dimension ld >= s
+// (columns s..ld zero): an FP32 image, fl32(Z / sqrt(m)) or the unscaled Z, and/or the BF16 image
+// of Z (either pointer may be null).
+cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, bool unscaled,
+                                __nv_bfloat16* ghi, cudaStream_t st);
 
 // Atilde (m x d) = G (m x s) B (s x d), FP32 SIMT, split-K with a fixed-order
 // reduction. partial: splits * m * d floats of scratch; returns splits used.
@@ -140,7 +141,7 @@ size_t backward_scratch_bytes(int64_t n, int64_t d, int64_t k, int64_t s, int64_
 cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_t d, int64_t s, int64_t m, int64_t k,
                                   uint64_t seed, const float* Atilde, const int32_t* perm, const int64_t* d_rank,
                                   const double* R, const float* Mfull, const float* w, const float* G32,
-                                  const __nv_bfloat16* Ghi, const __nv_bfloat16* Glo, int64_t ldg, bool identity,
+                                  const __nv_bfloat16* Ghi, int64_t ldg, float g_scale, bool identity,
                                   void* scratch, int chunks, float* gradA, cudaStream_t st);
 
 // ---- final.cu: fused final pass (SIMT) ----

@@ -15,7 +15,7 @@ int handle_scratch(lev_handle* h, int which, size_t bytes, void** out);
 int handle_num_sms(lev_handle* h);
 int32_t* handle_status(lev_handle* h);
 int handle_gaussian(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
-                    const float** g32, const __nv_bfloat16** ghi, const __nv_bfloat16** glo);
+                    const float** g32, const __nv_bfloat16** ghi);
 int handle_fail(int code, const char* msg);
 
 // A~ (m x d) = G B with prec in {LEV_TF32, LEV_BF16, LEV_BF16X3}.

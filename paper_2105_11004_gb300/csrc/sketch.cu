@@ -267,28 +267,22 @@ __global__ void __launch_bounds__(128) k_countsketch_csr(
 
 // G (m x s) by counter into images with leading dimension ld (columns s..ld are 0):
 // an FP32 copy (optionally rounded to TF32) and/or BF16 hi and lo copies.
+// Entries of G by counter: Z = the BF16 rounding (to nearest even) of the FP32 rounding of the
+// Box-Muller draw, G = Z / sqrt(m). g32: FP32 image, either fl32(Z / sqrt(m)) or (unscaled) Z
+// itself, which TF32 holds exactly; ghi: Z in BF16 (exact). The unscaled images leave the
+// 1 / sqrt(m) to the Gaussian stage's reduction.
 __global__ void k_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t key, double scale, float* g32,
-                               int tf32_round, __nv_bfloat16* ghi, __nv_bfloat16* glo) {
+                               int unscaled, __nv_bfloat16* ghi) {
     const int64_t total = m * ld;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (; i < total; i += stride) {
         const int64_t j = i / ld, b = i % ld;
-        const double g = b < s ? box_muller(key, (uint64_t)(j * s + b)) * scale : 0.0;   // entry j*s + b of G
-        if (g32) {
-            float f = (float)g;
-            if (tf32_round) {
-                uint32_t r;
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
-                f = __uint_as_float(r);
-            }
-            g32[i] = f;
-        }
-        if (ghi) {
-            const __nv_bfloat16 h = __double2bfloat16(g);
-            ghi[i] = h;
-            if (glo) glo[i] = __double2bfloat16(g - (double)__bfloat162float(h));
-        }
+        const double g = b < s ? box_muller(key, (uint64_t)(j * s + b)) : 0.0;   // draw j*s + b
+        const __nv_bfloat16 z = __float2bfloat16_rn((float)g);
+        const float zf = __bfloat162float(z);
+        if (g32) g32[i] = unscaled ? zf : (float)((double)zf * scale);
+        if (ghi) ghi[i] = z;
     }
 }
 
@@ -456,11 +450,11 @@ cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, bool tf32_round,
-                                __nv_bfloat16* ghi, __nv_bfloat16* glo, cudaStream_t st) {
+cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, bool unscaled,
+                                __nv_bfloat16* ghi, cudaStream_t st) {
     const double scale = 1.0 / sqrt((double)m);
     k_gen_gaussian<<<grid_for(m * ld, 256, 152 * 32), 256, 0, st>>>(
-        m, s, ld, stream_key(seed, kStreamG), scale, g32, tf32_round ? 1 : 0, ghi, glo);
+        m, s, ld, stream_key(seed, kStreamG), scale, g32, unscaled ? 1 : 0, ghi);
     return cudaGetLastError();
 }
 

@@ -9,8 +9,10 @@
 // ring of shared-memory stages:
 //   warp 0: TMA producer (one thread); warp 1: TMEM allocation and the MMA
 //   issuer (one thread); warps 2..5: epilogue (tcgen05.ld, partial stores).
-// Forms: BF16 (one MMA per K step), BF16X3 (hi*hi + lo*hi + hi*lo with G and B
-// split into BF16 hi + lo), TF32 (operands rounded to TF32 once).
+// G = Z / sqrt(m) with Z exact in BF16 (the BF16 rounding of the counter draws), so G is never
+// split: the MMAs take Z and the reduction applies 1 / sqrt(m). Forms: BF16 (Z times B rounded to
+// BF16, one MMA per K step), BF16X3 (Z B_hi + Z B_lo, B split into BF16 hi + lo: two MMAs), TF32
+// (Z, exact in TF32, times B rounded to TF32).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -75,7 +77,6 @@ __device__ __forceinline__ bool gwait(uint32_t bar, uint32_t parity, GCtl* ctl, 
 // Grid: x = m tile * n_tiles + n tile, y = K slice. Partial P[z][c][i] (c < d, i < m).
 template <int F>
 __global__ void __launch_bounds__(192, 1) k_gauss_tc(const __grid_constant__ CUtensorMap tmG,
-                                                     const __grid_constant__ CUtensorMap tmGlo,
                                                      const __grid_constant__ CUtensorMap tmB,
                                                      const __grid_constant__ CUtensorMap tmBlo, int m, int d, int nt,
                                                      int n_tiles, int kb_per_slice, int kb_total,
@@ -84,8 +85,7 @@ __global__ void __launch_bounds__(192, 1) k_gauss_tc(const __grid_constant__ CUt
     constexpr int STAGES = T::kStages;
     const int A_BYTES = kRowsM * 128;
     const int B_BYTES = nt * 128;
-    const int PART = A_BYTES + B_BYTES;                    // one (hi or lo) set of operands
-    const int STAGE_BYTES = PART * (T::kSplit ? 2 : 1);
+    const int STAGE_BYTES = A_BYTES + B_BYTES * (T::kSplit ? 2 : 1);   // Z tile, B_hi (and B_lo) tile
     const uint32_t idesc = make_idesc(T::kTf32, kRowsM, nt);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -129,10 +129,7 @@ __global__ void __launch_bounds__(192, 1) k_gauss_tc(const __grid_constant__ CUt
                 const int x = (kb0 + i) * T::kKbe;
                 tma_load_2d(sb, &tmG, x, mt * kRowsM, bar);
                 tma_load_2d(sb + A_BYTES, &tmB, x, ntile * nt, bar);
-                if constexpr (T::kSplit) {
-                    tma_load_2d(sb + PART, &tmGlo, x, mt * kRowsM, bar);
-                    tma_load_2d(sb + PART + A_BYTES, &tmBlo, x, ntile * nt, bar);
-                }
+                if constexpr (T::kSplit) tma_load_2d(sb + A_BYTES + B_BYTES, &tmBlo, x, ntile * nt, bar);
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
         }
@@ -151,10 +148,8 @@ __global__ void __launch_bounds__(192, 1) k_gauss_tc(const __grid_constant__ CUt
                     const uint32_t ko = (uint32_t)ks * 32u;
                     const uint32_t acc = (i | ks) != 0 ? 1u : 0u;
                     tc_mma<T::kTf32>(tmem, sw128_desc(sb + ko), sw128_desc(sb + A_BYTES + ko), idesc, acc);
-                    if constexpr (T::kSplit) {
-                        tc_mma<false>(tmem, sw128_desc(sb + PART + ko), sw128_desc(sb + A_BYTES + ko), idesc, 1u);
-                        tc_mma<false>(tmem, sw128_desc(sb + ko), sw128_desc(sb + PART + A_BYTES + ko), idesc, 1u);
-                    }
+                    if constexpr (T::kSplit)
+                        tc_mma<false>(tmem, sw128_desc(sb + ko), sw128_desc(sb + A_BYTES + B_BYTES + ko), idesc, 1u);
                 }
                 tc_commit(smem_u32(&ctl->empty[stage]));
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -194,13 +189,15 @@ __global__ void __launch_bounds__(192, 1) k_gauss_tc(const __grid_constant__ CUt
     }
 }
 
-__global__ void k_gauss_reduce(const float* __restrict__ P, int splits, int m, int d, float* __restrict__ At) {
+// A~ = scale * (sum of the K-slice partials, in slice order); scale = 1 / sqrt(m) (G = Z / sqrt(m)).
+__global__ void k_gauss_reduce(const float* __restrict__ P, int splits, int m, int d, float scale,
+                               float* __restrict__ At) {
     const int64_t total = (int64_t)m * d;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / m), i = (int)(e % m);        // i fastest: coalesced partial reads
         float acc = 0.f;
         for (int z = 0; z < splits; ++z) acc += P[(int64_t)z * total + e];
-        At[(int64_t)i * d + c] = acc;
+        At[(int64_t)i * d + c] = acc * scale;
     }
 }
 
@@ -247,10 +244,10 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
                  cudaStream_t st) {
     using T = GTraits<F>;
     const int64_t ld = (s + 63) / 64 * 64;                // padded K: 16-byte row strides, whole 128-byte rows
-    // G image (cached in the handle): kind 2 = BF16 hi + lo (ld), kind 3 = TF32-rounded FP32 (ld)
+    // G image (cached in the handle): kind 2 = Z in BF16 (ld), kind 3 = Z in FP32 (ld; exact in TF32)
     const float* g32 = nullptr;
-    const __nv_bfloat16 *ghi = nullptr, *glo = nullptr;
-    int rc = handle_gaussian(h, m, s, seed, T::kTf32 ? 3 : 2, st, &g32, &ghi, &glo);
+    const __nv_bfloat16* ghi = nullptr;
+    int rc = handle_gaussian(h, m, s, seed, T::kTf32 ? 3 : 2, st, &g32, &ghi);
     if (rc != LEV_OK) return rc;
     // B^T in the operand type
     const size_t bt_elems = (size_t)d * ld;
@@ -274,26 +271,24 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
     void* part = nullptr;
     rc = handle_scratch(h, 1, sizeof(float) * (size_t)splits * m * d, &part);
     if (rc != LEV_OK) return rc;
-    CUtensorMap mG, mGlo, mB, mBlo;
+    CUtensorMap mG, mB, mBlo;
     const void* gimg = T::kTf32 ? static_cast<const void*>(g32) : static_cast<const void*>(ghi);
     bool ok = make_map(&mG, gimg, T::kTf32, m, ld, ld, T::kKbe, kRowsM) &&
               make_map(&mB, bt, T::kTf32, d, ld, ld, T::kKbe, nt);
     if (T::kSplit)
-        ok = ok && make_map(&mGlo, glo, false, m, ld, ld, T::kKbe, kRowsM) &&
-             make_map(&mBlo, bt_lo, false, d, ld, ld, T::kKbe, nt);
-    else {
-        mGlo = mG;
+        ok = ok && make_map(&mBlo, bt_lo, false, d, ld, ld, T::kKbe, nt);
+    else
         mBlo = mB;
-    }
     if (!ok) return handle_fail(LEV_ECUDA, "cuTensorMapEncodeTiled failed for the Gaussian stage");
-    const int stage_bytes = (kRowsM * 128 + nt * 128) * (T::kSplit ? 2 : 1);
+    const int stage_bytes = kRowsM * 128 + nt * 128 * (T::kSplit ? 2 : 1);
     const size_t smem = 1024 + (size_t)T::kStages * stage_bytes + sizeof(GCtl) + 64;
     cudaError_t e = cudaFuncSetAttribute(k_gauss_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     dim3 grid((unsigned)(m_tiles * n_tiles), (unsigned)splits);
-    k_gauss_tc<F><<<grid, 192, smem, st>>>(mG, mGlo, mB, mBlo, (int)m, (int)d, nt, n_tiles, kb_per_slice, kb_total,
+    k_gauss_tc<F><<<grid, 192, smem, st>>>(mG, mB, mBlo, (int)m, (int)d, nt, n_tiles, kb_per_slice, kb_total,
                                            static_cast<float*>(part), handle_status(h));
-    k_gauss_reduce<<<152 * 4, 256, 0, st>>>(static_cast<const float*>(part), splits, (int)m, (int)d, Atilde);
+    k_gauss_reduce<<<152 * 4, 256, 0, st>>>(static_cast<const float*>(part), splits, (int)m, (int)d,
+                                            (float)(1.0 / std::sqrt((double)m)), Atilde);
     e = cudaGetLastError();
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     return LEV_OK;
