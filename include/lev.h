@@ -288,12 +288,13 @@ int lev_exact_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t
 
 /* Alg. 7 (LS-HRN-exact) on CSR A (row_ptr: n + 1 int64; col: nnz int32; val: nnz FP32; all
  * device; the CSR conventions of lev_sketch_csr): K and k from the pivoted QR of the CountSketch
- * + Gaussian sketch, then B = A_K^T A_K as the sum of the rows' outer products (Lemma 3: FP64
- * products of the FP32 entries, exact, summed by FP64 atomics, so the last bits of B and of
+ * + Gaussian sketch, then B = A_K^T A_K as the sum of the rows' outer products (Lemma 3: products
+ * of the FP32 entries exact; rows of at most max(32, d/5) entries summed by FP64 atomics, longer
+ * rows densified and summed by the compensated dense Gram kernel, so the last bits of B and of
  * theta may differ between runs), its Cholesky factor B = R^T R with the pivots forced, and
  * theta_i = ||A_{i,K} R^{-1}||^2 by the CSR final pass (LEV_FP32 only); d <= 1024.
  * theta: device n. perm: device d int32 or NULL. rank: host, may be NULL; the call synchronises
- * `stream` twice. Errors: as lev_estimate_csr; LEV_ERANK0 sets theta to 0. */
+ * `stream` three times. Errors: as lev_estimate_csr; LEV_ERANK0 sets theta to 0. */
 int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
                   int64_t n, int64_t d, int64_t nnz, const lev_params* p, float* theta,
                   int64_t* rank, int32_t* perm, void* stream);

@@ -85,6 +85,8 @@ struct lev_handle {
     int64_t last_swaps = 0;
     int64_t rank_ws_d = 0;   // d of the last carve of rank_ws
     Buf csr_p;     // CSR final pass, second form of Lemma 1: P = Mfull Mfull^T (FP64), Gram partials, Mfull^T
+    Buf csr_heavy; // Alg. 7 on CSR: count and indices of the long rows
+    Buf csr_dense; // Alg. 7 on CSR: the long rows densified, their Gram partials and Gram matrix
     Buf lsqr_u;    // LSQR: the unnormalised left vector u (n FP32)
     Buf lsqr_ws;   // LSQR: state, short vectors, pass partials, N^T
     double* host_lsqr = nullptr;   // pinned LSQR state read back by the host
@@ -553,7 +555,8 @@ int lev_destroy(lev_handle* h) {
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
                   &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
                   &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->tc_pad,
-                  &h->exact_gp, &h->srht_c, &h->rank_ws, &h->lsqr_u, &h->lsqr_ws, &h->csr_p};
+                  &h->exact_gp, &h->srht_c, &h->rank_ws, &h->lsqr_u, &h->lsqr_ws, &h->csr_p, &h->csr_heavy,
+                  &h->csr_dense};
     for (Buf* b : all) release(*b);
     for (int i = 0; i < 2; ++i) {
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
@@ -939,10 +942,31 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
         return rc;
     }
     LEV_TRY(rc);
-    // step 4: B = A_K^T A_K from the rows' outer products (Lemma 3), FP64 (all of A^T A, read
-    // at K in pivot order); step 5 by the Cholesky factor B = R^T R with the pivots of step 2
-    // forced
-    LEV_CUDA(lev::launch_gram_csr_fp64(row_ptr, col, val, n, d, qs.G, st));
+    // step 4: B = A_K^T A_K (all of A^T A, read at K in pivot order), the sum of the rows' outer
+    // products (Lemma 3): rows of more than max(32, d / 5) entries are densified and their Gram
+    // formed by the compensated dense kernel (about 30x the rate of the FP64 atomics per product,
+    // so it pays beyond about d / 5 entries); the others add their pairs by FP64 atomics. Step 5
+    // by the Cholesky factor B = R^T R with the pivots of step 2 forced
+    const int64_t max_len = std::max<int64_t>(32, d / 5);
+    LEV_TRY(ensure(h->csr_heavy, sizeof(int32_t) * (size_t)n + 256));
+    auto* hcount = reinterpret_cast<unsigned long long*>(h->csr_heavy.ptr);
+    auto* hidx = reinterpret_cast<int32_t*>(static_cast<char*>(h->csr_heavy.ptr) + 256);
+    LEV_CUDA(lev::launch_heavy_rows(row_ptr, n, max_len, hcount, hidx, st));
+    LEV_CUDA(cudaMemcpyAsync(h->host_rank + 3, hcount, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    LEV_CUDA(cudaStreamSynchronize(st));
+    const int64_t nh = h->host_rank[3];
+    const double* Gheavy = nullptr;
+    if (nh > 0) {
+        const size_t gp = lev::gram_partial_doubles(nh, d);
+        LEV_TRY(ensure(h->csr_dense, sizeof(double) * (gp + (size_t)d * d) + sizeof(float) * (size_t)nh * d));
+        double* Gh = static_cast<double*>(h->csr_dense.ptr);
+        double* Gp2 = Gh + (size_t)d * d;
+        float* H = reinterpret_cast<float*>(Gp2 + gp);
+        LEV_CUDA(lev::launch_densify_rows(row_ptr, col, val, hidx, hcount, nh, d, H, st));
+        LEV_CUDA(lev::launch_gram_fp64(H, d, nh, d, Gp2, Gh, st));
+        Gheavy = Gh;
+    }
+    LEV_CUDA(lev::launch_gram_csr_light(row_ptr, col, val, n, d, max_len, Gheavy, qs.G, st));
     LEV_CUDA(lev::launch_factor_gram(n, d, tau_of(p), perm, k, qs, perm, (double*)h->R.ptr, h->status, st));
     int64_t k2 = 0;
     rc = finish(h, qs, &k2, st);

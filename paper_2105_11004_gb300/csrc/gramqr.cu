@@ -128,15 +128,18 @@ __global__ void k_gram_reduce(const double* __restrict__ Gp, int d, int splits, 
 // their order (and the last bits of G) varies between runs. Duplicate columns of a row add up
 // (the pair p != q on one cell counts twice, once for each order); columns outside [0, d) are
 // skipped.
+// Rows with more than max_len entries are left to the dense route (k_heavy_rows, k_densify_rows,
+// the compensated Gram of the densified rows).
 __global__ void __launch_bounds__(256) k_gram_csr_fp64(const int64_t* __restrict__ row_ptr,
                                                        const int32_t* __restrict__ col,
                                                        const float* __restrict__ val, int64_t n, int d,
-                                                       double* __restrict__ G) {
+                                                       int64_t max_len, double* __restrict__ G) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < n; i += nwarps) {
         const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
+        if (p1 - p0 > max_len) continue;
         for (int64_t pb = p0; pb < p1; pb += 32) {
             const int cnt = (int)min((int64_t)32, p1 - pb);
             int my_c = -1;
@@ -159,6 +162,36 @@ __global__ void __launch_bounds__(256) k_gram_csr_fp64(const int64_t* __restrict
                 }
             }
         }
+    }
+}
+
+// Indices of the rows with more than max_len entries (in no fixed order) and their count.
+__global__ void k_heavy_rows(const int64_t* __restrict__ row_ptr, int64_t n, int64_t max_len,
+                             unsigned long long* __restrict__ count, int32_t* __restrict__ idx) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (row_ptr[i + 1] - row_ptr[i] > max_len) idx[atomicAdd(count, 1ull)] = (int32_t)i;
+}
+
+// H (nh x d FP32, zeroed by the caller): row h = CSR row idx[h]; a repeated column adds.
+__global__ void k_densify_rows(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               const float* __restrict__ val, const int32_t* __restrict__ idx,
+                               const unsigned long long* __restrict__ count, int d, float* __restrict__ H) {
+    const int64_t nh = (int64_t)*count;
+    for (int64_t hr = blockIdx.x; hr < nh; hr += gridDim.x) {
+        const int64_t i = idx[hr];
+        for (int64_t e = row_ptr[i] + threadIdx.x; e < row_ptr[i + 1]; e += blockDim.x) {
+            const int c = col[e];
+            if ((unsigned)c < (unsigned)d) atomicAdd(H + hr * d + c, val[e]);
+        }
+    }
+}
+
+// G[i][j] += D[i][j] for i <= j.
+__global__ void k_add_upper(double* __restrict__ G, const double* __restrict__ D, int d) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)d * d;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / d), j = (int)(e % d);
+        if (i <= j) G[e] += D[e];
     }
 }
 
@@ -465,13 +498,39 @@ cudaError_t launch_gram_fp64(const float* A, int64_t lda, int64_t m, int64_t d, 
 
 cudaError_t launch_gram_csr_fp64(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
                                  int64_t d, double* G, cudaStream_t st) {
+    return launch_gram_csr_light(row_ptr, col, val, n, d, INT64_MAX, nullptr, G, st);
+}
+
+cudaError_t launch_gram_csr_light(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n, int64_t d,
+                                  int64_t max_len, const double* Gheavy, double* G, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(G, 0, sizeof(double) * (size_t)(d * d), st);
     if (e != cudaSuccess) return e;
     int64_t grid = (n * 32 + 255) / 256;
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
-    k_gram_csr_fp64<<<(unsigned)grid, 256, 0, st>>>(row_ptr, col, val, n, (int)d, G);
+    k_gram_csr_fp64<<<(unsigned)grid, 256, 0, st>>>(row_ptr, col, val, n, (int)d, max_len, G);
+    if (Gheavy) k_add_upper<<<152 * 4, 256, 0, st>>>(G, Gheavy, (int)d);
     k_mirror_upper<<<152 * 4, 256, 0, st>>>(G, (int)d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heavy_rows(const int64_t* row_ptr, int64_t n, int64_t max_len, unsigned long long* count,
+                              int32_t* idx, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (n + 255) / 256;
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    k_heavy_rows<<<(unsigned)grid, 256, 0, st>>>(row_ptr, n, max_len, count, idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_densify_rows(const int64_t* row_ptr, const int32_t* col, const float* val, const int32_t* idx,
+                                const unsigned long long* count, int64_t nh, int64_t d, float* H, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(H, 0, sizeof(float) * (size_t)(nh * d), st);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = nh < 152 * 16 ? (nh > 0 ? nh : 1) : 152 * 16;
+    k_densify_rows<<<(unsigned)grid, 256, 0, st>>>(row_ptr, col, val, idx, count, (int)d, H);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,15 @@ cudaError_t launch_gram_fp64(const float* A, int64_t lda, int64_t m, int64_t d, 
 // atomics (the order of the sums varies between runs).
 cudaError_t launch_gram_csr_fp64(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
                                  int64_t d, double* G, cudaStream_t st);
+// The same over the rows of at most max_len entries, plus Gheavy (d x d FP64 upper, may be null):
+// the Gram of the longer rows formed densely. launch_heavy_rows lists the longer rows (count on
+// the device); launch_densify_rows writes them as an nh x d FP32 matrix.
+cudaError_t launch_gram_csr_light(const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n, int64_t d,
+                                  int64_t max_len, const double* Gheavy, double* G, cudaStream_t st);
+cudaError_t launch_heavy_rows(const int64_t* row_ptr, int64_t n, int64_t max_len, unsigned long long* count,
+                              int32_t* idx, cudaStream_t st);
+cudaError_t launch_densify_rows(const int64_t* row_ptr, const int32_t* col, const float* val, const int32_t* idx,
+                                const unsigned long long* count, int64_t nh, int64_t d, float* H, cudaStream_t st);
 // The grid pivoted Cholesky of q.G (rank test as lev_rrqr's with min(m, d) steps; forced pivots
 // optional): fills q.Rorig, q.piv, q.rank.
 cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,
