@@ -54,7 +54,8 @@ __device__ inline void tile_coords(int t, int nt, int& bi, int& bj) {
     bj = bi + t;
 }
 
-constexpr int kDot2Rows = 64;          // rows per error-free block before the FP64 add
+constexpr int kDot2Rows = 64;         // rows per error-free block before the FP64 add
+constexpr int kGramShort = 8;         // CSR rows of at most this many entries: k_gram_csr_short
 
 __global__ void __launch_bounds__(256) k_gram_dot2(const float* __restrict__ At, int64_t lda, int m, int d,
                                                    int rows_per_split, double* __restrict__ Gp) {
@@ -129,7 +130,8 @@ __global__ void k_gram_reduce(const double* __restrict__ Gp, int d, int splits, 
 // (the pair p != q on one cell counts twice, once for each order); columns outside [0, d) are
 // skipped.
 // Rows with more than max_len entries are left to the dense route (k_heavy_rows, k_densify_rows,
-// the compensated Gram of the densified rows).
+// the compensated Gram of the densified rows), rows of at most kGramShort entries to
+// k_gram_csr_short.
 __global__ void __launch_bounds__(256) k_gram_csr_fp64(const int64_t* __restrict__ row_ptr,
                                                        const int32_t* __restrict__ col,
                                                        const float* __restrict__ val, int64_t n, int d,
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(256) k_gram_csr_fp64(const int64_t* __restrict
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < n; i += nwarps) {
         const int64_t p0 = row_ptr[i], p1 = row_ptr[i + 1];
-        if (p1 - p0 > max_len) continue;
+        if (p1 - p0 > max_len || p1 - p0 <= kGramShort) continue;
         for (int64_t pb = p0; pb < p1; pb += 32) {
             const int cnt = (int)min((int64_t)32, p1 - pb);
             int my_c = -1;
@@ -160,6 +162,61 @@ __global__ void __launch_bounds__(256) k_gram_csr_fp64(const int64_t* __restrict
                     const int a = cp < cq ? cp : cq, b = cp < cq ? cq : cp;
                     atomicAdd(&G[(int64_t)a * d + b], x);
                 }
+            }
+        }
+    }
+}
+
+// Rows of at most kGramShort (8) entries: 8 lanes a row, four rows a warp (a row is a short chain of
+// dependent loads, so a warp keeps four in flight, the next four rows' bounds loaded ahead); lane
+// l holds entry l, the pairs p <= q of the row (row-major upper triangle, at most 36) go round the
+// 8 lanes in 5 fixed rounds, each adding its product by an FP64 atomic as in k_gram_csr_fp64.
+__device__ __forceinline__ void tri_pair_g(int t, int len, int& p, int& q) {
+    p = 0;
+    while (t >= len - p) {
+        t -= len - p;
+        ++p;
+    }
+    q = p + t;
+}
+
+__global__ void __launch_bounds__(256) k_gram_csr_short(const int64_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const float* __restrict__ val, int64_t n, int d,
+                                                        double* __restrict__ G) {
+    const int lane = threadIdx.x & 31, seg = lane >> 3, sl = lane & 7;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t rn = warp * 4 + seg;
+    int64_t np0 = rn < n ? row_ptr[rn] : 0, np1 = rn < n ? row_ptr[rn + 1] : 0;
+    for (int64_t r0 = warp * 4; r0 < n; r0 += nwarps * 4) {
+        const int64_t r = r0 + seg;
+        const int64_t p0 = np0, p1 = np1;
+        const int len = (int)(p1 - p0);
+        const bool mine = r < n && len <= kGramShort;
+        int c = -1;
+        double v = 0.0;
+        if (mine && sl < len) {
+            c = col[p0 + sl];
+            v = (double)val[p0 + sl];
+        }
+        rn = r + nwarps * 4;
+        np0 = rn < n ? row_ptr[rn] : 0;
+        np1 = rn < n ? row_ptr[rn + 1] : 0;
+        if ((unsigned)c >= (unsigned)d) { c = -1; v = 0.0; }
+        const int npairs = mine ? len * (len + 1) / 2 : 0;
+#pragma unroll
+        for (int round = 0; round < 5; ++round) {
+            const int t = round * 8 + sl;
+            int pp = 0, qq = 0;
+            if (t < npairs) tri_pair_g(t, len, pp, qq);
+            const int cp = __shfl_sync(0xffffffffu, c, seg * 8 + pp), cq = __shfl_sync(0xffffffffu, c, seg * 8 + qq);
+            const double vp = __shfl_sync(0xffffffffu, v, seg * 8 + pp), vq = __shfl_sync(0xffffffffu, v, seg * 8 + qq);
+            if (t < npairs && cp >= 0 && cq >= 0) {
+                double x = vp * vq;
+                if (cq == cp && qq != pp) x *= 2.0;
+                const int a = cp < cq ? cp : cq, b = cp < cq ? cq : cp;
+                atomicAdd(&G[(int64_t)a * d + b], x);
             }
         }
     }
@@ -509,6 +566,10 @@ cudaError_t launch_gram_csr_light(const int64_t* row_ptr, const int32_t* col, co
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
     k_gram_csr_fp64<<<(unsigned)grid, 256, 0, st>>>(row_ptr, col, val, n, (int)d, max_len, G);
+    int64_t grid_s = (n * 8 + 255) / 256;               // four rows a warp
+    if (grid_s > 152 * 64) grid_s = 152 * 64;
+    if (grid_s < 1) grid_s = 1;
+    k_gram_csr_short<<<(unsigned)grid_s, 256, 0, st>>>(row_ptr, col, val, n, (int)d, G);
     if (Gheavy) k_add_upper<<<152 * 4, 256, 0, st>>>(G, Gheavy, (int)d);
     k_mirror_upper<<<152 * 4, 256, 0, st>>>(G, (int)d);
     return cudaGetLastError();
