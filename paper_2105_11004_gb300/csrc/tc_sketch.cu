@@ -201,33 +201,40 @@ __global__ void k_gauss_reduce(const float* __restrict__ P, int splits, int m, i
     }
 }
 
-// B (s x d FP32 row-major) -> B^T (d x ld) in the operand type; columns s..ld zero.
+// B (s x d FP32 row-major) -> B^T (d x ld) in the operand type; columns s..ld zero. Tiles of 64 k
+// x 32 columns: a warp reads 32 consecutive floats of a row of B, and writes two consecutive k of
+// one column per lane (a BF16 pair, or two TF32 words), so both sides move whole 128-byte lines.
 template <int F>
 __global__ void k_transpose_operand(const float* __restrict__ B, int64_t s, int d, int64_t ld, void* __restrict__ hi,
                                     void* __restrict__ lo) {
     using T = GTraits<F>;
-    __shared__ float tile[32][33];
-    const int64_t k0 = (int64_t)blockIdx.x * 32;
+    __shared__ float tile[64][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 64;
     const int c0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 32 x 8
-    for (int yy = ty; yy < 32; yy += 8) {
+    for (int yy = ty; yy < 64; yy += 8) {
         const int64_t k = k0 + yy;
         const int c = c0 + tx;
         tile[yy][tx] = (k < s && c < d) ? B[k * d + c] : 0.f;
     }
     __syncthreads();
-    for (int yy = ty; yy < 32; yy += 8) {
-        const int c = c0 + yy;
-        const int64_t k = k0 + tx;
-        if (c >= d || k >= ld) continue;
-        const float x = tile[tx][yy];
+    const int64_t k = k0 + 2 * tx;                               // even; ld is a multiple of 64
+    if (k >= ld) return;
+    for (int cc = ty; cc < 32; cc += 8) {
+        const int c = c0 + cc;
+        if (c >= d) continue;
+        const float x0 = tile[2 * tx][cc], x1 = tile[2 * tx + 1][cc];
+        const int64_t o = (int64_t)c * ld + k;
         if constexpr (T::kTf32) {
-            reinterpret_cast<uint32_t*>(hi)[(int64_t)c * ld + k] = f32_to_tf32(x);
+            reinterpret_cast<uint2*>(static_cast<uint32_t*>(hi) + o)[0] = make_uint2(f32_to_tf32(x0), f32_to_tf32(x1));
         } else {
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            reinterpret_cast<__nv_bfloat16*>(hi)[(int64_t)c * ld + k] = h;
-            if constexpr (T::kSplit)
-                reinterpret_cast<__nv_bfloat16*>(lo)[(int64_t)c * ld + k] = __float2bfloat16_rn(x - __bfloat162float(h));
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(hi) + o)[0] = h;
+            if constexpr (T::kSplit) {
+                const float2 hf = __bfloat1622float2(h);
+                reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(lo) + o)[0] =
+                    __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+            }
         }
     }
 }
@@ -255,7 +262,7 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
     rc = handle_scratch(h, 2, bt_elems * T::kElem * (T::kSplit ? 2 : 1), &bt);
     if (rc != LEV_OK) return rc;
     void* bt_lo = T::kSplit ? static_cast<void*>(static_cast<uint8_t*>(bt) + bt_elems * T::kElem) : nullptr;
-    dim3 tg((unsigned)((ld + 31) / 32), (unsigned)((d + 31) / 32));
+    dim3 tg((unsigned)((ld + 63) / 64), (unsigned)((d + 31) / 32));
     k_transpose_operand<F><<<tg, 256, 0, st>>>(B, s, (int)d, ld, bt, bt_lo);
     // tiles and K slices
     const int nt_full = (int)std::min<int64_t>(kMaxNt, (d + 15) / 16 * 16);
