@@ -384,6 +384,7 @@ struct RankWs {
     unsigned* work;
     int32_t *order, *sweeps;
     unsigned* version;
+    float* Yhl;        // 2 d x d FP32: the double-float rows of the Jacobi
 };
 int rank_ws(lev_handle* h, int64_t d, RankWs* w) {
     LEV_TRY(ensure(h->rank_ws, sizeof(double) * lev::rank_scratch_doubles(d)));
@@ -400,6 +401,7 @@ int rank_ws(lev_handle* h, int64_t d, RankWs* w) {
     w->order = reinterpret_cast<int32_t*>(w->work + 64);
     w->sweeps = w->order + d;
     w->version = reinterpret_cast<unsigned*>(w->sweeps + 2);
+    w->Yhl = reinterpret_cast<float*>(ws + (((reinterpret_cast<char*>(w->version + d) - reinterpret_cast<char*>(ws)) + 63) / 64) * 8);
     return LEV_OK;
 }
 
@@ -430,7 +432,7 @@ int select_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, cons
     int32_t *order = rw.order, *sweeps = rw.sweeps;
     if (svd) {
         LEV_TRY(rrqr_common(h, Atilde, m, d, 0.0, nullptr, 0, perm, R, qs, st));      // every step
-        LEV_CUDA(lev::launch_svd_rank(R, qs->rank, d, tau_of(p), Y, work, sigma_out ? sigma_out : sig, order,
+        LEV_CUDA(lev::launch_svd_rank(R, qs->rank, d, tau_of(p), Y, rw.Yhl, work, sigma_out ? sigma_out : sig, order,
                                       qs->rank, sweeps, rw.version, h->status, h->num_sms, st));
     } else {
         LEV_TRY(rrqr_common(h, Atilde, m, d, tau_of(p), nullptr, 0, perm, R, qs, st));

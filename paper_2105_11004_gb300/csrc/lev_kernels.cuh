@@ -94,13 +94,14 @@ cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t
 size_t qr_scratch_bytes(int64_t m, int64_t d);
 
 // Rank decisions (rank.cu). launch_svd_rank: sigma (d, descending) of the first *d_rows rows of R
-// (d x d, d <= 1024) by one-sided Jacobi on a copy Y (d x d), order[j] = the row of Y holding
+// (d x d, d <= 1024) by one-sided Jacobi in double-float arithmetic on a split copy Yhl (2 d^2
+// FP32), joined back into Y (d x d FP64); order[j] = the row of Y holding
 // sigma_j (its normalised row is the right singular vector), *rank_out = #{sigma_j > tau sigma_1};
 // work: 64 uint32 zeroed here. launch_srrqr_step: one strong-RRQR step at fixed k from R (k rows
 // of the forced factor, pivot order), Rs (R11 scaled and transposed), G (the Gram matrix): out =
 // {rho^2, i, j} of the largest rho, and perm[i] <-> perm[j] when rho > phi.
 size_t rank_scratch_doubles(int64_t d);
-cudaError_t launch_svd_rank(const double* R, const int64_t* d_rows, int64_t d, double tau, double* Y,
+cudaError_t launch_svd_rank(const double* R, const int64_t* d_rows, int64_t d, double tau, double* Y, float* Yhl,
                             unsigned* work, double* sigma, int32_t* order, int64_t* rank_out, int32_t* sweeps_out,
                             unsigned* version, int32_t* status, int num_sms, cudaStream_t st);
 cudaError_t launch_srrqr_step(const double* R, const double* Rs, const double* G, int32_t* perm, int64_t d, int64_t k,
