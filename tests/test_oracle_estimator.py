@@ -139,3 +139,20 @@ def test_sketch_spectrum_bounds():
     alpha, eps = 0.3, 0.5
     assert sv[0] < ((1 + alpha) + np.sqrt(k / m)) * (1 + eps)
     assert sv[-1] > ((1 - alpha) - np.sqrt(k / m)) * (1 - eps)
+
+
+def test_back_substitution_and_omega_factor():
+    """Step 6 (M = R_11^{-1} Omega, Alg. 8 step 4): a hand-solved 3 x 3 system, the residual
+    R_11 M - Omega, and R_11^{-1} itself against the textbook inverse of a triangular matrix."""
+    from oracle.linalg import back_substitute
+    R = np.array([[2.0, 1.0, -1.0], [0.0, 4.0, 2.0], [0.0, 0.0, 0.5]])
+    # x3 = 1 / 0.5 = 2; x2 = (8 - 2 x3) / 4 = 1; x1 = (1 - x2 + x3) / 2 = 1
+    np.testing.assert_array_equal(back_substitute(R, np.array([[1.0], [8.0], [1.0]]))[:, 0], [1.0, 1.0, 2.0])
+    rs = np.random.default_rng(5)
+    R11 = np.triu(rs.standard_normal((40, 40))) + 8 * np.eye(40)
+    M = E.omega_factor(R11, 12, seed=3)
+    np.testing.assert_allclose(R11 @ M, rng.omega(40, 12, 3), atol=1e-13)
+    assert M.shape == (40, 12)
+    Minv = E.omega_factor(R11, 0, seed=3, omega_identity=True)
+    np.testing.assert_allclose(Minv, np.linalg.inv(R11), atol=1e-13)
+    assert np.all(np.tril(Minv, -1) == 0)                       # the inverse stays upper triangular
