@@ -607,11 +607,16 @@ cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t
 cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,
                                     const QrScratch& q, int32_t* status, cudaStream_t st) {
     cudaError_t e;
-    // cooperative grid over the SMs (one CTA per SM), own columns in shared memory
+    // cooperative grid over the SMs (at most one CTA per SM), own columns in shared memory. Up to
+    // d = 256 a step is bound by the latency of the published row, not by the FP64 work, so each
+    // CTA takes three columns (ceil(d / 3) CTAs): a factorisation alone takes about 7% longer, and
+    // the SMs it leaves free run the kernels of other batches in flight. The grid does not change
+    // the result (every CTA takes the same pivots; each entry sees the same operations).
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int pgrid = sms < (int)d ? sms : (int)d;
+    int pgrid = sms < (int)d ? sms : (int)d;
+    if (d <= 256 && pgrid > (int)(d + 2) / 3) pgrid = (int)(d + 2) / 3;
     const size_t ncl = ((size_t)d + pgrid - 1) / pgrid;
     if (ncl > 32) return cudaErrorInvalidConfiguration;          // per-CTA bookkeeping holds 32 columns
     const size_t smem = sizeof(double) * (ncl * d + 3 * (size_t)d) + sizeof(int) * (size_t)d + 64;

@@ -7,6 +7,7 @@
     python -m paper_2105_11004_gb300.stage_runner lsqr --n 262144 --d 256
     python -m paper_2105_11004_gb300.stage_runner svd --m 1024 --d 256 --rank 200
     python -m paper_2105_11004_gb300.stage_runner exact_csr --n 1000000 --d 1024
+    python -m paper_2105_11004_gb300.stage_runner estimate_csr --n 8000000 --d 1024
 
 Inputs are seeded and synthetic (the generators of the ``workloads`` module); every stage runs
 through the C ABI exactly as ``lev_estimate_dense`` runs it. The script prints the CUDA-event time
@@ -21,7 +22,7 @@ import sys
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("stage", choices=["final", "rrqr", "sketch", "backward", "lsqr", "svd", "exact_csr"])
+    ap.add_argument("stage", choices=["final", "rrqr", "sketch", "backward", "lsqr", "svd", "exact_csr", "estimate_csr"])
     ap.add_argument("--n", type=int, default=262144)
     ap.add_argument("--d", type=int, default=256)
     ap.add_argument("--k", type=int, default=256)
@@ -96,6 +97,13 @@ def main(argv=None):
         p = L.make_params(s=262144, m=4096, k=256, tau=1e-5, seed=a.seed, sketch_prec="bf16x3")
         theta = torch.empty(a.n, device="cuda")
         ms = timed(lambda: L.lev_exact_csr(h, rp, cl, vl, a.n, a.d, p, theta))
+    elif a.stage == "estimate_csr":
+        # the whole estimate on the CSR workload of the bench (8 entries a row, 1% rows of 256)
+        C = W.csr_uniform(a.n, a.d, seed=2)
+        rp, cl, vl = (torch.from_numpy(v).cuda() for v in (C.row_ptr, C.col, C.val))
+        p = L.make_params(s=262144, m=4096, k=256, tau=1e-5, seed=12, sketch_prec="bf16x3")
+        theta = torch.empty(a.n, device="cuda")
+        ms = timed(lambda: L.lev_estimate_csr(h, rp, cl, vl, a.n, a.d, p, theta, want_rank=False))
     else:
         p = L.make_params(s=a.s, m=a.m, k=a.k, tau=a.tau, seed=a.seed, sketch_prec="bf16x3", final_prec="bf16x3")
         w = torch.rand(a.n, device="cuda")
