@@ -196,7 +196,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the rank-rule and least-squares measurements")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR 8e6 x 1024 measurement")
     ap.add_argument("--csr-large", action="store_true", help="also measure the CSR 8e7 x 1024 (~1e9 nnz) workload")
-    ap.add_argument("--streams", type=int, default=4,
+    ap.add_argument("--streams", type=int, default=6,
                     help="batches in flight: step i runs on stream i mod S with its own handle, so one batch's "
                          "latency-bound pivoted Cholesky overlaps another batch's HBM- and tensor-bound kernels")
     args = ap.parse_args()
