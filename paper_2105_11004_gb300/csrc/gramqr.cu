@@ -20,7 +20,8 @@
 //     chain at the sketch sizes (m = 1,024 to 4,096).
 //     Upper 32 x 32 tiles split over rows, split partials reduced in a fixed
 //     order and mirrored;
-//   k_pchol_grid: one cooperative grid (one CTA per SM); CTA c owns the
+//   k_pchol_grid: one cooperative grid (at most one CTA per SM; ceil(d/3) CTAs
+//     up to d = 256, where a step is latency-bound); CTA c owns the
 //     columns l = c mod gridDim of the Schur complement in shared memory. All
 //     CTAs keep a replicated Schur diagonal and take the same pivot p_j (largest
 //     diagonal, ties to the lowest column) and the same rank decision
@@ -269,8 +270,8 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
-// Pivoted Cholesky of G (d x d FP64, symmetric) on one cooperative grid (one
-// CTA per SM). CTA c owns the columns l = c mod gridDim and keeps them in shared
+// Pivoted Cholesky of G (d x d FP64, symmetric) on one cooperative grid (at
+// most one CTA per SM). CTA c owns the columns l = c mod gridDim and keeps them in shared
 // memory. Every CTA keeps a replicated copy of the Schur diagonal, updated with
 // the same FMAs as the owners' columns, so all CTAs take the same pivots and the
 // same rank decisions without exchanging them.
