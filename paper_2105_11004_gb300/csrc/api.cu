@@ -51,7 +51,7 @@ struct GCache {
     size_t bytes = 0;
     uint64_t seed = 0;
     int64_t m = -1, s = -1;
-    int kind = -1;   // 0: FP32 (ld = s); 2: BF16 hi + lo (ld = s rounded up to 64); 3: TF32-rounded FP32 (ld)
+    int kind = -1;   // 0: FP32 Z/sqrt(m) (ld = s); 2: Z in BF16 (ld = s rounded up to 64); 3: Z in FP32 (ld)
 };
 
 }  // namespace
@@ -200,9 +200,11 @@ int check_prec(int32_t prec, const char* what) {
 double tau_of(const lev_params* p) { return p->tau > 0 ? p->tau : 1e-5; }
 
 // Make sure G (m x s) for (seed, kind) is in the cache; returns its pointers.
-// Kind 0: FP32, leading dimension s. Kind 2: BF16 hi then lo, leading dimension
-// s rounded up to 64 (TMA rows of whole 128-byte lines). Kind 3: FP32 rounded
-// to TF32, same padded leading dimension.
+// G = Z / sqrt(m) with Z the BF16 rounding of the Gaussian draw. Kind 0: FP32
+// entries Z / sqrt(m), leading dimension s. Kind 2: Z in BF16 (exact), leading
+// dimension s rounded up to 64 (TMA rows of whole 128-byte lines); the tensor-core
+// stage applies 1 / sqrt(m) in its reduction. Kind 3: Z in FP32 (exact in TF32),
+// same padded leading dimension, same deferred scale.
 int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
              const float** g32, const __nv_bfloat16** ghi) {
     GCache& g = h->g;
