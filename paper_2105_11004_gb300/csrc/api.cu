@@ -539,9 +539,12 @@ int lev_create(lev_handle** out, int device) {
     LEV_CUDA(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(LEV_EINVAL, "device %d out of range (%d devices)", device, ndev);
     LEV_CUDA(cudaSetDevice(device));
+    int sms = 0;
+    LEV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    if (sms < 1) return fail(LEV_ECUDA, "device %d reports %d SMs", device, sms);
     lev_handle* h = new lev_handle();
     h->device = device;
-    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    h->num_sms = sms;
     if (cudaMalloc(&h->status, 64) != cudaSuccess || cudaMemset(h->status, 0, 64) != cudaSuccess ||
         cudaMallocHost(&h->host_rank, 64) != cudaSuccess) {
         cudaGetLastError();

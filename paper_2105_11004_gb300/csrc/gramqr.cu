@@ -31,6 +31,7 @@
 //
 // The Gram route resolves |R_jj| / |R_00| down to about sqrt(m u) ~ 1e-7; the
 // caller uses the Householder kernel when tau is below 1e-6 or d > 1024.
+#include <atomic>
 #include <climits>
 
 #include "lev_common.cuh"
@@ -515,12 +516,14 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
 // SM with the most CTAs sets the time: take the split count whose CTA total fills its last wave
 // over the SMs best (the largest such count within 1%), with the FP64 partials held to 4 MB.
 int gram_splits(int64_t m, int64_t d) {
-    static int sms = 0;
+    static std::atomic<int> sms_cached{0};               // host threads share it
+    int sms = sms_cached.load(std::memory_order_relaxed);
     if (sms == 0) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                       cudaSuccess || sms < 1)
             sms = 152;
+        sms_cached.store(sms, std::memory_order_relaxed);
     }
     const int64_t T = gram_tiles((int)d);
     const int64_t blocks = (m + 15) / 16;
@@ -614,8 +617,9 @@ cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int3
     // the SMs it leaves free run the kernels of other batches in flight. The grid does not change
     // the result (every CTA takes the same pivots; each entry sees the same operations).
     int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (sms < 1 || d < 1) return cudaErrorInvalidValue;
     int pgrid = sms < (int)d ? sms : (int)d;
     if (d <= 256 && pgrid > (int)(d + 2) / 3) pgrid = (int)(d + 2) / 3;
     const size_t ncl = ((size_t)d + pgrid - 1) / pgrid;

@@ -520,8 +520,9 @@ extern "C" int lev_rrqr_noalloc(const float* Atilde, int64_t m, int64_t d, doubl
     const size_t status_off = qr_layout(m, d, base, &q);
     int32_t* status = reinterpret_cast<int32_t*>(base + status_off);
     int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && sms < 1) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess) e = launch_pivoted_qr(Atilde, m, d, tau, nullptr, 0, q, perm, R, status, sms, st);
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     if (!rank) return LEV_OK;

@@ -28,6 +28,7 @@
 // and "accumulator drained" to the even CTA's mbarriers; MMA completions are
 // multicast to both. Every wait is bounded (2 s of %globaltimer); on expiry the
 // CTA records the failure in the status word and leaves its loops.
+#include <atomic>
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -454,16 +455,16 @@ int run_final_tc(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t ld
     // split never leaves a group waiting for a free SM (or SM pair) behind the others
     int64_t groups = handle_num_sms(h);
     if (T::kPair == 2) {
-        static int cached[64] = {};
+        static std::atomic<int> cached[64] = {};         // resident clusters per device (host threads share it)
         int dev = 0;
-        cudaGetDevice(&dev);
-        int clusters = dev < 64 ? cached[dev] : 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return handle_fail(LEV_ECUDA, "no current CUDA device");
+        int clusters = dev >= 0 && dev < 64 ? cached[dev].load(std::memory_order_relaxed) : 0;
         if (clusters == 0) {
             cfg.gridDim = dim3((unsigned)(groups & ~1));
             e = cudaOccupancyMaxActiveClusters(&clusters, k_final_tc<F>, &cfg);
             if (e != cudaSuccess || clusters < 1)
                 return handle_fail(LEV_ECUDA, "no resident 2-CTA cluster for the final pass");
-            if (dev < 64) cached[dev] = clusters;
+            if (dev >= 0 && dev < 64) cached[dev].store(clusters, std::memory_order_relaxed);
         }
         groups = clusters;
     }
