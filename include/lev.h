@@ -113,6 +113,12 @@ int lev_destroy(lev_handle* h);
 /* Message of the last failing call on this thread ("" if none). Never NULL. */
 const char* lev_last_error(void);
 
+/* Device memory the handle holds now, in bytes: its scratch buffers (grown on demand by the calls
+ * made on it, never shrunk) and its caches of G, Omega and the CountSketch bucket permutation.
+ * Host only (no device work, no synchronisation). lev_destroy releases all of it.
+ * Errors: LEV_EINVAL (NULL handle or bytes). */
+int lev_workspace_bytes(lev_handle* h, int64_t* bytes);
+
 /* Fill *p with the paper's practical defaults (Alg. 3: eps = 1/2, delta = 1/3,
  * gamma = 2), tau = 1e-5, seed 0, FP32 stages, sizes 0 (derived), no flags. */
 int lev_params_init(lev_params* p);

@@ -42,6 +42,7 @@ SIGNATURES = {
     "lev_create": (ctypes.c_int, [_P(_c_void_p), ctypes.c_int]),
     "lev_destroy": (ctypes.c_int, [_c_void_p]),
     "lev_last_error": (ctypes.c_char_p, []),
+    "lev_workspace_bytes": (ctypes.c_int, [_c_void_p, _P(_i64)]),
     "lev_params_init": (ctypes.c_int, [_P(lev_params)]),
     "lev_resolve_sizes": (ctypes.c_int, [_P(lev_params), _i64, _i64, _P(_i64), _P(_i64), _P(_i64)]),
     "lev_sketch_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p, _c_void_p]),
@@ -344,6 +345,13 @@ def lev_rrqr_noalloc(Atilde, tau, perm, R, stream=None) -> int:
     rc = _check(lib.lev_rrqr_noalloc(_ptr(Atilde), m, d, float(tau), _ptr(perm), _ptr(R), ctypes.byref(r),
                                      _stream(stream)), allow=(LEV_ERANK0,))
     return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_workspace_bytes(h: Handle) -> int:
+    """Device memory the handle holds now (scratch and caches), in bytes."""
+    b = _i64()
+    _check(lib.lev_workspace_bytes(h.ptr, ctypes.byref(b)))
+    return b.value
 
 
 def lev_set_timing(h: Handle, enable: bool = True):

@@ -99,6 +99,18 @@ struct lev_handle {
 
 namespace {
 
+// Every scratch buffer of a handle: the one list that lev_destroy releases and lev_workspace_bytes
+// counts.
+template <class F>
+void for_each_buf(lev_handle* h, F f) {
+    Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
+                  &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
+                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->tc_pad,
+                  &h->exact_gp, &h->srht_c, &h->rank_ws, &h->lsqr_u, &h->lsqr_ws, &h->csr_p, &h->csr_heavy,
+                  &h->csr_dense};
+    for (Buf* b : all) f(*b);
+}
+
 int ensure(Buf& b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return LEV_OK;
@@ -559,12 +571,7 @@ int lev_destroy(lev_handle* h) {
     if (!h) return LEV_OK;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
-                  &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
-                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->tc_pad,
-                  &h->exact_gp, &h->srht_c, &h->rank_ws, &h->lsqr_u, &h->lsqr_ws, &h->csr_p, &h->csr_heavy,
-                  &h->csr_dense};
-    for (Buf* b : all) release(*b);
+    for_each_buf(h, [](Buf& b) { release(b); });
     for (int i = 0; i < 2; ++i) {
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
         if (h->ev_used[i]) cudaEventDestroy(h->ev_used[i]);
@@ -579,6 +586,14 @@ int lev_destroy(lev_handle* h) {
     if (h->host_rank) cudaFreeHost(h->host_rank);
     if (h->host_lsqr) cudaFreeHost(h->host_lsqr);
     delete h;
+    return LEV_OK;
+}
+
+int lev_workspace_bytes(lev_handle* h, int64_t* bytes) {
+    if (!h || !bytes) return fail(LEV_EINVAL, "handle or bytes is NULL");
+    size_t total = h->g.bytes + (h->status ? 64 : 0);
+    for_each_buf(h, [&total](Buf& b) { total += b.bytes; });
+    *bytes = (int64_t)total;
     return LEV_OK;
 }
 

@@ -518,3 +518,22 @@ def test_invalid_arguments(L, h):
     with pytest.raises(L.LevError):
         L.lev_final_dense(h, A, torch.zeros((4, 8), device="cuda"), 9, theta)
     assert L.lev_device_status(h) == 0
+
+
+def test_workspace_bytes_counts_scratch_and_caches(L):
+    """lev_workspace_bytes: the status word on a fresh handle; after an estimate at least the cached
+    G (Z in BF16, m x s); unchanged by a second call of the same shapes (buffers only grow)."""
+    import torch
+    h = L.Handle(0)
+    try:
+        assert L.lev_workspace_bytes(h) == 64
+        A = to_dev(W.dense_gaussian(4096, 32, 1).astype(np.float32))
+        p = L.make_params(s=2048, m=128, k=16, tau=1e-8, seed=2, sketch_prec="bf16x3", final_prec="bf16x3")
+        theta = torch.empty(4096, device="cuda")
+        assert L.lev_estimate_dense(h, A, p, theta) == 32
+        b1 = L.lev_workspace_bytes(h)
+        assert b1 >= 64 + 128 * 2048 * 2
+        L.lev_estimate_dense(h, A, p, theta)
+        assert L.lev_workspace_bytes(h) == b1
+    finally:
+        h.close()
