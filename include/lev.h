@@ -26,8 +26,13 @@
  *  - Layouts: dense matrices are row-major with a leading dimension (elements);
  *    CSR uses int64 row_ptr (n+1), int32 col (nnz, any order within a row,
  *    duplicates are summed) and FP32 values.
- *  - Limits: 1 <= d <= 4096, 1 <= n < 2^31, 1 <= s < 2^31, m >= d, 1 <= k <= 4096.
- *  - Thread safety: a handle may be used by one host thread at a time.
+ *  - Limits: 1 <= d <= 4096, 1 <= n < 2^31, 1 <= s < 2^31, 1 <= m <= 2^20 (m < d is
+ *    accepted: the rank is then at most m), 1 <= k <= 4096.
+ *  - Thread safety: a handle may be used by one host thread at a time. Its scratch is shared by
+ *    all its calls, so calls of one handle on different streams must not run concurrently; work
+ *    in flight on several streams takes one handle per stream (the caches of G, Omega and the
+ *    bucket permutation are the exception: each records an event that a later call on another
+ *    stream waits for).
  *
  * Random streams (both the library and its test oracle implement these from
  * the published definitions; no code is shared):
