@@ -28,11 +28,10 @@
  *    duplicates are summed) and FP32 values.
  *  - Limits: 1 <= d <= 4096, 1 <= n < 2^31, 1 <= s < 2^31, 1 <= m <= 2^20 (m < d is
  *    accepted: the rank is then at most m), 1 <= k <= 4096.
- *  - Thread safety: a handle may be used by one host thread at a time. Its scratch is shared by
- *    all its calls, so calls of one handle on different streams must not run concurrently; work
- *    in flight on several streams takes one handle per stream (the caches of G, Omega and the
- *    bucket permutation are the exception: each records an event that a later call on another
- *    stream waits for).
+ *  - Thread safety: a handle may be used by one host thread at a time. Its scratch and caches are
+ *    shared by all its calls, so calls of one handle on different streams must not overlap on
+ *    the device (order them, e.g. with an event); work in flight on several streams takes one
+ *    handle per stream.
  *
  * Random streams (both the library and its test oracle implement these from
  * the published definitions; no code is shared):
