@@ -138,15 +138,19 @@ class Handle:
             pass
 
 
-_handles = {}
-_lock = threading.Lock()
+_tls = threading.local()
 
 
 def default_handle(device: int = 0) -> Handle:
-    with _lock:
-        if device not in _handles:
-            _handles[device] = Handle(device)
-        return _handles[device]
+    """The calling thread's handle on `device`, created on first use. A handle serves one host
+    thread at a time (include/lev.h), so host threads do not share their default handles."""
+    handles = getattr(_tls, "handles", None)
+    if handles is None:
+        handles = _tls.handles = {}
+    h = handles.get(device)
+    if h is None:
+        h = handles[device] = Handle(device)
+    return h
 
 
 def make_params(s=0, m=0, k=0, tau=1e-5, seed=0, sketch_prec="fp32", final_prec="fp32", eps=0.5,

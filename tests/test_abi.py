@@ -83,3 +83,32 @@ def test_null_handle_is_einval(lev):
     rc = lev.lib.lev_sketch_dense(None, None, 10, 4, 4, ctypes.byref(lev.make_params()), None, None)
     assert rc == lev.LEV_EINVAL
     assert b"handle" in lev.lib.lev_last_error()
+
+
+def test_default_handle_is_per_thread(lev, monkeypatch):
+    """A handle serves one host thread at a time: default_handle gives each thread its own, and
+    the same one on every call from that thread (a stand-in Handle; no GPU)."""
+    import threading
+
+    made = []
+
+    class FakeHandle:
+        def __init__(self, device=0):
+            self.device = device
+            made.append(self)
+
+    monkeypatch.setattr(lev, "Handle", FakeHandle)
+    monkeypatch.setattr(lev, "_tls", threading.local())
+    h0 = lev.default_handle(0)
+    assert lev.default_handle(0) is h0 and lev.default_handle(1) is not h0
+    got = {}
+
+    def worker():
+        got["a"] = lev.default_handle(0)
+        got["b"] = lev.default_handle(0)
+
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert got["a"] is got["b"] and got["a"] is not h0
+    assert len(made) == 3
