@@ -541,7 +541,7 @@ def csr_timing(L, h, name, reps):
     out = {"n": n, "d": d, "nnz": C.nnz, "rank": r, "ms_per_step": ms, "rows_per_s": n / (ms * 1e-3),
            "csr_gbs_two_passes": 2 * csr_bytes / (ms * 1e-3) / 1e9, "stages_ms": stages,
            "sketch_prec": "bf16x3", "final_prec": "fp32", "generation_s": gen_s}
-    # the same estimate with an SRHT after the CountSketch (Sec. 3.1): t from the quoted SRHT
+    # the same estimate with an SRHT after the CountSketch (Sec. 4.1): t from the quoted SRHT
     # theorem, 4 (sqrt(d) + sqrt(ln(s d)))^2 ln d, rounded up to a multiple of 64
     t = int(np.ceil(4 * (np.sqrt(d) + np.sqrt(np.log(cfg["s"] * d))) ** 2 * np.log(d) / 64.0) * 64)
     ps = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3",
@@ -563,7 +563,7 @@ def csr_timing(L, h, name, reps):
     out["lstsq"] = {"rank": kp, "precondition_ms": pre_ms, "iterations": its, "lsqr_ms": ls_ms,
                     "csr_gbs_per_pass": (its + 1) * (csr_bytes + 8 * n) / (ls_ms * 1e-3) / 1e9}
     # Alg. 7 (LS-HRN-exact) on the same matrix: B = A_K^T A_K from the rows' outer products
-    # (Lemma 3, FP64), its forced-pivot Cholesky, theta = ||A_K R^{-1}||^2 (k = d)
+    # (Lemma 8, Sec. 5.1, FP64), its forced-pivot Cholesky, theta = ||A_K R^{-1}||^2 (k = d)
     r_e = L.lev_exact_csr(h, rp, cl, vl, n, d, p, theta)
     ms_e = timed(lambda: L.lev_exact_csr(h, rp, cl, vl, n, d, p, theta), max(1, reps // 2))
     lens = np.diff(C.row_ptr).astype(np.float64)

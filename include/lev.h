@@ -6,7 +6,7 @@
  * randomization": a CountGauss sketch A~ = G S A (Alg. 3), a column-pivoted QR
  * of the sketch that reveals the numerical rank r and the selected columns K
  * (Alg. 4), and the squared row norms theta~_i = ||A_{i,K} R_11^{-1} Omega||^2
- * (Alg. 8 steps 4-5, eq. (24)). The problem statement (Sec. 1; Alg. 10
+ * (Alg. 8 steps 4-5; the squared row norms of A (Pi_1 A)^+ Pi_2, eq. (10)). The problem statement (Sec. 1; Alg. 10
  * Require/Ensure): a tall matrix A (n x d, n >> d, dense or sparse, any rank)
  * in; the estimated leverage scores theta~ (n) and the numerical rank r out.
  *
@@ -38,11 +38,11 @@
  *  - splitmix64(key, c): state = key + (c+1) * 0x9E3779B97F4A7C15 (mod 2^64),
  *    then the splitmix64 finaliser (Steele, Lea and Flood 2014);
  *  - key_t = seed XOR (t * 0xD1B54A32D192ED03), t = 1 hash, 2 G, 3 Omega;
- *  - CountSketch (Sec. 2.3.3): x = splitmix64(key_1, i), bucket h(i) =
+ *  - CountSketch (Sec. 3.4.3): x = splitmix64(key_1, i), bucket h(i) =
  *    (hi32(x) * s) >> 32, sign = +1 if bit 0 of x is 0 else -1;
  *  - N(0,1) number c of stream t: Box-Muller, cosine branch, with
  *    u1 = ((splitmix64(key_t, 2c) >> 11) + 1) 2^-53, u2 = (splitmix64(key_t, 2c+1) >> 11) 2^-53;
- *  - G[j, b] = Z_{j*s + b} / sqrt(m) (Sec. 2.3.1 scaling) with Z_c the BF16 rounding (to nearest
+ *  - G[j, b] = Z_{j*s + b} / sqrt(m) (Sec. 3.4.1 scaling) with Z_c the BF16 rounding (to nearest
  *    even) of the FP32 rounding of N_c, so that G is exact in the tensor cores' 16-bit operand
  *    type; Omega[p, q] = N_{p*k + q} / sqrt(k), p the pivot position (0 <= p < r), q < k.
  */
@@ -71,12 +71,12 @@ extern "C" {
                            the final pass; Z*B_hi + Z*B_lo in the Gaussian stage (G exact in BF16) */
 
 /* Flags (lev_params.flags). */
-#define LEV_OMEGA_IDENTITY  1u  /* Omega = I_r, k = r (the Pi_2-free mode of Sec. 6.4) */
+#define LEV_OMEGA_IDENTITY  1u  /* Omega = I_r, k = r (the Pi_2-free mode of Sec. 7.4) */
 #define LEV_SKETCH_IDENTITY 2u  /* S = I, G = I, A~ = A (tests; needs n <= 65536) */
 #define LEV_FORCE_PIVOTS    4u  /* take perm_in[0..rank_in) as the pivots, no rank test */
 #define LEV_HOST_ASYNC      8u  /* lev_estimate_dense with host buffers and rank == NULL: enqueue only */
-#define LEV_SKETCH_SRHT    16u  /* A~ = G F S A: an SRHT F (t = srht_t rows) after the CountSketch (Sec. 3.1) */
-#define LEV_RANK_SVD       32u  /* rank = #{sigma_j(A~) > tau sigma_1(A~)} (Alg. 11 step 3, Sec. 6.2); columns
+#define LEV_SKETCH_SRHT    16u  /* A~ = G F S A: an SRHT F (t = srht_t rows) after the CountSketch (Sec. 4.1) */
+#define LEV_RANK_SVD       32u  /* rank = #{sigma_j(A~) > tau sigma_1(A~)} (Alg. 11 step 3, Sec. 7.2); columns
                                    from the pivoted QR run to the end; d <= 1024 */
 #define LEV_SRRQR          64u  /* after the rank: strong-RRQR swaps at that rank until every
                                    rho_ij <= phi (Alg. 2); d <= 1024 */
@@ -90,7 +90,7 @@ typedef struct lev_params {
     int64_t  s;            /* CountSketch buckets (the paper's r); 0 = from eps, delta */
     int64_t  m;            /* rows of G; 0 = ceil(gamma d) */
     int64_t  k;            /* columns of Omega; 0 = JL size 4 ln n / (eps^2/2 - eps^3/3) */
-    double   tau;          /* rank rule |R_jj| > tau |R_00| (Sec. 6.2); <= 0 means 1e-5 */
+    double   tau;          /* rank rule |R_jj| > tau |R_00| (Sec. 7.2); <= 0 means 1e-5 */
     uint64_t seed;         /* seed of the three random streams */
     int32_t  sketch_prec;  /* LEV_FP32 | LEV_TF32 | LEV_BF16 | LEV_BF16X3 for A~ = G B */
     int32_t  final_prec;   /* same set for theta~ = ||A M_full||^2 */
@@ -129,7 +129,7 @@ int lev_params_init(lev_params* p);
 
 /* Resolve the sizes a call with (p, n, d) would use: s = ceil((d^2+d) /
  * ((2 eps - eps^2)^2 delta)) (Alg. 3 step 1), m = ceil(gamma d) (Alg. 3 step 2),
- * k = ceil(4 ln n / (eps^2/2 - eps^3/3)) (Gaussian JLT lemma, Sec. 2.3.1),
+ * k = ceil(4 ln n / (eps^2/2 - eps^3/3)) (Gaussian JLT lemma, Sec. 3.4.1),
  * each unless set explicitly in p. Any output pointer may be NULL. */
 int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d,
                       int64_t* s, int64_t* m, int64_t* k);
@@ -146,9 +146,9 @@ int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d,
 /* CountGauss sketch of dense A (Alg. 3): Atilde (m x d, row-major, ld = d,
  * FP32, device) = G (S A). A: device, n x d FP32, leading dimension lda >= d.
  * p->sketch_prec selects the arithmetic of the product G B. With LEV_SKETCH_SRHT
- * the CountSketch is followed by the SRHT F = sqrt(s/t) P H D of Sec. 2.3.2 (D:
+ * the CountSketch is followed by the SRHT F = sqrt(s/t) P H D of Sec. 3.4.2 (D:
  * signs of stream 4; H: Walsh-Hadamard / sqrt(s); P: t uniform row draws of
- * stream 5, multiply-shift of the high word), S~ = F S (Sec. 3.1), and G is
+ * stream 5, multiply-shift of the high word), S~ = F S (Sec. 4.1), and G is
  * m x t: A~ = G (F (S A)). s must be a power of two, at most 2^24.
  * Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA. */
 int lev_sketch_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
@@ -163,10 +163,10 @@ int lev_sketch_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, co
                    float* Atilde, void* stream);
 
 /* Column-pivoted Householder QR of the sketch in FP64 (Alg. 4 step 2, with the
- * xGEQP3-style pivoting of Sec. 6): at step j the remaining column with the
+ * xGEQP3-style pivoting of Sec. 7): at step j the remaining column with the
  * largest trailing norm (recomputed exactly, ties to the lowest original index)
  * becomes column j; the factorisation stops at the first j with
- * |R_jj| <= tau |R_00| and *rank = j (Sec. 6.2 rank check); diag(R) >= 0.
+ * |R_jj| <= tau |R_00| and *rank = j (Sec. 7.2 rank check); diag(R) >= 0.
  * Atilde: device, m x d FP32 row-major (ld = d). perm: device, d int32; entries
  * 0..r-1 are the pivots in order, r..d-1 the other columns in increasing order.
  * R: device, d x d FP64 row-major; rows 0..r-1 hold [R_11 R_12] in pivoted
@@ -179,7 +179,7 @@ int lev_rrqr(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double ta
 /* The pivoted QR of A~ (as lev_rrqr) with the rank rule of p->flags, tau = p->tau:
  *  - no flag: the diagonal test of lev_rrqr;
  *  - LEV_RANK_SVD: the QR runs to the end (column order only) and the rank is the number of
- *    singular values of A~ above tau sigma_1 (Alg. 11 step 3; Sec. 6.2 advises the singular
+ *    singular values of A~ above tau sigma_1 (Alg. 11 step 3; Sec. 7.2 advises the singular
  *    values where the diagonal of R misses a small gap), from a one-sided Jacobi SVD of R;
  *  - LEV_SRRQR: then strong-RRQR swaps at that rank (Alg. 2, Gu and Eisenstat): while the
  *    largest rho_ij = sqrt((R11^{-1} R12)_ij^2 + (gamma_j(R22) ||e_i^T R11^{-1}||)^2) exceeds
@@ -201,7 +201,7 @@ int lev_rank_stats(lev_handle* h, int64_t* swaps, int32_t* jacobi_sweeps);
 /* Alg. 11 (CountGaussPrecondition) on dense A (device, n x d FP32, lda >= d): the CountGauss
  * sketch A~ = G S A with p's sizes, seed and sketch_prec, its SVD (the LEV_RANK_SVD path of
  * lev_rrqr_select), k = #{sigma_j > p->tau sigma_1}, and N = V_k Sigma_k^{-1} written to N (device,
- * d x d FP64, row-major; columns >= k are zero). By the GSA preconditioning theorem (Sec. 5.2)
+ * d x d FP64, row-major; columns >= k are zero). By Theorem 8 (GSA preconditioning, Sec. 6.2)
  * kappa(A N) <= xi eta with high probability, whatever kappa(A) is. rank: host, may be NULL.
  * sigma: device d doubles or NULL (the sketch's singular values, descending). d <= 1024.
  * Synchronises `stream`. Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0. */
@@ -282,7 +282,7 @@ int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
 
 /* Alg. 7 (LS-HRN-exact) on dense A: the columns K and the rank k come from the
  * pivoted QR of the CountGauss sketch (as in lev_estimate_dense, with p's sizes,
- * tau, seed and sketch_prec); then B = A_K^T A_K in FP64 (Lemma 3: the Gram
+ * tau, seed and sketch_prec); then B = A_K^T A_K in FP64 (Lemma 8, Sec. 5.1: the Gram
  * matrix of A, products of the FP32 entries exact, sums in FP64, restricted to K
  * in pivot order), its Cholesky factor B = R^T R (step 5 asks for the SVD
  * B = V Sigma^2 V^T; both give theta_i = a_K B^{-1} a_K^T, B being positive
@@ -298,7 +298,7 @@ int lev_exact_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t
 
 /* Alg. 7 (LS-HRN-exact) on CSR A (row_ptr: n + 1 int64; col: nnz int32; val: nnz FP32; all
  * device; the CSR conventions of lev_sketch_csr): K and k from the pivoted QR of the CountSketch
- * + Gaussian sketch, then B = A_K^T A_K as the sum of the rows' outer products (Lemma 3: products
+ * + Gaussian sketch, then B = A_K^T A_K as the sum of the rows' outer products (Lemma 8, Sec. 5.1: products
  * of the FP32 entries exact; rows of at most max(32, d/5) entries summed by FP64 atomics, longer
  * rows densified and summed by the compensated dense Gram kernel, so the last bits of B and of
  * theta may differ between runs), its Cholesky factor B = R^T R with the pivots forced, and

@@ -5,14 +5,14 @@ TEST INFRASTRUCTURE ONLY: nothing in the product path may import this module.
 The estimator is Alg. 10 (LS-HRN-approx): Alg. 4 (CountGaussSRRQR: the
 CountGauss sketch of Alg. 3, then a rank-revealing QR of the sketch) selects
 the columns K and gives R_11; then steps 4-5 of Alg. 8 run on A_{:,K} with
-the orthogonaliser R_11 and a Gaussian JL matrix Omega (eq. (24):
-theta~_i = ||e_i^T A_K R_11^{-1} Omega||^2).
+the orthogonaliser R_11 and a Gaussian JL matrix Omega (the squared row norms of
+A (Pi_1 A)^+ Pi_2 of eq. (10): theta~_i = ||e_i^T A_K R_11^{-1} Omega||^2).
 
 Step order (each function cites its step):
- 1. hash and sign of every row (CountSketch definition, Sec. 2.3.3);
+ 1. hash and sign of every row (CountSketch definition, Sec. 3.4.3);
  2. B = S A, summed in FP64 (Alg. 3, step 3, first product);
- 3. A~ = G B with G = N(0,1)/sqrt(m) (Alg. 3 step 3, Sec. 2.3.1 scaling);
- 4. pivoted QR of A~, rank r, R_11 (Alg. 4 step 2, xGEQP3-style, Sec. 6);
+ 3. A~ = G B with G = N(0,1)/sqrt(m) (Alg. 3 step 3, Sec. 3.4.1 scaling);
+ 4. pivoted QR of A~, rank r, R_11 (Alg. 4 step 2, xGEQP3-style, Sec. 7);
  5. Omega (r x k) = N(0,1)/sqrt(k), rows indexed by pivot position;
  6. M = R_11^{-1} Omega (Alg. 8 step 4 with the QR orthogonaliser);
  7. theta~_i = sum_q (sum_{p<r} A[i, P_p] M[p, q])^2 (Alg. 8 step 5).
@@ -25,7 +25,7 @@ Readings where the paper is silent (also listed in the design notes):
 
 Modes: ``sketch_identity`` replaces S and G by identities (s = m = n) and
 ``omega_identity`` replaces Omega by I_r (k = r); with both, theta~ is the exact
-leverage of A_K (Thm 1 with k = rank(A) gives equality).
+leverage of A_K (Theorem 1, Sec. 2.2, with k = rank(A) gives equality).
 """
 from __future__ import annotations
 
@@ -43,7 +43,7 @@ def _as_float64(A):
 
 
 def count_sketch(A, s: int, seed: int, block: int = 1 << 18, row0: int = 0) -> np.ndarray:
-    """B = S A (s x d), S the CountSketch of rows 0..n-1 (Sec. 2.3.3), FP64 sums.
+    """B = S A (s x d), S the CountSketch of rows 0..n-1 (Sec. 3.4.3), FP64 sums.
 
     With row0 > 0, A is the block of rows row0..row0+n-1 of a larger matrix and the result is
     S_{:,row0:row0+n} A: each row is hashed by its global index (block matrix product)."""
@@ -89,7 +89,7 @@ def fwht(X: np.ndarray) -> np.ndarray:
 
 
 def srht(B: np.ndarray, t: int, seed: int) -> np.ndarray:
-    """C = F B with the SRHT F = sqrt(s/t) P H D of Sec. 2.3.2 (t x s): D the signs of stream 4,
+    """C = F B with the SRHT F = sqrt(s/t) P H D of Sec. 3.4.2 (t x s): D the signs of stream 4,
     H the Walsh-Hadamard matrix scaled by 1/sqrt(s), P t uniform row draws (stream 5)."""
     s = B.shape[0]
     X = fwht(rng.srht_signs(s, seed)[:, None] * B)
@@ -98,7 +98,7 @@ def srht(B: np.ndarray, t: int, seed: int) -> np.ndarray:
 
 def sketch(A, s: int, m: int, seed: int, srht_t: int = 0, row0: int = 0) -> np.ndarray:
     """CountGauss sketch A~ = G (S A) of Alg. 3 (FP64); with srht_t > 0 the CountSketch is
-    followed by an SRHT to t rows (S~ = F S, Sec. 3.1) and G is m x t. With row0 > 0, A is a
+    followed by an SRHT to t rows (S~ = F S, Sec. 4.1) and G is m x t. With row0 > 0, A is a
     block of rows starting at global row row0 (see count_sketch)."""
     B = count_sketch(A, s, seed, row0=row0)
     if srht_t:
@@ -149,7 +149,7 @@ def estimate(A, s: int, m: int, k: int, tau: float, seed: int, *,
     """Alg. 10 end to end: returns theta (n), rank, perm (d), Atilde, R (r x d), M (r x k).
 
     ``Atilde`` may be passed in to run steps 4-7 on a given sketch. ``rank_rule="svd"`` takes
-    the rank from the singular values of the sketch (Alg. 11 step 3, Sec. 6.2) and the columns
+    the rank from the singular values of the sketch (Alg. 11 step 3, Sec. 7.2) and the columns
     from its pivoted QR run to the end; ``srrqr_phi >= 1`` then improves the selected columns by
     strong-RRQR swaps at that rank (oracle/rank.py).
     """

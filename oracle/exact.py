@@ -8,9 +8,9 @@ whose columns are an orthonormal basis of range(A).
 
 Two routes:
 * ``exact_leverage_qr``: column-pivoted Householder QR of A (the rank rule of
-  Sec. 6.2 on diag(R)); theta_i = ||Q[i, :rank]||^2.
+  Sec. 7.2 on diag(R)); theta_i = ||Q[i, :rank]||^2.
 * ``exact_leverage_gram``: Alg. 5 (Gram matrix A^T A formed as a sum of row
-  outer products, Lemma 3; symmetric eigendecomposition; keep eigenvalues
+  outer products, Lemma 8, Sec. 5.1; symmetric eigendecomposition; keep eigenvalues
   lambda_j > tau^2 lambda_max; theta_i = ||A_i V_k Lambda_k^{-1/2}||^2).
 
 And Alg. 7 (LS-HRN-exact), ``ls_hrn_exact``: the columns K and the rank k come
@@ -37,7 +37,7 @@ def exact_leverage_qr(A: np.ndarray, tau: float):
 
 
 def gram(A, block: int = 1 << 16) -> np.ndarray:
-    """A^T A accumulated over row blocks (Lemma 3: sum of row outer products)."""
+    """A^T A accumulated over row blocks (Lemma 8, Sec. 5.1: sum of row outer products)."""
     d = A.shape[1]
     Gm = np.zeros((d, d))
     for r0 in range(0, A.shape[0], block):
@@ -75,8 +75,8 @@ def ls_hrn_exact(A, s: int, m: int, tau: float, seed: int, *, sketch_identity: b
     """Alg. 7 (LS-HRN-exact), FP64. Returns (theta, rank, perm).
 
     Steps 1-3: K and k from the column-pivoted QR of the sketch A~ = G S A (Alg. 3 and 4, the
-    GEQP3-style pivoting and rank rule of Sec. 6; A~ = A when ``sketch_identity``); A_K = A P_k.
-    Step 4: B = A_K^T A_K as a sum of row outer products (Lemma 3).
+    GEQP3-style pivoting and rank rule of Sec. 7; A~ = A when ``sketch_identity``); A_K = A P_k.
+    Step 4: B = A_K^T A_K as a sum of row outer products (Lemma 8, Sec. 5.1).
     Step 5: B = V Sigma^2 V^T (B is symmetric positive definite when the k columns are linearly
     independent, so its SVD is its eigendecomposition).
     Step 6: theta_i = ||e_i^T A_K V Sigma^{-1}||^2.

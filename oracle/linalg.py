@@ -3,14 +3,14 @@
 TEST INFRASTRUCTURE ONLY: nothing in the product path may import this module.
 
 Follows the classical pivoted QR of Businger and Golub that the paper's
-implementation uses through LAPACK xGEQP3 (Sec. 6, first paragraph, and
-Sec. 6.2), with these readings where the paper is silent:
+implementation uses through LAPACK xGEQP3 (Sec. 7, first paragraph, and
+Sec. 7.2), with these readings where the paper is silent:
 
 * pivot rule: at step j the remaining column with the largest trailing norm
   ||W[j:, c]|| is brought to position j; trailing norms are recomputed from
   scratch at every step (no norm downdating); exact ties go to the lowest
   original column index;
-* rank rule (Sec. 6.2: the rank is read off the diagonal of R by comparing
+* rank rule (Sec. 7.2: the rank is read off the diagonal of R by comparing
   |R_kk| with c |R_11|): r is the number of leading steps with
   |R_jj| > tau |R_00|; the factorisation stops at the first step that fails;
 * sign rule: diag(R) >= 0 (rows of R and columns of Q are flipped together).

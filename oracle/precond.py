@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: nothing in the product path may import this module.
 
 Alg. 11 (CountGaussPrecondition): A~ = G S A (Alg. 3), its SVD A~ = U Sigma V^T, the rank
 k = #{sigma_j > zeta sigma_1} (the reading of step 3 in oracle/rank.py), N = V_{:, :k} Sigma_k^{-1}.
-By the theorem on GSA preconditioning (Sec. 5.2), kappa(A N) <= xi eta with high probability,
+By Theorem 8 (GSA preconditioning, Sec. 6.2), kappa(A N) <= xi eta with high probability,
 xi = (1 + a + sqrt(k/m)) / (1 - a - sqrt(k/m)), eta = (1 + eps) / (1 - eps), whatever kappa(A) is,
 and N y^ = A^+ b for the minimum-length solution y^ of min_y ||A N y - b||.
 
@@ -34,7 +34,7 @@ def precondition(A, s: int, m: int, seed: int, zeta: float, srht_t: int = 0):
 
 
 def kappa_bound(k: int, m: int, alpha: float, eps: float) -> float:
-    """xi eta of the GSA preconditioning theorem."""
+    """xi eta of Theorem 8 (GSA preconditioning, Sec. 6.2)."""
     q = np.sqrt(k / m)
     return (1 + alpha + q) / (1 - alpha - q) * (1 + eps) / (1 - eps)
 

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY: nothing in the product path may import this module.
 
-* SVD rank (Alg. 11 step 3, and Sec. 6.2: where the |R_kk| < c |R_11| test of the pivoted QR
+* SVD rank (Alg. 11 step 3, and Sec. 7.2: where the |R_kk| < c |R_11| test of the pivoted QR
   misses a small gap, as on fixed_svd_1e7, the rank is better read off the singular values and
   the pivoted QR kept only for the column order): k = #{j : sigma_j > zeta sigma_1}.
   Reading: Alg. 11 writes an argmax over the set {sigma_j : sigma_j / sigma_1 <= zeta}, which taken

@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: nothing in the product path may import this module.
 
-The paper leaves the generators open. CountSketch (Sec. 2.3.3) needs a hash
-h: [n] -> [r] and random signs; the Gaussian embeddings (Sec. 2.3.1) need
+The paper leaves the generators open. CountSketch (Sec. 3.4.3) needs a hash
+h: [n] -> [r] and random signs; the Gaussian embeddings (Sec. 3.4.1) need
 i.i.d. N(0,1) entries. This oracle draws all of them from the splitmix64
 generator (Steele, Lea and Flood, OOPSLA 2014) used as a pure function of
 (key, counter), so every entry depends only on the seed and its index:
@@ -24,11 +24,11 @@ generator (Steele, Lea and Flood, OOPSLA 2014) used as a pure function of
 * Entries of the Gaussian sketch G (stream 2): Z_c / sqrt(m) with Z_c the draw rounded to FP32
   and then to BF16 (8-bit significand), both to nearest even. Reading: the paper's G is Gaussian;
   the BF16 rounding moves each entry by at most 2^-9 of itself (the singular values of G U by
-  about as much, inside the slack of the embedding lemmas of Sec. 3.2), and makes G exact in the
+  about as much, inside the slack of the embedding lemmas of Sec. 4.2), and makes G exact in the
   tensor cores' 16-bit operand type, so that G B needs no split of G.
 
 Reading note (the paper asks for 2-wise independent h and 4-wise independent
-signs, Sec. 2.3.3): splitmix64 is not provably k-wise independent; it is used
+signs, Sec. 3.4.3): splitmix64 is not provably k-wise independent; it is used
 as a counter-based hash so that the CPU and GPU sides can both evaluate it.
 """
 from __future__ import annotations
@@ -70,7 +70,7 @@ def bucket_and_sign(n: int, s: int, seed: int, start: int = 0):
 
 
 def srht_signs(s: int, seed: int) -> np.ndarray:
-    """Diagonal of D of the SRHT (Sec. 2.3.2): +1 / -1 from bit 0 of stream 4 at counters 0..s-1."""
+    """Diagonal of D of the SRHT (Sec. 3.4.2): +1 / -1 from bit 0 of stream 4 at counters 0..s-1."""
     x = splitmix64(stream_key(seed, STREAM_SRHT_SIGN), np.arange(s, dtype=np.uint64))
     return np.where((x & np.uint64(1)) == 0, 1.0, -1.0)
 
@@ -104,7 +104,7 @@ def bf16_round(x) -> np.ndarray:
 
 def sketch_gaussian(seed: int, counters, m: int) -> np.ndarray:
     """Entries of G by counter: Z / sqrt(m), Z = bf16_round(N_c) (the BF16 rounding of the
-    counter's Box-Muller draw, Sec. 2.3.1 scaling)."""
+    counter's Box-Muller draw, Sec. 3.4.1 scaling)."""
     return bf16_round(gaussian(seed, STREAM_G, counters)) / np.sqrt(m)
 
 

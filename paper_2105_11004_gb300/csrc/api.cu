@@ -965,7 +965,7 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     }
     LEV_TRY(rc);
     // step 4: B = A_K^T A_K (all of A^T A, read at K in pivot order), the sum of the rows' outer
-    // products (Lemma 3): rows of more than max(32, d / 5) entries are densified and their Gram
+    // products (Lemma 8, Sec. 5.1): rows of more than max(32, d / 5) entries are densified and their Gram
     // formed by the compensated dense kernel (about 30x the rate of the FP64 atomics per product,
     // so it pays beyond about d / 5 entries); the others add their pairs by FP64 atomics. Step 5
     // by the Cholesky factor B = R^T R with the pivots of step 2 forced

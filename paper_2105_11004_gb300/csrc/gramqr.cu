@@ -1,6 +1,6 @@
 // Rank-revealing QR of the sketch through its Gram matrix (FP64), sm_103a.
 //
-// The pivoted QR of Alg. 4 (xGEQP3-style greatest-trailing-norm pivoting, Sec. 6)
+// The pivoted QR of Alg. 4 (xGEQP3-style greatest-trailing-norm pivoting, Sec. 7)
 // and the pivoted Cholesky factorisation of G = A~^T A~ produce the same
 // permutation, rank and R in exact arithmetic: the squared trailing column
 // norms of the QR are the diagonal of the Schur complement of G, and the rows
@@ -124,7 +124,7 @@ __global__ void k_gram_reduce(const double* __restrict__ Gp, int d, int splits, 
     }
 }
 
-// B = A^T A of a CSR matrix as the sum of its rows' outer products (Lemma 3), FP64, into the
+// B = A^T A of a CSR matrix as the sum of its rows' outer products (Lemma 8, Sec. 5.1), FP64, into the
 // upper triangle of G (d x d, zeroed by the caller). One warp per row: the first 32 entries of a
 // chunk are held one per lane and broadcast in turn as entry p; the lanes take the entries q >= p
 // of the row. A product of two FP32 values is exact in FP64; the sums are FP64 atomics in L2, so

@@ -28,7 +28,7 @@ __host__ __device__ __forceinline__ uint64_t stream_key(uint64_t seed, int t) {
     return seed ^ ((uint64_t)t * kStreamMul);
 }
 
-// CountSketch hash of row i (Sec. 2.3.3): bucket by multiply-shift of the high
+// CountSketch hash of row i (Sec. 3.4.3): bucket by multiply-shift of the high
 // word, sign from bit 0.
 __device__ __forceinline__ uint32_t bucket_of(uint64_t x, uint32_t s) {
     return (uint32_t)(((x >> 32) * (uint64_t)s) >> 32);

@@ -1,7 +1,7 @@
 // Rank-revealing QR of the sketch and the small factor M = R_11^{-1} Omega, FP64.
 //
 // Pivoted QR (Alg. 4 step 2 with the xGEQP3-style pivoting the paper's
-// implementation uses, Sec. 6): one cooperatively launched persistent kernel.
+// implementation uses, Sec. 7): one cooperatively launched persistent kernel.
 // The FP64 working copy W (m x d, column-major) stays in global memory (it is
 // L2 resident: 32 MB at 4096 x 1024). Every CTA owns a fixed set of columns.
 // Step j, in every CTA after a grid barrier:

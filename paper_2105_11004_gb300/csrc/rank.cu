@@ -5,7 +5,7 @@
 //    pair is orthogonal, after which the row norms are the singular values and the normalised rows
 //    the right singular vectors of R. One cooperative grid; the pairs of a round are disjoint
 //    (round-robin order), a bounded grid barrier separates the rounds. The rank is then the count
-//    of sigma_j > tau sigma_1 (Alg. 11 step 3; Sec. 6.2: the singular values see a gap that the
+//    of sigma_j > tau sigma_1 (Alg. 11 step 3; Sec. 7.2: the singular values see a gap that the
 //    diagonal of R can miss);
 //  * strong-RRQR measures at a fixed k (Alg. 2 after Gu and Eisenstat): from R in pivot order,
 //    Z = R11^{-1} [I | R12], the row norms of R11^{-1}, gamma_j^2 = G_jj - ||R[:k, j]||^2 (the

@@ -1,7 +1,7 @@
 // CountGauss sketch A~ = G (S A) (Alg. 3) on sm_103a.
 //
 //  * bucket permutation: counting sort of the rows by their CountSketch bucket
-//    (hash and sign of Sec. 2.3.3), rows ascending inside a bucket, so that the
+//    (hash and sign of Sec. 3.4.3), rows ascending inside a bucket, so that the
 //    sums below run in a fixed order (bit-identical repeat runs);
 //  * CountSketch: one warp per bucket gathers its rows with 128-bit loads and
 //    writes the bucket row of B = S A once (no atomics);

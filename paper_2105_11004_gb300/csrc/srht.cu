@@ -1,4 +1,4 @@
-// Subsampled randomized Hadamard transform after the CountSketch (Sec. 2.3.2 and Sec. 3.1):
+// Subsampled randomized Hadamard transform after the CountSketch (Sec. 3.4.2 and Sec. 4.1):
 // C = F B with F = sqrt(s/t) P H D (t x s), applied to B = S A (s x d, FP32, row-major) before the
 // Gaussian stage, which then multiplies an m x t Gaussian matrix instead of an m x s one.
 //   D: signs from bit 0 of stream 4 at row b;

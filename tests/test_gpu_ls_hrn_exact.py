@@ -89,7 +89,7 @@ def test_rejects_unsupported(L, h):
     assert e.value.code == L.LEV_EINVAL
 
 
-# ---- CSR A (lev_exact_csr): B = A_K^T A_K by the rows' outer products (Lemma 3) ----
+# ---- CSR A (lev_exact_csr): B = A_K^T A_K by the rows' outer products (Lemma 8, Sec. 5.1) ----
 
 def _run_csr(L, h, C, **cfg):
     import torch

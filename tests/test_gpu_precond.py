@@ -3,7 +3,7 @@ against the FP64 oracle (oracle/precond.py) and numpy's least squares.
 
 * N: N N^T (unique, unlike N's signs) against the oracle's SVD of the same sketch (the GPU sketch
   read back: the SVD step alone), to 1e-8 of its largest entry; k equal.
-* The GSA preconditioning theorem on the GPU's N: kappa(A N) <= xi eta (m = 4d, alpha = 0.3,
+* Theorem 8 (GSA preconditioning, Sec. 6.2) on the GPU's N: kappa(A N) <= xi eta (m = 4d, alpha = 0.3,
   eps = 1/2) for kappa(A) up to 1e6, with FP32 and split-BF16 sketches.
 * LSQR: x against numpy's minimum-norm least squares. The passes round in FP32 (backward error
   about atol = 1e-6), so for b = A x0 + e with ||e|| = 1e-3 ||b|| the forward error is bounded

@@ -62,7 +62,7 @@ def test_singular_values_and_rank(L, h, m, d):
 
 
 def test_svd_rank_finds_fixed_svd_1e7(L, h):
-    """Sec. 6.2's matrix: singular values 1 (15), 1e-6 (15), 1e-7 (30), cutoff 10^-6.5: rank 30 from
+    """Sec. 7.2's matrix: singular values 1 (15), 1e-6 (15), 1e-7 (30), cutoff 10^-6.5: rank 30 from
     the singular values of the sketch (FP32 sketch arithmetic). kappa(R11) is about 1e6 at the
     selected columns, so theta~ moves by O(u_32 kappa) with the FP32 rounding of the sketch and
     of the final pass; it is checked against the oracle's steps 4-7 on the GPU's own sketch, within

@@ -1,4 +1,4 @@
-"""GPU parity of the CountSketch + SRHT + Gaussian sketch (LEV_SKETCH_SRHT, Sec. 3.1) against
+"""GPU parity of the CountSketch + SRHT + Gaussian sketch (LEV_SKETCH_SRHT, Sec. 4.1) against
 the FP64 oracle.
 
 Sketch entries within c |G| |F| |S| |A| entrywise, where |F| = |H|/sqrt(t) has every entry

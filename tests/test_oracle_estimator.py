@@ -11,7 +11,7 @@ def test_count_sketch_equals_explicit_product():
     A = W.dense_gaussian(50, 3, 1)
     b, sign = rng.bucket_and_sign(50, 7, seed=4)
     S = np.zeros((7, 50))
-    for i in range(50):                       # one +-1 per column of S (Sec. 2.3.3)
+    for i in range(50):                       # one +-1 per column of S (Sec. 3.4.3)
         S[b[i], i] = sign[i]
     np.testing.assert_allclose(E.count_sketch(A, 7, 4), S @ A, atol=1e-14)
     # row blocking does not change the result
@@ -32,7 +32,7 @@ def test_gaussian_stage_equals_explicit_product():
 
 
 def test_identity_modes_reduce_to_exact_leverage():
-    """S = I, G = I, Omega = I: theta~ is the exact leverage (Thm 1, equality case)."""
+    """S = I, G = I, Omega = I: theta~ is the exact leverage (Theorem 1, Sec. 2.2, equality case)."""
     A = W.dense_gaussian(400, 9, 2)
     th, r = exact.exact_leverage_qr(A, 1e-12)
     e = E.estimate(A, 0, 0, 0, 1e-12, 0, sketch_identity=True, omega_identity=True)
@@ -50,7 +50,7 @@ def test_rank_deficient_identity_mode_matches_leverage_of_A():
 
 
 def test_sketch_preserves_leverage_with_omega_identity():
-    """Pi_1 = GS an OSE: theta~(Omega = I) within (1 +- eps)^-2 of theta (Sec. 2.2, Alg. 8)."""
+    """Pi_1 = GS an OSE: theta~(Omega = I) within (1 +- eps)^-2 of theta (Sec. 3.3, Alg. 8)."""
     A = W.dense_gaussian(4000, 8, 3)
     th, _ = exact.exact_leverage_qr(A, 1e-12)
     d = 8
@@ -62,7 +62,7 @@ def test_sketch_preserves_leverage_with_omega_identity():
 
 
 def test_jl_tail_per_row():
-    """theta~_i / theta_i ~ chi^2_k / k when the sketch is exact; JL tail bound (Sec. 2.3.1)."""
+    """theta~_i / theta_i ~ chi^2_k / k when the sketch is exact; JL tail bound (Sec. 3.4.1)."""
     A = W.dense_gaussian(20000, 6, 7)
     th, _ = exact.exact_leverage_qr(A, 1e-12)
     k = 64
@@ -77,7 +77,7 @@ def test_jl_tail_per_row():
 
 
 def test_full_estimator_small_dense():
-    """The small dense workload: full rank 20, theta~ approximates theta (Sec. 5.2)."""
+    """The small dense workload: full rank 20, theta~ approximates theta (Sec. 6.2)."""
     cfg = W.CONFIGS["dense_2000x20_f64"]
     A = W.dense_gaussian(cfg["n"], cfg["d"], cfg["data_seed"])
     th, r = exact.exact_leverage_qr(A, cfg["tau"])
@@ -132,7 +132,7 @@ def test_final_pass_equals_mfull_product():
 
 
 def test_sketch_spectrum_bounds():
-    """Lemma spectrum_gsu (Sec. 3.2) with G scaled by 1/sqrt(m)."""
+    """Lemma 5 (the spectrum of GSU, Sec. 4.2) with G scaled by 1/sqrt(m)."""
     n, k, m, s = 20000, 10, 200, 600
     U = np.linalg.qr(np.random.default_rng(1).standard_normal((n, k)))[0]
     sv = np.linalg.svd(E.sketch(U, s, m, 21), compute_uv=False)

@@ -120,7 +120,7 @@ def _profile(spec):
 
 @pytest.mark.slow
 def test_paper_stated_ranks(golden_dir):
-    """Ranks the paper states for fixed_svd_2.5e4 and fixed_svd_1e7 (Sec. 6.2, 6.4)."""
+    """Ranks the paper states for fixed_svd_2.5e4 and fixed_svd_1e7 (Sec. 7.2, 7.4)."""
     from oracle import estimator
     for name, n, d, prof, thr, rule, want in _paper_rank_rows(golden_dir):
         n, d, thr = int(n), int(d), float(thr)
@@ -134,6 +134,6 @@ def test_paper_stated_ranks(golden_dir):
             got = linalg.pivoted_qr(A, thr).rank
             assert want == "not30" and got != 30, name
         elif rule == "qr_sketch":
-            # Alg. 4 on the CountGauss sketch with m = 2d, r = 5(d^2 + d) (Sec. 6.2)
+            # Alg. 4 on the CountGauss sketch with m = 2d, r = 5(d^2 + d) (Sec. 7.2)
             e = estimator.estimate(A, 5 * (d * d + d), 2 * d, d, thr, seed=3)
             assert e.rank == int(want), name

@@ -1,11 +1,11 @@
 """Pins of the oracle's CountGauss preconditioner (Alg. 11) and LSQR (oracle/precond.py).
 
-* Lemma on the spectrum of AN (Sec. 5.2): the singular values of A N are those of (G S U)^+, U the
+* Lemma 9 (the spectrum of AN, Sec. 6.2): the singular values of A N are those of (G S U)^+, U the
   left singular vectors of A, whatever Sigma is. With the seeded U of fixed_svd, A N therefore has
-  the same singular values for kappa(A) = 1e2 and 1e8 (the linspace spectra of Sec. 6.3), and they
+  the same singular values for kappa(A) = 1e2 and 1e8 (the linspace spectra of Sec. 7.3), and they
   equal 1 / sigma(G S U) computed directly from U.
-* The GSA preconditioning theorem: kappa(A N) <= xi eta (m = 4d, alpha = 0.3, eps = 1/2 for the
-  CountSketch size 5 (d^2 + d) of Sec. 6.2).
+* Theorem 8 (GSA preconditioning, Sec. 6.2): kappa(A N) <= xi eta (m = 4d, alpha = 0.3, eps = 1/2 for the
+  CountSketch size 5 (d^2 + d) of Sec. 7.2).
 * N y^ = A^+ b (the theorem's consistency part): against numpy's minimum-norm least squares, also
   for rank-deficient A (the tolerance zeta drops the zero singular values).
 * LSQR: N = I on a well-conditioned problem equals numpy's least squares; preconditioning cuts the

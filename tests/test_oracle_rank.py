@@ -1,7 +1,7 @@
 """Pins of the oracle's SVD rank rule and strong-RRQR swaps (oracle/rank.py).
 
-* SVD rank: matrices with known singular values (fixed_svd, Sec. 6.1's table: 15 ones, 15 at
-  1e-6, 30 at 1e-7; and 15 ones, 15 at 1e-3, 30 at 4e-5) give the rank the table and Sec. 6.4
+* SVD rank: matrices with known singular values (fixed_svd, Sec. 7.1's table: 15 ones, 15 at
+  1e-6, 30 at 1e-7; and 15 ones, 15 at 1e-3, 30 at 4e-5) give the rank the table and Sec. 7.4
   state at the paper's cutoffs (10^-6.5 and 2e-4), on A and on its CountGauss sketch (Lemma on the
   spectrum of GSA: the sketch keeps each singular value within a constant factor, far inside a
   gap of 10).
@@ -103,7 +103,7 @@ def test_measures_against_definitions():
 
 
 def test_estimate_with_svd_rank_on_fixed_svd_2_5e4():
-    """Sec. 6.4's case: fixed_svd_2.5e4 with the cutoff 2e-4 has numerical rank 30; the estimate
+    """Sec. 7.4's case: fixed_svd_2.5e4 with the cutoff 2e-4 has numerical rank 30; the estimate
     with the SVD rule finds it, and equals the forced-pivot estimate at those columns."""
     sig = np.concatenate([np.ones(15), np.full(15, 1e-3), np.full(30, 4e-5)])
     A = W.fixed_svd(4000, 60, sig, seed=7)

@@ -1,4 +1,4 @@
-"""Pins for the oracle's SRHT (Sec. 2.3.2) and the CountSketch + SRHT + Gaussian sketch (Sec. 3.1).
+"""Pins for the oracle's SRHT (Sec. 3.4.2) and the CountSketch + SRHT + Gaussian sketch (Sec. 4.1).
 
 The Walsh-Hadamard transform against scipy's Hadamard matrix and its involution, the sign and
 row draws against their distributions, the subspace-embedding bounds of the SRHT theorem the

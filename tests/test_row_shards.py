@@ -1,7 +1,7 @@
 """Row shards on CPU: the oracle's block sketches, the host logic of the sharded path, and its one
 collective over world-size-2 gloo.
 
-The CountSketch S is one fixed s x n matrix (Sec. 2.3.3), so for a partition of the rows into
+The CountSketch S is one fixed s x n matrix (Sec. 3.4.3), so for a partition of the rows into
 blocks P_p, S A = sum_p S_{:,P_p} A_{P_p,:} (block matrix product), and G (and the SRHT F) act
 linearly on S A. The pins: each block's sketch against an explicit S built row by row from the
 hash, the sum of the blocks against the whole matrix's sketch, and the sharded estimate (sum of

@@ -7,7 +7,7 @@ so both the CPU oracle and the CUDA path can read the same bytes from it.
 Every generator uses ``numpy.random.default_rng(seed)`` (PCG64), computes in
 FP64 and rounds to the requested storage type at the end.
 
-Workload shapes (the paper's own datasets, timg80 and kl02 of Sec. 6.1, are
+Workload shapes (the paper's own datasets, timg80 and kl02 of Sec. 7.1, are
 not available; these stand in for them with the same roles):
 
 * ``dense_gaussian``      -- small full-rank dense matrix (correctness case).
@@ -17,12 +17,12 @@ not available; these stand in for them with the same roles):
                              row plus a small fraction of heavy rows.
 * ``dense_heavy_rows``    -- N(0,1) dense matrix with a fraction of rows x100
                              (the backward-pass workload) and U(0,1) weights.
-* ``csr_dup_columns``     -- tall CSR matrix shaped like timg80 (Sec. 6.1,
-                             Table 2: 79,302,017 x 1,024) with column pairs
+* ``csr_dup_columns``     -- tall CSR matrix shaped like timg80 (Sec. 7.1,
+                             Table 6: 79,302,017 x 1,024) with column pairs
                              made exactly dependent (column j+d/2 = 2 x col j).
 * ``fixed_svd``           -- dense matrix with a prescribed singular-value
                              profile and seeded Haar-orthogonal factors (the
-                             fixed_svd_* matrices of Sec. 6.1).
+                             fixed_svd_* matrices of Sec. 7.1).
 """
 from __future__ import annotations
 
