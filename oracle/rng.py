@@ -82,15 +82,26 @@ def srht_rows(t: int, s: int, seed: int) -> np.ndarray:
     return (((x >> np.uint64(32)) * np.uint64(s)) >> np.uint64(32)).astype(np.int64)
 
 
+def unit_open_closed(x) -> np.ndarray:
+    """u in (0, 1] from a 64-bit word: ((x >> 11) + 1) 2^-53 (the u1 of Box-Muller, never 0)."""
+    return ((np.asarray(x, dtype=np.uint64) >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+
+
+def unit_closed_open(x) -> np.ndarray:
+    """u in [0, 1) from a 64-bit word: (x >> 11) 2^-53 (the u2 of Box-Muller)."""
+    return (np.asarray(x, dtype=np.uint64) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
 def gaussian(seed: int, stream: int, counters) -> np.ndarray:
-    """Box-Muller standard normals (FP64) for the given counters of a stream."""
+    """Box-Muller standard normals (FP64) for the given counters of a stream: sqrt(-2 ln u1)
+    cos(2 pi u2), cosine branch only (the generator definition of the random streams)."""
     c = np.asarray(counters, dtype=np.uint64)
     key = stream_key(seed, stream)
     with np.errstate(over="ignore"):
         x1 = splitmix64(key, np.uint64(2) * c)
         x2 = splitmix64(key, np.uint64(2) * c + np.uint64(1))
-    u1 = ((x1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
-    u2 = (x2 >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    u1 = unit_open_closed(x1)
+    u2 = unit_closed_open(x2)
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
 
 

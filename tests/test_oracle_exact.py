@@ -137,3 +137,13 @@ def test_paper_stated_ranks(golden_dir):
             # Alg. 4 on the CountGauss sketch with m = 2d, r = 5(d^2 + d) (Sec. 7.2)
             e = estimator.estimate(A, 5 * (d * d + d), 2 * d, d, thr, seed=3)
             assert e.rank == int(want), name
+
+
+def test_gram_blocks_sum_to_the_gram_matrix():
+    """Lemma 8 (Sec. 5.1): A^T A as the sum over row blocks of their outer products, dense and
+    CSR, with blocks far smaller than n (the sum of all blocks, not the last one)."""
+    import scipy.sparse as sp
+    A = np.random.default_rng(3).standard_normal((103, 7))
+    np.testing.assert_allclose(exact.gram(A, block=16), A.T @ A, rtol=1e-13, atol=1e-12)
+    C = sp.random(103, 7, density=0.3, random_state=4, format="csr")
+    np.testing.assert_allclose(exact.gram(C, block=10), (C.T @ C).toarray(), rtol=1e-13, atol=1e-12)

@@ -129,3 +129,24 @@ def test_sketch_gaussian_entries_are_bf16_draws():
     bits = z.astype(np.float32).view(np.uint32)
     assert np.all(bits & 0xFFFF == 0) and np.all(z.astype(np.float32) == z)
     assert abs(z.mean()) < 0.02 and abs(z.var() - 1) < 0.02
+
+
+def test_gaussian_sketch_entry_j_b_is_draw_j_s_plus_b():
+    """G[j, b] is draw number j*s + b of the G stream (row-major counters, the published
+    definition), for entries spread over rows, columns and the block boundaries."""
+    m, s, seed = 48, 1000, 6
+    G = rng.gaussian_sketch_block(m, s, seed, 0, s)
+    for j, b in [(0, 0), (0, 999), (1, 0), (17, 313), (47, 999), (30, 1)]:
+        z = rng.bf16_round(rng.gaussian(seed, rng.STREAM_G, [j * s + b]))[0]
+        assert G[j, b] == z / np.sqrt(m)
+    assert G[1, 0] != G[0, 1]
+
+
+def test_uniform_maps_hit_their_interval_ends():
+    """u1 lies in (0, 1] and u2 in [0, 1), 53-bit grids: the all-zero word gives 2^-53 and 0, the
+    all-ones word 1 and 1 - 2^-53 exactly (so ln u1 is finite and u1 = 1 is reachable)."""
+    lo, hi = np.uint64(0), np.uint64(0xFFFFFFFFFFFFFFFF)
+    assert rng.unit_open_closed(lo) == 2.0 ** -53 and rng.unit_open_closed(hi) == 1.0
+    assert rng.unit_closed_open(lo) == 0.0 and rng.unit_closed_open(hi) == 1.0 - 2.0 ** -53
+    # consecutive words above bit 11 step by exactly 2^-53
+    assert rng.unit_open_closed(np.uint64(1 << 11)) - rng.unit_open_closed(lo) == 2.0 ** -53

@@ -55,3 +55,12 @@ def test_ls_hrn_exact_with_srht_sketch_is_exact_at_full_rank():
     assert k == 10
     H = A @ np.linalg.pinv(A.T @ A) @ A.T
     np.testing.assert_allclose(th, np.diag(H), rtol=0, atol=1e-10)
+
+
+def test_srht_rows_are_the_top_bits_for_a_power_of_two_s():
+    """Multiply-shift of the high word: for s = 2^q a row is the top q bits of the high word of
+    stream 5 (a modulo would take the low ones)."""
+    s, t, seed = 1 << 10, 300, 4
+    x = rng.splitmix64(rng.stream_key(seed, rng.STREAM_SRHT_ROWS), np.arange(t))
+    top = (x >> np.uint64(54)).astype(np.int64)
+    assert np.array_equal(rng.srht_rows(t, s, seed), top)
