@@ -39,8 +39,9 @@ def kappa_bound(k: int, m: int, alpha: float, eps: float) -> float:
     return (1 + alpha + q) / (1 - alpha - q) * (1 + eps) / (1 - eps)
 
 
-def lsqr(A, b, N, max_iter: int = 1000, atol: float = 1e-14, btol: float = 1e-14):
-    """min_y ||A N y - b|| by LSQR; returns (x = N y, y, iterations, ||r|| estimate)."""
+def lsqr(A, b, N, max_iter: int = 1000, atol: float = 1e-14, btol: float = 1e-14, return_anorm: bool = False):
+    """min_y ||A N y - b|| by LSQR (Paige and Saunders); returns (x = N y, y, iterations, ||r||
+    estimate), and with ``return_anorm`` also the ||A N||_F estimate of the stopping rule."""
     A = np.asarray(A, dtype=np.float64) if not hasattr(A, "tocsr") else A.astype(np.float64)
     b = np.asarray(b, dtype=np.float64)
     B = lambda v: A @ (N @ v)
@@ -48,12 +49,12 @@ def lsqr(A, b, N, max_iter: int = 1000, atol: float = 1e-14, btol: float = 1e-14
     y = np.zeros(N.shape[1])
     beta = np.linalg.norm(b)
     if beta == 0:
-        return N @ y, y, 0, 0.0
+        return (N @ y, y, 0, 0.0) + ((0.0,) if return_anorm else ())
     u = b / beta
     v = Bt(u)
     alpha = np.linalg.norm(v)
     if alpha == 0:
-        return N @ y, y, 0, beta
+        return (N @ y, y, 0, beta) + ((0.0,) if return_anorm else ())
     v = v / alpha
     w = v.copy()
     phibar, rhobar = beta, alpha
@@ -79,4 +80,4 @@ def lsqr(A, b, N, max_iter: int = 1000, atol: float = 1e-14, btol: float = 1e-14
         w = v - (theta / rho) * w
         if phibar * alpha * abs(c) <= atol * np.sqrt(bnorm2) * phibar or phibar <= btol * np.linalg.norm(b):
             break
-    return N @ y, y, it, phibar
+    return (N @ y, y, it, phibar) + ((float(np.sqrt(bnorm2)),) if return_anorm else ())

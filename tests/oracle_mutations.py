@@ -71,6 +71,21 @@ MUTS = [
     ("backward.py", "return 2.0 * (np.eye(n) - H)", "return 2.0 * (np.eye(n) + H)", "exact gradient I + H"),
     ("backward.py", "Rbar = -solve_triangular", "Rbar = solve_triangular", "Rbar sign"),
     ("backward.py", "T_rows = sign[:, None] * Gt[b]", "T_rows = Gt[b]", "S^T signs dropped"),
+    ("estimator.py", "At += rng.gaussian_sketch_block(m, s, seed, c0, c1) @ B[c0:c1]",
+     "At = rng.gaussian_sketch_block(m, s, seed, c0, c1) @ B[c0:c1]", "Gaussian-stage blocks not summed"),
+    ("estimator.py", "B += prod.toarray() if sp.issparse(prod) else prod",
+     "B = prod.toarray() if sp.issparse(prod) else prod", "CountSketch blocks not summed"),
+    ("rank.py", "sgn = np.where(np.diag(R) < 0, -1.0, 1.0)", "sgn = np.ones(R.shape[0])", "r_factor signs"),
+    ("precond.py", "k = rank_svd(sig, zeta)", "k = rank_svd(sig, zeta * zeta)", "Alg. 11 rank zeta^2"),
+    ("precond.py", "phibar * alpha * abs(c) <= atol", "phibar * alpha * c <= atol", "LSQR stop without |c|"),
+    ("precond.py", "bnorm2 += alpha * alpha + beta * beta", "bnorm2 += alpha * alpha", "LSQR norm estimate"),
+    ("exact.py", "B = gram(A_K, block)", "B = gram(A, block)", "Alg. 7 Gram of all columns"),
+    ("exact.py", "Q = qr.q_thin(qr.rank)", "Q = qr.q_thin(max(qr.rank - 1, 1))", "thin Q one column short"),
+    ("linalg.py", "return Q * self._signs[None, :cols]", "return Q", "thin Q signs"),
+    ("rng.py", "    return np.where((x & np.uint64(1)) == 0, 1.0, -1.0)\n\n\ndef srht_rows",
+     "    return np.where((x & np.uint64(2)) == 0, 1.0, -1.0)\n\n\ndef srht_rows", "SRHT sign bit"),
+    ("rng.py", "return (int(seed) ^ ((stream * _STREAM_MUL) & _MASK64)) & _MASK64",
+     "return (int(seed) + ((stream * _STREAM_MUL) & _MASK64)) & _MASK64", "stream key by addition"),
 ]
 
 

@@ -79,3 +79,17 @@ def test_lsqr_plain_and_iteration_counts():
     it_pre = P.lsqr(A, b, N, atol=1e-10, btol=1e-10)[2]
     it_plain = P.lsqr(A, b, np.eye(D), atol=1e-10, btol=1e-10, max_iter=2000)[2]
     assert it_pre < 40 and it_plain > 3 * it_pre
+
+
+def test_lsqr_norm_estimate_closed_form():
+    """The ||A N||_F estimate of the stopping rule (Paige and Saunders): with orthonormal columns
+    and N = I, LSQR ends after one step and A v_1 = alpha_1 u_1 + beta_2 u_2, so the estimate
+    sqrt(alpha_1^2 + alpha_2^2 + beta_2^2) is ||A v_1|| = 1 (alpha_2 = 0)."""
+    rs = np.random.default_rng(8)
+    Q = np.linalg.qr(rs.standard_normal((300, 12)))[0]
+    b = rs.standard_normal(300)
+    x, y, it, rn, an = P.lsqr(Q, b, np.eye(12), atol=1e-12, btol=1e-12, return_anorm=True)
+    assert it == 1
+    assert abs(an - 1.0) < 1e-12
+    np.testing.assert_allclose(x, Q.T @ b, atol=1e-12)
+    np.testing.assert_allclose(rn, np.linalg.norm(b - Q @ (Q.T @ b)), rtol=1e-12)

@@ -117,3 +117,14 @@ def test_estimate_with_svd_rank_on_fixed_svd_2_5e4():
     R = K.r_factor(g.Atilde, g.perm)
     rho = K.srrqr_measures(R, 30)[0]
     assert rho.max() <= 2.0
+
+
+def test_r_factor_has_a_nonnegative_diagonal():
+    """R of the QR at a column order, normalised to diag(R) >= 0: numpy's R up to row signs."""
+    rs = np.random.default_rng(12)
+    X = rs.standard_normal((40, 9))
+    perm = rs.permutation(9)
+    R = K.r_factor(X, perm)
+    assert np.all(np.diag(R) >= 0)
+    np.testing.assert_allclose(np.abs(R), np.abs(np.linalg.qr(X[:, perm], mode="r")), atol=1e-12)
+    np.testing.assert_allclose(R.T @ R, X[:, perm].T @ X[:, perm], atol=1e-10)

@@ -150,3 +150,14 @@ def test_uniform_maps_hit_their_interval_ends():
     assert rng.unit_closed_open(lo) == 0.0 and rng.unit_closed_open(hi) == 1.0 - 2.0 ** -53
     # consecutive words above bit 11 step by exactly 2^-53
     assert rng.unit_open_closed(np.uint64(1 << 11)) - rng.unit_open_closed(lo) == 2.0 ** -53
+
+
+def test_stream_key_is_a_xor():
+    """key_t = seed XOR (t C mod 2^64): XOR with key_t(0) gives the seed back, and seed t C gives 0."""
+    C = 0xD1B54A32D192ED03
+    for t in (1, 2, 3, 4, 5):
+        base = rng.stream_key(0, t)
+        assert base == (t * C) % (1 << 64)
+        for seed in (0, 1, 12345, (1 << 64) - 1):
+            assert rng.stream_key(seed, t) ^ base == seed
+        assert rng.stream_key(base, t) == 0

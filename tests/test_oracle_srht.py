@@ -64,3 +64,11 @@ def test_srht_rows_are_the_top_bits_for_a_power_of_two_s():
     x = rng.splitmix64(rng.stream_key(seed, rng.STREAM_SRHT_ROWS), np.arange(t))
     top = (x >> np.uint64(54)).astype(np.int64)
     assert np.array_equal(rng.srht_rows(t, s, seed), top)
+
+
+def test_srht_signs_are_bit_0_of_stream_4():
+    """D of the SRHT: +1 where bit 0 of the stream-4 word is 0, else -1 (the published definition)."""
+    x = rng.splitmix64(rng.stream_key(5, rng.STREAM_SRHT_SIGN), np.arange(256))
+    want = np.where((x & np.uint64(1)) == 0, 1.0, -1.0)
+    assert np.array_equal(rng.srht_signs(256, 5), want)
+    assert np.array_equal(rng.srht_signs(256, 5), rng.srht_signs(300, 5)[:256])
