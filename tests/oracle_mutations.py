@@ -86,6 +86,22 @@ MUTS = [
      "    return np.where((x & np.uint64(2)) == 0, 1.0, -1.0)\n\n\ndef srht_rows", "SRHT sign bit"),
     ("rng.py", "return (int(seed) ^ ((stream * _STREAM_MUL) & _MASK64)) & _MASK64",
      "return (int(seed) + ((stream * _STREAM_MUL) & _MASK64)) & _MASK64", "stream key by addition"),
+    ("estimator.py", "forced_perm = rank_mod.srrqr(Atilde, forced_rank, srrqr_phi, forced_perm)[0]",
+     "forced_perm = rank_mod.srrqr(Atilde, max(forced_rank - 1, 0), srrqr_phi, forced_perm)[0]",
+     "Alg. 10 SRRQR at rank - 1"),
+    ("estimator.py", "forced_rank = rank_mod.rank_svd(rank_mod.singular_values(Atilde), tau)",
+     "forced_rank = rank_mod.rank_svd(rank_mod.singular_values(Atilde.T @ Atilde), tau)",
+     "SVD rule on the Gram matrix"),
+    ("linalg.py", "trailing = np.sqrt(np.sum(W[j:, j:] ** 2, axis=0))",
+     "trailing = np.sqrt(np.sum(W[:, j:] ** 2, axis=0))", "trailing norms include eliminated rows"),
+    ("exact.py", "X = V[:, :k] / np.sqrt(lam[:k])[None, :]", "X = V[:, :k] * np.sqrt(lam[:k])[None, :]",
+     "Gram route scaled the wrong way"),
+    ("estimator.py", "X = fwht(rng.srht_signs(s, seed)[:, None] * B)",
+     "X = rng.srht_signs(s, seed)[:, None] * fwht(B)", "SRHT as D H instead of H D"),
+    ("backward.py", 'C @ M.T, lower=False, trans="T")', 'C @ M.T, lower=False, trans="N")',
+     "adjoint solve not transposed"),
+    ("rng.py", "return gaussian(seed, STREAM_OMEGA, idx) / np.sqrt(k)",
+     "return gaussian(seed, STREAM_G, idx) / np.sqrt(k)", "Omega from the G stream"),
 ]
 
 

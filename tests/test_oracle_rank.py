@@ -128,3 +128,40 @@ def test_r_factor_has_a_nonnegative_diagonal():
     assert np.all(np.diag(R) >= 0)
     np.testing.assert_allclose(np.abs(R), np.abs(np.linalg.qr(X[:, perm], mode="r")), atol=1e-12)
     np.testing.assert_allclose(R.T @ R, X[:, perm].T @ X[:, perm], atol=1e-10)
+
+
+def test_estimate_takes_srrqr_swaps_at_the_svd_rank():
+    """Alg. 10 with the SVD rank rule and strong RRQR (identity sketch, so A~ = A): on the Kahan
+    matrix the SVD rule gives k = n - 1; at phi = 1.05 the greedy pivoted order breaks the SRRQR
+    bounds there, and the estimate's columns are the swaps at that k from that order, which meet
+    every bound."""
+    n, phi = 30, 1.05
+    A = _kahan(n)
+    sA = K.singular_values(A)
+    zeta = 10 * sA[-1] / sA[0]
+    assert sA[-2] > zeta * sA[0]
+    greedy = pivoted_qr(A, 0.0).perm
+    assert not _bounds_hold(A, greedy, n - 1, phi)
+    e = E.estimate(A, 0, 0, 0, zeta, 0, sketch_identity=True, omega_identity=True, rank_rule="svd",
+                   srrqr_phi=phi)
+    assert e.rank == n - 1
+    assert _bounds_hold(A, e.perm, n - 1, phi)
+    assert np.array_equal(e.perm, K.srrqr(A, n - 1, phi, greedy)[0])
+
+
+def test_estimate_srrqr_uses_the_rank_it_found():
+    """The swaps run at the rank the SVD rule finds (k = 8 of 12 on a seeded rank-8 matrix with
+    noise 1e-10): at phi = 1.0001 they pick a different column set than swaps at k - 1 would, and
+    the result is the strong-RRQR order at k from the greedy start."""
+    rs = np.random.default_rng(3)
+    U = np.linalg.qr(rs.standard_normal((200, 8)))[0]
+    A = U @ np.diag(np.logspace(0, -2, 8)) @ rs.standard_normal((8, 12)) + 1e-10 * rs.standard_normal((200, 12))
+    phi = 1.0001
+    e = E.estimate(A, 0, 0, 0, 1e-6, 0, sketch_identity=True, omega_identity=True, rank_rule="svd",
+                   srrqr_phi=phi)
+    assert e.rank == 8
+    greedy = pivoted_qr(A, 0.0).perm
+    want = K.srrqr(A, 8, phi, greedy)[0]
+    assert np.array_equal(e.perm, want)
+    assert set(want[:8].tolist()) != set(K.srrqr(A, 7, phi, greedy)[0][:8].tolist())
+    assert K.srrqr_measures(K.r_factor(A, e.perm), 8)[0].max() <= phi

@@ -72,3 +72,17 @@ def test_srht_signs_are_bit_0_of_stream_4():
     want = np.where((x & np.uint64(1)) == 0, 1.0, -1.0)
     assert np.array_equal(rng.srht_signs(256, 5), want)
     assert np.array_equal(rng.srht_signs(256, 5), rng.srht_signs(300, 5)[:256])
+
+
+def test_srht_equals_its_explicit_matrix_product():
+    """F = sqrt(s/t) P H D (Sec. 3.4.2) built as explicit matrices (scipy's Sylvester Hadamard
+    scaled by 1/sqrt(s), the stream-4 signs on the diagonal of D, the stream-5 rows in P): F B
+    equals the oracle's srht(B); D acts before H."""
+    s, t, seed = 64, 20, 3
+    B = np.random.default_rng(0).standard_normal((s, 5))
+    H = scipy.linalg.hadamard(s) / np.sqrt(s)
+    D = np.diag(rng.srht_signs(s, seed))
+    P = np.zeros((t, s))
+    P[np.arange(t), rng.srht_rows(t, s, seed)] = 1.0
+    F = np.sqrt(s / t) * P @ H @ D
+    np.testing.assert_allclose(E.srht(B, t, seed), F @ B, atol=1e-12)
