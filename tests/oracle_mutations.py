@@ -102,6 +102,15 @@ MUTS = [
      "adjoint solve not transposed"),
     ("rng.py", "return gaussian(seed, STREAM_OMEGA, idx) / np.sqrt(k)",
      "return gaussian(seed, STREAM_G, idx) / np.sqrt(k)", "Omega from the G stream"),
+    ("exact.py", "order = np.argsort(lam)[::-1]", "order = np.argsort(lam)", "Gram eigenvalues ascending"),
+    ("backward.py", "    Om = np.eye(r) if omega_identity else rng.omega(r, k, seed)\n    M = solve_triangular(R11, Om, lower=False)\n    Y = AK @ M\n    return",
+     "    Om = np.eye(r) if omega_identity else rng.omega(r, k, seed)\n    M = solve_triangular(R11.T, Om, lower=True)\n    Y = AK @ M\n    return",
+     "theta_fixed solves with R^T"),
+    ("rank.py", "dets.append(float(np.prod(np.abs(np.diag(R)[:k]))))",
+     "dets.append(float(np.prod(np.abs(np.diag(R)[:k + 1]))))", "SRRQR det over k + 1"),
+    ("rng.py", "np.arange(start, start + n, dtype=np.uint64))", "np.arange(n, dtype=np.uint64))", "hash ignores start"),
+    ("linalg.py", "Q[j:, :] -= np.outer(v, beta * (v @ Q[j:, :]))", "Q[j:, :] += np.outer(v, beta * (v @ Q[j:, :]))",
+     "thin Q reflector sign"),
 ]
 
 
