@@ -112,3 +112,15 @@ def test_default_handle_is_per_thread(lev, monkeypatch):
     t.join()
     assert got["a"] is got["b"] and got["a"] is not h0
     assert len(made) == 3
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU or library fallback: the binding without liblev.so refuses to import."""
+    import shutil
+    import sys
+    shutil.copytree(os.path.join(ROOT, "paper_2105_11004_gb300"), tmp_path / "paper_2105_11004_gb300",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__", "csrc"))
+    r = subprocess.run([sys.executable, "-c", "import paper_2105_11004_gb300"], cwd=tmp_path, capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "liblev.so is not built" in r.stderr
