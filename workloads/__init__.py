@@ -172,9 +172,7 @@ def csr_dup_columns(n: int, d: int, nnz_per_row: int = 12, pairs: int = 10,
         nb = r1 - r0
         c = free[_distinct_sorted_columns(rng, nb, nnz_per_row, free.size)]
         v = rng.standard_normal((nb, nnz_per_row))
-        has = c[:, 0] < pairs                            # sorted, so a pair column is first
-        # a row can hold several pair columns; handle them generally
-        pmask = c < pairs
+        pmask = c < pairs                                # a row can hold several pair columns
         extra = pmask.sum(axis=1)
         counts[r0:r1] = nnz_per_row + extra
         if extra.any():
@@ -189,7 +187,6 @@ def csr_dup_columns(n: int, d: int, nnz_per_row: int = 12, pairs: int = 10,
         else:
             rows_cols.append(c.ravel().astype(np.int32))
             rows_vals.append(v.ravel())
-        del has
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=row_ptr[1:])
     col = np.concatenate(rows_cols)
