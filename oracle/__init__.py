@@ -5,7 +5,7 @@ CPU-baseline leg of ``bench.py`` may import this package. The CUDA library in
 ``paper_2105_11004_gb300`` shares no code with it and never calls it.
 
 Contents:
-* ``oracle.rng``       -- splitmix64 hash/sign, Box-Muller streams, BF16 rounding of G;
+* ``oracle.rng``       -- splitmix64 hash/sign, Box-Muller streams, entries of G and Omega;
 * ``oracle.linalg``    -- column-pivoted Householder QR, back-substitution;
 * ``oracle.exact``     -- exact leverage scores (QR route, Gram route Alg. 5), Alg. 7;
 * ``oracle.estimator`` -- Alg. 10 step by step (Alg. 3 -> Alg. 4 -> Alg. 8), SRHT variant;

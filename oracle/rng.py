@@ -21,11 +21,9 @@ generator (Steele, Lea and Flood, OOPSLA 2014) used as a pure function of
   u1 = ((splitmix64(key_t, 2c) >> 11) + 1) * 2^-53 in (0, 1],
   u2 = (splitmix64(key_t, 2c+1) >> 11) * 2^-53 in [0, 1),
   g = sqrt(-2 ln u1) * cos(2 pi u2).
-* Entries of the Gaussian sketch G (stream 2): Z_c / sqrt(m) with Z_c the draw rounded to FP32
-  and then to BF16 (8-bit significand), both to nearest even. Reading: the paper's G is Gaussian;
-  the BF16 rounding moves each entry by at most 2^-9 of itself (the singular values of G U by
-  about as much, inside the slack of the embedding lemmas of Sec. 4.2), and makes G exact in the
-  tensor cores' 16-bit operand type, so that G B needs no split of G.
+* Entries of the Gaussian sketch G (stream 2): N_c / sqrt(m), the FP64 draw itself scaled as a
+  Gaussian embedding (Sec. 3.4.1). The paper's G is Gaussian; no rounding of the draws is part of
+  the method.
 
 Reading note (the paper asks for 2-wise independent h and 4-wise independent
 signs, Sec. 3.4.3): splitmix64 is not provably k-wise independent; it is used
@@ -105,23 +103,14 @@ def gaussian(seed: int, stream: int, counters) -> np.ndarray:
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
 
 
-def bf16_round(x) -> np.ndarray:
-    """x (FP64) rounded to FP32, then to BF16 (8-bit significand), both to nearest even; as FP64."""
-    f = np.asarray(x, dtype=np.float64).astype(np.float32)
-    bits = f.view(np.uint32).astype(np.uint64)
-    bits = (bits + np.uint64(0x7FFF) + ((bits >> np.uint64(16)) & np.uint64(1))) & np.uint64(0xFFFF0000)
-    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
-
-
 def sketch_gaussian(seed: int, counters, m: int) -> np.ndarray:
-    """Entries of G by counter: Z / sqrt(m), Z = bf16_round(N_c) (the BF16 rounding of the
-    counter's Box-Muller draw, Sec. 3.4.1 scaling)."""
-    return bf16_round(gaussian(seed, STREAM_G, counters)) / np.sqrt(m)
+    """Entries of G by counter: N_c / sqrt(m), N_c the counter's Box-Muller draw (stream 2; the
+    Gaussian embedding of Sec. 3.4.1 scaled by 1/sqrt(m))."""
+    return gaussian(seed, STREAM_G, counters) / np.sqrt(m)
 
 
 def gaussian_sketch_block(m: int, s: int, seed: int, c0: int, c1: int) -> np.ndarray:
-    """Columns c0..c1-1 of G (m x s): G[j, b] = Z_{j*s+b} / sqrt(m), Z the BF16 rounding of the
-    draw N_{j*s+b}."""
+    """Columns c0..c1-1 of G (m x s): G[j, b] = N_{j*s+b} / sqrt(m)."""
     j = np.arange(m, dtype=np.uint64)[:, None]
     b = np.arange(c0, c1, dtype=np.uint64)[None, :]
     with np.errstate(over="ignore"):
