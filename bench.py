@@ -569,7 +569,7 @@ def csr_timing(L, h, name, reps):
     lens = np.diff(C.row_ptr).astype(np.float64)
     out["exact"] = {"algorithm": "Alg. 7 (LS-HRN-exact), lev_exact_csr", "rank": r_e, "ms_per_call": ms_e,
                     "rows_per_s": n / (ms_e * 1e-3), "gram_pairs": float(np.sum(lens * (lens + 1) / 2)),
-                    "note": "two host synchronisations per call (after each factorisation)"}
+                    "note": "three host synchronisations per call (after each factorisation and after counting the long rows)"}
     return out
 
 

@@ -42,9 +42,10 @@
  *    (hi32(x) * s) >> 32, sign = +1 if bit 0 of x is 0 else -1;
  *  - N(0,1) number c of stream t: Box-Muller, cosine branch, with
  *    u1 = ((splitmix64(key_t, 2c) >> 11) + 1) 2^-53, u2 = (splitmix64(key_t, 2c+1) >> 11) 2^-53;
- *  - G[j, b] = Z_{j*s + b} / sqrt(m) (Sec. 3.4.1 scaling) with Z_c the BF16 rounding (to nearest
- *    even) of the FP32 rounding of N_c, so that G is exact in the tensor cores' 16-bit operand
- *    type; Omega[p, q] = N_{p*k + q} / sqrt(k), p the pivot position (0 <= p < r), q < k.
+ *  - G[j, b] = N_{j*s + b} / sqrt(m) (a Gaussian embedding, Sec. 3.4.1 scaling) for the draws N_c
+ *    of stream 2; the tensor-core forms of the Gaussian stage take fl32(N_c) in their operand type
+ *    (the BF16 hi + lo pair with LEV_BF16X3, about 2^-17 of N_c) and apply 1/sqrt(m) in FP32;
+ *    Omega[p, q] = N_{p*k + q} / sqrt(k) (stream 3), p the pivot position (0 <= p < r), q < k.
  */
 #ifndef LEV_H
 #define LEV_H
@@ -67,8 +68,7 @@ extern "C" {
 #define LEV_FP32    0   /* FP32 SIMT FMA */
 #define LEV_TF32    1   /* tcgen05 kind::tf32, FP32 accumulate */
 #define LEV_BF16    2   /* tcgen05 kind::f16 with BF16 operands, FP32 accumulate */
-#define LEV_BF16X3  3   /* split hi+lo BF16 of FP32 operands, FP32 accumulate: hi*hi + lo*hi + hi*lo in
-                           the final pass; Z*B_hi + Z*B_lo in the Gaussian stage (G exact in BF16) */
+#define LEV_BF16X3  3   /* split hi+lo BF16 of FP32 operands, FP32 accumulate: hi*hi + lo*hi + hi*lo */
 
 /* Flags (lev_params.flags). */
 #define LEV_OMEGA_IDENTITY  1u  /* Omega = I_r, k = r (the Pi_2-free mode of Sec. 7.4) */
@@ -162,11 +162,19 @@ int lev_sketch_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, co
                    int64_t n, int64_t d, int64_t nnz, const lev_params* p,
                    float* Atilde, void* stream);
 
-/* Column-pivoted Householder QR of the sketch in FP64 (Alg. 4 step 2, with the
- * xGEQP3-style pivoting of Sec. 7): at step j the remaining column with the
- * largest trailing norm (recomputed exactly, ties to the lowest original index)
- * becomes column j; the factorisation stops at the first j with
- * |R_jj| <= tau |R_00| and *rank = j (Sec. 7.2 rank check); diag(R) >= 0.
+/* Column-pivoted QR of the sketch in FP64 (Alg. 4 step 2, with the xGEQP3-style
+ * pivoting of Sec. 7): at step j the remaining column with the largest trailing
+ * norm (recomputed exactly, ties to the lowest original index) becomes column j;
+ * the factorisation stops at the first j with |R_jj| <= tau |R_00| and
+ * *rank = j (Sec. 7.2 rank check); diag(R) >= 0. Two routes give the same pivots,
+ * rank and R (identical in exact arithmetic):
+ *  - d <= 1024 and tau >= 1e-6: the Gram matrix A~^T A~ (products of the FP32
+ *    entries exact, sums compensated to about FP64 accuracy), then a pivoted
+ *    Cholesky factorisation of it in FP64 (the squared trailing norms of the QR
+ *    are the diagonal of its Schur complements); R then agrees with the
+ *    Householder R to about u kappa(R_11)^2 relative, and ranks are resolved down
+ *    to about 1e-7 of |R_00|, hence the tau condition;
+ *  - otherwise a column-pivoted Householder QR in FP64 on one cooperative grid.
  * Atilde: device, m x d FP32 row-major (ld = d). perm: device, d int32; entries
  * 0..r-1 are the pivots in order, r..d-1 the other columns in increasing order.
  * R: device, d x d FP64 row-major; rows 0..r-1 hold [R_11 R_12] in pivoted
@@ -335,23 +343,6 @@ int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
 /* Device-side status word of the handle: nonzero after a bounded wait gave up. */
 int lev_device_status(lev_handle* h, int32_t* status);
 
-/* lev_rrqr without any allocation. The paper has no counterpart: this entry
- * point exists for callers that cannot call cudaMalloc -- code that lives inside
- * another allocator's fixed memory budget (for example a serving framework's
- * pool) and latency-critical paths that cannot afford the implicit device
- * synchronisation of cudaMalloc/cudaFree. It computes exactly what lev_rrqr
- * computes (same kernels, same arguments and results; no handle), on the
- * calling thread's current device, with its scratch in a fixed 8 MiB device
- * array that every GPU which loads the library holds until the process exits.
- * Limit: the QR working set (about 8 (m d + 2 d^2) bytes plus the partial sums
- * of the Gram matrix) must fit in 8 MiB; for example m = 1024, d = 256 uses
- * 5.6 MiB. Larger shapes return LEV_EINVAL.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call clears what must start at zero; all calls share the one array,
- * so calls that overlap on the GPU (different streams, or different host
- * threads) race and give wrong results. Errors: LEV_EINVAL, LEV_ECUDA,
- * LEV_ETIMEOUT, LEV_ERANK0. */
 /* Diagnostics (no counterpart in the paper). With timing on (enable != 0) every pivoted QR of
  * the handle (lev_rrqr and the rrqr stage of lev_estimate_*) records CUDA events on its stream
  * before the factorisation, after the Gram product with its reduction (Gram route; nothing
@@ -363,6 +354,28 @@ int lev_device_status(lev_handle* h, int32_t* status);
 int lev_set_timing(lev_handle* h, int enable);
 int lev_rrqr_timing(lev_handle* h, float* gram_ms, float* factor_ms);
 
+/* lev_rrqr without any allocation. The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code that lives inside
+ * another allocator's fixed memory budget (for example a serving framework's
+ * pool) and latency-critical paths that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree. It computes exactly what lev_rrqr
+ * computes (same kernels, same arguments and results; no handle), on the
+ * calling thread's current device, with its scratch in a fixed 8 MiB device
+ * array that every GPU which loads the library holds until the process exits.
+ * Limit: the QR working set must fit in 8 MiB: about 8 (m d + 3 d^2) bytes plus,
+ * on the Gram route (lev_rrqr), the Gram matrix's partial sums (at most 4 MiB;
+ * their count follows the device's SM count, so a shape near the limit may be
+ * accepted on one GPU model and rejected on another). For example m = 1024,
+ * d = 256 fits. Larger shapes return LEV_EINVAL.
+ * The first call in a CUDA context (and the first after the current context
+ * changed, e.g. after cudaDeviceReset) looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call clears what must start at zero; all calls share the one array,
+ * so calls that overlap on the GPU (different streams, or different host
+ * threads) race and give wrong results. rank: host, may be NULL; with a rank
+ * pointer the call reads the rank into host memory and synchronises `stream`,
+ * without one it only enqueues the work. Errors: LEV_EINVAL, LEV_ECUDA,
+ * LEV_ETIMEOUT, LEV_ERANK0. */
 int lev_rrqr_noalloc(const float* Atilde, int64_t m, int64_t d, double tau,
                      int32_t* perm, double* R, int64_t* rank, void* stream);
 

@@ -342,12 +342,16 @@ def lev_backward_dense(h: Handle, A, p: lev_params, Atilde, perm, d_rank, R, Mfu
                                   _ptr(d_rank), _ptr(R), _ptr(Mfull), _ptr(w), _ptr(gradA), _stream(stream)))
 
 
-def lev_rrqr_noalloc(Atilde, tau, perm, R, stream=None) -> int:
-    """lev_rrqr without allocation (fixed device scratch; see include/lev.h)."""
+def lev_rrqr_noalloc(Atilde, tau, perm, R, stream=None, want_rank: bool = True):
+    """lev_rrqr without allocation (fixed device scratch; see include/lev.h). With want_rank=False
+    no rank pointer is passed: the call only enqueues the work and returns None."""
     m, d = Atilde.shape
     r = _i64()
-    rc = _check(lib.lev_rrqr_noalloc(_ptr(Atilde), m, d, float(tau), _ptr(perm), _ptr(R), ctypes.byref(r),
-                                     _stream(stream)), allow=(LEV_ERANK0,))
+    rc = _check(lib.lev_rrqr_noalloc(_ptr(Atilde), m, d, float(tau), _ptr(perm), _ptr(R),
+                                     ctypes.byref(r) if want_rank else None, _stream(stream)),
+                allow=(LEV_ERANK0,))
+    if not want_rank:
+        return None
     return 0 if rc == LEV_ERANK0 else r.value
 
 

@@ -212,17 +212,17 @@ int check_prec(int32_t prec, const char* what) {
 double tau_of(const lev_params* p) { return p->tau > 0 ? p->tau : 1e-5; }
 
 // Make sure G (m x s) for (seed, kind) is in the cache; returns its pointers.
-// G = Z / sqrt(m) with Z the BF16 rounding of the Gaussian draw. Kind 0: FP32
-// entries Z / sqrt(m), leading dimension s. Kind 2: Z in BF16 (exact), leading
-// dimension s rounded up to 64 (TMA rows of whole 128-byte lines); the tensor-core
-// stage applies 1 / sqrt(m) in its reduction. Kind 3: Z in FP32 (exact in TF32),
-// same padded leading dimension, same deferred scale.
+// G = N / sqrt(m) with N the FP64 counter draws. Kind 0: FP32 entries fl32(N / sqrt(m)), leading
+// dimension s. Kind 2: the BF16 pair of fl32(N), hi then lo (two m x ld images, ld = s rounded up
+// to 64: TMA rows of whole 128-byte lines); the tensor-core stage applies 1 / sqrt(m) in its
+// reduction. Kind 3: the TF32 rounding of fl32(N) in FP32 words, same padded leading dimension,
+// same deferred scale.
 int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
              const float** g32, const __nv_bfloat16** ghi) {
     GCache& g = h->g;
     const int64_t ld = kind == 0 ? s : (s + 63) / 64 * 64;
     const size_t elems = (size_t)m * (size_t)ld;
-    const size_t bytes = kind == 2 ? elems * sizeof(__nv_bfloat16) : elems * sizeof(float);
+    const size_t bytes = kind == 2 ? 2 * elems * sizeof(__nv_bfloat16) : elems * sizeof(float);
     if (!(g.ptr && g.seed == seed && g.m == m && g.s == s && g.kind == kind)) {
         if (g.bytes < bytes) {
             if (g.ptr) cudaFree(g.ptr);
@@ -238,9 +238,9 @@ int ensure_g(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaS
         }
         cudaError_t e;
         if (kind == 2)
-            e = lev::launch_gen_gaussian(m, s, ld, seed, nullptr, false, (__nv_bfloat16*)g.ptr, st);
+            e = lev::launch_gen_gaussian(m, s, ld, seed, nullptr, 2, (__nv_bfloat16*)g.ptr, st);
         else
-            e = lev::launch_gen_gaussian(m, s, ld, seed, (float*)g.ptr, kind == 3, nullptr, st);
+            e = lev::launch_gen_gaussian(m, s, ld, seed, (float*)g.ptr, kind == 3 ? 1 : 0, nullptr, st);
         if (e != cudaSuccess) return fail(LEV_ECUDA, "G generation: %s", cudaGetErrorString(e));
         g.seed = seed;
         g.m = m;
@@ -1116,7 +1116,8 @@ int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
         LEV_TRY(ensure_g(h, z.m, z.s, p->seed, kind, st, &g32, &ghi));
         if (kind != 0) ldg = (z.s + 63) / 64 * 64;
     }
-    // the BF16 (kind 2) and TF32 (kind 3) images hold the unscaled Z; the FP32 image is Z / sqrt(m)
+    // the BF16 pair (kind 2) and the TF32 image (kind 3) hold the unscaled draws; the FP32 image is
+    // N / sqrt(m)
     const float g_scale = (identity || p->sketch_prec == LEV_FP32) ? 1.f : (float)(1.0 / std::sqrt((double)z.m));
     const int chunks = lev::backward_chunks(n, d, z.k);
     LEV_TRY(ensure(h->bwd, lev::backward_scratch_bytes(n, d, z.k, z.s, z.m, chunks)));

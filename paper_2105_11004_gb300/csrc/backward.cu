@@ -267,8 +267,8 @@ __global__ void k_xbar(const float* __restrict__ At, const double* __restrict__ 
     }
 }
 
-// T (s x d) = G^T Xbar_full, G = g_scale * (the image: FP32, or BF16 when B16), m x s with leading
-// dimension ldg.
+// T (s x d) = G^T Xbar_full, G = g_scale * (the image: FP32, or the BF16 pair hi + lo when B16, lo
+// m ldg entries after hi; the sum is exact in FP32), m x s with leading dimension ldg.
 template <bool B16>
 __global__ void __launch_bounds__(256) k_gt_x(const float* __restrict__ G32, const __nv_bfloat16* __restrict__ Ghi,
                                               int64_t ldg, int m, int64_t s, float g_scale,
@@ -291,7 +291,10 @@ __global__ void __launch_bounds__(256) k_gt_x(const float* __restrict__ G32, con
             const int j = j0 + jj;
             const int64_t b = b0 + u;
             float g = 0.f;
-            if (j < m && b < s) g = B16 ? __bfloat162float(Ghi[(int64_t)j * ldg + b]) : G32[(int64_t)j * ldg + b];
+            if (j < m && b < s) {
+                const int64_t o = (int64_t)j * ldg + b;
+                g = B16 ? __bfloat162float(Ghi[o]) + __bfloat162float(Ghi[(int64_t)m * ldg + o]) : G32[o];
+            }
             Gs[jj][u] = g;
             Xs[jj][u] = (j < m && c0 + u < d) ? Xf[(int64_t)j * d + c0 + u] : 0.f;
         }

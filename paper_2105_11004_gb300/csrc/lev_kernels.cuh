@@ -24,10 +24,11 @@ cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, c
                                    int64_t d, int64_t s, const int* off, const uint32_t* perm,
                                    float* B, cudaStream_t st);
 
-// G = Z / sqrt(m) (m x s, Z the BF16 rounding of the counter draws) with leading dimension ld >= s
-// (columns s..ld zero): an FP32 image, fl32(Z / sqrt(m)) or the unscaled Z, and/or the BF16 image
-// of Z (either pointer may be null).
-cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, bool unscaled,
+// G[j, b] = N_{j s + b} / sqrt(m) (m x s, N the counter draws of stream 2) as an image with leading
+// dimension ld >= s (columns s..ld zero). form 0: g32 = fl32(N / sqrt(m)); form 1: g32 = the TF32
+// rounding of fl32(N), unscaled; form 2: ghi = bf16(fl32(N)) and ghi + m ld = bf16(fl32(N) - hi),
+// unscaled.
+cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, int form,
                                 __nv_bfloat16* ghi, cudaStream_t st);
 
 // Atilde (m x d) = G (m x s) B (s x d), FP32 SIMT, split-K with a fixed-order

@@ -15,6 +15,8 @@
 //      which also write their new trailing norms and row j of R.
 // A second small kernel orders the columns (pivots first, then the rest in
 // increasing id) and writes R in pivoted order with diag(R) >= 0.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "lev_common.cuh"
@@ -468,18 +470,54 @@ cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int6
 // __device__ array of kRrqrNoAllocBytes that every GPU which loads the library
 // holds until the process exits. Host code must not pass the array's name to a
 // kernel (in host code it is only a stand-in for the device symbol); its device
-// address is looked up with cudaGetSymbolAddress once per device, on the first
-// call made with that device current, and that first call should come before
-// any stream capture. All calls share the array: the pieces that must start at
-// zero (barrier counter, status word, R scratch) are cleared by every call on
-// its stream, and calls that overlap on the GPU race with one another.
+// address is looked up with cudaGetSymbolAddress on the first call made in a
+// CUDA context (a device's primary context, or a context made current by the
+// caller) and looked up again whenever the current context differs from the one
+// the cached address belongs to (after a cudaDeviceReset, for example). That
+// first call should come before any stream capture. All calls share the array:
+// the pieces that must start at zero (barrier counter, status word, R scratch)
+// are cleared by every call on its stream, and calls that overlap on the GPU
+// race with one another.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr size_t kRrqrNoAllocBytes = size_t(8) << 20;   // 8 MiB
 __device__ __align__(256) unsigned char g_rrqr_noalloc_scratch[kRrqrNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices] = {};
+struct NoAllocAddr {
+    unsigned long long ctx_id = 0;   // CUDA context the address belongs to
+    void* addr = nullptr;
+};
+NoAllocAddr g_noalloc_addr[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current CUDA context (0 if none is current or the driver
+// entry points are unavailable). Called with g_noalloc_mu held.
+unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        resolved = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        cudaGetLastError();
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 }  // namespace
 
 }  // namespace lev
@@ -494,7 +532,7 @@ extern "C" int lev_rrqr_noalloc(const float* Atilde, int64_t m, int64_t d, doubl
     if (need > kRrqrNoAllocBytes)
         return handle_fail(LEV_EINVAL,
                            "lev_rrqr_noalloc: m x d too large for the fixed 8 MiB scratch "
-                           "(the QR working set is about 8 (m d + 2 d^2) bytes plus the Gram split partials)");
+                           "(the QR working set is about 8 (m d + 3 d^2) bytes plus the Gram split partials)");
     if (tau <= 0) tau = 1e-5;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -504,16 +542,20 @@ extern "C" int lev_rrqr_noalloc(const float* Atilde, int64_t m, int64_t d, doubl
     char* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        NoAllocAddr& slot = g_noalloc_addr[dev];
+        const unsigned long long ctx = current_ctx_id();
+        if (!slot.addr || ctx == 0 || ctx != slot.ctx_id) {
             void* addr = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&addr, g_rrqr_noalloc_scratch);
             if (e != cudaSuccess || !addr) {
                 cudaGetLastError();
+                slot.addr = nullptr;
                 return handle_fail(LEV_ECUDA, "lev_rrqr_noalloc: cudaGetSymbolAddress failed");
             }
-            g_noalloc_addr[dev] = addr;
+            slot.addr = addr;
+            slot.ctx_id = current_ctx_id();   // the lookup made the runtime's context current
         }
-        base = static_cast<char*>(g_noalloc_addr[dev]);
+        base = static_cast<char*>(slot.addr);
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     QrScratch q;

@@ -265,24 +265,32 @@ __global__ void __launch_bounds__(128) k_countsketch_csr(
     }
 }
 
-// G (m x s) by counter into images with leading dimension ld (columns s..ld are 0):
-// an FP32 copy (optionally rounded to TF32) and/or BF16 hi and lo copies.
-// Entries of G by counter: Z = the BF16 rounding (to nearest even) of the FP32 rounding of the
-// Box-Muller draw, G = Z / sqrt(m). g32: FP32 image, either fl32(Z / sqrt(m)) or (unscaled) Z
-// itself, which TF32 holds exactly; ghi: Z in BF16 (exact). The unscaled images leave the
+// G (m x s) by counter into an image with leading dimension ld (columns s..ld are 0). G[j, b] =
+// N_{j s + b} / sqrt(m), N the FP64 Box-Muller draw of stream 2. Images: g32 with form 0, fl32(N /
+// sqrt(m)) (the FP32 SIMT stage); g32 with form 1, the TF32 rounding (nearest, ties away) of fl32(N),
+// unscaled; ghi (form 2), the BF16 pair hi = bf16(fl32(N)), lo = bf16(fl32(N) - hi) at ghi and
+// ghi + m ld, unscaled (hi + lo carries N to about 2^-17 of itself). The unscaled images leave
 // 1 / sqrt(m) to the Gaussian stage's reduction.
 __global__ void k_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t key, double scale, float* g32,
-                               int unscaled, __nv_bfloat16* ghi) {
+                               int form, __nv_bfloat16* ghi) {
     const int64_t total = m * ld;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (; i < total; i += stride) {
         const int64_t j = i / ld, b = i % ld;
         const double g = b < s ? box_muller(key, (uint64_t)(j * s + b)) : 0.0;   // draw j*s + b
-        const __nv_bfloat16 z = __float2bfloat16_rn((float)g);
-        const float zf = __bfloat162float(z);
-        if (g32) g32[i] = unscaled ? zf : (float)((double)zf * scale);
-        if (ghi) ghi[i] = z;
+        if (form == 0) {
+            g32[i] = (float)(g * scale);
+        } else if (form == 1) {
+            uint32_t t;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"((float)g));
+            g32[i] = __uint_as_float(t);
+        } else {
+            const float gf = (float)g;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(gf);
+            ghi[i] = hi;
+            ghi[total + i] = __float2bfloat16_rn(gf - __bfloat162float(hi));
+        }
     }
 }
 
@@ -450,11 +458,11 @@ cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, bool unscaled,
+cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, int form,
                                 __nv_bfloat16* ghi, cudaStream_t st) {
     const double scale = 1.0 / sqrt((double)m);
     k_gen_gaussian<<<grid_for(m * ld, 256, 152 * 32), 256, 0, st>>>(
-        m, s, ld, stream_key(seed, kStreamG), scale, g32, unscaled ? 1 : 0, ghi);
+        m, s, ld, stream_key(seed, kStreamG), scale, g32, form, ghi);
     return cudaGetLastError();
 }
 

@@ -23,22 +23,43 @@ def _sketch(m, d, r, seed):
     return X.astype(np.float32)
 
 
-def test_rrqr_noalloc_matches_rrqr_twice():
+def _compare(L, h, m, d, r, tau, seed, want_rank=True):
     import torch
+    At = to_dev(_sketch(m, d, r, seed=seed))
+    perm_a = torch.empty(d, dtype=torch.int32, device="cuda")
+    R_a = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    rank_a = L.lev_rrqr(h, At, tau, perm_a, R_a)
+    perm_b = torch.full((d,), -1, dtype=torch.int32, device="cuda")
+    R_b = torch.full((d, d), float("nan"), dtype=torch.float64, device="cuda")
+    rank_b = L.lev_rrqr_noalloc(At, tau, perm_b, R_b, want_rank=want_rank)
+    if not want_rank:
+        # the call only enqueued its work: the rank is the number of nonzero rows of R
+        torch.cuda.synchronize()
+        rank_b = int(np.count_nonzero(np.diag(to_np(R_b))))
+    assert rank_a == rank_b == r
+    assert np.array_equal(to_np(perm_a), to_np(perm_b))
+    Ra, Rb = to_np(R_a), to_np(R_b)
+    assert np.max(np.abs(Ra - Rb)) <= 1e-10 * np.max(np.abs(Ra))
+
+
+def test_rrqr_noalloc_matches_rrqr_twice():
+    """Two calls in a row on the Gram route (d <= 1024, tau >= 1e-6), each against lev_rrqr."""
     L = lev_module()
     h = L.Handle(0)
     for call, (m, d, r, tau) in enumerate([(1024, 256, 200, 1e-4), (300, 64, 40, 1e-5)]):
-        At = to_dev(_sketch(m, d, r, seed=call))
-        perm_a = torch.empty(d, dtype=torch.int32, device="cuda")
-        R_a = torch.empty((d, d), dtype=torch.float64, device="cuda")
-        rank_a = L.lev_rrqr(h, At, tau, perm_a, R_a)
-        perm_b = torch.full((d,), -1, dtype=torch.int32, device="cuda")
-        R_b = torch.full((d, d), float("nan"), dtype=torch.float64, device="cuda")
-        rank_b = L.lev_rrqr_noalloc(At, tau, perm_b, R_b)
-        assert rank_a == rank_b == r
-        assert np.array_equal(to_np(perm_a), to_np(perm_b))
-        Ra, Rb = to_np(R_a), to_np(R_b)
-        assert np.max(np.abs(Ra - Rb)) <= 1e-10 * np.max(np.abs(Ra))
+        _compare(L, h, m, d, r, tau, seed=call)
+    h.close()
+
+
+def test_rrqr_noalloc_householder_route_and_no_rank_pointer():
+    """tau < 1e-6 takes the Householder route through the same fixed array (a full-rank sketch, so
+    the rank is exact at that threshold); then a call without a
+    rank pointer (no synchronisation inside the call) on both routes."""
+    L = lev_module()
+    h = L.Handle(0)
+    _compare(L, h, 300, 64, 64, 1e-7, seed=5)
+    _compare(L, h, 300, 64, 64, 1e-7, seed=6, want_rank=False)
+    _compare(L, h, 1024, 256, 200, 1e-4, seed=7, want_rank=False)
     h.close()
 
 
