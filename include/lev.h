@@ -80,6 +80,7 @@ extern "C" {
                                    from the pivoted QR run to the end; d <= 1024 */
 #define LEV_SRRQR          64u  /* after the rank: strong-RRQR swaps at that rank until every
                                    rho_ij <= phi (Alg. 2); d <= 1024 */
+#define LEV_CSR_UNCHECKED 128u  /* the caller vouches for the CSR structure: no validation pass */
 
 typedef struct lev_handle lev_handle;
 
@@ -134,6 +135,14 @@ int lev_params_init(lev_params* p);
 int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d,
                       int64_t* s, int64_t* m, int64_t* k);
 
+/* Build the handle's caches of data-independent operands for a call with (n, d, p) on `stream`,
+ * ahead of the first call that needs them: the CountSketch bucket permutation (Sec. 3.4.3, per
+ * seed, n, s and row0), G in the operand form of p->sketch_prec (Alg. 3 step 3; m x t with
+ * LEV_SKETCH_SRHT) and Omega (d <= 1024, unless LEV_OMEGA_IDENTITY). Later calls with the same
+ * seed and sizes reuse them. Asynchronous; no arrays are read. Errors: LEV_EINVAL, LEV_ENOMEM,
+ * LEV_ECUDA. */
+int lev_prepare(lev_handle* h, int64_t n, int64_t d, const lev_params* p, void* stream);
+
 /* Row shards. S A = sum_p S_{:,P_p} A_{P_p,:} for any partition of the rows into blocks P_p
  * (block matrix product), and G and the SRHT act linearly on S A, so the sketch of a matrix
  * whose rows are split across processes is the SUM of the sketches of its row blocks when each
@@ -156,8 +165,11 @@ int lev_sketch_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_
 
 /* CountGauss sketch of CSR A (Alg. 3); arguments as lev_sketch_dense, with A
  * given by device arrays row_ptr (n+1, int64, row_ptr[0] = 0, non-decreasing,
- * row_ptr[n] = nnz), col (nnz, int32 in [0, d)) and val (nnz, FP32). Column
- * indices are not checked on the device; out-of-range columns are skipped. */
+ * row_ptr[n] = nnz), col (nnz, int32 in [0, d)) and val (nnz, FP32). Every CSR entry
+ * point checks the structure of row_ptr first, in one device pass whose verdict it reads
+ * (one synchronisation of `stream`), and returns LEV_EINVAL before any kernel reads col or
+ * val if it is malformed; LEV_CSR_UNCHECKED in p->flags skips the check (the caller vouches
+ * for row_ptr). Out-of-range columns are skipped by the kernels. */
 int lev_sketch_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
                    int64_t n, int64_t d, int64_t nnz, const lev_params* p,
                    float* Atilde, void* stream);
@@ -317,6 +329,28 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
                   int64_t n, int64_t d, int64_t nnz, const lev_params* p, float* theta,
                   int64_t* rank, int32_t* perm, void* stream);
 
+/* Exact leverage scores of A itself (Sec. 1: theta_i = diag(A (A^T A)^+ A^T)_i, the squared row norms
+ * of an orthonormal basis of range(A)), by the Gram route of Alg. 5 with the QR orthogonaliser: the
+ * Gram matrix A^T A (products of the FP32 entries exact, sums compensated to about FP64 accuracy),
+ * its pivoted Cholesky factorisation in FP64 (the pivots, rank and R of a column-pivoted QR of A in
+ * exact arithmetic; rank rule |R_jj| > tau |R_00| of Sec. 7.2), and theta_i = ||A_{i,K} R_11^{-1}||^2
+ * by the FP32 final pass. No sketch and no Omega: the reference the estimator approximates.
+ * A: device, n x d FP32 (lda >= d); theta: device, n FP32. perm: device d int32 or NULL (the
+ * columns K in pivot order first). rank: host, may be NULL; the call synchronises `stream` once.
+ * d <= 1024; tau >= 1e-6 (the Gram route resolves |R_jj| / |R_00| down to about 1e-7; tau <= 0
+ * means 1e-5). Errors: LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0 (theta = 0). */
+int lev_exact_reference_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, double tau,
+                              float* theta, int64_t* rank, int32_t* perm, void* stream);
+
+/* The same for CSR A (device arrays, the conventions of lev_sketch_csr): A^T A as the sum of the
+ * rows' outer products (Lemma 8, Sec. 5.1; rows of more than max(32, d / 5) entries densified and
+ * summed by the compensated dense kernel, the others by FP64 atomics, so the last bits of A^T A and
+ * theta may differ between runs), then the pivoted Cholesky and the CSR final pass. The call
+ * synchronises `stream` twice (the count of long rows, the rank). */
+int lev_exact_reference_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
+                            int64_t n, int64_t d, int64_t nnz, double tau, float* theta, int64_t* rank,
+                            int32_t* perm, void* stream);
+
 /* The whole estimator on CSR A (arrays as lev_sketch_csr, device or host). */
 int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val,
                      int64_t n, int64_t d, int64_t nnz, const lev_params* p,
@@ -339,6 +373,12 @@ int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
                        const lev_params* p, const float* Atilde, const int32_t* perm,
                        const int64_t* d_rank, const double* R, const float* Mfull,
                        const float* w, float* gradA, void* stream);
+
+/* Fault injection for tests of the error paths (host side only; nothing is injected on the
+ * device): with the environment variable LEV_FAULT set to "alloc" every scratch allocation that a
+ * call needs reports failure (LEV_ENOMEM), to "launch" the launch of the pivoted QR reports failure
+ * (LEV_ECUDA), to "timeout" the status read after a synchronisation reports an expired device wait
+ * (LEV_ETIMEOUT). Unset, it costs one getenv per such point. */
 
 /* Device-side status word of the handle: nonzero after a bounded wait gave up. */
 int lev_device_status(lev_handle* h, int32_t* status);

@@ -18,7 +18,7 @@ from .build import LIB_PATH, build as build_library  # noqa: F401
 LEV_OK, LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0 = 0, 1, 2, 3, 4, 5
 LEV_FP32, LEV_TF32, LEV_BF16, LEV_BF16X3 = 0, 1, 2, 3
 LEV_OMEGA_IDENTITY, LEV_SKETCH_IDENTITY, LEV_FORCE_PIVOTS, LEV_HOST_ASYNC, LEV_SKETCH_SRHT = 1, 2, 4, 8, 16
-LEV_RANK_SVD, LEV_SRRQR = 32, 64
+LEV_RANK_SVD, LEV_SRRQR, LEV_CSR_UNCHECKED = 32, 64, 128
 PRECISIONS = {"fp32": LEV_FP32, "tf32": LEV_TF32, "bf16": LEV_BF16, "bf16x3": LEV_BF16X3}
 
 # Every symbol include/lev.h declares, with (restype, argtypes).
@@ -45,6 +45,11 @@ SIGNATURES = {
     "lev_workspace_bytes": (ctypes.c_int, [_c_void_p, _P(_i64)]),
     "lev_params_init": (ctypes.c_int, [_P(lev_params)]),
     "lev_resolve_sizes": (ctypes.c_int, [_P(lev_params), _i64, _i64, _P(_i64), _P(_i64), _P(_i64)]),
+    "lev_prepare": (ctypes.c_int, [_c_void_p, _i64, _i64, _P(lev_params), _c_void_p]),
+    "lev_exact_reference_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _dbl, _c_void_p, _P(_i64),
+                                                 _c_void_p, _c_void_p]),
+    "lev_exact_reference_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64, _dbl,
+                                               _c_void_p, _P(_i64), _c_void_p, _c_void_p]),
     "lev_sketch_dense": (ctypes.c_int, [_c_void_p, _c_void_p, _i64, _i64, _i64, _P(lev_params), _c_void_p, _c_void_p]),
     "lev_sketch_csr": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i64, _i64, _i64,
                                       _P(lev_params), _c_void_p, _c_void_p]),
@@ -194,6 +199,31 @@ def lev_resolve_sizes(p: lev_params, n: int, d: int):
 
 
 # ---- C-ABI entry points (torch tensors in, status-checked) ----
+
+def lev_prepare(h: Handle, n: int, d: int, p: lev_params, stream=None):
+    """Build the handle's caches (bucket permutation, G, Omega) for a call with (n, d, p)."""
+    _check(lib.lev_prepare(h.ptr, n, d, ctypes.byref(p), _stream(stream)))
+
+
+def lev_exact_reference_dense(h: Handle, A, tau, theta, perm=None, stream=None) -> int:
+    """Exact leverage scores of dense A (device) by the Gram route; returns the rank."""
+    n, d = A.shape
+    r = _i64()
+    rc = _check(lib.lev_exact_reference_dense(h.ptr, _ptr(A), n, d, A.stride(0), float(tau), _ptr(theta),
+                                              ctypes.byref(r), _ptr(perm) if perm is not None else None,
+                                              _stream(stream)), allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
+
+
+def lev_exact_reference_csr(h: Handle, row_ptr, col, val, n, d, tau, theta, perm=None, stream=None) -> int:
+    """Exact leverage scores of CSR A (device arrays) by the Gram route; returns the rank."""
+    r = _i64()
+    rc = _check(lib.lev_exact_reference_csr(h.ptr, _ptr(row_ptr), _ptr(col), _ptr(val), n, d, col.numel(),
+                                            float(tau), _ptr(theta), ctypes.byref(r),
+                                            _ptr(perm) if perm is not None else None, _stream(stream)),
+                allow=(LEV_ERANK0,))
+    return 0 if rc == LEV_ERANK0 else r.value
+
 
 def lev_sketch_dense(h: Handle, A, p: lev_params, Atilde, stream=None):
     n, d = A.shape

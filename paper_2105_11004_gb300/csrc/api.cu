@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -34,6 +35,14 @@ int fail(int code, const char* fmt, ...) {
             return fail(e_ == cudaErrorMemoryAllocation ? LEV_ENOMEM : LEV_ECUDA, "%s: %s (%s:%d)", \
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
     } while (0)
+
+// Host-side fault injection for the tests of the error paths (nothing is injected on the device):
+// LEV_FAULT=alloc makes the next scratch allocation report failure, LEV_FAULT=launch the launch of
+// the pivoted QR, LEV_FAULT=timeout the read of the device status word after a synchronisation.
+bool fault_is(const char* kind) {
+    const char* f = getenv("LEV_FAULT");
+    return f && strcmp(f, kind) == 0;
+}
 
 #define LEV_TRY(expr)              \
     do {                           \
@@ -120,6 +129,7 @@ int ensure(Buf& b, size_t bytes) {
         b.bytes = 0;
         if (e != cudaSuccess) return fail(LEV_ECUDA, "cudaFree: %s", cudaGetErrorString(e));
     }
+    if (fault_is("alloc")) return fail(LEV_ENOMEM, "cudaMalloc(%zu bytes) failed (injected by LEV_FAULT=alloc)", bytes);
     cudaError_t e = cudaMalloc(&b.ptr, bytes);
     if (e != cudaSuccess) {
         b.ptr = nullptr;
@@ -366,6 +376,7 @@ int rrqr_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, double
                 lev::QrScratch* qs, cudaStream_t st) {
     LEV_TRY(ensure(h->qr, lev::qr_scratch_bytes(m, d)));
     lev::qr_scratch_carve(h->qr.ptr, m, d, qs);
+    if (fault_is("launch")) return fail(LEV_ECUDA, "pivoted QR launch failed (injected by LEV_FAULT=launch)");
     LEV_CUDA(lev::launch_pivoted_qr(Atilde, m, d, tau, forced, forced_rank, *qs, perm, R, h->status,
                                     h->num_sms, st, h->timing ? h->tmark : nullptr));
     if (h->timing) h->timed_once = true;
@@ -380,6 +391,8 @@ int finish(lev_handle* h, const lev::QrScratch& qs, int64_t* rank, cudaStream_t 
     LEV_CUDA(cudaMemcpyAsync(h->host_rank + 1, h->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     LEV_CUDA(cudaStreamSynchronize(st));
     memcpy(&status, h->host_rank + 1, sizeof(int32_t));
+    if (fault_is("timeout") && status == 0)
+        return fail(LEV_ETIMEOUT, "a bounded device wait gave up (injected by LEV_FAULT=timeout)");
     if (status != 0) {
         cudaMemsetAsync(h->status, 0, sizeof(int32_t), st);
         return fail(LEV_ETIMEOUT, "a bounded device wait gave up (status %d)", status);
@@ -473,6 +486,53 @@ int select_common(lev_handle* h, const float* Atilde, int64_t m, int64_t d, cons
         h->last_swaps = it + 1;
         if (it + 1 >= max_swaps) return fail(LEV_EINVAL, "strong RRQR did not settle in %lld swaps", (long long)max_swaps);
     }
+    return LEV_OK;
+}
+
+// The CSR structure of the input contract (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz), checked
+// by one device pass over row_ptr whose verdict the host reads (one synchronisation) before any kernel
+// reads col or val. Skipped with LEV_CSR_UNCHECKED.
+int check_csr(lev_handle* h, const int64_t* row_ptr, int64_t n, int64_t nnz, uint32_t flags, cudaStream_t st) {
+    if (flags & LEV_CSR_UNCHECKED) return LEV_OK;
+    int32_t* bad = h->status + 1;
+    LEV_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+    LEV_CUDA(lev::launch_check_csr(row_ptr, n, nnz, bad, st));
+    int32_t* hb = reinterpret_cast<int32_t*>(h->host_rank + 4);
+    LEV_CUDA(cudaMemcpyAsync(hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    LEV_CUDA(cudaStreamSynchronize(st));
+    const int32_t v = *hb;
+    if (v == 0) return LEV_OK;
+    return fail(LEV_EINVAL, "malformed CSR row_ptr:%s%s%s", (v & 1) ? " row_ptr[0] != 0;" : "",
+                (v & 2) ? " row_ptr decreases;" : "", (v & 4) ? " row_ptr[n] != nnz;" : "");
+}
+
+// B = A^T A of CSR A (d x d FP64) as the sum of the rows' outer products (Lemma 8, Sec. 5.1): rows of
+// more than max(32, d / 5) entries are densified and their Gram formed by the compensated dense
+// kernel (about 30x the rate of the FP64 atomics per product, so it pays beyond about d / 5
+// entries); the others add their pairs by FP64 atomics. Synchronises `st` once (the count of long
+// rows sizes the dense part).
+int csr_gram(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n, int64_t d,
+             double* G, cudaStream_t st) {
+    const int64_t max_len = std::max<int64_t>(32, d / 5);
+    LEV_TRY(ensure(h->csr_heavy, sizeof(int32_t) * (size_t)n + 256));
+    auto* hcount = reinterpret_cast<unsigned long long*>(h->csr_heavy.ptr);
+    auto* hidx = reinterpret_cast<int32_t*>(static_cast<char*>(h->csr_heavy.ptr) + 256);
+    LEV_CUDA(lev::launch_heavy_rows(row_ptr, n, max_len, hcount, hidx, st));
+    LEV_CUDA(cudaMemcpyAsync(h->host_rank + 3, hcount, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    LEV_CUDA(cudaStreamSynchronize(st));
+    const int64_t nh = h->host_rank[3];
+    const double* Gheavy = nullptr;
+    if (nh > 0) {
+        const size_t gp = lev::gram_partial_doubles(nh, d);
+        LEV_TRY(ensure(h->csr_dense, sizeof(double) * (gp + (size_t)d * d) + sizeof(float) * (size_t)nh * d));
+        double* Gh = static_cast<double*>(h->csr_dense.ptr);
+        double* Gp2 = Gh + (size_t)d * d;
+        float* H = reinterpret_cast<float*>(Gp2 + gp);
+        LEV_CUDA(lev::launch_densify_rows(row_ptr, col, val, hidx, hcount, nh, d, H, st));
+        LEV_CUDA(lev::launch_gram_fp64(H, d, nh, d, Gp2, Gh, st));
+        Gheavy = Gh;
+    }
+    LEV_CUDA(lev::launch_gram_csr_light(row_ptr, col, val, n, d, max_len, Gheavy, G, st));
     return LEV_OK;
 }
 
@@ -625,6 +685,35 @@ int lev_device_status(lev_handle* h, int32_t* status) {
     return LEV_OK;
 }
 
+int lev_prepare(lev_handle* h, int64_t n, int64_t d, const lev_params* p, void* stream) {
+    LEV_TRY(set_device(h));
+    Sizes z;
+    LEV_TRY(resolve(p, n, d, &z, true));
+    LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->flags & LEV_SKETCH_IDENTITY) return LEV_OK;
+    LEV_TRY(bucket_perm(h, n, z.s, p->seed, z.row0, st));
+    // G in the image the Gaussian stage of sketch_prec reads (m x t after an SRHT)
+    const int64_t cols = (p->flags & LEV_SKETCH_SRHT) ? (int64_t)p->srht_t : z.s;
+    if (cols < 1 || cols > z.s) return fail(LEV_EINVAL, "LEV_SKETCH_SRHT needs 1 <= srht_t <= s");
+    const int kind = p->sketch_prec == LEV_FP32 ? 0 : (p->sketch_prec == LEV_TF32 ? 3 : 2);
+    LEV_TRY(ensure_g(h, z.m, cols, p->seed, kind, st, nullptr, nullptr));
+    if (!(p->flags & LEV_OMEGA_IDENTITY) && d <= 1024) {
+        const void* p0 = h->omega.ptr;
+        LEV_TRY(ensure(h->omega, sizeof(double) * (size_t)d * z.k));
+        if (!h->ev_omega) LEV_CUDA(cudaEventCreateWithFlags(&h->ev_omega, cudaEventDisableTiming));
+        if (!(h->omega_seed == p->seed && h->omega_d == d && h->omega_k == z.k && h->omega.ptr == p0)) {
+            h->omega_d = -1;
+            LEV_CUDA(lev::launch_gen_omega(p->seed, d, z.k, (double*)h->omega.ptr, st));
+            LEV_CUDA(cudaEventRecord(h->ev_omega, st));
+            h->omega_seed = p->seed;
+            h->omega_d = d;
+            h->omega_k = z.k;
+        }
+    }
+    return LEV_OK;
+}
+
 int lev_sketch_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda,
                      const lev_params* p, float* Atilde, void* stream) {
     LEV_TRY(set_device(h));
@@ -644,6 +733,7 @@ int lev_sketch_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, co
     if (!row_ptr || (nnz > 0 && (!col || !val)) || !Atilde) return fail(LEV_EINVAL, "NULL array");
     if (nnz < 0) return fail(LEV_EINVAL, "nnz < 0");
     LEV_TRY(check_prec(p->sketch_prec, "sketch"));
+    LEV_TRY(check_csr(h, row_ptr, n, nnz, p->flags, (cudaStream_t)stream));
     return sketch_common_csr(h, row_ptr, col, val, n, d, p, z, Atilde, (cudaStream_t)stream);
 }
 
@@ -718,6 +808,7 @@ int lev_precondition_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* c
     if (is_host_pointer(row_ptr) || is_host_pointer(N)) return fail(LEV_EINVAL, "lev_precondition_csr takes device arrays");
     LEV_TRY(check_prec(p->sketch_prec, "sketch"));
     cudaStream_t st = (cudaStream_t)stream;
+    LEV_TRY(check_csr(h, row_ptr, n, nnz, p->flags, st));
     LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
     LEV_TRY(sketch_common_csr(h, row_ptr, col, val, n, d, p, z, (float*)h->Atilde.ptr, st));
     return precondition_tail(h, z, d, p, N, rank, sigma, st);
@@ -778,6 +869,7 @@ int lev_lsqr_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, cons
     if (is_host_pointer(row_ptr) || is_host_pointer(N) || is_host_pointer(b) || is_host_pointer(x))
         return fail(LEV_EINVAL, "lev_lsqr_csr takes device arrays");
     cudaStream_t st = (cudaStream_t)stream;
+    LEV_TRY(check_csr(h, row_ptr, n, nnz, 0u, st));
     const int parts = lev::lsqr_parts(h->num_sms);
     LEV_TRY(ensure(h->lsqr_u, sizeof(float) * (size_t)n));
     LEV_TRY(ensure(h->lsqr_ws, sizeof(double) * lev::lsqr_scratch_doubles(d, parts)));
@@ -821,6 +913,7 @@ int lev_final_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > 4096 || k < 1 || k > 4096 || nnz < 0)
         return fail(LEV_EINVAL, "bad shape");
     if (prec != LEV_FP32) return fail(LEV_EINVAL, "the CSR final pass supports LEV_FP32 only");
+    LEV_TRY(check_csr(h, row_ptr, n, nnz, 0u, (cudaStream_t)stream));
     LEV_TRY(final_csr(h, row_ptr, col, val, n, d, nnz, Mfull, k, theta, (cudaStream_t)stream));
     return LEV_OK;
 }
@@ -948,6 +1041,7 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     if (p->final_prec != LEV_FP32) return fail(LEV_EINVAL, "the CSR final pass supports LEV_FP32 only");
     LEV_TRY(check_prec(p->sketch_prec, "sketch"));
     cudaStream_t st = (cudaStream_t)stream;
+    LEV_TRY(check_csr(h, row_ptr, n, nnz, p->flags, st));
     // steps 1-3 (Alg. 7): K and the rank k from the pivoted QR of the CountGauss sketch
     LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
     LEV_TRY(sketch_common_csr(h, row_ptr, col, val, n, d, p, z, (float*)h->Atilde.ptr, st));
@@ -965,30 +1059,8 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     }
     LEV_TRY(rc);
     // step 4: B = A_K^T A_K (all of A^T A, read at K in pivot order), the sum of the rows' outer
-    // products (Lemma 8, Sec. 5.1): rows of more than max(32, d / 5) entries are densified and their Gram
-    // formed by the compensated dense kernel (about 30x the rate of the FP64 atomics per product,
-    // so it pays beyond about d / 5 entries); the others add their pairs by FP64 atomics. Step 5
-    // by the Cholesky factor B = R^T R with the pivots of step 2 forced
-    const int64_t max_len = std::max<int64_t>(32, d / 5);
-    LEV_TRY(ensure(h->csr_heavy, sizeof(int32_t) * (size_t)n + 256));
-    auto* hcount = reinterpret_cast<unsigned long long*>(h->csr_heavy.ptr);
-    auto* hidx = reinterpret_cast<int32_t*>(static_cast<char*>(h->csr_heavy.ptr) + 256);
-    LEV_CUDA(lev::launch_heavy_rows(row_ptr, n, max_len, hcount, hidx, st));
-    LEV_CUDA(cudaMemcpyAsync(h->host_rank + 3, hcount, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    LEV_CUDA(cudaStreamSynchronize(st));
-    const int64_t nh = h->host_rank[3];
-    const double* Gheavy = nullptr;
-    if (nh > 0) {
-        const size_t gp = lev::gram_partial_doubles(nh, d);
-        LEV_TRY(ensure(h->csr_dense, sizeof(double) * (gp + (size_t)d * d) + sizeof(float) * (size_t)nh * d));
-        double* Gh = static_cast<double*>(h->csr_dense.ptr);
-        double* Gp2 = Gh + (size_t)d * d;
-        float* H = reinterpret_cast<float*>(Gp2 + gp);
-        LEV_CUDA(lev::launch_densify_rows(row_ptr, col, val, hidx, hcount, nh, d, H, st));
-        LEV_CUDA(lev::launch_gram_fp64(H, d, nh, d, Gp2, Gh, st));
-        Gheavy = Gh;
-    }
-    LEV_CUDA(lev::launch_gram_csr_light(row_ptr, col, val, n, d, max_len, Gheavy, qs.G, st));
+    // products (csr_gram); step 5 by the Cholesky factor B = R^T R with the pivots of step 2 forced
+    LEV_TRY(csr_gram(h, row_ptr, col, val, n, d, qs.G, st));
     LEV_CUDA(lev::launch_factor_gram(n, d, tau_of(p), perm, k, qs, perm, (double*)h->R.ptr, h->status, st));
     int64_t k2 = 0;
     rc = finish(h, qs, &k2, st);
@@ -1006,6 +1078,77 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     LEV_TRY(final_csr(h, row_ptr, col, val, n, d, nnz, (const float*)h->Mfull.ptr, d, theta, st));
     if (rank) *rank = k2;
     return LEV_OK;
+}
+
+// Exact leverage of A itself by the Gram route (Alg. 5 with the QR orthogonaliser): the Gram matrix
+// already in q->G, its pivoted Cholesky with the rank rule |R_jj| > tau |R_00| (the same pivots and
+// R as a column-pivoted QR of A in exact arithmetic), M = R_11^{-1} (Omega = I) scattered into Mfull,
+// then theta_i = ||A_{i,K} R_11^{-1}||^2 by the FP32 final pass (dense or CSR).
+static int exact_reference_tail(lev_handle* h, lev::QrScratch& q, int64_t n, int64_t d, double tau, const float* A,
+                                int64_t lda, const int64_t* rp, const int32_t* cl, const float* vl, int64_t nnz,
+                                float* theta, int64_t* rank, int32_t* perm_out, cudaStream_t st) {
+    LEV_TRY(ensure(h->R, sizeof(double) * (size_t)d * d));
+    LEV_TRY(ensure(h->perm_d, sizeof(int32_t) * (size_t)d));
+    int32_t* perm = perm_out ? perm_out : (int32_t*)h->perm_d.ptr;
+    LEV_CUDA(lev::launch_factor_gram(n, d, tau, nullptr, 0, q, perm, (double*)h->R.ptr, h->status, st));
+    int64_t k = 0;
+    int rc = finish(h, q, &k, st);
+    if (rc == LEV_ERANK0) {
+        LEV_CUDA(cudaMemsetAsync(theta, 0, sizeof(float) * (size_t)n, st));
+        if (rank) *rank = 0;
+        return rc;
+    }
+    LEV_TRY(rc);
+    LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * d));
+    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, q.rank, d, d, 0, true, (float*)h->Mfull.ptr, st));
+    if (A)
+        LEV_CUDA(lev::launch_final_dense_fp32(A, lda, n, d, (const float*)h->Mfull.ptr, d, theta, st));
+    else
+        LEV_TRY(final_csr(h, rp, cl, vl, n, d, nnz, (const float*)h->Mfull.ptr, d, theta, st));
+    if (rank) *rank = k;
+    return LEV_OK;
+}
+
+int lev_exact_reference_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, double tau,
+                              float* theta, int64_t* rank, int32_t* perm, void* stream) {
+    LEV_TRY(set_device(h));
+    if (!A || !theta) return fail(LEV_EINVAL, "NULL array");
+    if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > 1024 || lda < d)
+        return fail(LEV_EINVAL, "bad shape n=%lld d=%lld lda=%lld (d <= 1024)", (long long)n, (long long)d,
+                    (long long)lda);
+    if (tau <= 0) tau = 1e-5;
+    if (tau < 1e-6) return fail(LEV_EINVAL, "tau = %g below the Gram route's resolution (1e-6)", tau);
+    if (is_host_pointer(A) || is_host_pointer(theta))
+        return fail(LEV_EINVAL, "lev_exact_reference_dense takes device arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    LEV_TRY(ensure(h->qr, lev::qr_scratch_bytes(1, d)));
+    lev::QrScratch q;
+    lev::qr_scratch_carve(h->qr.ptr, 1, d, &q);
+    LEV_TRY(ensure(h->exact_gp, sizeof(double) * lev::gram_partial_doubles(n, d)));
+    q.Gp = (double*)h->exact_gp.ptr;
+    LEV_CUDA(lev::launch_gram_fp64(A, lda, n, d, q.Gp, q.G, st));
+    return exact_reference_tail(h, q, n, d, tau, A, lda, nullptr, nullptr, nullptr, 0, theta, rank, perm, st);
+}
+
+int lev_exact_reference_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                            int64_t d, int64_t nnz, double tau, float* theta, int64_t* rank, int32_t* perm,
+                            void* stream) {
+    LEV_TRY(set_device(h));
+    if (!row_ptr || (nnz > 0 && (!col || !val)) || !theta) return fail(LEV_EINVAL, "NULL array");
+    if (n < 1 || n >= (int64_t)1 << 31 || d < 1 || d > 1024 || nnz < 0)
+        return fail(LEV_EINVAL, "bad shape n=%lld d=%lld (d <= 1024)", (long long)n, (long long)d);
+    if (tau <= 0) tau = 1e-5;
+    if (tau < 1e-6) return fail(LEV_EINVAL, "tau = %g below the Gram route's resolution (1e-6)", tau);
+    if (is_host_pointer(row_ptr) || (nnz > 0 && (is_host_pointer(col) || is_host_pointer(val))) ||
+        is_host_pointer(theta))
+        return fail(LEV_EINVAL, "lev_exact_reference_csr takes device arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    LEV_TRY(check_csr(h, row_ptr, n, nnz, 0u, st));
+    LEV_TRY(ensure(h->qr, lev::qr_scratch_bytes(1, d)));
+    lev::QrScratch q;
+    lev::qr_scratch_carve(h->qr.ptr, 1, d, &q);
+    LEV_TRY(csr_gram(h, row_ptr, col, val, n, d, q.G, st));
+    return exact_reference_tail(h, q, n, d, tau, nullptr, 0, row_ptr, col, val, nnz, theta, rank, perm, st);
 }
 
 int lev_estimate_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const lev_params* p,
@@ -1084,6 +1227,7 @@ int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, 
         LEV_TRY(ensure(h->stageTheta, sizeof(float) * (size_t)n));
         dT = (float*)h->stageTheta.ptr;
     }
+    LEV_TRY(check_csr(h, rp, n, nnz, p->flags, st));
     LEV_TRY(ensure(h->Atilde, sizeof(float) * (size_t)z.m * d));
     LEV_TRY(sketch_common_csr(h, rp, cl, vl, n, d, p, z, (float*)h->Atilde.ptr, st));
     lev::QrScratch qs;

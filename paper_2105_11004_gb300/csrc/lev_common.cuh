@@ -44,6 +44,33 @@ __device__ __forceinline__ double box_muller(uint64_t key, uint64_t c) {
     return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
 
+// The same draw in FP32 arithmetic, within a few FP32 ulp of the FP64 draw (the entries of G:
+// 1e9 of them at the largest sketch, where FP64's 1/64 rate would dominate the generation).
+// The 53-bit integers behind u1 and u2 are kept exact until one final conversion each:
+//  * ln u1: logf(u1) for u1 <= 1/2; log1pf(-t) with t = 1 - u1 = (2^53 - 1 - a) 2^-53 above, so
+//    that ln u1 keeps its relative accuracy as u1 -> 1 (a = x1 >> 11, u1 = (a + 1) 2^-53);
+//  * cos(2 pi u2) = cos(2 pi v), v = min(u2, 1 - u2) = b' 2^-53 in [0, 1/2]: cospi(2 v) for
+//    v < 1/8, else sinpi(1/2 - 2 v) with 1/2 - 2 v = (2^51 - b') 2^-52 formed in integers, so
+//    that the result keeps its relative accuracy near the zero at v = 1/4.
+__device__ __forceinline__ float box_muller_f32(uint64_t key, uint64_t c) {
+    const uint64_t a = splitmix64(key, 2ull * c) >> 11;
+    const uint64_t b = splitmix64(key, 2ull * c + 1ull) >> 11;
+    const uint64_t top = 1ull << 53;
+    float L;
+    if (a + 1ull <= (top >> 1))
+        L = logf((float)(a + 1ull) * 0x1.0p-53f);
+    else
+        L = log1pf(-(float)(top - 1ull - a) * 0x1.0p-53f);
+    const float r = sqrtf(-2.0f * L);
+    const uint64_t bp = b <= (top >> 1) ? b : top - b;                     // v = bp 2^-53
+    float cs;
+    if (bp < (1ull << 50))
+        cs = cospif((float)bp * 0x1.0p-52f);
+    else
+        cs = sinpif((float)((int64_t)(1ull << 51) - (int64_t)bp) * 0x1.0p-52f);
+    return r * cs;
+}
+
 // ---------------------------------------------------------------------------
 // Device status word: bounded waits record why they gave up, then return.
 // ---------------------------------------------------------------------------

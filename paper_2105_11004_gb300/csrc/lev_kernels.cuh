@@ -38,6 +38,9 @@ cudaError_t launch_gaussian_stage_fp32(const float* G, const float* B, int64_t m
                                        int64_t d, float* partial, int splits, float* Atilde,
                                        cudaStream_t st);
 
+// CSR structure check: *bad |= 1 (row_ptr[0] != 0), 2 (row_ptr decreases), 4 (row_ptr[n] != nnz).
+cudaError_t launch_check_csr(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t* bad, cudaStream_t st);
+
 // Identity sketch: Atilde = A (n x d) copied densely (ld = d).
 cudaError_t launch_copy_dense(const float* A, int64_t lda, int64_t n, int64_t d, float* out,
                               cudaStream_t st);

@@ -266,27 +266,27 @@ __global__ void __launch_bounds__(128) k_countsketch_csr(
 }
 
 // G (m x s) by counter into an image with leading dimension ld (columns s..ld are 0). G[j, b] =
-// N_{j s + b} / sqrt(m), N the FP64 Box-Muller draw of stream 2. Images: g32 with form 0, fl32(N /
-// sqrt(m)) (the FP32 SIMT stage); g32 with form 1, the TF32 rounding (nearest, ties away) of fl32(N),
-// unscaled; ghi (form 2), the BF16 pair hi = bf16(fl32(N)), lo = bf16(fl32(N) - hi) at ghi and
-// ghi + m ld, unscaled (hi + lo carries N to about 2^-17 of itself). The unscaled images leave
-// 1 / sqrt(m) to the Gaussian stage's reduction.
-__global__ void k_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t key, double scale, float* g32,
+// N_{j s + b} / sqrt(m), N the Box-Muller draw of stream 2 evaluated in FP32 (box_muller_f32: a
+// few FP32 ulp of the FP64 draw). Images: g32 with form 0, fl32(N / sqrt(m)) (the FP32 SIMT
+// stage); g32 with form 1, the TF32 rounding (nearest, ties away) of N, unscaled; ghi (form 2), the
+// BF16 pair hi = bf16(N), lo = bf16(N - hi) at ghi and ghi + m ld, unscaled (hi + lo carries N
+// to about 2^-17 of itself). The unscaled images leave 1 / sqrt(m) to the Gaussian stage's
+// reduction.
+__global__ void k_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t key, float scale, float* g32,
                                int form, __nv_bfloat16* ghi) {
     const int64_t total = m * ld;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (; i < total; i += stride) {
         const int64_t j = i / ld, b = i % ld;
-        const double g = b < s ? box_muller(key, (uint64_t)(j * s + b)) : 0.0;   // draw j*s + b
+        const float gf = b < s ? box_muller_f32(key, (uint64_t)(j * s + b)) : 0.0f;   // draw j*s + b
         if (form == 0) {
-            g32[i] = (float)(g * scale);
+            g32[i] = gf * scale;
         } else if (form == 1) {
             uint32_t t;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"((float)g));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(gf));
             g32[i] = __uint_as_float(t);
         } else {
-            const float gf = (float)g;
             const __nv_bfloat16 hi = __float2bfloat16_rn(gf);
             ghi[i] = hi;
             ghi[total + i] = __float2bfloat16_rn(gf - __bfloat162float(hi));
@@ -460,7 +460,7 @@ cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, c
 
 cudaError_t launch_gen_gaussian(int64_t m, int64_t s, int64_t ld, uint64_t seed, float* g32, int form,
                                 __nv_bfloat16* ghi, cudaStream_t st) {
-    const double scale = 1.0 / sqrt((double)m);
+    const float scale = (float)(1.0 / sqrt((double)m));
     k_gen_gaussian<<<grid_for(m * ld, 256, 152 * 32), 256, 0, st>>>(
         m, s, ld, stream_key(seed, kStreamG), scale, g32, form, ghi);
     return cudaGetLastError();
@@ -483,6 +483,24 @@ cudaError_t launch_gaussian_stage_fp32(const float* G, const float* B, int64_t m
     dim3 grid((unsigned)((d + SG_BN - 1) / SG_BN), (unsigned)((m + SG_BM - 1) / SG_BM), (unsigned)splits);
     k_sgemm_splitk<<<grid, 256, 0, st>>>(G, B, (int)m, (int)d, s, kchunk, partial);
     k_reduce_splits<<<grid_for(m * d, 256, 152 * 8), 256, 0, st>>>(partial, splits, m * d, Atilde);
+    return cudaGetLastError();
+}
+
+// The CSR structure of the input contract: bad |= 1 if row_ptr[0] != 0, 2 if row_ptr decreases
+// somewhere, 4 if row_ptr[n] != nnz. Reads row_ptr[0..n] only.
+__global__ void k_check_csr(const int64_t* __restrict__ rp, int64_t n, int64_t nnz, int32_t* bad) {
+    int flags = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = rp[i];
+        if (i == 0 && a != 0) flags |= 1;
+        if (i < n && rp[i + 1] < a) flags |= 2;
+        if (i == n && a != nnz) flags |= 4;
+    }
+    if (flags) atomicOr(bad, flags);
+}
+
+cudaError_t launch_check_csr(const int64_t* row_ptr, int64_t n, int64_t nnz, int32_t* bad, cudaStream_t st) {
+    k_check_csr<<<grid_for(n + 1, 256, 152 * 8), 256, 0, st>>>(row_ptr, n, nnz, bad);
     return cudaGetLastError();
 }
 

@@ -124,3 +124,13 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
                        text=True, timeout=120)
     assert r.returncode != 0
     assert "ImportError" in r.stderr and "liblev.so is not built" in r.stderr
+
+
+def test_binding_constants_match_header(lev):
+    """Every status code, precision and flag the header defines has the same value in the binding."""
+    with open(os.path.join(ROOT, "include", "lev.h")) as f:
+        txt = f.read()
+    defs = dict(re.findall(r"^#define (LEV_[A-Z0-9_]+)\s+(\d+)u?\b", txt, re.M))
+    assert {"LEV_OK", "LEV_EINVAL", "LEV_BF16X3", "LEV_SKETCH_SRHT", "LEV_CSR_UNCHECKED"} <= set(defs)
+    for name, value in defs.items():
+        assert getattr(lev, name) == int(value), name

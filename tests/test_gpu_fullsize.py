@@ -252,3 +252,63 @@ def test_csr_8e7x1024_rank1014(L, h):
     assert abs(got / float(np.sum(Mf64 * (B @ Mf64))) - 1) < 1e-5
     want_sum = r * m / (m - r - 1)
     assert abs(got / want_sum - 1) < 0.1
+
+
+def _first_pivot_difference(gp, e, r):
+    """First step t at which the GPU's pivot differs from the oracle's, with the relative gap of the
+    two columns' squared trailing norms at that step (from the oracle's R, pivot order)."""
+    diff = np.flatnonzero(gp[:r] != e.perm[:r])
+    if diff.size == 0:
+        return None
+    t = int(diff[0])
+    pos = {int(c): q for q, c in enumerate(e.perm)}
+    R = e.R
+
+    def trailing(c):
+        q = pos[int(c)]
+        return float(np.sum(R[t:q + 1, q] ** 2)) if q < R.shape[0] else float(np.sum(R[t:, q] ** 2))
+
+    a, b = trailing(e.perm[t]), trailing(gp[t])
+    return t, int(e.perm[t]), int(gp[t]), abs(a - b) / a
+
+
+def _csr_end_to_end(L, h, C, cfg):
+    """The GPU estimate of CSR C (split-BF16 sketch, FP32 CSR final pass) against the oracle's FP64
+    estimate on the same matrix: rank, pivots on the first r positions, theta~ on every row (at the
+    GPU's pivots, so that a pivot difference would still leave theta~ comparable)."""
+    import torch
+    n, d = C.shape
+    s, m, k, tau, seed = cfg["s"], cfg["m"], cfg["k"], cfg["tau"], cfg["seed"]
+    p = L.make_params(s=s, m=m, k=k, tau=tau, seed=seed, sketch_prec="bf16x3")
+    theta_t = torch.empty(n, device="cuda")
+    perm_t = torch.empty(d, dtype=torch.int32, device="cuda")
+    r = L.lev_estimate_csr(h, to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val), n, d, p, theta_t, perm_t)
+    theta, gp = to_np(theta_t).astype(np.float64), to_np(perm_t)
+    A = sp.csr_matrix((C.val.astype(np.float64), C.col, C.row_ptr), shape=(n, d))
+    e = E.estimate(A, s, m, k, tau, seed)
+    assert r == e.rank
+    d0 = _first_pivot_difference(gp, e, r)
+    if d0 is not None:
+        e = E.estimate(A, s, m, k, tau, seed, forced_perm=gp, forced_rank=r, Atilde=e.Atilde)
+    assert max_rel(theta, e.theta) <= 1e-4
+    assert d0 is None, "first pivot difference at step %d: oracle column %d, GPU column %d, gap %.2e" % d0
+    return r
+
+
+def test_csr_8e6x1024_end_to_end_against_oracle(L, h):
+    """The CSR 8e6 x 1024 workload end to end against the oracle's own FP64 estimate (its sketch,
+    its Householder QR, its final pass): rank, the 1,024 pivots in order, theta~ on all 8e6 rows
+    within the 1e-4 bar of the split-BF16 sketch with the FP32 CSR final pass."""
+    cfg = W.CONFIGS["csr_8e6x1024"]
+    C = W.csr_uniform(cfg["n"], cfg["d"], seed=cfg["data_seed"])
+    assert _csr_end_to_end(L, h, C, cfg) == cfg["d"]
+
+
+def test_csr_8e7x1024_prefix_end_to_end_against_oracle(L, h):
+    """The first 4,194,304 rows of the CSR 8e7 x 1024 workload (the generator draws in blocks of 2^20
+    rows, so these are exactly the matrix's first rows), with its s, m, k: rank 1,014 from the ten
+    doubled column pairs, the pivots in order and theta~ on every row against the oracle's FP64
+    estimate; d = 1,024 takes the same pivoted-Cholesky route as the whole matrix."""
+    cfg = W.CONFIGS["csr_8e7x1024_rank1014"]
+    C = W.csr_dup_columns(4 << 20, cfg["d"], seed=cfg["data_seed"])
+    assert _csr_end_to_end(L, h, C, cfg) == 1014

@@ -50,6 +50,34 @@ def test_sketch_dense_parity(L, h, n, d, s, m):
     assert np.all(err <= 2e-5 * scale + 1e-30), float(np.max(err / (scale + 1e-30)))
 
 
+# Relative error of one entry of G as each form's Gaussian stage applies it: the FP32 draw is a few
+# FP32 ulp of the FP64 one; the operand then carries it to 2^-16 (BF16 hi + lo), 2^-11 (TF32) or
+# 2^-8 (BF16) of itself.
+G_ENTRY_TOL = {"fp32": 1e-6, "bf16x3": 2e-5, "tf32": 1e-3, "bf16": 4e-3}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32", "bf16"])
+def test_gaussian_entries_match_oracle_draws(L, h, prec):
+    """The entries of G entry by entry: with A = I (n = d) column i of S A is sigma_i e_{h(i)}, so
+    column i of A~ = G S A is sigma_i G[:, h(i)], one column of G read back through the sketch.
+    Against the oracle's FP64 Box-Muller draws (stream 2) divided by sqrt(m): every entry within
+    the form's relative bound, including draws near 0 (u1 near 1, or cos near its zero)."""
+    import torch
+    from oracle import rng as orng
+    d, s, m, seed = 512, 65536, 256, 7
+    A = np.eye(d, dtype=np.float32)
+    p = L.make_params(s=s, m=m, seed=seed, sketch_prec=prec)
+    At = torch.empty((m, d), dtype=torch.float32, device="cuda")
+    L.lev_sketch_dense(h, to_dev(A), p, At)
+    b, sign = orng.bucket_and_sign(d, s, seed)
+    idx = np.arange(m, dtype=np.uint64)[:, None] * np.uint64(s) + b.astype(np.uint64)[None, :]
+    want = orng.sketch_gaussian(seed, idx, m) * sign[None, :]
+    got = to_np(At).astype(np.float64)
+    rel = np.abs(got - want) / np.abs(want)
+    assert np.all(rel <= G_ENTRY_TOL[prec]), (prec, float(rel.max()))
+    assert np.median(rel) < G_ENTRY_TOL[prec] / 2
+
+
 SKETCH_TC_TOL = {"bf16x3": 1e-4, "tf32": 2e-3, "bf16": 1.6e-2}
 
 
@@ -125,13 +153,14 @@ def _rank_deficient_sketch(m, d, r, seed):
 
 @pytest.mark.parametrize("m,d,r,tau", [(96, 24, 24, 1e-5), (300, 64, 40, 1e-5), (1024, 256, 200, 1e-4),
                                        (50, 70, 50, 1e-5), (8, 1, 1, 1e-5), (700, 513, 300, 1e-5),
-                                       (96, 24, 24, 1e-9), (300, 64, 64, 1e-9)])
+                                       (96, 24, 24, 1e-9), (300, 64, 64, 1e-9), (1024, 512, 400, 1e-5),
+                                       (2048, 1024, 900, 1e-5), (60, 20, 20, 1e-5), (1024, 256, 256, 1e-5)])
 def test_rrqr_parity(L, h, m, d, r, tau):
     """Pivots and rank bit-exact, R close to the oracle's Householder R.
 
-    d <= 512 with tau >= 1e-6 runs the Gram route (pivoted Cholesky of A~^T A~), whose R
-    differs from Householder's by O(u kappa(R_11)^2); the other cases run the
-    Householder kernel (O(u kappa))."""
+    d <= 1024 with tau >= 1e-6 runs the Gram route (pivoted Cholesky of A~^T A~ on one
+    cooperative grid, FP64), whose R differs from Householder's by O(u kappa(R_11)^2); the other
+    cases run the Householder kernel (O(u kappa))."""
     import torch
     At = _rank_deficient_sketch(m, d, r, seed=m + d)
     perm = torch.empty(d, dtype=torch.int32, device="cuda")
@@ -518,6 +547,31 @@ def test_invalid_arguments(L, h):
     with pytest.raises(L.LevError):
         L.lev_final_dense(h, A, torch.zeros((4, 8), device="cuda"), 9, theta)
     assert L.lev_device_status(h) == 0
+
+
+def test_prepare_builds_the_caches_and_changes_no_result(L):
+    """lev_prepare builds G, the bucket permutation and Omega ahead of the first call: the estimate
+    that follows is bit-identical to one on a fresh handle, and the prepared handle already holds
+    at least the G pair (two m x s BF16 images)."""
+    import torch
+    A = to_dev(W.dense_gaussian(6000, 48, 3).astype(np.float32))
+    p = L.make_params(s=4096, m=192, k=32, tau=1e-6, seed=8, sketch_prec="bf16x3", final_prec="bf16x3")
+    h1, h2 = L.Handle(0), L.Handle(0)
+    try:
+        L.lev_prepare(h1, 6000, 48, p)
+        assert L.lev_workspace_bytes(h1) >= 64 + 2 * 192 * 4096 * 2
+        t1 = torch.empty(6000, device="cuda")
+        t2 = torch.empty(6000, device="cuda")
+        r1 = L.lev_estimate_dense(h1, A, p, t1)
+        r2 = L.lev_estimate_dense(h2, A, p, t2)
+        assert r1 == r2 == 48
+        assert torch.equal(t1, t2)
+        with pytest.raises(L.LevError) as e:
+            L.lev_prepare(h1, 6000, 48, L.make_params(s=0, eps=2.0))
+        assert e.value.code == L.LEV_EINVAL
+    finally:
+        h1.close()
+        h2.close()
 
 
 def test_workspace_bytes_counts_scratch_and_caches(L):
