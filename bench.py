@@ -127,6 +127,88 @@ def allmax(world, x):
     return float(t.item())
 
 
+def gpu_numa_placement(device: int):
+    """Run this process (and so its pinned host buffers, placed on first touch) on the CPUs local to
+    the GPU: the PCI device's NUMA node and CPU list from sysfs. Returns what was found and done."""
+    info = {"pci_bus_id": None, "numa_node": None, "cpus": None, "pinned_to_node": False}
+    try:
+        import torch
+        props = torch.cuda.get_device_properties(device)
+        bus = getattr(props, "pci_bus_id", None)
+        if bus is None:
+            uuid = str(getattr(props, "uuid", ""))
+            out = subprocess.run(["nvidia-smi", "--query-gpu=uuid,pci.bus_id", "--format=csv,noheader"],
+                                 capture_output=True, text=True, timeout=20).stdout
+            for line in out.splitlines():
+                u, b = [x.strip() for x in line.split(",")]
+                if uuid and uuid.replace("GPU-", "") in u:
+                    bus = b
+        if isinstance(bus, int):
+            bus = "%04x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), bus, getattr(props, "pci_device_id", 0))
+        if bus:
+            dom, rest = bus.split(":", 1)
+            bus = ("%04x:" % int(dom, 16)) + rest.lower()
+            info["pci_bus_id"] = bus
+            base = f"/sys/bus/pci/devices/{bus}"
+            with open(f"{base}/numa_node") as f:
+                node = int(f.read().strip())
+            info["numa_node"] = node
+            with open(f"{base}/local_cpulist") as f:
+                cpus = set()
+                for part in f.read().strip().split(","):
+                    a, _, b = part.partition("-")
+                    cpus.update(range(int(a), int(b or a) + 1))
+            allowed = set(os.sched_getaffinity(0))
+            use = sorted(cpus & allowed)
+            if use and node >= 0:
+                os.sched_setaffinity(0, use)
+                info["cpus"] = len(use)
+                info["pinned_to_node"] = True
+    except Exception as e:                       # no sysfs entry (or no permission): leave it as is
+        info["error"] = str(e)[:120]
+    return info
+
+
+def host_link(A_host, A_dev, theta_host, theta_dev, reps=3):
+    """Pinned host <-> device copy rates on a side stream, CUDA events (best of reps)."""
+    import torch
+    st = torch.cuda.Stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h2d, d2h = [], []
+    for _ in range(reps):
+        with torch.cuda.stream(st):
+            a.record(st)
+            A_dev.copy_(A_host, non_blocking=True)
+            b.record(st)
+        torch.cuda.synchronize()
+        h2d.append(A_host.numel() * A_host.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9)
+        with torch.cuda.stream(st):
+            a.record(st)
+            theta_host.copy_(theta_dev, non_blocking=True)
+            b.record(st)
+        torch.cuda.synchronize()
+        d2h.append(theta_host.numel() * theta_host.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9)
+    return max(h2d), max(d2h)
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def make_input(cfg):
     return W.dense_lowrank_skewed(cfg["n"], cfg["d"], cfg["rank"], seed=cfg["data_seed"])
 
@@ -276,7 +358,7 @@ def main():
     ap.add_argument("--no-exact", action="store_true", help="skip the Alg. 7 (LS-HRN-exact) measurement")
     ap.add_argument("--no-extras", action="store_true", help="skip the rank-rule and least-squares measurements")
     ap.add_argument("--no-csr", action="store_true", help="skip the CSR 8e6 x 1024 measurement")
-    ap.add_argument("--csr-large", action="store_true", help="also measure the CSR 8e7 x 1024 (~1e9 nnz) workload")
+    ap.add_argument("--no-csr-large", action="store_true", help="skip the CSR 8e7 x 1024 (~1e9 nnz) workload")
     ap.add_argument("--streams", type=int, default=6,
                     help="batches in flight: step i runs on stream i mod S with its own handle, so one batch's "
                          "latency-bound pivoted Cholesky overlaps another batch's HBM- and tensor-bound kernels")
@@ -308,6 +390,19 @@ def main():
     torch.cuda.set_device(local)
     import paper_2105_11004_gb300 as L
 
+    placement = gpu_numa_placement(local)            # before any pinned host buffer exists
+    # the ~1e9-nonzero CSR workload takes minutes to generate on the host: start it now, in a thread,
+    # so that it overlaps the GPU work of the other sections
+    large = {}
+    gen_thread = None
+    if not args.no_csr and not args.no_csr_large:
+        def _gen_large():
+            c = W.CONFIGS["csr_8e7x1024_rank1014"]
+            t0 = time.perf_counter()
+            large["C"] = W.csr_dup_columns(c["n"], c["d"], seed=c["data_seed"])
+            large["gen_s"] = time.perf_counter() - t0
+        gen_thread = threading.Thread(target=_gen_large, daemon=True)
+        gen_thread.start()
     n, d = cfg["n"], cfg["d"]
     A_np = make_input(cfg)
     A_host = torch.from_numpy(A_np).pin_memory()
@@ -321,6 +416,20 @@ def main():
     p = params(args.final_prec)
     theta = torch.empty(n, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    # cacheable setup (the handle keeps G, the bucket permutation and Omega per seed and sizes):
+    # lev_prepare timed with a seed the handle has not seen, after a first call has sized the buffers
+    L.lev_prepare(h, n, d, p)
+    torch.cuda.synchronize()
+    q = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"] + 1000,
+                      sketch_prec=args.sketch_prec)
+    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_.record(stream)
+    L.lev_prepare(h, n, d, q)
+    b_.record(stream)
+    torch.cuda.synchronize()
+    setup = {"ms": a_.elapsed_time(b_)}
+    setup["what"] = (f"G ({cfg['m']} x {cfg['s']}, BF16 hi + lo pair of the FP32 draws), the CountSketch bucket "
+                     f"permutation ({n} rows) and Omega ({d} x {cfg['k']}) for a new seed (lev_prepare)")
     # kernels of one lev_estimate_dense step with the bucket permutation, G and Omega cached:
     # CountSketch, then the Gaussian stage (split-K SGEMM + reduce, or operand transpose + tcgen05
     # GEMM + reduce), Gram + reduce + row fill + pivoted Cholesky + two assembly kernels, the scaled
@@ -491,10 +600,17 @@ def main():
            "rank_found": rank_found, "stages_ms": stages, "final_ms_by_form": final_ms, "forms": forms,
            "ms_per_step_one_batch_in_flight": forms.get(args.final_prec, {}).get("ms_per_step"),
            "theta_equal_across_streams": same_theta,
+           "setup_ms": setup, "host_placement": placement,
+           "step_hbm": {"algorithmic_bytes": 2 * n * d * 4 + cfg["s"] * d * 4 + n * 4,
+                        "gbs_one_batch": None, "gbs_batches_in_flight": (2 * n * d * 4 + cfg["s"] * d * 4 + n * 4)
+                        / (ms * 1e-3) / 1e9, "note": "A read twice (CountSketch, final pass), B written, theta written"},
            "roofline": roof, "dominant_stage": dominant, "dominant_kernel": dominant_kernel,
            "kernel_ms": kernel_ms, "rooflines": rooflines,
            "roofline_final_pass": rooflines["final"],
            "clocks": clocks, "gpu_launches": kernels_per_step * args.steps}
+    one = out["ms_per_step_one_batch_in_flight"]
+    if one:
+        out["step_hbm"]["gbs_one_batch"] = out["step_hbm"]["algorithmic_bytes"] / (one * 1e-3) / 1e9
 
     # Alg. 7 (LS-HRN-exact) on the same batch: the sketch's QR selects K, the FP64 Gram matrix of A
     # (2.1e10 FMA at n = 1e6, d = 256) gives B = A_K^T A_K, then its Cholesky and the final pass
@@ -544,8 +660,12 @@ def main():
 
     if not args.no_csr:
         out["csr"] = {"csr_8e6x1024": csr_timing(L, h, "csr_8e6x1024", reps)}
-        if args.csr_large:
-            out["csr"]["csr_8e7x1024_rank1014"] = csr_timing(L, h, "csr_8e7x1024_rank1014", 3)
+        if gen_thread is not None:
+            t0 = time.perf_counter()
+            gen_thread.join()
+            wait_s = time.perf_counter() - t0
+            out["csr"]["csr_8e7x1024_rank1014"] = csr_large_timing(L, h, "csr_8e7x1024_rank1014", 3, large)
+            out["csr"]["csr_8e7x1024_rank1014"]["generation_wait_s"] = wait_s
 
     if not args.no_e2e:
         # end to end through the public API with pinned host A and theta: every step copies A
@@ -568,19 +688,27 @@ def main():
         torch.cuda.synchronize()
         te = allmax(world, (time.perf_counter() - t0) / ke)
         same = bool(np.array_equal(theta_host.numpy(), theta_dev.cpu().numpy()))
+        h2d_gbs, d2h_gbs = host_link(A_host, torch.empty_like(A), theta_host, theta_dev)
         out["e2e"] = {"value": n * world / te, "unit": "rows/s", "h2d_bytes_per_step": n * d * 4,
                       "d2h_bytes_per_step": n * 4, "ms_per_step": te * 1e3, "steps": ke,
-                      "h2d_floor_ms": n * d * 4 / 211e9 * 1e3,
+                      "h2d_gbs_measured": h2d_gbs, "d2h_gbs_measured": d2h_gbs,
+                      "h2d_floor_ms": n * d * 4 / (h2d_gbs * 1e9) * 1e3,
+                      "floor_source": "pinned 1.02 GB host -> device copy timed by CUDA events in this run",
                       "api": "lev_estimate_dense, pinned host A and theta, LEV_HOST_ASYNC (copy of step i+1 "
                              "overlaps the kernels of step i; one synchronisation after the loop)",
                       "theta_equals_device_path": same}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t0 = time.perf_counter()
-        est = oracle_step(A_np, cfg)
-        dt = time.perf_counter() - t0
+        runs = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            est = oracle_step(A_np, cfg)
+            runs.append(time.perf_counter() - t0)
+        dt = float(np.median(runs))
+        one = single_thread_oracle(cfg, 262144)
         out["cpu_baseline"] = {"value": n / dt, "unit": "rows/s", "cores": cpu_threads(), "kind": "oracle",
-                               "sample": "one run of the FP64 oracle on the full workload", "seconds": dt}
+                               "sample": "the FP64 oracle on the full workload, median of 3 runs", "seconds": runs,
+                               "cpu_model": cpu_model(), "single_thread": one}
         out["oracle_rank"] = est.rank
         for f, th in form_theta.items():
             rel = np.abs(th.astype(np.float64) - est.theta) / est.theta
@@ -622,6 +750,11 @@ def csr_timing(L, h, name, reps):
         return a.elapsed_time(b) / k
 
     ms = timed(lambda: L.lev_estimate_csr(h, rp, cl, vl, n, d, p, theta, want_rank=False), reps)
+    # cacheable setup for a new seed: G (4096 x 262144 as the BF16 pair), bucket permutation, Omega
+    setup_ms = timed(lambda: L.lev_prepare(h, n, d, L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"],
+                                                                   seed=int(time.time_ns() % 10**9),
+                                                                   sketch_prec="bf16x3")), 1)
+    L.lev_prepare(h, n, d, p)
     At = torch.empty((cfg["m"], d), dtype=torch.float32, device="cuda")
     perm = torch.empty(d, dtype=torch.int32, device="cuda")
     R = torch.empty((d, d), dtype=torch.float64, device="cuda")
@@ -636,7 +769,7 @@ def csr_timing(L, h, name, reps):
               "final": timed(lambda: L.lev_final_csr(h, rp, cl, vl, n, d, Mf, "fp32", theta), reps)}
     csr_bytes = C.nnz * 8 + (n + 1) * 8
     out = {"n": n, "d": d, "nnz": C.nnz, "rank": r, "ms_per_step": ms, "rows_per_s": n / (ms * 1e-3),
-           "csr_gbs_two_passes": 2 * csr_bytes / (ms * 1e-3) / 1e9, "stages_ms": stages,
+           "csr_gbs_two_passes": 2 * csr_bytes / (ms * 1e-3) / 1e9, "stages_ms": stages, "setup_ms": setup_ms,
            "sketch_prec": "bf16x3", "final_prec": "fp32", "generation_s": gen_s}
     # the same estimate with an SRHT after the CountSketch (Sec. 4.1): t from the quoted SRHT
     # theorem, 4 (sqrt(d) + sqrt(ln(s d)))^2 ln d, rounded up to a multiple of 64
@@ -668,6 +801,81 @@ def csr_timing(L, h, name, reps):
                     "rows_per_s": n / (ms_e * 1e-3), "gram_pairs": float(np.sum(lens * (lens + 1) / 2)),
                     "note": "three host synchronisations per call (after each factorisation and after counting the long rows)"}
     return out
+
+
+def csr_large_timing(L, h, name, reps, pre):
+    """The whole estimate on the CSR 8e7 x 1024 workload (~1e9 nonzeros; split-BF16 Gaussian stage,
+    FP32 CSR final pass), generated on the host beforehand (pre["C"]): setup, step time, stages, rank."""
+    import torch
+    cfg = W.CONFIGS[name]
+    n, d = cfg["n"], cfg["d"]
+    C = pre.pop("C")
+    gen_s = pre.get("gen_s")
+    rp, cl, vl = (torch.from_numpy(x).cuda() for x in (C.row_ptr, C.col, C.val))
+    del C
+    nnz = cl.numel()
+    p = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3")
+    theta = torch.empty(n, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    setup_ms = timed(lambda: L.lev_prepare(h, n, d, L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"],
+                                                                   tau=cfg["tau"], seed=int(time.time_ns() % 10**9),
+                                                                   sketch_prec="bf16x3")), 1)
+    r = L.lev_estimate_csr(h, rp, cl, vl, n, d, p, theta)
+    ms = timed(lambda: L.lev_estimate_csr(h, rp, cl, vl, n, d, p, theta, want_rank=False), reps)
+    At = torch.empty((cfg["m"], d), dtype=torch.float32, device="cuda")
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    R = torch.empty((d, d), dtype=torch.float64, device="cuda")
+    Mf = torch.empty((d, cfg["k"]), dtype=torch.float32, device="cuda")
+    L.lev_sketch_csr(h, rp, cl, vl, n, d, p, At)
+    L.lev_rrqr(h, At, cfg["tau"], perm, R)
+    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
+    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
+    stages = {"sketch": timed(lambda: L.lev_sketch_csr(h, rp, cl, vl, n, d, p, At), reps),
+              "rrqr": timed(lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R), reps),
+              "omega": timed(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf), reps),
+              "final": timed(lambda: L.lev_final_csr(h, rp, cl, vl, n, d, Mf, "fp32", theta), reps)}
+    csr_bytes = nnz * 8 + (n + 1) * 8
+    out = {"n": n, "d": d, "nnz": nnz, "rank": r, "ms_per_step": ms, "rows_per_s": n / (ms * 1e-3),
+           "csr_gbs_two_passes": 2 * csr_bytes / (ms * 1e-3) / 1e9, "stages_ms": stages, "setup_ms": setup_ms,
+           "sketch_prec": "bf16x3", "final_prec": "fp32", "generation_s": gen_s,
+           "note": "row_ptr checked once per call; setup = G, bucket permutation and Omega for a new seed"}
+    del rp, cl, vl
+    torch.cuda.empty_cache()
+    return out
+
+
+def single_thread_oracle(cfg, rows):
+    """The FP64 oracle on a `rows`-row matrix of the dense workload's recipe (same rank, row scaling,
+    seed, s, m, k) in a child process whose BLAS and OpenMP pools have one thread: rows/s on one core,
+    a bounded sample (the fixed cost of generating G is included)."""
+    code = ("import os, sys, time\n"
+            "sys.path.insert(0, %r)\n"
+            "import numpy as np, workloads as W\n"
+            "from oracle import estimator as E\n"
+            "A = W.dense_lowrank_skewed(%d, %d, %d, seed=%d)[:%d].astype(np.float64)\n"
+            "t0 = time.perf_counter(); E.estimate(A, %d, %d, %d, %r, %d); print(time.perf_counter() - t0)\n"
+            % (ROOT, rows, cfg["d"], cfg["rank"], cfg["data_seed"], rows, cfg["s"], cfg["m"], cfg["k"], cfg["tau"],
+               cfg["seed"]))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        sec = float(r.stdout.strip().splitlines()[-1])
+        return {"value": rows / sec, "unit": "rows/s", "cores": 1, "seconds": sec,
+                "sample": f"a {rows}-row matrix of the dense workload's recipe, same s, m, k, one thread"}
+    except Exception as e:
+        return {"error": str(e)[:200]}
 
 
 def lstsq_timing(L, h, n, d, time_steps):

@@ -206,91 +206,106 @@ __global__ void __launch_bounds__(256) k_final_csr_fp32(
 }
 
 // CSR with the second form of Lemma 1 for short rows: theta~_i = a_i P a_i^T, P = Mfull Mfull^T
-// (d x d FP64), i.e. the sum over the entry pairs p <= q of (2 - [p = q]) a_p a_q P[c_p][c_q]:
-// nnz_i^2 / 2 FP64 terms from a matrix that sits in L2, against nnz_i k products and nnz_i rows of
+// (d x d), i.e. the sum over the entry pairs p <= q of (2 - [p = q]) a_p a_q P[c_p][c_q]:
+// nnz_i^2 / 2 terms from a matrix that sits in L2, against nnz_i k products and nnz_i rows of
 // Mfull for the first form. Repeated columns are handled as they stand (the double sum over the
 // pairs is the quadratic form); columns outside [0, d) count as zero.
 //
-// k_final_csr_short: rows of at most 8 entries, 8 lanes a row and four rows a warp (the chain of
-// dependent loads of a row, bounds then entries then P, is what limits this pass, so a warp keeps
-// four rows in flight); each lane holds one entry, the pairs (row-major upper triangle, at most 36)
-// go round the 8 lanes in 5 fixed rounds. Longer rows are left to k_final_csr_long.
-__device__ __forceinline__ void tri_pair(int t, int len, int& p, int& q) {
-    p = 0;
-    while (t >= len - p) {
-        t -= len - p;
-        ++p;
-    }
-    q = p + t;
+// The terms are summed in FP32 arithmetic with double-float accuracy (FP64 runs at 1/64 of the FP32
+// rate here and made this pass FP64-bound): P is held as a pair hi + lo of FP32 matrices (the FP64
+// Gram matrix of Mfull^T split once), each term's product is formed with its rounding errors
+// (TwoProduct of the two entries, the pair of P multiplied in), and every lane accumulates its
+// terms with TwoSum, so a row carries an error of a few 2^-48 of sum |terms| rather than 2^-24.
+__device__ __forceinline__ void df_add(float& sh, float& sl, float th, float tl) {
+    const float s = __fadd_rn(sh, th);
+    const float bb = __fsub_rn(s, sh);
+    float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(th, bb));
+    e = __fadd_rn(e, __fadd_rn(sl, tl));
+    sh = __fadd_rn(s, e);
+    sl = __fsub_rn(e, __fsub_rn(sh, s));
+}
+// (w a b) (P_hi + P_lo) as an unevaluated pair (w = 1 or 2, exact).
+__device__ __forceinline__ void df_term(float a, float b, float w, float2 P, float& th, float& tl) {
+    const float x = __fmul_rn(a, b);
+    const float xe = __fmaf_rn(a, b, -x);                             // a b = x + xe exactly
+    const float xw = __fmul_rn(x, w), xwe = __fmul_rn(xe, w);          // exact (w a power of two)
+    th = __fmul_rn(xw, P.x);
+    tl = __fmaf_rn(xw, P.x, -th);
+    tl = __fmaf_rn(xw, P.y, tl);
+    tl = __fmaf_rn(xwe, P.x, tl);
 }
 
-__global__ void __launch_bounds__(256) k_final_csr_short(const int64_t* __restrict__ row_ptr,
+// Rows with LO < len <= SEG entries (an empty row gets 0): SEG lanes a row, 32 / SEG rows a warp (a row is a short chain of
+// dependent loads, bounds then entries then P, so a warp keeps several in flight, the next rows'
+// bounds loaded ahead). Lane l of a row holds entry l; in step q the row's entry q is broadcast and
+// lane p <= q adds the pair (p, q), so each pair is taken once; the lanes' pairs are summed by
+// shuffles (TwoSum) at the end.
+template <int SEG, int LO>
+__global__ void __launch_bounds__(256) k_final_csr_pairs(const int64_t* __restrict__ row_ptr,
                                                          const int32_t* __restrict__ col,
                                                          const float* __restrict__ val, int64_t n, int d,
-                                                         const double* __restrict__ P, float* __restrict__ theta) {
-    const int lane = threadIdx.x & 31, seg = lane >> 3, sl = lane & 7;
+                                                         const float2* __restrict__ P, float* __restrict__ theta) {
+    constexpr int RPW = 32 / SEG;
+    const int lane = threadIdx.x & 31, seg = lane / SEG, sl = lane % SEG;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // one-deep pipeline: the bounds of the next four rows load while this four runs
-    int64_t rn = warp * 4 + seg;
+    int64_t rn = warp * RPW + seg;
     int64_t np0 = rn < n ? row_ptr[rn] : 0, np1 = rn < n ? row_ptr[rn + 1] : 0;
-    for (int64_t r0 = warp * 4; r0 < n; r0 += nwarps * 4) {
+    for (int64_t r0 = warp * RPW; r0 < n; r0 += nwarps * RPW) {
         const int64_t r = r0 + seg;
-        const bool rok = r < n;
         const int64_t p0 = np0, p1 = np1;
         const int len = (int)(p1 - p0);
-        const bool mine = rok && len <= 8;
+        const bool mine = r < n && len > LO && len <= SEG;
         int c = -1;
         float a = 0.f;
         if (mine && sl < len) {
             c = col[p0 + sl];
             a = val[p0 + sl];
         }
-        rn = r + nwarps * 4;
+        rn = r + nwarps * RPW;
         np0 = rn < n ? row_ptr[rn] : 0;
         np1 = rn < n ? row_ptr[rn + 1] : 0;
-        int my_c = 0;
-        double my_v = 0.0;
-        if ((unsigned)c < (unsigned)d) {
-            my_c = c;
-            my_v = (double)a;
-        }
-        const int npairs = mine ? len * (len + 1) / 2 : 0;
-        double acc = 0.0;
+        if ((unsigned)c >= (unsigned)d) { c = -1; a = 0.f; }
+        const int len_w = mine ? len : 0;
+        int steps = len_w;                                            // the longest row of the warp
 #pragma unroll
-        for (int round = 0; round < 5; ++round) {
-            const int t = round * 8 + sl;
-            int pp = 0, qq = 0;
-            if (t < npairs) tri_pair(t, len, pp, qq);
-            const int cp = __shfl_sync(0xffffffffu, my_c, seg * 8 + pp);
-            const int cq = __shfl_sync(0xffffffffu, my_c, seg * 8 + qq);
-            const double vp = __shfl_sync(0xffffffffu, my_v, seg * 8 + pp);
-            const double vq = __shfl_sync(0xffffffffu, my_v, seg * 8 + qq);
-            if (t < npairs) acc = fma((pp == qq ? 1.0 : 2.0) * vp * vq, P[(int64_t)cp * d + cq], acc);
+        for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(0xffffffffu, steps, o));
+        float sh = 0.f, sl2 = 0.f;
+        const int64_t prow = c >= 0 ? (int64_t)c * d : 0;
+        for (int q = 0; q < steps; ++q) {
+            const int cq = __shfl_sync(0xffffffffu, c, seg * SEG + q);
+            const float aq = __shfl_sync(0xffffffffu, a, seg * SEG + q);
+            if (q < len_w && sl <= q && c >= 0 && cq >= 0) {
+                float th, tl;
+                df_term(a, aq, sl == q ? 1.f : 2.f, P[prow + cq], th, tl);
+                df_add(sh, sl2, th, tl);
+            }
         }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        if (mine && sl == 0) theta[r] = (float)acc;
+#pragma unroll
+        for (int o = SEG / 2; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl2, o);
+            df_add(sh, sl2, oh, ol);
+        }
+        if (mine && sl == 0) theta[r] = __fadd_rn(sh, sl2);
     }
 }
 
-// Rows of more than 8 entries: a warp scans the bounds of 32 rows at once and takes each long row
-// in turn with the whole warp: the second form (one entry per lane, pairs round the lanes) up to 32
+// Rows of more than 16 entries: a warp scans the bounds of 32 rows at once and takes each such row
+// in turn with the whole warp: the second form (one entry per lane, the pair loop above) up to 32
 // entries, the first form (csr_row_norm) above.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_final_csr_long(const int64_t* __restrict__ row_ptr,
                                                         const int32_t* __restrict__ col,
                                                         const float* __restrict__ val, int64_t n, int d,
                                                         const float* __restrict__ M, int k,
-                                                        const double* __restrict__ P, float* __restrict__ theta) {
+                                                        const float2* __restrict__ P, float* __restrict__ theta) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r0 = warp * 32; r0 < n; r0 += nwarps * 32) {
         const int64_t rl = r0 + lane;
         const int64_t lenl = rl < n ? row_ptr[rl + 1] - row_ptr[rl] : 0;
-        unsigned todo = __ballot_sync(0xffffffffu, lenl > 8);
+        unsigned todo = __ballot_sync(0xffffffffu, lenl > 16);
         while (todo) {
             const int b = __ffs(todo) - 1;
             todo &= todo - 1;
@@ -302,28 +317,40 @@ __global__ void __launch_bounds__(256) k_final_csr_long(const int64_t* __restric
                 if (lane == 0) theta[i] = total;
                 continue;
             }
-            int my_c = 0;
-            double my_v = 0.0;
+            int c = -1;
+            float a = 0.f;
             if (lane < len) {
-                const int c = col[p0 + lane];
-                if ((unsigned)c < (unsigned)d) {
-                    my_c = c;
-                    my_v = (double)val[p0 + lane];
+                c = col[p0 + lane];
+                a = val[p0 + lane];
+                if ((unsigned)c >= (unsigned)d) { c = -1; a = 0.f; }
+            }
+            float sh = 0.f, sl2 = 0.f;
+            const int64_t prow = c >= 0 ? (int64_t)c * d : 0;
+            for (int q = 0; q < len; ++q) {
+                const int cq = __shfl_sync(0xffffffffu, c, q);
+                const float aq = __shfl_sync(0xffffffffu, a, q);
+                if (lane <= q && c >= 0 && cq >= 0) {
+                    float th, tl;
+                    df_term(a, aq, lane == q ? 1.f : 2.f, P[prow + cq], th, tl);
+                    df_add(sh, sl2, th, tl);
                 }
             }
-            const int npairs = len * (len + 1) / 2;
-            double acc = 0.0;
-            for (int base = 0; base < npairs; base += 32) {
-                const int t = base + lane;
-                int pp = 0, qq = 0;
-                if (t < npairs) tri_pair(t, len, pp, qq);
-                const int cp = __shfl_sync(0xffffffffu, my_c, pp), cq = __shfl_sync(0xffffffffu, my_c, qq);
-                const double vp = __shfl_sync(0xffffffffu, my_v, pp), vq = __shfl_sync(0xffffffffu, my_v, qq);
-                if (t < npairs) acc = fma((pp == qq ? 1.0 : 2.0) * vp * vq, P[(int64_t)cp * d + cq], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl2, o);
+                df_add(sh, sl2, oh, ol);
             }
-            acc = warp_sum(acc);
-            if (lane == 0) theta[i] = (float)acc;
+            if (lane == 0) theta[i] = __fadd_rn(sh, sl2);
         }
+    }
+}
+
+// Pdf (d x d pairs) = P split into FP32 hi + lo.
+__global__ void k_split_pairs(const double* __restrict__ P, int64_t count, float2* __restrict__ Pdf) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const double x = P[e];
+        const float h = (float)x;
+        Pdf[e] = make_float2(h, (float)(x - (double)h));
     }
 }
 
@@ -352,7 +379,8 @@ cudaError_t launch_final_dense_fp32(const float* A, int64_t lda, int64_t n, int6
 }
 
 size_t csr_gram_scratch_bytes(int64_t d, int64_t k) {
-    return sizeof(double) * (size_t)(d * d + gram_partial_doubles(k, d)) + sizeof(float) * (size_t)(k * d) + 1024;
+    return sizeof(double) * (size_t)(d * d + gram_partial_doubles(k, d)) + sizeof(float) * (size_t)(k * d) +
+           sizeof(float2) * (size_t)(d * d) + 1024;
 }
 
 bool csr_gram_pays(int64_t n, int64_t d, int64_t nnz, int64_t k) {
@@ -364,24 +392,30 @@ cudaError_t launch_final_csr_gram(const int64_t* row_ptr, const int32_t* col, co
     double* P = reinterpret_cast<double*>(scratch);
     double* Gp = P + d * d;
     float* MT = reinterpret_cast<float*>(Gp + gram_partial_doubles(k, d));
+    float2* Pdf = reinterpret_cast<float2*>(reinterpret_cast<uintptr_t>(MT + k * d + 3) & ~uintptr_t(7));
     int tg = (int)((d * k + 255) / 256);
     if (tg > 152 * 8) tg = 152 * 8;
     k_transpose_mfull<<<tg, 256, 0, st>>>(Mfull, (int)d, (int)k, MT);
-    cudaError_t e = launch_gram_fp64(MT, d, k, d, Gp, P, st);           // P = Mfull Mfull^T
+    cudaError_t e = launch_gram_fp64(MT, d, k, d, Gp, P, st);           // P = Mfull Mfull^T (FP64-grade)
     if (e != cudaSuccess) return e;
+    k_split_pairs<<<152 * 4, 256, 0, st>>>(P, d * d, Pdf);
     const bool vec = (reinterpret_cast<uintptr_t>(Mfull) % 16 == 0) && (k % 4 == 0);
-    int64_t grid = (n * 8 + 255) / 256;                 // four rows a warp
+    int64_t grid = (n * 8 + 255) / 256;                 // four rows of up to 8 entries a warp
     if (grid > 152 * 64) grid = 152 * 64;
     if (grid < 1) grid = 1;
-    k_final_csr_short<<<(unsigned)grid, 256, 0, st>>>(row_ptr, col, val, n, (int)d, P, theta);
+    k_final_csr_pairs<8, -1><<<(unsigned)grid, 256, 0, st>>>(row_ptr, col, val, n, (int)d, Pdf, theta);  // empty rows too
+    int64_t grid16 = (n * 16 + 255) / 256;              // two rows of 9 to 16 entries a warp
+    if (grid16 > 152 * 64) grid16 = 152 * 64;
+    if (grid16 < 1) grid16 = 1;
+    k_final_csr_pairs<16, 8><<<(unsigned)grid16, 256, 0, st>>>(row_ptr, col, val, n, (int)d, Pdf, theta);
     int64_t grid_l = (n + 255) / 256;                   // 32 rows scanned a warp
     if (grid_l > 152 * 16) grid_l = 152 * 16;
     if (grid_l < 1) grid_l = 1;
     if (vec)
-        k_final_csr_long<true><<<(unsigned)grid_l, 256, 0, st>>>(row_ptr, col, val, n, (int)d, Mfull, (int)k, P,
+        k_final_csr_long<true><<<(unsigned)grid_l, 256, 0, st>>>(row_ptr, col, val, n, (int)d, Mfull, (int)k, Pdf,
                                                                 theta);
     else
-        k_final_csr_long<false><<<(unsigned)grid_l, 256, 0, st>>>(row_ptr, col, val, n, (int)d, Mfull, (int)k, P,
+        k_final_csr_long<false><<<(unsigned)grid_l, 256, 0, st>>>(row_ptr, col, val, n, (int)d, Mfull, (int)k, Pdf,
                                                                  theta);
     return cudaGetLastError();
 }
