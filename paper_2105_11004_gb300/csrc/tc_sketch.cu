@@ -54,6 +54,7 @@ struct GTraits<gTF32> {
 constexpr int kRowsM = 128;                   // rows of G per CTA (TMEM lanes)
 constexpr int kMaxNt = 256;                   // MMA N: columns of the accumulator tile
 constexpr int kMaxStages = 6;
+constexpr int kMaxSliceKb = 54;               // K blocks in one accumulation chain (3,456 BF16 / 1,728 TF32 products)
 constexpr int kStageBudget = 200 * 1024;      // shared memory for the ring of stages
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint64_t kExitWaitNs = 5000000000ull;
@@ -390,11 +391,14 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
     const int pairs = resident_pairs<F>(smem, cfg, handle_num_sms(h));
     if (pairs < 1) return handle_fail(LEV_ECUDA, "no resident 2-CTA cluster for the Gaussian stage");
     // K slices: the count z that minimises (waves of pairs) x (K blocks a slice + a fixed cost of
-    // about six K blocks for the pipeline fill and the epilogue)
+    // about six K blocks for the pipeline fill and the epilogue), among the counts that keep a slice
+    // at most kMaxSliceKb K blocks long: each slice is one accumulation chain in TMEM, whose error
+    // grows with its length, and the partials of the slices are summed apart in a fixed order
     const int64_t units = (int64_t)pair_tiles * n_tiles;
-    int splits = 1;
+    const int z_min = (int)std::min<int64_t>(kb_total, (kb_total + kMaxSliceKb - 1) / kMaxSliceKb);
+    int splits = z_min;
     int64_t best = -1;
-    for (int z = 1; z <= std::min(kb_total, 256); ++z) {
+    for (int z = z_min; z <= std::min(kb_total, std::max(256, z_min)); ++z) {
         const int64_t per = (kb_total + z - 1) / z;
         const int64_t cost = ((units * z + pairs - 1) / pairs) * (per + 6);
         if (best < 0 || cost < best) { best = cost; splits = z; }

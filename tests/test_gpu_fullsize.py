@@ -6,8 +6,10 @@ own intermediates:
 * QR: pivots form a permutation, diag(R) > 0, the Gram identity
   (A~ P)^T (A~ P) = R^T R on sampled entries of the leading r x r block, the rank;
 * final pass: theta~ of sampled rows from the GPU's Mfull, in FP64.
-The end-to-end comparison with the oracle's own sketch runs at the dense workload
-size (the oracle finishes it in seconds).
+The end-to-end comparison with the oracle's own estimate (its sketch, its Householder QR, its
+final pass) runs at the dense workload size (the oracle finishes it in seconds), on the whole
+CSR 8e6 x 1024 workload and on a 4,194,304-row prefix of the CSR 8e7 x 1024 workload (the
+oracle takes a few minutes of host time for each: about 1e9 FP64 Gaussian draws for G).
 """
 import numpy as np
 import pytest
@@ -272,10 +274,18 @@ def _first_pivot_difference(gp, e, r):
     return t, int(e.perm[t]), int(gp[t]), abs(a - b) / a
 
 
+# Relative gap of two squared trailing norms below which the pivot choice between the two columns is
+# a tie at the precision of the split-BF16 sketch (each product carried to about 2^-16 of itself): the
+# GPU's sketch and the oracle's FP64 sketch may order such a pair differently, and either order is a
+# correct greedy pivot.
+PIVOT_TIE = 1e-5
+
+
 def _csr_end_to_end(L, h, C, cfg):
     """The GPU estimate of CSR C (split-BF16 sketch, FP32 CSR final pass) against the oracle's FP64
-    estimate on the same matrix: rank, pivots on the first r positions, theta~ on every row (at the
-    GPU's pivots, so that a pivot difference would still leave theta~ comparable)."""
+    estimate on the same matrix: rank; pivots equal on the first r positions up to the first step
+    where the two candidates' squared trailing norms tie to within PIVOT_TIE (from there the greedy
+    paths may part, both correct); theta~ on every row against the oracle run at the GPU's pivots."""
     import torch
     n, d = C.shape
     s, m, k, tau, seed = cfg["s"], cfg["m"], cfg["k"], cfg["tau"], cfg["seed"]
@@ -291,14 +301,17 @@ def _csr_end_to_end(L, h, C, cfg):
     if d0 is not None:
         e = E.estimate(A, s, m, k, tau, seed, forced_perm=gp, forced_rank=r, Atilde=e.Atilde)
     assert max_rel(theta, e.theta) <= 1e-4
-    assert d0 is None, "first pivot difference at step %d: oracle column %d, GPU column %d, gap %.2e" % d0
+    assert d0 is None or d0[3] <= PIVOT_TIE, \
+        "first pivot difference at step %d: oracle column %d, GPU column %d, gap %.2e" % d0
     return r
 
 
 def test_csr_8e6x1024_end_to_end_against_oracle(L, h):
     """The CSR 8e6 x 1024 workload end to end against the oracle's own FP64 estimate (its sketch,
-    its Householder QR, its final pass): rank, the 1,024 pivots in order, theta~ on all 8e6 rows
-    within the 1e-4 bar of the split-BF16 sketch with the FP32 CSR final pass."""
+    its Householder QR, its final pass): rank, the 1,024 pivots in order up to the first tie at the
+    sketch's precision (one measured run: equal through step 696, then two columns whose squared
+    trailing norms differ by 3.4e-9 relative), theta~ on all 8e6 rows within the 1e-4 bar of the
+    split-BF16 sketch with the FP32 CSR final pass."""
     cfg = W.CONFIGS["csr_8e6x1024"]
     C = W.csr_uniform(cfg["n"], cfg["d"], seed=cfg["data_seed"])
     assert _csr_end_to_end(L, h, C, cfg) == cfg["d"]
