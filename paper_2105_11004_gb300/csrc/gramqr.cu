@@ -22,12 +22,13 @@
 //     order and mirrored;
 //   k_pchol_grid: one cooperative grid (at most one CTA per SM; ceil(d/3) CTAs
 //     up to d = 256, where a step is latency-bound); CTA c owns the
-//     columns l = c mod gridDim of the Schur complement in shared memory. All
-//     CTAs keep a replicated Schur diagonal and take the same pivot p_j (largest
-//     diagonal, ties to the lowest column) and the same rank decision
-//     S_pp <= tau^2 S_00 without exchanging them; the owner of each pivot
-//     publishes its updated column, unscaled, as soon as it is up to date, and
-//     the others wait for that row only (no flag, no grid barrier per step).
+//     columns l = c mod gridDim of the Schur complement in shared memory, in
+//     double-float arithmetic (FP32 pairs, about 48 bits; FP64 runs at 1/64 of
+//     the FP32 rate here). All CTAs keep a replicated Schur diagonal and take the
+//     same pivot p_j (largest diagonal, ties to the lowest column) and the same
+//     rank decision S_pp <= tau^2 S_00 without exchanging them; the owner of each
+//     pivot publishes its updated column, unscaled, as soon as it is up to date,
+//     and the others wait for that row only (no flag, no grid barrier per step).
 //
 // The Gram route resolves |R_jj| / |R_00| down to about sqrt(m u) ~ 1e-7; the
 // caller uses the Householder kernel when tau is below 1e-6 or d > 1024.
@@ -290,14 +291,11 @@ __device__ __forceinline__ uint64_t gtimer() {
 // The owner writes row j of R (scaled, original column order) to Rorig off the
 // critical path; nothing reads Rorig before the kernel ends.
 constexpr unsigned long long kUnwritten = 0xFFF40000DEADBEEFull;
+constexpr int kRowsPerThread = 4;                  // d <= 1024 rows over 256 threads
 __device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void st_relaxed_gpu_f64(double* p, double v) {
-    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
 __global__ void k_fill_unwritten(unsigned long long* R, int64_t count) {
@@ -305,64 +303,114 @@ __global__ void k_fill_unwritten(unsigned long long* R, int64_t count) {
         R[e] = kUnwritten;
 }
 
-// The Schur diagonal is compared through its bit pattern (int64 order = double order
-// for non-negative values; any positive value beats every non-positive one).
-__device__ __forceinline__ bool positive_finite(long long b) { return b > 0 && b < 0x7FF0000000000000LL; }
-
-// Order-preserving unsigned key of a double (larger value, larger key); 0 is below every value
-// and marks inactive entries.
-__device__ __forceinline__ unsigned long long order_key(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+// ---- double-float arithmetic: a value is an FP32 pair (hi, lo), |lo| <= ulp(hi) / 2, about 48
+// significant bits, operated on with error-free transformations (TwoSum, FMA-based TwoProduct). FP64
+// runs at 1/64 of the FP32 rate on this GPU, and the Schur updates of the pivoted Cholesky are
+// FP64-issue-bound at d = 1,024 in FP64.
+__device__ __forceinline__ float2 df_from_double(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+// a b (TwoProduct of the high parts, cross terms by FMA, renormalised)
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float h = __fadd_rn(p, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, p)));
+}
+// x - a b (TwoSum of the high parts; the low parts and the product's error into the error term)
+__device__ __forceinline__ float2 df_sub_mul(float2 x, float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float pe = __fmaf_rn(a.x, b.x, -p);
+    pe = __fmaf_rn(a.x, b.y, pe);
+    pe = __fmaf_rn(a.y, b.x, pe);
+    const float s = __fsub_rn(x.x, p);
+    const float bb = __fsub_rn(s, x.x);
+    float err = __fadd_rn(__fsub_rn(x.x, __fsub_rn(s, bb)), __fsub_rn(-p, bb));
+    err = __fadd_rn(err, __fsub_rn(x.y, pe));
+    const float h = __fadd_rn(s, err);
+    return make_float2(h, __fsub_rn(err, __fsub_rn(h, s)));
+}
+// 1 / sqrt(v) for a positive double-float v: an FP32 estimate, one FP32 Newton step, then one step
+// y + y (1 - v y^2) / 2 with the residual formed in double-float (to about 2^-46)
+__device__ __forceinline__ float2 df_inv_sqrt(float2 v) {
+    float y = rsqrtf(v.x);
+    y = __fmul_rn(y, __fmaf_rn(__fmul_rn(-0.5f, v.x), __fmul_rn(y, y), 1.5f));
+    const float yy = __fmul_rn(y, y);
+    const float yye = __fmaf_rn(y, y, -yy);
+    const float2 t = df_mul(v, make_float2(yy, yye));
+    const float res = __fadd_rn(__fsub_rn(1.0f, t.x), -t.y);
+    const float corr = __fmul_rn(__fmul_rn(0.5f, y), res);
+    const float h = __fadd_rn(y, corr);
+    return make_float2(h, __fsub_rn(corr, __fsub_rn(h, y)));
+}
+// order-preserving keys of an FP32 value and of a double-float (hi first, then lo); 0 marks "none"
+__device__ __forceinline__ unsigned order_key32(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ unsigned long long df_key(float2 v) {
+    return ((unsigned long long)order_key32(v.x) << 32) | order_key32(v.y);
+}
+__device__ __forceinline__ unsigned long long df_bits(float2 v) {
+    return ((unsigned long long)__float_as_uint(v.y) << 32) | __float_as_uint(v.x);
+}
+__device__ __forceinline__ float2 df_of_bits(unsigned long long b) {
+    return make_float2(__uint_as_float((unsigned)b), __uint_as_float((unsigned)(b >> 32)));
+}
+__device__ __forceinline__ void st_relaxed_gpu_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// 1/sqrt(x) for a positive finite x: an FP32 estimate of the exponent-reduced argument, then two
-// Newton-Raphson steps y <- y (3 - x y^2) / 2 in FP64 (the error squares each step: ~2^-22 to
-// ~2^-44 to FP64 rounding). Subnormal x takes CUDA's rsqrt.
-__device__ __forceinline__ double inv_sqrt_pos(double x) {
-    const long long b = __double_as_longlong(x);
-    const int E = (int)((b >> 52) & 0x7FF) - 1023;
-    if (E == -1023) return rsqrt(x);
-    const int h = E >> 1;                                               // x = m 2^(2h), m in [1, 4)
-    const double m = __longlong_as_double(b - ((long long)(2 * h) << 52));
-    double y = (double)rsqrtf((float)m);
-    y = __longlong_as_double(__double_as_longlong(y) - ((long long)h << 52));   // y ~ 1/sqrt(x)
-    y = y * fma(-0.5 * x, y * y, 1.5);
-    y = y * fma(-0.5 * x, y * y, 1.5);
-    return y;
-}
-
+// The Schur complement is held in double-float: G is first scaled by 2^-e (e even, the largest
+// diagonal entry in [1, 4)), so that every value the factorisation can pivot on stays inside FP32's
+// exponent range (a forced pivot whose Schur diagonal falls below about 2^-126 of the largest
+// diagonal entry stops the factorisation as a non-positive one would). Rows of R are written as
+// double-float pairs into the bytes of Rorig, scaled by 2^(-e/2); k_df_to_fp64 turns them into
+// FP64 with rscale_out = 2^(e/2) afterwards. The published rows U hold the pairs' 8-byte patterns
+// (the "unwritten" sentinel has a NaN low part, which no pair has).
 __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict__ Gm, int d, int m, double tau,
                                                        const int32_t* __restrict__ forced, int forced_rank,
-                                                       double* __restrict__ U, double* __restrict__ Rorig,
-                                                       int32_t* __restrict__ piv, int64_t* __restrict__ rank_out,
-                                                       int32_t* status) {
+                                                       unsigned long long* __restrict__ U, float2* __restrict__ Rdf,
+                                                       double* __restrict__ rscale_out, int32_t* __restrict__ piv,
+                                                       int64_t* __restrict__ rank_out, int32_t* status) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int G = gridDim.x, me = blockIdx.x;
     const int ncl = (d - me + G - 1) / G;                        // columns me, me + G, ...
-    double* S = reinterpret_cast<double*>(smem);                  // ncl x d (own columns)
-    double* ubuf = S + (size_t)ncl * d;                           // d: unscaled row (owner's own entries)
-    double* rbuf = ubuf + d;                                      // d: row j of R
-    double* diag = rbuf + d;                                      // d: replicated Schur diagonal
+    float2* S = reinterpret_cast<float2*>(smem);                  // ncl x d (own columns)
+    float2* ubuf = S + (size_t)ncl * d;                           // d: unscaled row (owner's own entries)
+    float2* rbuf = ubuf + d;                                      // d: row j of R
+    float2* diag = rbuf + d;                                      // d: replicated Schur diagonal
     int* active = reinterpret_cast<int*>(diag + d);               // d
     __shared__ unsigned long long red_k[8];
     __shared__ int red_i[8];
+    __shared__ double red_d[8];
     __shared__ volatile int s_abort;
-    __shared__ double s_inv;
-    // steps whose pivot this CTA owns, by local column: the step and the pivot's Schur diagonal
-    // (the diagonal entries of R, sqrt of those, are written after the loop)
-    __shared__ int own_j[32];
-    __shared__ double own_bv[32];
+    __shared__ float2 s_inv;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // prescale 2^-e from the largest diagonal entry (the same in every CTA)
+    double mx = 0.0;
+    for (int i = tid; i < d; i += 256) mx = fmax(mx, Gm[(int64_t)i * d + i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red_d[wid] = mx;
+    __syncthreads();
+    mx = red_d[0];
+    for (int w = 1; w < 8; ++w) mx = fmax(mx, red_d[w]);
+    int ex = 0;
+    if (mx > 0.0 && mx < 1.0e300) ex = ilogb(mx) & ~1;
+    const double scale = ldexp(1.0, -ex);
+    if (me == 0 && tid == 0) *rscale_out = ldexp(1.0, ex / 2);
     for (int lc = 0; lc < ncl; ++lc) {
         const double* src = Gm + (int64_t)(lc * G + me) * d;     // column = row (symmetric)
-        for (int i = tid; i < d; i += 256) S[(size_t)lc * d + i] = src[i];
+        for (int i = tid; i < d; i += 256) S[(size_t)lc * d + i] = df_from_double(src[i] * scale);
     }
     for (int i = tid; i < d; i += 256) {
         active[i] = 1;
-        diag[i] = Gm[(int64_t)i * d + i];
+        diag[i] = df_from_double(Gm[(int64_t)i * d + i] * scale);
     }
-    for (int lc = tid; lc < 32; lc += 256) own_j[lc] = -1;
     if (tid == 0) s_abort = 0;
     __syncthreads();
     // largest active diagonal entry, ties to the lowest index: per thread over its own indices,
@@ -373,7 +421,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         int bi = INT_MAX;
         for (int i = tid; i < d; i += 256)
             if (active[i]) {
-                const unsigned long long k = order_key(diag[i]);
+                const unsigned long long k = df_key(diag[i]);
                 if (k > bk) { bk = k; bi = i; }                       // i increases: ties keep the lowest
             }
         const unsigned hi = (unsigned)(bk >> 32), lo = (unsigned)bk;
@@ -389,15 +437,14 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
             if (red_k[w] > bk || (red_k[w] == bk && red_i[w] < bi)) { bk = red_k[w]; bi = red_i[w]; }
         return bk == 0 ? INT_MAX : bi;
     };
-    // rank test on the pivot's squared trailing norm: stop at a non-positive pivot, or
-    // (unforced) at s_pp <= tau^2 s_00; evaluated identically by every thread
-    long long thr = 0;
+    // rank test on the pivot's squared trailing norm: stop at a pivot that is not positive and
+    // finite, or (unforced) at s_pp <= tau^2 s_00, compared through keys; the same in every thread
+    unsigned long long thr = 0;
     auto stops = [&](int j, int p) -> bool {
-        const double bv = diag[p];
-        const long long b = __double_as_longlong(bv);
-        if (!positive_finite(b)) return true;
-        if (j == 0) thr = __double_as_longlong(tau * tau * bv);
-        return !forced && b <= thr;
+        const float2 v = diag[p];
+        if (!(v.x > 0.f) || !(v.x < 3.0e38f)) return true;
+        if (j == 0) thr = df_key(df_from_double(tau * tau * df_to_double(v)));
+        return !forced && df_key(v) <= thr;
     };
     const int steps = forced ? min(forced_rank, min(m, d)) : min(m, d);
     int j = 0;
@@ -409,31 +456,41 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     }
     if (go) {
         if (p % G == me) {
-            const double* col = S + (size_t)(p / G) * d;
+            const float2* col = S + (size_t)(p / G) * d;
             for (int i = tid; i < d; i += 256)
                 if (i != p) {
                     ubuf[i] = col[i];
-                    st_relaxed_gpu_f64(U + i, col[i]);
+                    st_relaxed_gpu_u64(U + i, df_bits(col[i]));
                 }
         }
-        if (tid == 0) s_inv = inv_sqrt_pos(diag[p]);
-        if (tid == 0 && p % G == me) { own_j[p / G] = 0; own_bv[p / G] = diag[p]; }
+        if (tid == 0) s_inv = df_inv_sqrt(diag[p]);
         __syncthreads();
     }
     for (; go && j < steps; ++j) {
-        const double inv = s_inv;
+        const float2 inv = s_inv;
         const bool owner = (p % G) == me;
         // 1. row j of R: unscaled entries (own copy or the published row, bounded spin), scaled,
         //    and the replicated diagonal updated, index by index
-        const unsigned long long* urow = reinterpret_cast<const unsigned long long*>(U + (int64_t)j * d);
-        for (int i = tid; i < d; i += 256) {
-            double r = 0.0;
+        const unsigned long long* urow = U + (int64_t)j * d;
+        // the published entries of this thread (at most kRowsPerThread), all loads issued before any
+        // is waited on, so that they share one L2 round trip
+        unsigned long long first[kRowsPerThread];
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const int i = tid + 256 * k;
+            first[k] = (!owner && i < d && active[i] && i != p) ? ld_relaxed_gpu_u64(urow + i) : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const int i = tid + 256 * k;
+            if (i >= d) break;
+            float2 r = make_float2(0.f, 0.f);
             if (active[i] && i != p) {
-                double u;
+                float2 u;
                 if (owner) {
                     u = ubuf[i];
                 } else {
-                    unsigned long long bits = ld_relaxed_gpu_u64(urow + i);
+                    unsigned long long bits = first[k];
                     if (bits == kUnwritten) {
                         const uint64_t t0 = gtimer();
                         for (uint32_t it = 0;; ++it) {
@@ -446,18 +503,19 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
                             }
                         }
                     }
-                    u = __longlong_as_double((long long)bits);
+                    u = df_of_bits(bits);
                 }
-                r = u * inv;
-                diag[i] = fma(-r, r, diag[i]);
+                r = df_mul(u, inv);
+                diag[i] = df_sub_mul(diag[i], r, r);
             }
             if (i == p) active[i] = 0;
             rbuf[i] = r;
         }
         if (owner) {
-            double* row = Rorig + (int64_t)j * d;
+            float2* row = Rdf + (int64_t)j * d;
             for (int i = tid; i < d; i += 256)
                 if (i != p && active[i]) row[i] = rbuf[i];
+            if (tid == 0) row[p] = df_mul(diag[p], inv);              // R_jj = s_pp / sqrt(s_pp)
         }
         if (me == 0 && tid == 0) piv[j] = p;
         // 2. the next pivot and its rank test (one barrier)
@@ -472,42 +530,44 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         const bool go_on = j + 1 < steps && pn >= 0 && pn < d && active[pn] && !stops(j + 1, pn);
         // 3. owner of the next pivot: its column first, published unscaled entry by entry
         if (go_on && pn % G == me) {
-            double* col = S + (size_t)(pn / G) * d;
-            const double rc = rbuf[pn];
-            double* urow_n = U + (int64_t)(j + 1) * d;
+            float2* col = S + (size_t)(pn / G) * d;
+            const float2 rc = rbuf[pn];
+            unsigned long long* urow_n = U + (int64_t)(j + 1) * d;
             for (int i = tid; i < d; i += 256)
                 if (active[i]) {
-                    const double v = fma(-rbuf[i], rc, col[i]);
+                    const float2 v = df_sub_mul(col[i], rbuf[i], rc);
                     col[i] = v;
                     if (i != pn) {
                         ubuf[i] = v;
-                        st_relaxed_gpu_f64(urow_n + i, v);
+                        st_relaxed_gpu_u64(urow_n + i, df_bits(v));
                     }
                 }
         }
         // 4. the next step's scale factor (every CTA, while the row travels)
-        if (go_on && tid == 0) {
-            s_inv = inv_sqrt_pos(diag[pn]);
-            if (pn % G == me) { own_j[pn / G] = j + 1; own_bv[pn / G] = diag[pn]; }
-        }
+        if (go_on && tid == 0) s_inv = df_inv_sqrt(diag[pn]);
         // 5. the other own columns
         for (int lc = 0; lc < ncl; ++lc) {
             const int c = lc * G + me;
             if (c == pn || !active[c]) continue;
-            const double rc = rbuf[c];
-            double* col = S + (size_t)lc * d;
+            const float2 rc = rbuf[c];
+            float2* col = S + (size_t)lc * d;
             for (int i = tid; i < d; i += 256)
-                if (active[i]) col[i] = fma(-rbuf[i], rc, col[i]);
+                if (active[i]) col[i] = df_sub_mul(col[i], rbuf[i], rc);
         }
         __syncthreads();
         if (!go_on) { ++j; break; }
         p = pn;
     }
-    // R_jj = sqrt(s_pp) for the steps this CTA owned (steps at or beyond the rank were never taken)
-    __syncthreads();
-    for (int lc = tid; lc < ncl; lc += 256)
-        if (own_j[lc] >= 0 && own_j[lc] < j) Rorig[(int64_t)own_j[lc] * d + lc * G + me] = sqrt(own_bv[lc]);
     if (me == 0 && tid == 0) *rank_out = j;
+}
+
+// R (d x d) from the double-float rows k_pchol_grid wrote into the same bytes: (hi + lo) rscale.
+__global__ void k_df_to_fp64(double* __restrict__ R, const double* __restrict__ rscale, int64_t count) {
+    const double sc = *rscale;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = reinterpret_cast<const float2*>(R)[e];
+        R[e] = ((double)v.x + (double)v.y) * sc;
+    }
 }
 
 }  // namespace
@@ -619,22 +679,26 @@ cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int3
     int sms = 0, dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if (sms < 1 || d < 1) return cudaErrorInvalidValue;
+    if (sms < 1 || d < 1 || d > 256 * kRowsPerThread) return cudaErrorInvalidValue;
     int pgrid = sms < (int)d ? sms : (int)d;
     if (d <= 256 && pgrid > (int)(d + 2) / 3) pgrid = (int)(d + 2) / 3;
     const size_t ncl = ((size_t)d + pgrid - 1) / pgrid;
     if (ncl > 32) return cudaErrorInvalidConfiguration;          // per-CTA bookkeeping holds 32 columns
-    const size_t smem = sizeof(double) * (ncl * d + 3 * (size_t)d) + sizeof(int) * (size_t)d + 64;
+    const size_t smem = sizeof(float2) * (ncl * d + 3 * (size_t)d) + sizeof(int) * (size_t)d + 64;
     if ((e = cudaFuncSetAttribute(k_pchol_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     k_fill_unwritten<<<152 * 4, 256, 0, st>>>(reinterpret_cast<unsigned long long*>(q.U), d * d);
     const double* S = q.G;
     const int32_t* fp = forced;
     int fr = (int)forced_rank, di = (int)d, mi = (int)m;
-    void* kargs[] = {&S, &di, &mi, &tau, &fp, &fr, (void*)&q.U, (void*)&q.Rorig, (void*)&q.piv, (void*)&q.rank,
-                     &status};
+    unsigned long long* U = reinterpret_cast<unsigned long long*>(q.U);
+    float2* Rdf = reinterpret_cast<float2*>(q.Rorig);
+    double* rscale = q.norms;                                    // unused by the Gram route otherwise
+    void* kargs[] = {&S, &di, &mi, &tau, &fp, &fr, &U, &Rdf, &rscale, (void*)&q.piv, (void*)&q.rank, &status};
     e = cudaLaunchCooperativeKernel((const void*)k_pchol_grid, dim3((unsigned)pgrid), dim3(256), kargs, smem, st);
-    return e;
+    if (e != cudaSuccess) return e;
+    k_df_to_fp64<<<152 * 2, 256, 0, st>>>(q.Rorig, q.norms, d * d);
+    return cudaGetLastError();
 }
 
 }  // namespace lev
