@@ -284,8 +284,15 @@ def run_stage(a):
     if a.stage in ("final", "sketch", "backward"):
         A = torch.from_numpy(W.dense_lowrank_skewed(a.n, a.d, min(a.rank, a.d), seed=a.seed)).cuda()
     if a.stage == "final":
+        # shaped as the estimator's factor: rank nonzero rows (the selected columns) and, when
+        # rank < k, its first rank columns (the reduced form of lev_omega_factor)
         rs = np.random.default_rng(a.seed)
-        Mf = torch.from_numpy((rs.standard_normal((a.d, a.k)) / np.sqrt(a.d)).astype(np.float32)).cuda()
+        M = rs.standard_normal((a.d, a.k)) / np.sqrt(a.d)
+        r = min(a.rank, a.d)
+        M[rs.permutation(a.d)[r:], :] = 0.0
+        if r < a.k:
+            M[:, r:] = 0.0
+        Mf = torch.from_numpy(M.astype(np.float32)).cuda()
         theta = torch.empty(a.n, device="cuda")
         ms = timed(lambda: L.lev_final_dense(h, A, Mf, a.prec, theta))
     elif a.stage == "sketch":
@@ -505,11 +512,12 @@ def main():
     L.lev_sketch_dense(h, A, p, At)
     r = L.lev_rrqr(h, At, cfg["tau"], perm, R)
     d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
-    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
+    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], L.LEV_OMEGA_REDUCED, Mf)
     stages = {
         "sketch": time_steps(lambda: L.lev_sketch_dense(h, A, p, At), reps),
         "rrqr": time_steps(lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R), reps),
-        "omega": time_steps(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf), reps),
+        "omega": time_steps(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"],
+                                                       L.LEV_OMEGA_REDUCED, Mf), reps),
     }
     final_ms = {f: time_steps(lambda f=f: L.lev_final_dense(h, A, Mf, f, theta), reps)
                 for f in sorted(set(list(forms) + [args.final_prec]))}
@@ -762,10 +770,11 @@ def csr_timing(L, h, name, reps):
     L.lev_sketch_csr(h, rp, cl, vl, n, d, p, At)
     L.lev_rrqr(h, At, cfg["tau"], perm, R)
     d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
-    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
+    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], L.LEV_OMEGA_REDUCED, Mf)
     stages = {"sketch": timed(lambda: L.lev_sketch_csr(h, rp, cl, vl, n, d, p, At), reps),
               "rrqr": timed(lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R), reps),
-              "omega": timed(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf), reps),
+              "omega": timed(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"],
+                                                        L.LEV_OMEGA_REDUCED, Mf), reps),
               "final": timed(lambda: L.lev_final_csr(h, rp, cl, vl, n, d, Mf, "fp32", theta), reps)}
     csr_bytes = C.nnz * 8 + (n + 1) * 8
     out = {"n": n, "d": d, "nnz": C.nnz, "rank": r, "ms_per_step": ms, "rows_per_s": n / (ms * 1e-3),
@@ -841,10 +850,11 @@ def csr_large_timing(L, h, name, reps, pre):
     L.lev_sketch_csr(h, rp, cl, vl, n, d, p, At)
     L.lev_rrqr(h, At, cfg["tau"], perm, R)
     d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
-    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf)
+    L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], L.LEV_OMEGA_REDUCED, Mf)
     stages = {"sketch": timed(lambda: L.lev_sketch_csr(h, rp, cl, vl, n, d, p, At), reps),
               "rrqr": timed(lambda: lib_rrqr_nosync(L, h, At, cfg["tau"], perm, R), reps),
-              "omega": timed(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"], 0, Mf), reps),
+              "omega": timed(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"],
+                                                        L.LEV_OMEGA_REDUCED, Mf), reps),
               "final": timed(lambda: L.lev_final_csr(h, rp, cl, vl, n, d, Mf, "fp32", theta), reps)}
     csr_bytes = nnz * 8 + (n + 1) * 8
     out = {"n": n, "d": d, "nnz": nnz, "rank": r, "ms_per_step": ms, "rows_per_s": n / (ms * 1e-3),
@@ -916,7 +926,8 @@ def backward_timing(L, h, reps):
     def fwd():
         L.lev_sketch_dense(h, A, p, st["Atilde"])
         lib_rrqr_nosync(L, h, st["Atilde"], cfg["tau"], st["perm"], st["R"])
-        L.lev_omega_factor(h, st["R"], st["perm"], st["d_rank"], cfg["d"], cfg["k"], cfg["seed"], 0, st["Mfull"])
+        L.lev_omega_factor(h, st["R"], st["perm"], st["d_rank"], cfg["d"], cfg["k"], cfg["seed"], L.LEV_OMEGA_REDUCED,
+                           st["Mfull"])
         L.lev_final_dense(h, A, st["Mfull"], "bf16x3", theta)
 
     def bwd():

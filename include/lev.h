@@ -81,6 +81,7 @@ extern "C" {
 #define LEV_SRRQR          64u  /* after the rank: strong-RRQR swaps at that rank until every
                                    rho_ij <= phi (Alg. 2); d <= 1024 */
 #define LEV_CSR_UNCHECKED 128u  /* the caller vouches for the CSR structure: no validation pass */
+#define LEV_OMEGA_REDUCED 256u  /* lev_omega_factor: the r-column factor R_11^{-1} L_r when r < k (below) */
 
 typedef struct lev_handle lev_handle;
 
@@ -138,7 +139,8 @@ int lev_resolve_sizes(const lev_params* p, int64_t n, int64_t d,
 /* Build the handle's caches of data-independent operands for a call with (n, d, p) on `stream`,
  * ahead of the first call that needs them: the CountSketch bucket permutation (Sec. 3.4.3, per
  * seed, n, s and row0), G in the operand form of p->sketch_prec (Alg. 3 step 3; m x t with
- * LEV_SKETCH_SRHT) and Omega (d <= 1024, unless LEV_OMEGA_IDENTITY). Later calls with the same
+ * LEV_SKETCH_SRHT) and Omega with the Cholesky factor of its Gram matrix (d <= 1024, unless
+ * LEV_OMEGA_IDENTITY; see lev_omega_factor). Later calls with the same
  * seed and sizes reuse them. Asynchronous; no arrays are read. Errors: LEV_EINVAL, LEV_ENOMEM,
  * LEV_ECUDA. */
 int lev_prepare(lev_handle* h, int64_t n, int64_t d, const lev_params* p, void* stream);
@@ -262,6 +264,15 @@ int lev_lsqr_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, cons
  * scattered into Mfull (device, d x k FP32 row-major): row perm[p] holds M[p, :]
  * and the d - r rows outside K are 0. R, perm as produced by lev_rrqr; d_rank:
  * device int64 holding r (read on the device, no host round trip).
+ * With LEV_OMEGA_REDUCED (d <= 1024) and r < k, row perm[p] holds row p of
+ * W = R_11^{-1} L_r in columns 0..r-1 and zeros after, where L_r (r x r, lower
+ * triangular) is the Cholesky factor of Omega_r Omega_r^T, Omega_r the first r
+ * rows of Omega. Then W W^T = M M^T, so every final pass gives the same
+ * theta~_i = ||a_K,i M||^2 = ||a_K,i W||^2 up to rounding, and the dense
+ * tensor-core final pass multiplies r columns instead of k. L_r is the leading
+ * block of one factor per (seed, d, k) (Cholesky factors of leading blocks
+ * nest), computed with Omega and kept by the handle. The estimate entry points
+ * always take this form.
  * Errors: LEV_EINVAL, LEV_ECUDA. */
 int lev_omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int64_t* d_rank,
                      int64_t d, int64_t k, uint64_t seed, uint32_t flags,

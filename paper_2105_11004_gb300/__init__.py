@@ -18,7 +18,7 @@ from .build import LIB_PATH, build as build_library  # noqa: F401
 LEV_OK, LEV_EINVAL, LEV_ENOMEM, LEV_ECUDA, LEV_ETIMEOUT, LEV_ERANK0 = 0, 1, 2, 3, 4, 5
 LEV_FP32, LEV_TF32, LEV_BF16, LEV_BF16X3 = 0, 1, 2, 3
 LEV_OMEGA_IDENTITY, LEV_SKETCH_IDENTITY, LEV_FORCE_PIVOTS, LEV_HOST_ASYNC, LEV_SKETCH_SRHT = 1, 2, 4, 8, 16
-LEV_RANK_SVD, LEV_SRRQR, LEV_CSR_UNCHECKED = 32, 64, 128
+LEV_RANK_SVD, LEV_SRRQR, LEV_CSR_UNCHECKED, LEV_OMEGA_REDUCED = 32, 64, 128, 256
 PRECISIONS = {"fp32": LEV_FP32, "tf32": LEV_TF32, "bf16": LEV_BF16, "bf16x3": LEV_BF16X3}
 
 # Every symbol include/lev.h declares, with (restype, argtypes).
@@ -482,7 +482,7 @@ def finish_shard(h: Handle, A_local, p: lev_params, Atilde, k: int, csr=None, st
         return theta, 0, perm
     d_rank = torch.tensor([r], dtype=torch.int64, device=dev)
     Mfull = torch.empty((d, k), dtype=torch.float32, device=dev)
-    lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, p.flags, Mfull, stream)
+    lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, p.flags | LEV_OMEGA_REDUCED, Mfull, stream)
     if csr is None:
         lev_final_dense(h, A_local, Mfull, p.final_prec, theta, stream)
     else:
@@ -528,7 +528,7 @@ def forward_state(A, p: lev_params, handle: Handle | None = None):
     lev_sketch_dense(h, A, p, Atilde)
     r = lev_rrqr(h, Atilde, p.tau, perm, R)
     d_rank = torch.tensor([r], dtype=torch.int64, device=dev)
-    lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, p.flags, Mfull)
+    lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, p.flags | LEV_OMEGA_REDUCED, Mfull)
     lev_final_dense(h, A, Mfull, p.final_prec, theta)
     return theta, dict(Atilde=Atilde, perm=perm, d_rank=d_rank, rank=r, R=R, Mfull=Mfull, handle=h)
 

@@ -86,6 +86,10 @@ struct lev_handle {
     uint64_t omega_seed = 0;
     int64_t omega_d = -1, omega_k = -1;
     cudaEvent_t ev_omega = nullptr;
+    // the Cholesky factor of Omega's Gram matrix (launch_omega_chol scratch and its forced pivots),
+    // valid for the cached Omega when omega_chol_ok
+    Buf omega_chol;
+    bool omega_chol_ok = false;
     // host A of lev_estimate_dense: two stage buffers filled by a copy stream of the handle
     Buf stageA[2];
     Buf exact_gp;  // split partials of the Gram matrix of A (LS-HRN-exact)
@@ -114,7 +118,7 @@ template <class F>
 void for_each_buf(lev_handle* h, F f) {
     Buf* all[] = {&h->count, &h->off, &h->tmp, &h->perm_rows, &h->B, &h->partial, &h->Atilde, &h->qr,
                   &h->R, &h->perm_d, &h->Mfull, &h->stageA[0], &h->stageA[1], &h->stageTheta, &h->tc_ws, &h->tc_ws2,
-                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->tc_pad,
+                  &h->bwd, &h->csr_rp, &h->csr_col, &h->csr_val, &h->omega, &h->omega_rs, &h->omega_chol, &h->tc_pad,
                   &h->exact_gp, &h->srht_c, &h->rank_ws, &h->lsqr_u, &h->lsqr_ws, &h->csr_p, &h->csr_heavy,
                   &h->csr_dense};
     for (Buf* b : all) f(*b);
@@ -303,32 +307,70 @@ int bucket_perm(lev_handle* h, int64_t n, int64_t s, uint64_t seed, int64_t row0
     return LEV_OK;
 }
 
-// M = R_11^{-1} Omega into Mfull through the handle's Omega cache (drawn once per (seed, d, k)).
-int omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int64_t* d_rank, int64_t d, int64_t k,
-                 uint64_t seed, bool identity, float* Mfull, cudaStream_t st) {
-    const double* Om = nullptr;
-    if (!identity && d <= 1024) {
-        const void* p0 = h->omega.ptr;
-        LEV_TRY(ensure(h->omega, sizeof(double) * (size_t)d * k));
-        if (!h->ev_omega) LEV_CUDA(cudaEventCreateWithFlags(&h->ev_omega, cudaEventDisableTiming));
-        if (h->omega_seed == seed && h->omega_d == d && h->omega_k == k && h->omega.ptr == p0) {
-            LEV_CUDA(cudaStreamWaitEvent(st, h->ev_omega, 0));
-        } else {
+// Omega (d x k FP64, d <= 1024) of (seed, d, k), drawn once and kept by the handle; with `chol`
+// also the Cholesky factor of Omega_kc Omega_kc^T (kc = min(d, k)), kept with it. `st` waits for
+// an Omega (and factor) that an earlier call made, possibly on another stream.
+int ensure_omega(lev_handle* h, uint64_t seed, int64_t d, int64_t k, bool chol, cudaStream_t st,
+                 const double** Om, lev::QrScratch* qc) {
+    const int64_t kc = d < k ? d : k;
+    const size_t qbytes = (lev::qr_scratch_bytes(k, kc) + 255) & ~size_t(255);
+    const void* p0 = h->omega.ptr;
+    const void* c0 = h->omega_chol.ptr;
+    LEV_TRY(ensure(h->omega, sizeof(double) * (size_t)d * k));
+    if (chol) LEV_TRY(ensure(h->omega_chol, qbytes + sizeof(int32_t) * (size_t)kc));
+    if (!h->ev_omega) LEV_CUDA(cudaEventCreateWithFlags(&h->ev_omega, cudaEventDisableTiming));
+    const bool have = h->omega_seed == seed && h->omega_d == d && h->omega_k == k && h->omega.ptr == p0;
+    const bool have_chol = have && h->omega_chol_ok && h->omega_chol.ptr == c0;
+    if (have && (!chol || have_chol)) {
+        LEV_CUDA(cudaStreamWaitEvent(st, h->ev_omega, 0));
+    } else {
+        if (!have) {
             h->omega_d = -1;
+            h->omega_chol_ok = false;
             LEV_CUDA(lev::launch_gen_omega(seed, d, k, (double*)h->omega.ptr, st));
-            LEV_CUDA(cudaEventRecord(h->ev_omega, st));
-            h->omega_seed = seed;
-            h->omega_d = d;
-            h->omega_k = k;
+        } else {
+            LEV_CUDA(cudaStreamWaitEvent(st, h->ev_omega, 0));
         }
-        Om = (const double*)h->omega.ptr;
+        if (chol) {
+            lev::QrScratch q;
+            lev::qr_scratch_carve(h->omega_chol.ptr, k, kc, &q);
+            int32_t* iota = (int32_t*)((char*)h->omega_chol.ptr + qbytes);
+            LEV_CUDA(lev::launch_omega_chol((const double*)h->omega.ptr, d, k, q, iota, h->status, st));
+            h->omega_chol_ok = true;
+        }
+        LEV_CUDA(cudaEventRecord(h->ev_omega, st));
+        h->omega_seed = seed;
+        h->omega_d = d;
+        h->omega_k = k;
+    }
+    if (Om) *Om = (const double*)h->omega.ptr;
+    if (qc && chol) lev::qr_scratch_carve(h->omega_chol.ptr, k, kc, qc);
+    return LEV_OK;
+}
+
+// M = R_11^{-1} Omega into Mfull through the handle's Omega cache (drawn once per (seed, d, k)).
+// `reduced`: when r < k, R_11^{-1} L_r (r columns) instead, L_r L_r^T = Omega_r Omega_r^T.
+int omega_factor(lev_handle* h, const double* R, const int32_t* perm, const int64_t* d_rank, int64_t d, int64_t k,
+                 uint64_t seed, bool identity, bool reduced, float* Mfull, cudaStream_t st) {
+    const double* Om = nullptr;
+    const double* Lc = nullptr;
+    const int64_t* d_kc = nullptr;
+    const int64_t kc = d < k ? d : k;
+    if (!identity && d <= 1024) {
+        const bool chol = reduced;
+        lev::QrScratch qc;
+        LEV_TRY(ensure_omega(h, seed, d, k, chol, st, &Om, &qc));
+        if (chol) {
+            Lc = qc.Rorig;
+            d_kc = qc.rank;
+        }
     }
     double* Rs = nullptr;
     if (d <= 1024) {
         LEV_TRY(ensure(h->omega_rs, sizeof(double) * (size_t)d * d));
         Rs = (double*)h->omega_rs.ptr;
     }
-    LEV_CUDA(lev::launch_omega_factor(R, perm, d_rank, d, k, seed, identity, Om, Rs, Mfull, st));
+    LEV_CUDA(lev::launch_omega_factor(R, perm, d_rank, d, k, seed, identity, Om, Lc, kc, d_kc, Rs, Mfull, st));
     return LEV_OK;
 }
 
@@ -698,19 +740,8 @@ int lev_prepare(lev_handle* h, int64_t n, int64_t d, const lev_params* p, void* 
     if (cols < 1 || cols > z.s) return fail(LEV_EINVAL, "LEV_SKETCH_SRHT needs 1 <= srht_t <= s");
     const int kind = p->sketch_prec == LEV_FP32 ? 0 : (p->sketch_prec == LEV_TF32 ? 3 : 2);
     LEV_TRY(ensure_g(h, z.m, cols, p->seed, kind, st, nullptr, nullptr));
-    if (!(p->flags & LEV_OMEGA_IDENTITY) && d <= 1024) {
-        const void* p0 = h->omega.ptr;
-        LEV_TRY(ensure(h->omega, sizeof(double) * (size_t)d * z.k));
-        if (!h->ev_omega) LEV_CUDA(cudaEventCreateWithFlags(&h->ev_omega, cudaEventDisableTiming));
-        if (!(h->omega_seed == p->seed && h->omega_d == d && h->omega_k == z.k && h->omega.ptr == p0)) {
-            h->omega_d = -1;
-            LEV_CUDA(lev::launch_gen_omega(p->seed, d, z.k, (double*)h->omega.ptr, st));
-            LEV_CUDA(cudaEventRecord(h->ev_omega, st));
-            h->omega_seed = p->seed;
-            h->omega_d = d;
-            h->omega_k = z.k;
-        }
-    }
+    if (!(p->flags & LEV_OMEGA_IDENTITY) && d <= 1024)
+        LEV_TRY(ensure_omega(h, p->seed, d, z.k, true, st, nullptr, nullptr));
     return LEV_OK;
 }
 
@@ -891,8 +922,8 @@ int lev_omega_factor(lev_handle* h, const double* R, const int32_t* perm, const 
     LEV_TRY(set_device(h));
     if (!R || !perm || !d_rank || !Mfull) return fail(LEV_EINVAL, "NULL array");
     if (d < 1 || d > 4096 || k < 1 || k > 4096) return fail(LEV_EINVAL, "bad shape d=%lld k=%lld", (long long)d, (long long)k);
-    return omega_factor(h, R, perm, d_rank, d, k, seed, (flags & LEV_OMEGA_IDENTITY) != 0, Mfull,
-                        (cudaStream_t)stream);
+    return omega_factor(h, R, perm, d_rank, d, k, seed, (flags & LEV_OMEGA_IDENTITY) != 0,
+                        (flags & LEV_OMEGA_REDUCED) != 0, Mfull, (cudaStream_t)stream);
 }
 
 int lev_final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const float* Mfull,
@@ -935,7 +966,7 @@ static int estimate_tail(lev_handle* h, const Sizes& z, int64_t d, const lev_par
         LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
     LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * z.k));
     LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, qs->rank, d, z.k, p->seed,
-                         (p->flags & LEV_OMEGA_IDENTITY) != 0, (float*)h->Mfull.ptr, st));
+                         (p->flags & LEV_OMEGA_IDENTITY) != 0, true, (float*)h->Mfull.ptr, st));
     return LEV_OK;
 }
 
@@ -1017,7 +1048,8 @@ int lev_exact_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t
     LEV_TRY(rc);
     // step 6: theta_i = ||A_{i,K} R^{-1}||^2: M = R^{-1} (Omega = I) scattered into Mfull (d x d)
     LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * d));
-    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, q2.rank, d, d, p->seed, true, (float*)h->Mfull.ptr, st));
+    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, q2.rank, d, d, p->seed, true, false, (float*)h->Mfull.ptr,
+                         st));
     if (perm != (int32_t*)h->perm_d.ptr)
         LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
     LEV_TRY(final_dense(h, A, n, d, lda, (const float*)h->Mfull.ptr, d, p->final_prec, theta, st));
@@ -1072,7 +1104,8 @@ int lev_exact_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, con
     LEV_TRY(rc);
     // step 6: theta_i = ||A_{i,K} R^{-1}||^2 with M = R^{-1} (Omega = I) scattered into Mfull
     LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * d));
-    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, qs.rank, d, d, p->seed, true, (float*)h->Mfull.ptr, st));
+    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, qs.rank, d, d, p->seed, true, false, (float*)h->Mfull.ptr,
+                         st));
     if (perm != (int32_t*)h->perm_d.ptr)
         LEV_CUDA(cudaMemcpyAsync(h->perm_d.ptr, perm, sizeof(int32_t) * (size_t)d, cudaMemcpyDeviceToDevice, st));
     LEV_TRY(final_csr(h, row_ptr, col, val, n, d, nnz, (const float*)h->Mfull.ptr, d, theta, st));
@@ -1100,7 +1133,7 @@ static int exact_reference_tail(lev_handle* h, lev::QrScratch& q, int64_t n, int
     }
     LEV_TRY(rc);
     LEV_TRY(ensure(h->Mfull, sizeof(float) * (size_t)d * d));
-    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, q.rank, d, d, 0, true, (float*)h->Mfull.ptr, st));
+    LEV_TRY(omega_factor(h, (const double*)h->R.ptr, perm, q.rank, d, d, 0, true, false, (float*)h->Mfull.ptr, st));
     if (A)
         LEV_CUDA(lev::launch_final_dense_fp32(A, lda, n, d, (const float*)h->Mfull.ptr, d, theta, st));
     else

@@ -141,10 +141,20 @@ cudaError_t launch_pivoted_qr(const float* Atilde, int64_t m, int64_t d, double 
 
 // Mfull (d x k FP32) = scatter of R_11^{-1} Omega by perm; reads r from d_rank. Omega: d x k FP64
 // from launch_gen_omega (unused with omega_identity); Rs: d x d FP64 scratch. With d > 1024 or
-// without Rs the one-warp-per-column kernel runs and draws Omega itself.
+// without Rs the one-warp-per-column kernel runs and draws Omega itself. Lc (optional): the
+// factor of launch_omega_chol (kc x kc, its rank at d_kc); when r < k and r <= *d_kc, column q < r
+// of Mfull is R_11^{-1} times column q of L_r instead (L_r L_r^T = Omega_r Omega_r^T, Omega_r the
+// first r rows), the columns q >= r stay 0, and Mfull Mfull^T is unchanged.
 cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int64_t* d_rank,
                                 int64_t d, int64_t k, uint64_t seed, bool omega_identity,
-                                const double* Omega, double* Rs, float* Mfull, cudaStream_t st);
+                                const double* Omega, const double* Lc, int64_t kc, const int64_t* d_kc,
+                                double* Rs, float* Mfull, cudaStream_t st);
+// The Cholesky factor of Omega_kc Omega_kc^T (kc = min(d, k) leading rows of Omega): the Gram
+// product in FP64 into q.G, then the grid pivoted Cholesky with the pivots forced to 0, 1, ...
+// (iota: kc int32 scratch). Leaves the upper factor U (U^T U = Omega_kc Omega_kc^T) in q.Rorig
+// (row j, column i >= j; ld = kc) and the number of steps taken in q.rank. q: scratch for (k, kc).
+cudaError_t launch_omega_chol(const double* Omega, int64_t d, int64_t k, const QrScratch& q, int32_t* iota,
+                              int32_t* status, cudaStream_t st);
 // Omega (d x k FP64) of stream 3 of seed, every pivot position p < d.
 cudaError_t launch_gen_omega(uint64_t seed, int64_t d, int64_t k, double* Omega, cudaStream_t st);
 

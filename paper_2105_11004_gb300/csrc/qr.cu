@@ -273,6 +273,24 @@ __global__ void k_omega_factor(const double* __restrict__ R, const int32_t* __re
     for (int p = lane; p < r; p += 32) Mfull[(int64_t)perm[p] * k + q] = (float)Ms[p];
 }
 
+// G (kc x kc FP64, full) = Omega_kc Omega_kc^T, one thread an entry, the k products summed in order.
+__global__ void k_omega_gram(const double* __restrict__ Om, int kc, int k, double* __restrict__ G) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)kc * kc;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / kc), j = (int)(e % kc);
+        const int a = min(i, j), b = max(i, j);                  // the same sum for (i, j) and (j, i)
+        const double* x = Om + (int64_t)a * k;
+        const double* y = Om + (int64_t)b * k;
+        double s = 0.0;
+        for (int q = 0; q < k; ++q) s = fma(x[q], y[q], s);
+        G[e] = s;
+    }
+}
+
+__global__ void k_iota(int32_t* v, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = i;
+}
+
 // Omega (d x k FP64): entry (p, q) = N(0,1)/sqrt(k) from stream 3 at counter p k + q, for every pivot
 // position p < d (a call with rank r uses rows 0..r-1). Grid-wide; the handle caches the result.
 __global__ void k_gen_omega(uint64_t key, int d, int k, double inv_sqrt_k, double* __restrict__ Om) {
@@ -298,17 +316,25 @@ __global__ void k_scaled_transpose(const double* __restrict__ R, const int64_t* 
 // bottom) publishes x_j through shared memory (double-buffered by step parity, one barrier per
 // step) and every thread i < j subtracts Rs[j][i] x_j. The coefficients of the next four steps
 // are loaded ahead. Row i of M goes to row perm[i] of Mfull.
+// With the factor Lc of Omega's Gram matrix (upper U, row q holding column q of L = U^T) and
+// r < k, r <= *d_kc, the right-hand side is column q of L_r instead and the CTAs q >= r leave
+// their column 0.
 constexpr int OMEGA_PF = 4;
 __global__ void __launch_bounds__(1024) k_omega_solve(const double* __restrict__ R, const double* __restrict__ Rs,
-                                                      const double* __restrict__ Om, const int32_t* __restrict__ perm,
+                                                      const double* __restrict__ Om, const double* __restrict__ Lc,
+                                                      int kc, const int64_t* __restrict__ d_kc,
+                                                      const int32_t* __restrict__ perm,
                                                       const int64_t* __restrict__ d_rank, int d, int k, int identity,
                                                       float* __restrict__ Mfull) {
     __shared__ double xs[2];
     const int q = blockIdx.x, i = threadIdx.x;
     const int r = (int)min(max(*d_rank, (int64_t)0), (int64_t)d);
+    const bool reduced = Lc != nullptr && !identity && r < k && r <= kc && (int64_t)r <= *d_kc;
+    if (reduced && q >= r) return;                               // the whole CTA: Mfull column q stays 0
     double x = 0.0;
     if (i < r) {
-        const double w = identity ? (i == q ? 1.0 : 0.0) : Om[(int64_t)i * k + q];
+        const double w = identity ? (i == q ? 1.0 : 0.0)
+                                  : (reduced ? Lc[(int64_t)q * kc + i] : Om[(int64_t)i * k + q]);
         x = w / R[(int64_t)i * d + i];
     }
     // ring of coefficients: c[t] holds Rs[j - t][i] for the current step j
@@ -434,9 +460,23 @@ cudaError_t launch_factor_gram(int64_t m, int64_t d, double tau, const int32_t* 
     return cudaGetLastError();
 }
 
+cudaError_t launch_omega_chol(const double* Omega, int64_t d, int64_t k, const QrScratch& q, int32_t* iota,
+                              int32_t* status, cudaStream_t st) {
+    const int64_t kc = d < k ? d : k;
+    if (kc < 1 || kc > kGramMaxD) return cudaErrorInvalidValue;
+    int grid = (int)((kc * kc + 255) / 256);
+    if (grid > 152 * 4) grid = 152 * 4;
+    k_omega_gram<<<grid, 256, 0, st>>>(Omega, (int)kc, (int)k, q.G);
+    k_iota<<<(unsigned)((kc + 255) / 256), 256, 0, st>>>(iota, (int)kc);
+    cudaError_t e = cudaMemsetAsync(q.Rorig, 0, sizeof(double) * (size_t)(kc * kc), st);
+    if (e != cudaSuccess) return e;
+    return launch_pivoted_cholesky(k, kc, 0.0, iota, kc, q, status, st);
+}
+
 cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int64_t* d_rank,
                                 int64_t d, int64_t k, uint64_t seed, bool omega_identity,
-                                const double* Omega, double* Rs, float* Mfull, cudaStream_t st) {
+                                const double* Omega, const double* Lc, int64_t kc, const int64_t* d_kc,
+                                double* Rs, float* Mfull, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(Mfull, 0, sizeof(float) * (size_t)(d * k), st);
     if (e != cudaSuccess) return e;
     if (d <= 1024 && Rs && (Omega || omega_identity)) {
@@ -444,8 +484,8 @@ cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int6
         if (grid > 152 * 8) grid = 152 * 8;
         k_scaled_transpose<<<grid, 256, 0, st>>>(R, d_rank, (int)d, Rs);
         const int threads = (int)((d + 31) / 32 * 32);
-        k_omega_solve<<<(unsigned)k, threads, 0, st>>>(R, Rs, Omega, perm, d_rank, (int)d, (int)k,
-                                                       omega_identity ? 1 : 0, Mfull);
+        k_omega_solve<<<(unsigned)k, threads, 0, st>>>(R, Rs, Omega, Lc && d_kc ? Lc : nullptr, (int)kc, d_kc,
+                                                       perm, d_rank, (int)d, (int)k, omega_identity ? 1 : 0, Mfull);
         return cudaGetLastError();
     }
     const int warps = 1;                              // spread the FP64 work over the SMs

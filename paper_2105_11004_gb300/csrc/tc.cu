@@ -5,19 +5,25 @@
 // One persistent CTA per SM (BF16) or per SM of a 2-CTA cluster (BF16X3, TF32).
 // Shared memory holds the CTA's part of the packed operand image of Mfull^T and
 // a ring of slots; a slot holds one K block of the CTA's 128 rows of A.
-//   * warp 13 (producer): 2-D tensor TMA of a slot's FP32 boxes (32 columns x
+//   * warp 17 (producer): 2-D tensor TMA of a slot's FP32 boxes (32 columns x
 //     128 rows each, 128-byte swizzle);
-//   * warps 4..11 (converters): round the slot IN PLACE to the operand type.
+//   * warps 4..15 (converters, three groups of four): round the slot IN PLACE to
+//     the operand type; the groups take the slots in turn, so three are rounded
+//     at once.
 //     With 64-column K blocks the two FP32 boxes of row r occupy exactly the
 //     bytes that the BF16 hi row r and lo row r take in the 128-byte swizzled
 //     K-major operand layout (same row, same swizzle phase), so a warp that owns
 //     whole rows reads them, syncs, and writes them back; TF32 rounds each
 //     16-byte chunk where it lies;
-//   * warp 12 (MMA): allocates TMEM (two accumulators of 256 columns), loads the
-//     image once with bulk copies, and one thread issues tcgen05.mma (N = 256,
-//     32 bytes of K per instruction); the MMA completion frees the slot;
+//   * warp 16 (MMA): allocates TMEM (two accumulators of 256 columns), loads the
+//     image once with bulk copies, and one thread issues tcgen05.mma (N = the
+//     width of Mfull, 32 bytes of K per instruction); the MMA completion frees
+//     the slot;
 //   * warps 0..3 (epilogue): tcgen05.ld of the accumulator (TMEM lane = row),
-//     sum of squares over the 256 columns, one store per row.
+//     sum of squares over the N columns, one store per row.
+// N: Mfull's columns up to its last nonzero one, rounded up to 16 (k_mfull_width
+// finds it on the device). Trailing zero columns add nothing to theta~; the
+// r-column factor of lev_omega_factor's reduced form leaves k - r of them.
 // BF16: M = 128 per CTA; the 128 KB image of Mfull^T (256 x 256 BF16) fits one
 // CTA. BF16X3 (hi*hi + lo*hi + hi*lo) and TF32 need 256 KB for the image, so
 // they run as CTA pairs with cta_group::2: one thread of the even CTA issues an
@@ -66,11 +72,15 @@ struct FormTraits<kTF32> {
 
 constexpr int kTileRows = 128;                    // rows of A per CTA per tile (TMEM lanes)
 constexpr int kBoxBytes = kTileRows * 128;        // one FP32 box: 128 rows x 32 columns = one 16 KB K block
-constexpr int kNOut = 256;                        // MMA N: accumulator columns per row
-constexpr int kEpiWarps = 4, kCvtWarps = 8;
-constexpr int kMmaWarp = kEpiWarps + kCvtWarps;   // warp 12
-constexpr int kTmaWarp = kMmaWarp + 1;            // warp 13
-constexpr int kThreads = (kTmaWarp + 1) * 32;     // 448
+constexpr int kNOut = 256;                        // accumulator columns per row (the widest MMA N)
+// Converters: kCvtGroups groups of four warps; group g rounds the slot fills u with u mod
+// kCvtGroups = g, so each slot belongs to one group (the slot counts are multiples of it) and its
+// fills are taken in order, while the groups' slots are rounded at the same time.
+constexpr int kEpiWarps = 4, kCvtGroups = 3, kCvtWarpsPerGroup = 4;
+constexpr int kCvtWarps = kCvtGroups * kCvtWarpsPerGroup;
+constexpr int kMmaWarp = kEpiWarps + kCvtWarps;   // warp 16
+constexpr int kTmaWarp = kMmaWarp + 1;            // warp 17
+constexpr int kThreads = (kTmaWarp + 1) * 32;     // 576
 constexpr int kMaxSlots = 6;
 constexpr uint64_t kWaitNs = 2000000000ull;       // 2 s
 constexpr uint64_t kExitWaitNs = 5000000000ull;   // 5 s: a peer that timed out reaches the exit within one kWaitNs
@@ -133,7 +143,25 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b, float* ra, flo
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Round one slot in place. Converter warp w owns rows 16w .. 16w+15 of the slot.
+// MMA width for an Mfull whose columns from `width` on are zero: a multiple of 16 in [16, 256]
+// (a multiple of 8 rows of the image in each CTA of a pair).
+__device__ __forceinline__ int mma_width(const int* width) {
+    int w = *width;
+    w = w < 16 ? 16 : (w > kNOut ? kNOut : w);
+    return (w + 15) & ~15;
+}
+
+// *width = 1 + the last column of Mfull (d x k) holding a nonzero (or NaN) entry; 0 if none.
+__global__ void k_mfull_width(const float* __restrict__ M, int d, int k, int* width) {
+    int w = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)d * k;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (M[e] != 0.f) w = max(w, (int)(e % k) + 1);
+    w = (int)__reduce_max_sync(0xffffffffu, (unsigned)w);
+    if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(width, w);
+}
+
+// Round rows 16 cw .. 16 cw + 15 of one slot in place.
 template <int F>
 __device__ __forceinline__ void convert_slot(uint8_t* slot, int cw, int lane) {
     using T = FormTraits<F>;
@@ -177,16 +205,20 @@ __device__ __forceinline__ void convert_slot(uint8_t* slot, int cw, int lane) {
 template <int F>
 __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant__ CUtensorMap tmA, int64_t n,
                                                           int nkb, const uint8_t* __restrict__ image,
-                                                          uint32_t image_bytes, float* __restrict__ theta,
-                                                          int32_t* status) {
+                                                          uint32_t image_bytes, const int* __restrict__ width,
+                                                          float* __restrict__ theta, int32_t* status) {
     using T = FormTraits<F>;
     constexpr int PAIR = T::kPair;
     constexpr int NS = T::kSlots;
     constexpr int BOXES = T::kKbe / 32;                       // FP32 boxes per K block
     constexpr int SLOT_BYTES = BOXES * kBoxBytes;
-    constexpr uint32_t IDESC = make_idesc(T::kTf32, kTileRows * PAIR, kNOut);
-    static_assert(T::kNt * PAIR == kNOut, "the MMA covers 256 columns of Mfull");
+    static_assert(T::kNt * PAIR == kNOut, "the image holds up to 256 columns of Mfull");
+    const int ne = mma_width(width);                          // MMA N
+    const uint32_t kb_img_bytes = (uint32_t)(ne / PAIR) * 128u;   // one K block of this CTA's image
+    const uint32_t img_used = (uint32_t)nkb * kb_img_bytes * (T::kSplit ? 2u : 1u);
+    const uint32_t IDESC = make_idesc(T::kTf32, kTileRows * PAIR, ne);
     static_assert(NS <= kMaxSlots, "slot barriers");
+    static_assert(NS % kCvtGroups == 0, "each slot belongs to one converter group");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -206,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&ctl->sfull[s]), 1);
-            mbar_init(smem_u32(&ctl->cfull[s]), kCvtWarps * PAIR);
+            mbar_init(smem_u32(&ctl->cfull[s]), kCvtWarpsPerGroup * PAIR);
             mbar_init(smem_u32(&ctl->sempty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -266,9 +298,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
         if (lane == 0) {
             const uint8_t* src = image + (size_t)me * image_bytes;
             const uint32_t mbar = smem_u32(&ctl->mfull);
-            mbar_arrive_expect_tx(mbar, image_bytes);
-            for (uint32_t off = 0; off < image_bytes; off += 16384u) {
-                const uint32_t len = min(16384u, image_bytes - off);
+            mbar_arrive_expect_tx(mbar, img_used);
+            for (uint32_t off = 0; off < img_used; off += 16384u) {
+                const uint32_t len = min(16384u, img_used - off);
                 bulk_g2s(smem_u32(img + off), src + off, len, mbar);
             }
             bool ok = wait_bar(mbar, 0, ctl, status);
@@ -283,7 +315,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
                 uint32_t acc_phase = 0;
                 const uint32_t img_addr = smem_u32(img);
                 const uint32_t slot_addr = smem_u32(slots);
-                const uint32_t kb_img_bytes = (uint32_t)T::kNt * 128u;
                 const uint16_t both = (uint16_t)(PAIR == 2 ? 0x3 : 0x1);
                 for (int64_t tt = 0; ok && tt < my_tiles; ++tt) {
                     if (!wait_bar(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, ctl, status)) { ok = false; break; }
@@ -325,17 +356,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
         }
         __syncwarp();
     } else if (warp >= kEpiWarps) {
-        // ---------------- converters: each slot rounded in place, rows owned by warps
-        const int cw = warp - kEpiWarps;                      // 0..7
-        int s = 0;
-        uint32_t sph = 0;
-        for (int64_t u = 0; u < uses; ++u) {
-            if (!wait_bar(smem_u32(&ctl->sfull[s]), sph, ctl, status)) break;
-            convert_slot<F>(slots + s * SLOT_BYTES, cw, lane);
+        // ---------------- converters: each slot rounded in place by its group, 32 rows a warp
+        const int cw = warp - kEpiWarps;
+        const int grp = cw / kCvtWarpsPerGroup, wq = cw % kCvtWarpsPerGroup;
+        for (int64_t u = grp; u < uses; u += kCvtGroups) {
+            const int s = (int)(u % NS);
+            if (!wait_bar(smem_u32(&ctl->sfull[s]), (uint32_t)((u / NS) & 1), ctl, status)) break;
+            convert_slot<F>(slots + s * SLOT_BYTES, 2 * wq, lane);
+            convert_slot<F>(slots + s * SLOT_BYTES, 2 * wq + 1, lane);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) arrive_leader<PAIR>(smem_u32(&ctl->cfull[s]), me);
-            if (++s == NS) { s = 0; sph ^= 1u; }
         }
     } else {
         // ---------------- epilogue: TMEM lane = row of this CTA's 128
@@ -347,15 +378,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
             tc_fence_after();
             float sum = 0.f;
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kNOut);
+            for (int c = 0; c < ne; c += 32) {
+                if (c + 32 <= ne) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + (uint32_t)c, r);
+                    tmem_ld_wait();
 #pragma unroll
-            for (int c = 0; c < kNOut; c += 32) {
-                uint32_t r[32];
-                tmem_ld32(taddr + (uint32_t)c, r);
-                tmem_ld_wait();
+                    for (int j = 0; j < 32; ++j) {
+                        const float y = __uint_as_float(r[j]);
+                        sum = fmaf(y, y, sum);
+                    }
+                } else {
+                    uint32_t r[16];
+                    tmem_ld16(taddr + (uint32_t)c, r);
+                    tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float y = __uint_as_float(r[j]);
-                    sum = fmaf(y, y, sum);
+                    for (int j = 0; j < 16; ++j) {
+                        const float y = __uint_as_float(r[j]);
+                        sum = fmaf(y, y, sum);
+                    }
                 }
             }
             tc_fence_before();
@@ -385,14 +426,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
     }
 }
 
-// Pack Mfull (d x k FP32, row-major) into the operand image of Mfull^T:
-// per column half h, per K block kb, NT rows (columns q of Mfull) of 128 bytes,
-// 128-byte swizzled; split forms store the hi image then the lo image.
+// Pack Mfull (d x k FP32, row-major) into the operand image of Mfull^T for an MMA of width N
+// (mma_width): per column half h, per K block kb, NT = N / pairs rows (columns q = h NT + row of
+// Mfull) of 128 bytes, 128-byte swizzled; split forms store the hi image then the lo image.
 template <int F>
 __global__ void k_pack_image(const float* __restrict__ M, int d, int k, int nkb, uint8_t* __restrict__ image,
-                             uint32_t half_bytes) {
+                             uint32_t half_bytes, const int* __restrict__ width) {
     using T = FormTraits<F>;
-    constexpr int NT = T::kNt;
+    const int NT = mma_width(width) / T::kPair;
     const int64_t per_half = (int64_t)nkb * NT * T::kKbe;
     const int64_t total = per_half * T::kPair;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -426,11 +467,15 @@ int run_final_tc(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t ld
     const int nkb = (int)((d + T::kKbe - 1) / T::kKbe);
     const uint32_t half_bytes = (uint32_t)nkb * T::kNt * 128u * (T::kSplit ? 2u : 1u);
     void* ws = nullptr;
-    int rc = handle_scratch(h, 0, (size_t)half_bytes * T::kPair, &ws);
+    int rc = handle_scratch(h, 0, (size_t)half_bytes * T::kPair + 16, &ws);
     if (rc != LEV_OK) return rc;
     uint8_t* image = static_cast<uint8_t*>(ws);
-    k_pack_image<F><<<64, 256, 0, st>>>(Mfull, (int)d, (int)k, nkb, image, half_bytes);
-    cudaError_t e = cudaGetLastError();
+    int* width = reinterpret_cast<int*>(image + (size_t)half_bytes * T::kPair);
+    cudaError_t e = cudaMemsetAsync(width, 0, sizeof(int), st);
+    if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
+    k_mfull_width<<<32, 256, 0, st>>>(Mfull, (int)d, (int)k, width);
+    k_pack_image<F><<<64, 256, 0, st>>>(Mfull, (int)d, (int)k, nkb, image, half_bytes, width);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     CUtensorMap tmA;
     if (!make_map_2d(&tmA, A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, n, d, lda, 32, kTileRows))
@@ -471,7 +516,8 @@ int run_final_tc(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t ld
     if (groups > ntiles) groups = ntiles;
     if (groups < 1) groups = 1;
     cfg.gridDim = dim3((unsigned)(groups * T::kPair));
-    e = cudaLaunchKernelEx(&cfg, k_final_tc<F>, tmA, n, nkb, (const uint8_t*)image, half_bytes, theta, status);
+    e = cudaLaunchKernelEx(&cfg, k_final_tc<F>, tmA, n, nkb, (const uint8_t*)image, half_bytes, (const int*)width,
+                           theta, status);
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     return LEV_OK;
 }

@@ -101,7 +101,7 @@ def _run_stages(L, h, p, sketch, final, d, m, k):
     sketch(At)
     r = L.lev_rrqr(h, At, p.tau, perm, R)
     d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
-    L.lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, 0, Mf)
+    L.lev_omega_factor(h, R, perm, d_rank, d, k, p.seed, L.LEV_OMEGA_REDUCED, Mf)
     theta = final(Mf)
     torch.cuda.synchronize()
     return to_np(At), to_np(perm), to_np(R), r, to_np(Mf), theta

@@ -253,6 +253,37 @@ def test_omega_cache_follows_seed_and_shape(L, h):
         assert np.max(np.abs(got - want)) <= 1e-6 * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("d,r,k", [(256, 200, 256), (64, 20, 64), (300, 50, 100), (1024, 500, 600),
+                                   (40, 39, 40), (256, 256, 256), (256, 200, 128)])
+def test_omega_factor_reduced(L, h, d, r, k):
+    """LEV_OMEGA_REDUCED: for r < k, row perm[p] of Mfull holds row p of W = R_11^{-1} L_r in the
+    first r columns and zeros after, with L_r the Cholesky factor (lower, positive diagonal) of
+    Omega_r Omega_r^T for the oracle's first r rows of Omega; for r >= k it is M = R_11^{-1} Omega_r.
+    Either way Mfull Mfull^T is the oracle's M M^T, the only product theta~ depends on."""
+    import torch
+    from scipy.linalg import solve_triangular
+    rs = np.random.default_rng(d + r + k)
+    R = np.triu(rs.standard_normal((d, d)) * 0.05) + np.diag(1.0 + rs.random(d))
+    gp = rs.permutation(d).astype(np.int32)
+    Mf = torch.empty((d, k), dtype=torch.float32, device="cuda")
+    d_rank = torch.tensor([r], dtype=torch.int64, device="cuda")
+    L.lev_omega_factor(h, to_dev(R), to_dev(gp), d_rank, d, k, 31, L.LEV_OMEGA_REDUCED, Mf)
+    torch.cuda.synchronize()
+    got = to_np(Mf).astype(np.float64)
+    M = E.m_full(E.omega_factor(R[:r, :r], k, 31), gp, d)
+    if r < k:
+        Om = E.omega_factor(np.eye(r), k, 31)                 # Omega_r
+        W = solve_triangular(R[:r, :r], np.linalg.cholesky(Om @ Om.T), lower=False)
+        want = np.zeros((d, k))
+        want[gp[:r], :r] = W
+    else:
+        want = M
+    assert np.max(np.abs(got - want)) <= 1e-6 * np.max(np.abs(want))
+    assert np.all(got[gp[r:]] == 0)
+    P, Pw = got @ got.T, M @ M.T
+    assert np.max(np.abs(P - Pw)) <= 2e-6 * np.max(np.abs(Pw))
+
+
 # ---------------------------------------------------------------- final pass
 
 @pytest.mark.parametrize("n,d,k,lda", [(10007, 256, 256, 256), (999, 37, 100, 37), (5000, 64, 512, 80),
