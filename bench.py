@@ -519,9 +519,26 @@ def main():
         "omega": time_steps(lambda: L.lev_omega_factor(h, R, perm, d_rank, d, cfg["k"], cfg["seed"],
                                                        L.LEV_OMEGA_REDUCED, Mf), reps),
     }
-    final_ms = {f: time_steps(lambda f=f: L.lev_final_dense(h, A, Mf, f, theta), reps)
-                for f in sorted(set(list(forms) + [args.final_prec]))}
-    stages["final"] = final_ms[args.final_prec]
+    final_call_ms = {f: time_steps(lambda f=f: L.lev_final_dense(h, A, Mf, f, theta), reps)
+                     for f in sorted(set(list(forms) + [args.final_prec]))}
+    stages["final"] = final_call_ms[args.final_prec]
+    # the main kernel of each tensor-core final pass alone (events the library records around its
+    # launch, after the packing of Mfull's operand image); the FP32 SIMT pass is one kernel
+    L.lev_set_timing(h, True)
+    final_ms = {}
+    for f in final_call_ms:
+        if f == "fp32":
+            final_ms[f] = final_call_ms[f]
+            continue
+        ks = []
+        for _ in range(reps):
+            L.lev_final_dense(h, A, Mf, f, theta)
+            ks.append(L.lev_final_timing(h))
+        final_ms[f] = float(np.median(ks))
+    L.lev_set_timing(h, False)
+    # MMA width of the tensor-core pass: Mfull's columns up to its last nonzero one, rounded up to 16
+    nz_cols = np.nonzero(np.any(Mf.cpu().numpy() != 0, axis=0))[0]
+    mma_n = max(16, -(-(int(nz_cols[-1]) + 1 if nz_cols.size else 0) // 16) * 16)
     # the two kernels of the QR stage, from CUDA events the library records on the launching
     # stream around them (lev_set_timing): the Gram product and the grid pivoted Cholesky
     L.lev_set_timing(h, True)
@@ -532,7 +549,7 @@ def main():
         gram_ms.append(g_ms)
         chol_ms.append(f_ms)
     L.lev_set_timing(h, False)
-    kernel_ms = {"k_final_tc": stages["final"], "k_pchol_grid": float(np.median(chol_ms)),
+    kernel_ms = {"k_final_tc": final_ms[args.final_prec], "k_pchol_grid": float(np.median(chol_ms)),
                  "k_gram_dot2+reduce": float(np.median(gram_ms))}
 
     peaks, peak_src = load_peaks()
@@ -552,21 +569,23 @@ def main():
             roof = {"kernel": f"k_final_tc<{f}>", "bound": "hbm", "achieved": final_bytes / t / 1e9,
                     "peak": hbm_peak, "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})",
                     "algorithmic": final_bytes}
-            # the tensor pipe: executed MMA flops per form (Mfull is padded to 256 x 256; the split
-            # form runs three products hi*hi + lo*hi + hi*lo)
+            # the tensor pipe: executed MMA flops per form (K = d rounded up to the 64-column K
+            # block, N = mma_n; the split form runs three products hi*hi + lo*hi + hi*lo)
             mult = {"bf16": 1, "tf32": 1, "bf16x3": 3}[f]
             peak_tc = float(peaks.get("bf16_tflops", 1900.0)) * (0.5 if f == "tf32" else 1.0)
-            exec_flops = mult * 2.0 * n * 256 * 256
+            exec_flops = mult * 2.0 * n * mma_n * (-(-d // 64) * 64)
             roof["tensor"] = {"achieved": exec_flops / t / 1e12, "peak": peak_tc, "unit": "TFLOP/s",
                               "frac": exec_flops / t / 1e12 / peak_tc, "executed_flops": exec_flops,
                               "peak_source": "bf16_tflops burst (measured)"
                               + (" x 1/2 (TF32 nominal ratio)" if f == "tf32" else "")}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        # DRAM bytes per launch from the ncu capture of this kernel on 262,144 x 256 (k = 256),
-        # scaled by rows: read 268,741,888 + write 4,321,280 bytes
-        roof["traffic"] = ((268741888 + 4321280) * n / 262144
-                           if (f == "bf16x3" and d == 256 and cfg["k"] == 256) else None)
+        # DRAM bytes per launch from the ncu capture of this kernel (split BF16) on 262,144 x 256 with
+        # an Mfull of 208 nonzero columns, scaled by rows: read 268,707,072 + write 3,934,720 bytes
+        roof["traffic"] = ((268707072 + 3934720) * n / 262144
+                           if (f == "bf16x3" and d == 256 and mma_n == 208) else None)
         roof["ms"] = final_ms[f]
+        roof["call_ms"] = final_call_ms[f]
+        roof["mma_n"] = mma_n if f != "fp32" else None
         return roof
 
     rooflines = {"final": final_roof(args.final_prec)}
@@ -586,8 +605,10 @@ def main():
                           "achieved": chol_flops / (kernel_ms["k_pchol_grid"] * 1e-3) / 1e12, "peak": fp64_peak,
                           "unit": "TFLOP/s", "peak_source": "FP64 FMA rate measured on this GB300 (1.19 TFLOP/s)",
                           "algorithmic": chol_flops, "traffic": None, "ms": kernel_ms["k_pchol_grid"],
-                          "note": "latency-bound: each pivot step waits for one L2 round trip of the pivot row "
-                                  "and a chain of dependent FP64 operations; the FP64 work itself is ~9 us"}
+                          "note": "latency-bound: each pivot step waits for one L2 round trip of the published "
+                                  "row and a chain of dependent double-float (FP32 pair) operations; achieved is "
+                                  "counted in FP64-equivalent flops, whose whole count would take ~9 us at the "
+                                  "FP64 rate"}
     rooflines["pchol"]["frac"] = rooflines["pchol"]["achieved"] / fp64_peak
     dominant_kernel = max(kernel_ms, key=kernel_ms.get)
     dominant = max(stages, key=stages.get)

@@ -401,9 +401,13 @@ int lev_device_status(lev_handle* h, int32_t* status);
  * kernel (the grid pivoted Cholesky, or the Householder kernel). lev_rrqr_timing waits for the
  * events of the last such call and returns the two durations in milliseconds; either output
  * pointer may be NULL. Errors: LEV_EINVAL (timing off, or no QR since it was enabled),
- * LEV_ECUDA. */
+ * LEV_ECUDA. The tensor-core dense final pass (lev_final_dense with LEV_TF32, LEV_BF16 or
+ * LEV_BF16X3, and the final stage of lev_estimate_dense) likewise records events around its
+ * main kernel, after the packing of Mfull's operand image; lev_final_timing waits for those of
+ * the last such call and returns the kernel's duration. */
 int lev_set_timing(lev_handle* h, int enable);
 int lev_rrqr_timing(lev_handle* h, float* gram_ms, float* factor_ms);
+int lev_final_timing(lev_handle* h, float* kernel_ms);
 
 /* lev_rrqr without any allocation. The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc -- code that lives inside

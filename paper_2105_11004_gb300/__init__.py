@@ -85,6 +85,7 @@ SIGNATURES = {
                                     _c_void_p, _c_void_p, _i32, _dbl, _dbl, _P(_i32), _P(_dbl), _c_void_p]),
     "lev_set_timing": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
     "lev_rrqr_timing": (ctypes.c_int, [_c_void_p, _P(ctypes.c_float), _P(ctypes.c_float)]),
+    "lev_final_timing": (ctypes.c_int, [_c_void_p, _P(ctypes.c_float)]),
     "lev_rrqr_noalloc": (ctypes.c_int, [_c_void_p, _i64, _i64, _dbl, _c_void_p, _c_void_p, _P(_i64), _c_void_p]),
 }
 
@@ -401,6 +402,14 @@ def lev_rrqr_timing(h: Handle):
     g, f = ctypes.c_float(), ctypes.c_float()
     _check(lib.lev_rrqr_timing(h.ptr, ctypes.byref(g), ctypes.byref(f)))
     return g.value, f.value
+
+
+def lev_final_timing(h: Handle) -> float:
+    """Duration (ms) of the main kernel of the last tensor-core dense final pass on h since
+    lev_set_timing(h, True)."""
+    f = ctypes.c_float()
+    _check(lib.lev_final_timing(h.ptr, ctypes.byref(f)))
+    return f.value
 
 
 def lev_device_status(h: Handle) -> int:

@@ -76,8 +76,9 @@ struct lev_handle {
     // the CountSketch bucket permutation (off, perm_rows) of the last (seed, n, s), and an event
     // recorded after it was built so that a call on another stream waits for it
     // diagnostics: events around the Gram product and the factorisation of the last rrqr
-    bool timing = false, timed_once = false;
+    bool timing = false, timed_once = false, final_timed = false;
     cudaEvent_t tmark[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fmark[2] = {nullptr, nullptr};   // around the tensor-core final pass kernel
     uint64_t perm_seed = 0;
     int64_t perm_n = -1, perm_s = -1, perm_row0 = 0;
     cudaEvent_t ev_perm = nullptr;
@@ -613,6 +614,11 @@ int handle_scratch(lev_handle* h, int which, size_t bytes, void** out) {
     return LEV_OK;
 }
 int handle_num_sms(lev_handle* h) { return h->num_sms; }
+const cudaEvent_t* handle_final_marks(lev_handle* h) {
+    if (!h->timing) return nullptr;
+    h->final_timed = true;
+    return h->fmark;
+}
 int32_t* handle_status(lev_handle* h) { return h->status; }
 int handle_gaussian(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
                     const float** g32, const __nv_bfloat16** ghi) {
@@ -682,6 +688,8 @@ int lev_destroy(lev_handle* h) {
     if (h->ev_perm) cudaEventDestroy(h->ev_perm);
     for (int i = 0; i < 3; ++i)
         if (h->tmark[i]) cudaEventDestroy(h->tmark[i]);
+    for (int i = 0; i < 2; ++i)
+        if (h->fmark[i]) cudaEventDestroy(h->fmark[i]);
     if (h->ev_omega) cudaEventDestroy(h->ev_omega);
     if (h->g.ptr) cudaFree(h->g.ptr);
     if (h->status) cudaFree(h->status);
@@ -703,8 +711,22 @@ int lev_set_timing(lev_handle* h, int enable) {
     LEV_TRY(set_device(h));
     if (enable && !h->tmark[0])
         for (int i = 0; i < 3; ++i) LEV_CUDA(cudaEventCreate(&h->tmark[i]));
+    if (enable && !h->fmark[0])
+        for (int i = 0; i < 2; ++i) LEV_CUDA(cudaEventCreate(&h->fmark[i]));
     h->timing = enable != 0;
     h->timed_once = false;
+    h->final_timed = false;
+    return LEV_OK;
+}
+
+int lev_final_timing(lev_handle* h, float* kernel_ms) {
+    LEV_TRY(set_device(h));
+    if (!h->timing || !h->final_timed)
+        return fail(LEV_EINVAL, "timing is off or no tensor-core final pass ran since it was enabled");
+    LEV_CUDA(cudaEventSynchronize(h->fmark[1]));
+    float a = 0.f;
+    LEV_CUDA(cudaEventElapsedTime(&a, h->fmark[0], h->fmark[1]));
+    if (kernel_ms) *kernel_ms = a;
     return LEV_OK;
 }
 

@@ -13,6 +13,8 @@ namespace lev {
 // image of the final pass, 1 split-K partials, 2 operand B^T of the Gaussian stage, 3 padded A.
 int handle_scratch(lev_handle* h, int which, size_t bytes, void** out);
 int handle_num_sms(lev_handle* h);
+// The two events to record around the final pass kernel when the handle's timing is on, else null.
+const cudaEvent_t* handle_final_marks(lev_handle* h);
 int32_t* handle_status(lev_handle* h);
 int handle_gaussian(lev_handle* h, int64_t m, int64_t s, uint64_t seed, int kind, cudaStream_t st,
                     const float** g32, const __nv_bfloat16** ghi);

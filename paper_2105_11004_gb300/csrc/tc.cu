@@ -3,37 +3,41 @@
 // in the epilogue, so the n x k product never reaches memory.
 //
 // One persistent CTA per SM (BF16) or per SM of a 2-CTA cluster (BF16X3, TF32).
-// Shared memory holds the CTA's part of the packed operand image of Mfull^T and
-// a ring of slots; a slot holds one K block of the CTA's 128 rows of A.
+// Shared memory holds the CTA's part of the packed operand image of Mfull^T (the
+// B operand) and a ring of landing slots; a slot holds one K block of the CTA's
+// 128 rows of A in FP32. Tensor memory holds one accumulator (256 columns) and
+// a ring of A buffers: K blocks of the rows of A rounded to the operand type,
+// the MMAs' A operand.
 //   * warp 17 (producer): 2-D tensor TMA of a slot's FP32 boxes (32 columns x
 //     128 rows each, 128-byte swizzle);
-//   * warps 4..15 (converters, three groups of four): round the slot IN PLACE to
-//     the operand type; the groups take the slots in turn, so three are rounded
-//     at once.
-//     With 64-column K blocks the two FP32 boxes of row r occupy exactly the
-//     bytes that the BF16 hi row r and lo row r take in the 128-byte swizzled
-//     K-major operand layout (same row, same swizzle phase), so a warp that owns
-//     whole rows reads them, syncs, and writes them back; TF32 rounds each
-//     16-byte chunk where it lies;
-//   * warp 16 (MMA): allocates TMEM (two accumulators of 256 columns), loads the
-//     image once with bulk copies, and one thread issues tcgen05.mma (N = the
-//     width of Mfull, 32 bytes of K per instruction); the MMA completion frees
-//     the slot;
-//   * warps 0..3 (epilogue): tcgen05.ld of the accumulator (TMEM lane = row),
-//     sum of squares over the N columns, one store per row.
+//   * warps 8..15 (converters, two per TMEM lane quarter, each half of a K
+//     block), lane = row: read the row's FP32 values, free the slot (its bytes
+//     are in registers), round them (BF16 hi, BF16 lo, or TF32) and store them
+//     into the fill's A buffer with tcgen05.st once the MMAs of the buffer's
+//     previous fill have finished. A slot is busy only from its copy to its
+//     read; the A buffers (4 for the split form, 8 otherwise) decouple the
+//     converters from the MMAs;
+//   * warp 16 (MMA): allocates TMEM, loads the image once with bulk copies, and
+//     one thread issues tcgen05.mma with A from TMEM and B from shared memory
+//     (N = the width of Mfull, 32 bytes of K per instruction); the MMA
+//     completion frees the A buffer;
+//   * warps 0..7 (epilogue, two per TMEM lane quarter, each half of the
+//     columns): tcgen05.ld of the accumulator (TMEM lane = row), sums of squares,
+//     one store per row; then the MMAs of the next tile may overwrite it.
 // N: Mfull's columns up to its last nonzero one, rounded up to 16 (k_mfull_width
 // finds it on the device). Trailing zero columns add nothing to theta~; the
 // r-column factor of lev_omega_factor's reduced form leaves k - r of them.
 // BF16: M = 128 per CTA; the 128 KB image of Mfull^T (256 x 256 BF16) fits one
 // CTA. BF16X3 (hi*hi + lo*hi + hi*lo) and TF32 need 256 KB for the image, so
 // they run as CTA pairs with cta_group::2: one thread of the even CTA issues an
-// M = 256 MMA for the pair; each CTA holds its own 128 rows of A and half of
-// the image (128 columns of Mfull), and each CTA's TMEM receives its own rows
-// with all 256 columns. Nothing is loaded twice and no operand crosses between
-// the CTAs except through the MMA itself. The odd CTA reports "slot converted"
-// and "accumulator drained" to the even CTA's mbarriers; MMA completions are
-// multicast to both. Every wait is bounded (2 s of %globaltimer); on expiry the
-// CTA records the failure in the status word and leaves its loops.
+// M = 256 MMA for the pair; each CTA holds its own 128 rows of A (in its TMEM)
+// and half of the image (half of Mfull's columns), and each CTA's TMEM receives
+// its own rows with all N columns. Nothing is loaded twice and no operand
+// crosses between the CTAs except through the MMA itself. The odd CTA reports
+// "A buffer written" and "accumulator drained" to the even CTA's mbarriers; MMA
+// completions are multicast to both. Every wait is bounded (2 s of
+// %globaltimer); on expiry the CTA records the failure in the status word and
+// leaves its loops.
 #include <atomic>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -43,7 +47,6 @@
 #include "tc_common.cuh"
 
 namespace lev {
-
 namespace {
 
 using namespace tcx;
@@ -73,21 +76,24 @@ struct FormTraits<kTF32> {
 constexpr int kTileRows = 128;                    // rows of A per CTA per tile (TMEM lanes)
 constexpr int kBoxBytes = kTileRows * 128;        // one FP32 box: 128 rows x 32 columns = one 16 KB K block
 constexpr int kNOut = 256;                        // accumulator columns per row (the widest MMA N)
-// Converters: kCvtGroups groups of four warps; group g rounds the slot fills u with u mod
-// kCvtGroups = g, so each slot belongs to one group (the slot counts are multiples of it) and its
-// fills are taken in order, while the groups' slots are rounded at the same time.
-constexpr int kEpiWarps = 4, kCvtGroups = 3, kCvtWarpsPerGroup = 4;
-constexpr int kCvtWarps = kCvtGroups * kCvtWarpsPerGroup;
+// Epilogue and converters: eight warps each, two per TMEM lane quarter (warp mod 4). An epilogue
+// warp reads half of the accumulator columns of its quarter's 32 rows; a converter warp rounds half
+// of each K block of them, and takes every slot fill in order.
+constexpr int kEpiWarps = 8, kCvtWarps = 8;
 constexpr int kMmaWarp = kEpiWarps + kCvtWarps;   // warp 16
 constexpr int kTmaWarp = kMmaWarp + 1;            // warp 17
 constexpr int kThreads = (kTmaWarp + 1) * 32;     // 576
 constexpr int kMaxSlots = 6;
+constexpr int kMaxAbufs = 8;
 constexpr uint64_t kWaitNs = 2000000000ull;       // 2 s
 constexpr uint64_t kExitWaitNs = 5000000000ull;   // 5 s: a peer that timed out reaches the exit within one kWaitNs
 constexpr int32_t kStatusTcTimeout = 2;
 
 struct TcSmemCtl {
-    uint64_t sfull[kMaxSlots], cfull[kMaxSlots], sempty[kMaxSlots], tfull[2], tempty[2], mfull, ipeer, mdone, xbar;
+    uint64_t sfull[kMaxSlots], sempty[kMaxSlots], afull[kMaxAbufs], aempty[kMaxAbufs], tfull, tempty, mfull, ipeer,
+        mdone, xbar;
+    uint64_t pfull[2], pempty[2];
+    float part[2][kTileRows];   // the second column half's sums of squares, by tile parity
     uint32_t tmem_base;
     int32_t abort;
 };
@@ -122,6 +128,16 @@ __device__ __forceinline__ bool drain_bar(uint32_t bar, uint32_t parity, uint64_
     return true;
 }
 
+// Relaxed arrival on the mbarrier at `bar` in the even CTA of the pair (this CTA when unpaired):
+// hands over tensor-memory data (written, or read, and fenced by the caller).
+template <int PAIR>
+__device__ __forceinline__ void arrive_leader_tmem(uint32_t bar, uint32_t me) {
+    if (PAIR == 2 && me != 0)
+        mbar_arrive_relaxed_cluster(mapa_shared(bar, 0));
+    else
+        mbar_arrive_relaxed(bar);
+}
+
 // Arrive on the mbarrier at `bar` in the even CTA of the pair (this CTA when unpaired).
 template <int PAIR>
 __device__ __forceinline__ void arrive_leader(uint32_t bar, uint32_t me) {
@@ -151,55 +167,106 @@ __device__ __forceinline__ int mma_width(const int* width) {
     return (w + 15) & ~15;
 }
 
-// *width = 1 + the last column of Mfull (d x k) holding a nonzero (or NaN) entry; 0 if none.
+// *width = 1 + the last column of Mfull (d x k, k <= 256) holding a nonzero (or NaN) entry; 0 if
+// none (*width zeroed before). Block y covers rows y, y + gridDim.y, ...; thread x column x.
 __global__ void k_mfull_width(const float* __restrict__ M, int d, int k, int* width) {
+    __shared__ int wmax;
+    if (threadIdx.x == 0) wmax = 0;
+    __syncthreads();
     int w = 0;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)d * k;
-         e += (int64_t)gridDim.x * blockDim.x)
-        if (M[e] != 0.f) w = max(w, (int)(e % k) + 1);
+    const int q = threadIdx.x;
+    if (q < k)
+        for (int i = blockIdx.y; i < d; i += gridDim.y)
+            if (M[(int64_t)i * k + q] != 0.f) w = q + 1;
     w = (int)__reduce_max_sync(0xffffffffu, (unsigned)w);
-    if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(width, w);
+    if ((threadIdx.x & 31) == 0 && w > 0) atomicMax(&wmax, w);
+    __syncthreads();
+    if (threadIdx.x == 0 && wmax > 0) atomicMax(width, wmax);
 }
 
-// Round rows 16 cw .. 16 cw + 15 of one slot in place.
+// Half a K block of this lane's row of A (columns 32 h .. 32 h + 31 of a BF16 K block, 16 h .. 16 h
+// + 15 of a TF32 one): its FP32 values from the slot, then rounded to operand words, two BF16 or
+// one TF32 a word, lower K first: hi[0..16) and, for the split form, lo[0..16).
 template <int F>
-__device__ __forceinline__ void convert_slot(uint8_t* slot, int cw, int lane) {
+struct HalfRow {
+    static constexpr int kVec = FormTraits<F>::kKbe / 8;         // float4 per half row
+    float4 x[kVec];
+};
+template <int F>
+__device__ __forceinline__ void load_half_row(const uint8_t* slot, uint32_t row, int h, HalfRow<F>& v) {
+#pragma unroll
+    for (int q = 0; q < HalfRow<F>::kVec; ++q) {
+        const int g = h * HalfRow<F>::kVec + q;                   // 16-byte chunk of the row's K block
+        v.x[q] = *reinterpret_cast<const float4*>(slot + (g >> 3) * kBoxBytes + sw128_offset(row, (uint32_t)(g & 7) * 16u));
+    }
+}
+template <int F>
+struct HalfWords {
+    uint32_t hi[16];
+    uint32_t lo[FormTraits<F>::kSplit ? 16 : 1];
+};
+template <int F>
+__device__ __forceinline__ void round_half_row(const HalfRow<F>& v, HalfWords<F>& w) {
     using T = FormTraits<F>;
-    if constexpr (T::kTf32) {
-        // one box; each 16-byte chunk is rounded where it lies
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t task = (uint32_t)(q * 32 + lane);           // 16 rows x 8 chunks
-            const uint32_t row = (uint32_t)cw * 16u + (task >> 3), c = task & 7u;
-            uint4* p = reinterpret_cast<uint4*>(slot + sw128_offset(row, c * 16u));
-            const float4 x = *reinterpret_cast<const float4*>(p);
-            *p = make_uint4(f32_to_tf32(x.x), f32_to_tf32(x.y), f32_to_tf32(x.z), f32_to_tf32(x.w));
-        }
-    } else {
-        // two boxes (columns 0..31 and 32..63) -> BF16 hi K block in box 0's bytes, lo in box 1's
-        float4 x[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t task = (uint32_t)(q * 32 + lane);           // 16 rows x 16 chunks
-            const uint32_t row = (uint32_t)cw * 16u + (task >> 4), ch = task & 15u;
-            x[q] = *reinterpret_cast<const float4*>(slot + (ch >> 3) * kBoxBytes + sw128_offset(row, (ch & 7u) * 16u));
-        }
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t task = (uint32_t)(q * 32 + lane);
-            const uint32_t row = (uint32_t)cw * 16u + (task >> 4), ch = task & 15u;
-            const uint32_t off = sw128_offset(row, ch * 8u);
+    for (int q = 0; q < HalfRow<F>::kVec; ++q) {
+        const float4 x = v.x[q];
+        if constexpr (T::kTf32) {
+            w.hi[4 * q + 0] = f32_to_tf32(x.x);
+            w.hi[4 * q + 1] = f32_to_tf32(x.y);
+            w.hi[4 * q + 2] = f32_to_tf32(x.z);
+            w.hi[4 * q + 3] = f32_to_tf32(x.w);
+        } else {
             float r0, r1, r2, r3;
-            const uint2 hi = make_uint2(pack_bf16x2(x[q].x, x[q].y, &r0, &r1), pack_bf16x2(x[q].z, x[q].w, &r2, &r3));
-            *reinterpret_cast<uint2*>(slot + off) = hi;
+            w.hi[2 * q] = pack_bf16x2(x.x, x.y, &r0, &r1);
+            w.hi[2 * q + 1] = pack_bf16x2(x.z, x.w, &r2, &r3);
             if constexpr (T::kSplit) {
                 float u0, u1;
-                const uint2 lo = make_uint2(pack_bf16x2(r0, r1, &u0, &u1), pack_bf16x2(r2, r3, &u0, &u1));
-                *reinterpret_cast<uint2*>(slot + kBoxBytes + off) = lo;
+                w.lo[2 * q] = pack_bf16x2(r0, r1, &u0, &u1);
+                w.lo[2 * q + 1] = pack_bf16x2(r2, r3, &u0, &u1);
             }
         }
     }
+}
+
+// Sum of the squares of `cols` (a multiple of 16) consecutive accumulator columns of this thread's
+// TMEM lane from taddr on: two 32-column loads in flight per wait, then the 32- and 16-column rest.
+__device__ __forceinline__ float tmem_sum_squares(uint32_t taddr, int cols) {
+    float sum = 0.f;
+    int c = 0;
+    for (; c + 64 <= cols; c += 64) {
+        uint32_t r[32], q[32];
+        tmem_ld32(taddr + (uint32_t)c, r);
+        tmem_ld32(taddr + (uint32_t)c + 32u, q);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float y = __uint_as_float(r[j]), z = __uint_as_float(q[j]);
+            sum = fmaf(y, y, sum);
+            sum = fmaf(z, z, sum);
+        }
+    }
+    for (; c + 32 <= cols; c += 32) {
+        uint32_t r[32];
+        tmem_ld32(taddr + (uint32_t)c, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float y = __uint_as_float(r[j]);
+            sum = fmaf(y, y, sum);
+        }
+    }
+    if (c < cols) {
+        uint32_t r[16];
+        tmem_ld16(taddr + (uint32_t)c, r);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float y = __uint_as_float(r[j]);
+            sum = fmaf(y, y, sum);
+        }
+    }
+    return sum;
 }
 
 template <int F>
@@ -212,13 +279,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
     constexpr int NS = T::kSlots;
     constexpr int BOXES = T::kKbe / 32;                       // FP32 boxes per K block
     constexpr int SLOT_BYTES = BOXES * kBoxBytes;
+    constexpr uint32_t kAcols = T::kSplit ? 64u : 32u;        // TMEM columns of one K block of A
+    constexpr uint32_t kAbase = kNOut;                        // A buffers after the accumulator
+    constexpr int NA = (int)((512u - kAbase) / kAcols);       // A buffers: 4 (split form) or 8
+    constexpr uint32_t kKstepCols = 8u;                       // TMEM columns of A per MMA (32 bytes of K)
     static_assert(T::kNt * PAIR == kNOut, "the image holds up to 256 columns of Mfull");
+    static_assert(NS <= kMaxSlots && NA <= kMaxAbufs, "slot and A-buffer barriers");
     const int ne = mma_width(width);                          // MMA N
+    const uint32_t IDESC = make_idesc(T::kTf32, kTileRows * PAIR, ne);
     const uint32_t kb_img_bytes = (uint32_t)(ne / PAIR) * 128u;   // one K block of this CTA's image
     const uint32_t img_used = (uint32_t)nkb * kb_img_bytes * (T::kSplit ? 2u : 1u);
-    const uint32_t IDESC = make_idesc(T::kTf32, kTileRows * PAIR, ne);
-    static_assert(NS <= kMaxSlots, "slot barriers");
-    static_assert(NS % kCvtGroups == 0, "each slot belongs to one converter group");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -238,12 +308,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&ctl->sfull[s]), 1);
-            mbar_init(smem_u32(&ctl->cfull[s]), kCvtWarpsPerGroup * PAIR);
-            mbar_init(smem_u32(&ctl->sempty[s]), 1);
+            mbar_init(smem_u32(&ctl->sempty[s]), kCvtWarps);
         }
+        for (int b = 0; b < NA; ++b) {
+            mbar_init(smem_u32(&ctl->afull[b]), kCvtWarps * PAIR);
+            mbar_init(smem_u32(&ctl->aempty[b]), 1);
+        }
+        mbar_init(smem_u32(&ctl->tfull), 1);
+        mbar_init(smem_u32(&ctl->tempty), kEpiWarps * PAIR);
         for (int a = 0; a < 2; ++a) {
-            mbar_init(smem_u32(&ctl->tfull[a]), 1);
-            mbar_init(smem_u32(&ctl->tempty[a]), kEpiWarps * PAIR);
+            mbar_init(smem_u32(&ctl->pfull[a]), kEpiWarps / 2);
+            mbar_init(smem_u32(&ctl->pempty[a]), kEpiWarps / 2);
         }
         mbar_init(smem_u32(&ctl->mfull), 1);
         mbar_init(smem_u32(&ctl->ipeer), 1);
@@ -255,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
     __syncthreads();
     if (PAIR == 2) asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     if (warp == kMmaWarp) {
-        tmem_alloc_cg<PAIR>(smem_u32(&ctl->tmem_base), 2 * kNOut);
+        tmem_alloc_cg<PAIR>(smem_u32(&ctl->tmem_base), 512);
         tmem_relinquish_cg<PAIR>();
     }
     tc_fence_before();
@@ -266,11 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
     if (warp == kTmaWarp) {
         // ---------------- producer: this CTA's 128 rows of one K block per slot
         if (lane == 0) {
-            int s = 0;
-            uint32_t ph = 0;
             int64_t issued = 0;
             for (int64_t u = 0; u < uses; ++u) {
-                if (!wait_bar(smem_u32(&ctl->sempty[s]), ph ^ 1u, ctl, status)) break;
+                const int s = (int)(u % NS);
+                if (!wait_bar(smem_u32(&ctl->sempty[s]), (uint32_t)((u / NS) & 1) ^ 1u, ctl, status)) break;
                 const int64_t t = group + (u / nkb) * ngroups;
                 const int32_t x = (int32_t)(u % nkb) * T::kKbe;
                 const int32_t y = (int32_t)(t * kGroupRows + (int64_t)me * kTileRows);
@@ -280,18 +354,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
 #pragma unroll
                 for (int b = 0; b < BOXES; ++b) tma_load_2d(dst + b * kBoxBytes, &tmA, x + b * 32, y, bar);
                 ++issued;
-                if (++s == NS) { s = 0; ph ^= 1u; }
             }
-            // no copy may still be landing in this CTA's shared memory when it exits, and the
-            // last "slot free" signals of the MMA (multicast in a pair) have landed here
+            // no copy may still be landing in this CTA's shared memory when it exits
             for (int64_t j = issued > NS ? issued - NS : 0; j < issued; ++j)
                 drain_bar(smem_u32(&ctl->sfull[j % NS]), (uint32_t)((j / NS) & 1), kWaitNs, status);
-            if (issued == uses && !*(volatile int32_t*)&ctl->abort) {
-                for (int q = 0; q < NS; ++q) {
-                    const int64_t k_uses = uses / NS + (q < uses % NS ? 1 : 0);
-                    if (k_uses > 0) drain_bar(smem_u32(&ctl->sempty[q]), (uint32_t)((k_uses - 1) & 1), kWaitNs, status);
-                }
-            }
         }
         __syncwarp();
     } else if (warp == kMmaWarp) {
@@ -309,45 +375,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
                 if (ok) mbar_arrive_cluster(mapa_shared(smem_u32(&ctl->ipeer), 0));
             } else {
                 if (PAIR == 2) ok = ok && wait_bar(smem_u32(&ctl->ipeer), 0, ctl, status);
-                int s = 0;
-                uint32_t sph = 0;
-                int acc = 0;
-                uint32_t acc_phase = 0;
                 const uint32_t img_addr = smem_u32(img);
-                const uint32_t slot_addr = smem_u32(slots);
                 const uint16_t both = (uint16_t)(PAIR == 2 ? 0x3 : 0x1);
                 for (int64_t tt = 0; ok && tt < my_tiles; ++tt) {
-                    if (!wait_bar(smem_u32(&ctl->tempty[acc]), acc_phase ^ 1u, ctl, status)) { ok = false; break; }
+                    // the epilogue has read the previous tile's accumulator
+                    if (!wait_bar(smem_u32(&ctl->tempty), (uint32_t)(tt & 1) ^ 1u, ctl, status)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem + (uint32_t)(acc * kNOut);
                     for (int kb = 0; kb < nkb; ++kb) {
-                        if (!wait_bar(smem_u32(&ctl->cfull[s]), sph, ctl, status)) { ok = false; break; }
+                        const int64_t u = tt * nkb + kb;
+                        const int b = (int)(u % NA);
+                        if (!wait_bar(smem_u32(&ctl->afull[b]), (uint32_t)((u / NA) & 1), ctl, status)) {
+                            ok = false;
+                            break;
+                        }
                         tc_fence_after();
-                        const uint32_t a_hi = slot_addr + (uint32_t)s * SLOT_BYTES;
+                        const uint32_t a_hi = tmem + kAbase + (uint32_t)b * kAcols;
                         const uint32_t m_hi = img_addr + (uint32_t)kb * kb_img_bytes;
 #pragma unroll
                         for (int ks = 0; ks < 4; ++ks) {
-                            const uint32_t koff = (uint32_t)ks * 32u;
+                            const uint32_t acol = (uint32_t)ks * kKstepCols, koff = (uint32_t)ks * 32u;
                             const uint32_t accum = (kb | ks) != 0 ? 1u : 0u;
-                            tc_mma_cg<PAIR, T::kTf32>(d_tmem, sw128_desc(a_hi + koff), sw128_desc(m_hi + koff),
-                                                      IDESC, accum);
+                            tc_mma_ts<PAIR, T::kTf32>(tmem, a_hi + acol, sw128_desc(m_hi + koff), IDESC, accum);
                             if constexpr (T::kSplit) {
-                                const uint32_t a_lo = a_hi + kBoxBytes;
+                                const uint32_t a_lo = a_hi + 32u;
                                 const uint32_t m_lo = m_hi + (uint32_t)nkb * kb_img_bytes;
-                                tc_mma_cg<PAIR, false>(d_tmem, sw128_desc(a_lo + koff), sw128_desc(m_hi + koff),
-                                                       IDESC, 1u);
-                                tc_mma_cg<PAIR, false>(d_tmem, sw128_desc(a_hi + koff), sw128_desc(m_lo + koff),
-                                                       IDESC, 1u);
+                                tc_mma_ts<PAIR, false>(tmem, a_lo + acol, sw128_desc(m_hi + koff), IDESC, 1u);
+                                tc_mma_ts<PAIR, false>(tmem, a_hi + acol, sw128_desc(m_lo + koff), IDESC, 1u);
                             }
                         }
-                        // slot s is free again in both CTAs once these MMAs finish
-                        tc_commit_mc<PAIR>(smem_u32(&ctl->sempty[s]), both);
-                        if (++s == NS) { s = 0; sph ^= 1u; }
+                        // A buffer b is free again in both CTAs once these MMAs finish
+                        tc_commit_mc<PAIR>(smem_u32(&ctl->aempty[b]), both);
                     }
                     if (!ok) break;
-                    tc_commit_mc<PAIR>(smem_u32(&ctl->tfull[acc]), both);
-                    acc ^= 1;
-                    if (acc == 0) acc_phase ^= 1u;
+                    tc_commit_mc<PAIR>(smem_u32(&ctl->tfull), both);
                 }
                 // every MMA has finished before TMEM is freed
                 tc_commit_mc<PAIR>(smem_u32(&ctl->mdone), (uint16_t)0x1);
@@ -356,63 +416,78 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
         }
         __syncwarp();
     } else if (warp >= kEpiWarps) {
-        // ---------------- converters: each slot rounded in place by its group, 32 rows a warp
-        const int cw = warp - kEpiWarps;
-        const int grp = cw / kCvtWarpsPerGroup, wq = cw % kCvtWarpsPerGroup;
-        for (int64_t u = grp; u < uses; u += kCvtGroups) {
-            const int s = (int)(u % NS);
+        // ---------------- converters: lane = row of the warp's lane quarter, half h of each K block
+        const int cw = warp - kEpiWarps;                      // kEpiWarps is a multiple of 4
+        const int wq = cw & 3, h = cw >> 2;                   // wq = warp mod 4: the TMEM lanes it may access
+        const uint32_t row = (uint32_t)(wq * 32 + lane);
+        const uint32_t lane_addr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)h * 16u;
+        for (int64_t u = 0; u < uses; ++u) {
+            const int s = (int)(u % NS), b = (int)(u % NA);
             if (!wait_bar(smem_u32(&ctl->sfull[s]), (uint32_t)((u / NS) & 1), ctl, status)) break;
-            convert_slot<F>(slots + s * SLOT_BYTES, 2 * wq, lane);
-            convert_slot<F>(slots + s * SLOT_BYTES, 2 * wq + 1, lane);
-            fence_proxy_async_smem();
+            HalfRow<F> v;
+            load_half_row<F>(slots + s * SLOT_BYTES, row, h, v);
+            HalfWords<F> w;
             __syncwarp();
-            if (lane == 0) arrive_leader<PAIR>(smem_u32(&ctl->cfull[s]), me);
-        }
-    } else {
-        // ---------------- epilogue: TMEM lane = row of this CTA's 128
-        int acc = 0;
-        uint32_t acc_phase = 0;
-        for (int64_t tt = 0; tt < my_tiles; ++tt) {
-            const int64_t t = group + tt * ngroups;
-            if (!wait_bar(smem_u32(&ctl->tfull[acc]), acc_phase, ctl, status)) break;
+            if (lane == 0) mbar_arrive(smem_u32(&ctl->sempty[s]));      // the slot's bytes are in registers
+            round_half_row<F>(v, w);
+            // the MMAs that read A buffer b for fill u - NA have finished (both CTAs)
+            if (!wait_bar(smem_u32(&ctl->aempty[b]), (uint32_t)((u / NA) & 1) ^ 1u, ctl, status)) break;
             tc_fence_after();
-            float sum = 0.f;
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kNOut);
-            for (int c = 0; c < ne; c += 32) {
-                if (c + 32 <= ne) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + (uint32_t)c, r);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float y = __uint_as_float(r[j]);
-                        sum = fmaf(y, y, sum);
-                    }
-                } else {
-                    uint32_t r[16];
-                    tmem_ld16(taddr + (uint32_t)c, r);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float y = __uint_as_float(r[j]);
-                        sum = fmaf(y, y, sum);
-                    }
-                }
-            }
+            const uint32_t a = lane_addr + kAbase + (uint32_t)b * kAcols;
+            tmem_st16(a, w.hi);
+            if constexpr (T::kSplit) tmem_st16(a + 32u, w.lo);
+            tmem_st_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) arrive_leader<PAIR>(smem_u32(&ctl->tempty[acc]), me);
-            const int64_t row = t * kGroupRows + (int64_t)me * kTileRows + warp * 32 + lane;
-            if (row < n) theta[row] = sum;
-            acc ^= 1;
-            if (acc == 0) acc_phase ^= 1u;
+            if (lane == 0) arrive_leader_tmem<PAIR>(smem_u32(&ctl->afull[b]), me);
+        }
+        // the MMA completions multicast to this CTA's A-buffer barriers have all landed
+        if (cw == 0 && lane == 0 && !*(volatile int32_t*)&ctl->abort) {
+            for (int q = 0; q < NA; ++q) {
+                const int64_t k_uses = uses / NA + (q < uses % NA ? 1 : 0);
+                if (k_uses > 0) drain_bar(smem_u32(&ctl->aempty[q]), (uint32_t)((k_uses - 1) & 1), kWaitNs, status);
+            }
+        }
+    } else {
+        // ---------------- epilogue: TMEM lane = row of this CTA's 128; warp w reads columns
+        // [0, split) (w < 4) or [split, ne) (w >= 4) of rows 32 (w mod 4) .. + 31
+        const int wq = warp & 3, eh = warp >> 2;
+        const int split = min(ne, 64 * ((ne + 127) / 128));   // a multiple of 64 (or all of ne)
+        const uint32_t lanes = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(eh ? split : 0);
+        const int cols = eh ? ne - split : split;
+        for (int64_t tt = 0; tt < my_tiles; ++tt) {
+            const int64_t t = group + tt * ngroups;
+            if (!wait_bar(smem_u32(&ctl->tfull), (uint32_t)(tt & 1), ctl, status)) break;
+            tc_fence_after();
+            const float sum = tmem_sum_squares(lanes, cols);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) arrive_leader_tmem<PAIR>(smem_u32(&ctl->tempty), me);
+            // the second column half's warps hand their sums to the first's through part[tt & 1]
+            // (two buffers; each is refilled once the first half has read it)
+            const int pb = (int)(tt & 1);
+            const uint32_t pph = (uint32_t)((tt >> 1) & 1);
+            float* part = ctl->part[pb];
+            if (eh) {
+                if (!wait_bar(smem_u32(&ctl->pempty[pb]), pph ^ 1u, ctl, status)) break;
+                part[wq * 32 + lane] = sum;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ctl->pfull[pb]));
+            } else {
+                if (!wait_bar(smem_u32(&ctl->pfull[pb]), pph, ctl, status)) break;
+                const float other = part[wq * 32 + lane];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ctl->pempty[pb]));
+                const int64_t row = t * kGroupRows + (int64_t)me * kTileRows + wq * 32 + lane;
+                if (row < n) theta[row] = sum + other;
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == kMmaWarp) {
         tc_fence_after();
-        tmem_dealloc_cg<PAIR>(tmem, 2 * kNOut);
+        tmem_dealloc_cg<PAIR>(tmem, 512);
     }
     if (PAIR == 2) {
         // neither CTA leaves while its peer may still signal its mbarriers (bounded)
@@ -434,15 +509,14 @@ __global__ void k_pack_image(const float* __restrict__ M, int d, int k, int nkb,
                              uint32_t half_bytes, const int* __restrict__ width) {
     using T = FormTraits<F>;
     const int NT = mma_width(width) / T::kPair;
-    const int64_t per_half = (int64_t)nkb * NT * T::kKbe;
-    const int64_t total = per_half * T::kPair;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int h = (int)(e / per_half);
-        int64_t rem = e % per_half;
-        const int kb = (int)(rem / (NT * T::kKbe));
-        rem %= NT * T::kKbe;
-        const int nl = (int)(rem / T::kKbe), el = (int)(rem % T::kKbe);
+    const int per_half = nkb * NT * T::kKbe;                   // at most 2^16 entries (d, k <= 256)
+    const int total = per_half * T::kPair;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int h = e / per_half;
+        int rem = e - h * per_half;
+        const int kb = rem / (NT * T::kKbe);
+        rem -= kb * (NT * T::kKbe);
+        const int nl = rem / T::kKbe, el = rem % T::kKbe;
         const int q = h * NT + nl, kk = kb * T::kKbe + el;
         const float x = (q < k && kk < d) ? M[(int64_t)kk * k + q] : 0.f;
         uint8_t* dst = image + (size_t)h * half_bytes + (size_t)kb * NT * 128;
@@ -473,8 +547,8 @@ int run_final_tc(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t ld
     int* width = reinterpret_cast<int*>(image + (size_t)half_bytes * T::kPair);
     cudaError_t e = cudaMemsetAsync(width, 0, sizeof(int), st);
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
-    k_mfull_width<<<32, 256, 0, st>>>(Mfull, (int)d, (int)k, width);
-    k_pack_image<F><<<64, 256, 0, st>>>(Mfull, (int)d, (int)k, nkb, image, half_bytes, width);
+    k_mfull_width<<<dim3(1, 64), 256, 0, st>>>(Mfull, (int)d, (int)k, width);
+    k_pack_image<F><<<256, 256, 0, st>>>(Mfull, (int)d, (int)k, nkb, image, half_bytes, width);
     e = cudaGetLastError();
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     CUtensorMap tmA;
@@ -516,9 +590,12 @@ int run_final_tc(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t ld
     if (groups > ntiles) groups = ntiles;
     if (groups < 1) groups = 1;
     cfg.gridDim = dim3((unsigned)(groups * T::kPair));
+    const cudaEvent_t* marks = handle_final_marks(h);
+    if (marks && (e = cudaEventRecord(marks[0], st)) != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     e = cudaLaunchKernelEx(&cfg, k_final_tc<F>, tmA, n, nkb, (const uint8_t*)image, half_bytes, (const int*)width,
                            theta, status);
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
+    if (marks && (e = cudaEventRecord(marks[1], st)) != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     return LEV_OK;
 }
 
