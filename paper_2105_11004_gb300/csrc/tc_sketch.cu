@@ -181,12 +181,15 @@ __global__ void __launch_bounds__(192, 1) k_gauss_tc(const __grid_constant__ CUt
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0 && me != 0) {
-            // odd CTA: report each landed stage to the even CTA, whose MMAs read this CTA's half
+            // odd CTA: report each landed stage to the even CTA, whose MMAs read this CTA's half. The
+            // stage's bytes were written by TMA and are read by the MMAs (both the async proxy) and
+            // this thread has seen them land, so the report is a relaxed arrival (a cluster-scope
+            // release arrive costs about a microsecond under load)
             int q = 0;
             uint32_t phase = 0;
             for (int i = 0; i < nkb; ++i) {
                 if (!gwait(smem_u32(&ctl->full[q]), phase, ctl, status)) break;
-                mbar_arrive_cluster(mapa_shared(smem_u32(&ctl->full[q]), 0));
+                mbar_arrive_relaxed_cluster(mapa_shared(smem_u32(&ctl->full[q]), 0));
                 if (++q == stages) { q = 0; phase ^= 1u; }
             }
         } else if (lane == 0) {
