@@ -398,18 +398,8 @@ def main():
     import paper_2105_11004_gb300 as L
 
     placement = gpu_numa_placement(local)            # before any pinned host buffer exists
-    # the ~1e9-nonzero CSR workload takes minutes to generate on the host: start it now, in a thread,
-    # so that it overlaps the GPU work of the other sections
     large = {}
     gen_thread = None
-    if not args.no_csr and not args.no_csr_large:
-        def _gen_large():
-            c = W.CONFIGS["csr_8e7x1024_rank1014"]
-            t0 = time.perf_counter()
-            large["C"] = W.csr_dup_columns(c["n"], c["d"], seed=c["data_seed"])
-            large["gen_s"] = time.perf_counter() - t0
-        gen_thread = threading.Thread(target=_gen_large, daemon=True)
-        gen_thread.start()
     n, d = cfg["n"], cfg["d"]
     A_np = make_input(cfg)
     A_host = torch.from_numpy(A_np).pin_memory()
@@ -478,6 +468,50 @@ def main():
     clocks = sampler.summary(t_wall0, t_wall1)
     sampler.stop()
     same_theta = all(torch.equal(ths[0], t_) for t_ in ths[1:])
+
+    e2e_out = None
+    if not args.no_e2e:
+        # end to end through the public API with pinned host A and theta: every step copies A
+        # (1.02 GB) host -> device and theta (4 MB) back. LEV_HOST_ASYNC lets the call return once
+        # its work is enqueued, so the handle's copy stream moves step i+1's A while the kernels
+        # of step i run; the loop ends with a synchronisation and the copied theta is checked.
+        pa = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
+                           sketch_prec=args.sketch_prec, final_prec=args.final_prec, host_async=True)
+        theta_host = torch.empty(n, dtype=torch.float32).pin_memory()
+        theta_dev = torch.empty(n, dtype=torch.float32, device="cuda")
+        L.lev_estimate_dense(h, A, pa, theta_dev)
+        for _ in range(2):
+            L.lev_estimate_dense(h, A_host, pa, theta_host, want_rank=False)
+        torch.cuda.synchronize()
+        barrier(world)
+        ke = max(5, min(args.steps, 20))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            L.lev_estimate_dense(h, A_host, pa, theta_host, want_rank=False)
+        torch.cuda.synchronize()
+        te = allmax(world, (time.perf_counter() - t0) / ke)
+        same = bool(np.array_equal(theta_host.numpy(), theta_dev.cpu().numpy()))
+        h2d_gbs, d2h_gbs = host_link(A_host, torch.empty_like(A), theta_host, theta_dev)
+        e2e_out = {"value": n * world / te, "unit": "rows/s", "h2d_bytes_per_step": n * d * 4,
+                   "d2h_bytes_per_step": n * 4, "ms_per_step": te * 1e3, "steps": ke,
+                   "h2d_gbs_measured": h2d_gbs, "d2h_gbs_measured": d2h_gbs,
+                   "h2d_floor_ms": n * d * 4 / (h2d_gbs * 1e9) * 1e3,
+                   "floor_source": "pinned 1.02 GB host -> device copy timed by CUDA events in this run",
+                   "api": "lev_estimate_dense, pinned host A and theta, LEV_HOST_ASYNC (copy of step i+1 "
+                          "overlaps the kernels of step i; one synchronisation after the loop)",
+                   "theta_equals_device_path": same}
+
+    # the ~1e9-nonzero CSR workload takes about a minute to generate on the host: start it now, in a
+    # thread, so that it overlaps the GPU work of the other sections (after the headline step and the
+    # end-to-end copies, which it would disturb)
+    if not args.no_csr and not args.no_csr_large:
+        def _gen_large():
+            c = W.CONFIGS["csr_8e7x1024_rank1014"]
+            t0 = time.perf_counter()
+            large["C"] = W.csr_dup_columns(c["n"], c["d"], seed=c["data_seed"])
+            large["gen_s"] = time.perf_counter() - t0
+        gen_thread = threading.Thread(target=_gen_large, daemon=True)
+        gen_thread.start()
 
     def time_steps(fn, reps):
         fn()
@@ -687,6 +721,8 @@ def main():
     if not args.no_backward:
         out["backward"] = backward_timing(L, h, reps)
 
+    if e2e_out is not None:
+        out["e2e"] = e2e_out
     if not args.no_csr:
         out["csr"] = {"csr_8e6x1024": csr_timing(L, h, "csr_8e6x1024", reps)}
         if gen_thread is not None:
@@ -695,37 +731,7 @@ def main():
             wait_s = time.perf_counter() - t0
             out["csr"]["csr_8e7x1024_rank1014"] = csr_large_timing(L, h, "csr_8e7x1024_rank1014", 3, large)
             out["csr"]["csr_8e7x1024_rank1014"]["generation_wait_s"] = wait_s
-
-    if not args.no_e2e:
-        # end to end through the public API with pinned host A and theta: every step copies A
-        # (1.02 GB) host -> device and theta (4 MB) back. LEV_HOST_ASYNC lets the call return once
-        # its work is enqueued, so the handle's copy stream moves step i+1's A while the kernels
-        # of step i run; the loop ends with a synchronisation and the copied theta is checked.
-        pa = L.make_params(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"],
-                           sketch_prec=args.sketch_prec, final_prec=args.final_prec, host_async=True)
-        theta_host = torch.empty(n, dtype=torch.float32).pin_memory()
-        theta_dev = torch.empty(n, dtype=torch.float32, device="cuda")
-        L.lev_estimate_dense(h, A, pa, theta_dev)
-        for _ in range(2):
-            L.lev_estimate_dense(h, A_host, pa, theta_host, want_rank=False)
-        torch.cuda.synchronize()
-        barrier(world)
-        ke = max(5, min(args.steps, 20))
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            L.lev_estimate_dense(h, A_host, pa, theta_host, want_rank=False)
-        torch.cuda.synchronize()
-        te = allmax(world, (time.perf_counter() - t0) / ke)
-        same = bool(np.array_equal(theta_host.numpy(), theta_dev.cpu().numpy()))
-        h2d_gbs, d2h_gbs = host_link(A_host, torch.empty_like(A), theta_host, theta_dev)
-        out["e2e"] = {"value": n * world / te, "unit": "rows/s", "h2d_bytes_per_step": n * d * 4,
-                      "d2h_bytes_per_step": n * 4, "ms_per_step": te * 1e3, "steps": ke,
-                      "h2d_gbs_measured": h2d_gbs, "d2h_gbs_measured": d2h_gbs,
-                      "h2d_floor_ms": n * d * 4 / (h2d_gbs * 1e9) * 1e3,
-                      "floor_source": "pinned 1.02 GB host -> device copy timed by CUDA events in this run",
-                      "api": "lev_estimate_dense, pinned host A and theta, LEV_HOST_ASYNC (copy of step i+1 "
-                             "overlaps the kernels of step i; one synchronisation after the loop)",
-                      "theta_equals_device_path": same}
+            large.clear()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         runs = []
