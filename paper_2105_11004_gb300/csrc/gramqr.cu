@@ -1,4 +1,4 @@
-// Rank-revealing QR of the sketch through its Gram matrix (FP64), sm_103a.
+// Rank-revealing QR of the sketch through its Gram matrix (FP64-grade), sm_103a.
 //
 // The pivoted QR of Alg. 4 (xGEQP3-style greatest-trailing-norm pivoting, Sec. 7)
 // and the pivoted Cholesky factorisation of G = A~^T A~ produce the same
@@ -28,7 +28,12 @@
 //     same pivot p_j (largest diagonal, ties to the lowest column) and the same
 //     rank decision S_pp <= tau^2 S_00 without exchanging them; the owner of each
 //     pivot publishes its updated column, unscaled, as soon as it is up to date,
-//     and the others wait for that row only (no flag, no grid barrier per step).
+//     and the others wait for that row only (no flag, no grid barrier per step);
+//   k_pchol_cluster: the same factorisation for d <= 256 on one thread-block
+//     cluster of 8 or 16 CTAs, the columns in registers, the pivot column pulled
+//     from the owner's shared memory (a remote hop of about 250 ns instead of an
+//     L2 round trip); it holds 16 SMs instead of ceil(d/3), which the other
+//     kernels of batches in flight use.
 //
 // The Gram route resolves |R_jj| / |R_00| down to about sqrt(m u) ~ 1e-7; the
 // caller uses the Householder kernel when tau is below 1e-6 or d > 1024.
@@ -561,6 +566,255 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     if (me == 0 && tid == 0) *rank_out = j;
 }
 
+// ---- the same factorisation on one thread-block cluster (d <= 256) ----
+// C CTAs (8 or 16) of 256 T threads. CTA me owns the columns c = q C + me (q < NCL) of the Schur
+// complement; row i of them is held in registers by the T threads i + 256 t (t < T), NCL / T columns
+// each. The Schur diagonal is replicated: entry i is held by thread i (t = 0) in every CTA. A step
+// with pivot p: thread i of an active row reads entry i of column p from the owner's array F (shared
+// memory; each column written once when it becomes a pivot, sentinel-filled before; a remote load
+// repeated, bounded, until it is not the sentinel), forms r_i = u_i / sqrt(s_pp) and the new
+// diagonal entry, and writes r_i to the CTA's row buffer and its warp's argmax to shared memory; one
+// block barrier, after which the row's other threads read r_i; every thread takes the next pivot from the eight warp results
+// (ties to the lowest index, the same in every CTA). The thread holding the next pivot's column
+// applies row j to it first and publishes it; every thread then applies row j to its other columns
+// while that column travels. A retired row or
+// column has r = 0, so its updates leave it unchanged and no per-column flags are needed. Same
+// arithmetic, outputs and stopping rule as k_pchol_grid.
+constexpr int kClRows = 256;
+
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cl_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cl_mapa(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ unsigned long long cl_ld_u64(uint32_t addr) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.cluster.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cl_st_local_u64(uint32_t addr, unsigned long long v) {
+    asm volatile("st.relaxed.cluster.shared::cta.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+// Inverse of order_key32: the FP32 value a key was made from.
+__device__ __forceinline__ float key32_value(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+template <int NCL, int T>
+__global__ void __launch_bounds__(kClRows * T, 1) k_pchol_cluster(const double* __restrict__ Gm, int d, int m,
+                                                                  double tau, const int32_t* __restrict__ forced,
+                                                                  int forced_rank, float2* __restrict__ Rdf,
+                                                                  double* __restrict__ rscale_out,
+                                                                  int32_t* __restrict__ piv,
+                                                                  int64_t* __restrict__ rank_out, int32_t* status) {
+    constexpr int NQ = NCL / T;                                           // columns a thread holds
+    static_assert(NQ * T == NCL, "columns split evenly over a row's threads");
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int C = (int)cl_size(), me = (int)cl_rank();
+    unsigned long long* F = reinterpret_cast<unsigned long long*>(smem);   // NCL x d: published columns
+    float2* rb = reinterpret_cast<float2*>(F + (size_t)NCL * d);          // 2 x d: row j of R, by parity
+    __shared__ __align__(16) uint4 red[2][8];                              // per warp: key lo, key hi, index
+    __shared__ float2 s_next[2];                                          // forced: the next pivot's s_pp
+    __shared__ double red_d[8];
+    __shared__ volatile int s_abort;
+    const int i = threadIdx.x % kClRows, t = threadIdx.x / kClRows;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;            // warps 0..7: t = 0
+    const bool row_ok = i < d;
+    // prescale 2^-e from the largest diagonal entry (the same in every CTA)
+    if (t == 0) {
+        double mx = row_ok ? Gm[(int64_t)i * d + i] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) red_d[wid] = mx;
+    }
+    __syncthreads();
+    double mx = red_d[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = fmax(mx, red_d[w]);
+    int ex = 0;
+    if (mx > 0.0 && mx < 1.0e300) ex = ilogb(mx) & ~1;
+    const double scale = ldexp(1.0, -ex);
+    if (me == 0 && threadIdx.x == 0) *rscale_out = ldexp(1.0, ex / 2);
+    float2 S[NQ];                                                         // columns (t NQ + k) C + me
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        const int c = (t * NQ + k) * C + me;
+        S[k] = (row_ok && c < d) ? df_from_double(Gm[(int64_t)c * d + i] * scale) : make_float2(0.f, 0.f);
+    }
+    float2 dg = row_ok ? df_from_double(Gm[(int64_t)i * d + i] * scale) : make_float2(0.f, 0.f);
+    bool active = row_ok;
+    for (int e = threadIdx.x; e < NCL * d; e += kClRows * T) F[e] = kUnwritten;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    cl_sync();                                       // every CTA's F is filled before any is read
+
+    // the warp's largest active diagonal entry (key, lowest index among equal keys) into buffer b
+    auto warp_pick = [&](int b) {
+        const unsigned long long k = active ? df_key(dg) : 0ull;
+        const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
+        const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+        const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+        const unsigned mi = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml && k != 0ull) ? (unsigned)i : 0xffffffffu);
+        if (lane == 0) red[b][wid] = make_uint4(ml, mh, mi, 0u);
+    };
+    // after the barrier: the block's pick (INT_MAX if no active row) and its diagonal entry; lane w of
+    // every warp reads warp w's result (one 16-byte load), three redux operations combine them
+    auto block_pick = [&](int b, float2& val) -> int {
+        const uint4 e = red[b][lane & 7];
+        const unsigned mh = __reduce_max_sync(0xffffffffu, e.y);
+        const unsigned ml = __reduce_max_sync(0xffffffffu, e.y == mh ? e.x : 0u);
+        const unsigned mi = __reduce_min_sync(0xffffffffu, (e.y == mh && e.x == ml) ? e.z : 0xffffffffu);
+        val = make_float2(key32_value(mh), key32_value(ml));
+        return (mh == 0u && ml == 0u) ? INT_MAX : (int)mi;
+    };
+    // entry i of column c's slot in the owner's F (shared::cluster address)
+    auto remote_entry = [&](int c) -> uint32_t {
+        return cl_mapa((uint32_t)__cvta_generic_to_shared(F + (size_t)(c / C) * d + i), (uint32_t)(c % C));
+    };
+    // this thread's copy of column c (held by thread t = (c / C) / NQ of the owner), or 0
+    auto own_value = [&](int c) -> float2 {
+        float2 v = make_float2(0.f, 0.f);
+        const int q = c / C;
+#pragma unroll
+        for (int k = 0; k < NQ; ++k)
+            if (t * NQ + k == q) v = S[k];
+        return v;
+    };
+
+    const int steps = forced ? min(forced_rank, min(m, d)) : min(m, d);
+    unsigned long long thr = 0;
+    int j = 0, p = -1;
+    float2 sp = make_float2(0.f, 0.f);
+    bool go = false;
+    if (steps > 0) {
+        const int f0 = forced ? forced[0] : -1;
+        if (forced) {
+            if (t == 0 && i == f0) s_next[0] = active ? dg : make_float2(0.f, 0.f);
+        } else if (t == 0) {
+            warp_pick(0);
+        }
+        __syncthreads();
+        if (forced) {
+            p = f0;
+            sp = (p >= 0 && p < d) ? s_next[0] : make_float2(0.f, 0.f);
+        } else {
+            p = block_pick(0, sp);
+        }
+        go = p >= 0 && p < d && sp.x > 0.f && sp.x < 3.0e38f;
+        if (go) thr = df_key(df_from_double(tau * tau * df_to_double(sp)));
+        go = go && (forced || df_key(sp) > thr);
+        // the thread holding the first pivot's column publishes it (unscaled)
+        if (go && p % C == me && (p / C) / NQ == t && active && i != p)
+            cl_st_local_u64((uint32_t)__cvta_generic_to_shared(F + (size_t)(p / C) * d + i), df_bits(own_value(p)));
+    }
+    float2 inv = go ? df_inv_sqrt(sp) : make_float2(0.f, 0.f);
+    for (; go && j < steps; ++j) {
+        const int b = j & 1;
+        // 1. (threads t = 0) entry i of the pivot column (own copy, or the owner's F), row j of R, the
+        //    diagonal; the other threads of the row take r_i from the row buffer after the barrier
+        float2 r = make_float2(0.f, 0.f);
+        const bool was_active = active;
+        if (t == 0 && active && i != p) {
+            float2 u;
+            const int q = p / C;
+            if (p % C == me && q / NQ == 0) {
+                u = own_value(p);
+            } else {
+                // the owner's F: this CTA's (where thread q / NQ of the row published it) or another's
+                const uint32_t a = p % C == me ? (uint32_t)__cvta_generic_to_shared(F + (size_t)q * d + i)
+                                               : remote_entry(p);
+                unsigned long long bits = cl_ld_u64(a);
+                if (bits == kUnwritten) {
+                    const uint64_t t0 = gtimer();
+                    for (uint32_t it = 0;; ++it) {
+                        bits = cl_ld_u64(a);
+                        if (bits != kUnwritten) break;
+                        if ((it & 15u) == 15u && (s_abort || gtimer() - t0 > kClusterWaitNs)) {
+                            if (!s_abort) atomicExch(status, kStatusClusterTimeout);
+                            s_abort = 1;
+                            break;
+                        }
+                    }
+                }
+                u = df_of_bits(bits);
+            }
+            r = df_mul(u, inv);
+            dg = df_sub_mul(dg, r, r);
+        }
+        if (i == p) active = false;
+        if (t == 0) {
+            if (row_ok) rb[b * d + i] = r;
+            if (j % C == me && was_active) Rdf[(int64_t)j * d + i] = i == p ? df_mul(sp, inv) : r;   // R_jj = sqrt(s_pp)
+            if (me == 0 && i == 0) piv[j] = p;
+        }
+        // 2. the next pivot (one barrier)
+        const int fn = forced ? (j + 1 < steps ? forced[j + 1] : -1) : -1;
+        if (forced) {
+            if (t == 0 && i == fn) s_next[b ^ 1] = active ? dg : make_float2(0.f, 0.f);
+        } else if (t == 0) {
+            warp_pick(b);
+        }
+        __syncthreads();
+        if (s_abort) break;
+        int pn;
+        float2 spn;
+        if (forced) {
+            pn = fn;
+            spn = (pn >= 0 && pn < d) ? s_next[b ^ 1] : make_float2(0.f, 0.f);
+        } else {
+            pn = block_pick(b, spn);
+        }
+        const bool go_on = j + 1 < steps && pn >= 0 && pn < d && spn.x > 0.f && spn.x < 3.0e38f &&
+                           (forced || df_key(spn) > thr);
+        const float2* rj = rb + (size_t)b * d;
+        if (t != 0 && row_ok) r = rj[i];
+        // 3. the thread holding the next pivot's column: that column first, published unscaled
+        int kn = -1;
+        if (go_on && pn % C == me && (pn / C) / NQ == t) {
+            kn = (pn / C) - t * NQ;
+            const float2 rc = rj[pn];
+            float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < NQ; ++k)
+                if (k == kn) {
+                    S[k] = df_sub_mul(S[k], r, rc);
+                    v = S[k];
+                }
+            if (active && i != pn)
+                cl_st_local_u64((uint32_t)__cvta_generic_to_shared(F + (size_t)(pn / C) * d + i), df_bits(v));
+        }
+        // 4. the other held columns
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const int c = (t * NQ + k) * C + me;
+            if (k != kn && c < d) S[k] = df_sub_mul(S[k], r, rj[c]);
+        }
+        if (!go_on) {
+            ++j;
+            break;
+        }
+        inv = df_inv_sqrt(spn);
+        sp = spn;
+        p = pn;
+    }
+    if (me == 0 && threadIdx.x == 0) *rank_out = j;
+    // no CTA leaves while another may still read its F
+    __syncthreads();
+    cl_sync();
+}
+
 // R (d x d) from the double-float rows k_pchol_grid wrote into the same bytes: (hi + lo) rscale.
 __global__ void k_df_to_fp64(double* __restrict__ R, const double* __restrict__ rscale, int64_t count) {
     const double sc = *rscale;
@@ -668,9 +922,73 @@ cudaError_t launch_gram_pivoted_cholesky(const float* Atilde, int64_t m, int64_t
     return launch_pivoted_cholesky(m, d, tau, forced, forced_rank, q, status, st);
 }
 
+// The cluster form for d <= 256: C CTAs of one cluster, NCL columns a CTA. Returns
+// cudaErrorNotSupported (nothing launched) when no such cluster can be resident on this GPU.
+template <int NCL, int T>
+cudaError_t launch_pchol_cluster(int C, int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,
+                                 const QrScratch& q, int32_t* status, cudaStream_t st) {
+    static std::atomic<int> resident[2][64] = {};         // per (C > 8, device): 1 yes, -1 no, 0 unknown
+    const size_t smem = sizeof(unsigned long long) * (size_t)NCL * d + sizeof(float2) * 2 * (size_t)d;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kClRows * T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    std::atomic<int>* known = dev >= 0 && dev < 64 ? &resident[C > 8 ? 1 : 0][dev] : nullptr;
+    if (known && known->load(std::memory_order_relaxed) < 0) return cudaErrorNotSupported;
+    if (C > 8 && (e = cudaFuncSetAttribute(k_pchol_cluster<NCL, T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+                     cudaSuccess) {
+        cudaGetLastError();
+        if (known) known->store(-1, std::memory_order_relaxed);
+        return cudaErrorNotSupported;
+    }
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_pchol_cluster<NCL, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
+    if (!known || known->load(std::memory_order_relaxed) == 0) {
+        int clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&clusters, k_pchol_cluster<NCL, T>, &cfg);
+        if (e != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            if (known) known->store(-1, std::memory_order_relaxed);
+            return cudaErrorNotSupported;
+        }
+        if (known) known->store(1, std::memory_order_relaxed);
+    }
+    const double* S = q.G;
+    float2* Rdf = reinterpret_cast<float2*>(q.Rorig);
+    double* rscale = q.norms;
+    e = cudaLaunchKernelEx(&cfg, k_pchol_cluster<NCL, T>, S, (int)d, (int)m, tau, forced, (int)forced_rank, Rdf, rscale,
+                           (int32_t*)q.piv, (int64_t*)q.rank, status);
+    if (e != cudaSuccess) return e;
+    k_df_to_fp64<<<152 * 2, 256, 0, st>>>(q.Rorig, q.norms, d * d);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,
                                     const QrScratch& q, int32_t* status, cudaStream_t st) {
     cudaError_t e;
+    // d <= 256: one cluster (16 columns a CTA: 8 CTAs up to d = 128, 16 above; 32 columns on 8 CTAs
+    // where a 16-CTA cluster cannot be resident)
+    if (d >= 1 && d <= 256) {
+        if (d <= 128)
+            e = launch_pchol_cluster<16, 2>(8, m, d, tau, forced, forced_rank, q, status, st);
+        else if ((e = launch_pchol_cluster<16, 2>(16, m, d, tau, forced, forced_rank, q, status, st)) ==
+                 cudaErrorNotSupported)
+            e = launch_pchol_cluster<32, 2>(8, m, d, tau, forced, forced_rank, q, status, st);
+        if (e != cudaErrorNotSupported) return e;
+    }
     // cooperative grid over the SMs (at most one CTA per SM), own columns in shared memory. Up to
     // d = 256 a step is bound by the latency of the published row, not by the FP64 work, so each
     // CTA takes three columns (ceil(d / 3) CTAs): a factorisation alone takes about 7% longer, and
