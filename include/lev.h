@@ -389,7 +389,10 @@ int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
  * device): with the environment variable LEV_FAULT set to "alloc" every scratch allocation that a
  * call needs reports failure (LEV_ENOMEM), to "launch" the launch of the pivoted QR reports failure
  * (LEV_ECUDA), to "timeout" the status read after a synchronisation reports an expired device wait
- * (LEV_ETIMEOUT). Unset, it costs one getenv per such point. */
+ * (LEV_ETIMEOUT), and to "pivwait" the pivoted Cholesky of the Gram route never publishes the pivot
+ * column of its second step: the other CTAs' bounded waits for it run out (about a second each), the
+ * kernel records the timeout in the status word and returns, and the call reports LEV_ETIMEOUT. Unset,
+ * it costs one getenv per such point. */
 
 /* Device-side status word of the handle: nonzero after a bounded wait gave up. */
 int lev_device_status(lev_handle* h, int32_t* status);

@@ -36,9 +36,12 @@ int fail(int code, const char* fmt, ...) {
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                    \
     } while (0)
 
-// Host-side fault injection for the tests of the error paths (nothing is injected on the device):
-// LEV_FAULT=alloc makes the next scratch allocation report failure, LEV_FAULT=launch the launch of
-// the pivoted QR, LEV_FAULT=timeout the read of the device status word after a synchronisation.
+// Fault injection for the tests of the error paths, chosen on the host: LEV_FAULT=alloc makes the
+// next scratch allocation report failure, LEV_FAULT=launch the launch of the pivoted QR,
+// LEV_FAULT=timeout the read of the device status word after a synchronisation, and
+// LEV_FAULT=pivwait has the pivoted Cholesky withhold one published pivot column, so that the
+// bounded waits for it run out on the device (no trap, no fault: the kernels record the timeout in
+// the status word and return).
 bool fault_is(const char* kind) {
     const char* f = getenv("LEV_FAULT");
     return f && strcmp(f, kind) == 0;
@@ -614,6 +617,7 @@ int handle_scratch(lev_handle* h, int which, size_t bytes, void** out) {
     return LEV_OK;
 }
 int handle_num_sms(lev_handle* h) { return h->num_sms; }
+bool fault_pivot_wait() { return fault_is("pivwait"); }
 const cudaEvent_t* handle_final_marks(lev_handle* h) {
     if (!h->timing) return nullptr;
     h->final_timed = true;

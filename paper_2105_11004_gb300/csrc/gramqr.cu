@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
                                                        const int32_t* __restrict__ forced, int forced_rank,
                                                        unsigned long long* __restrict__ U, float2* __restrict__ Rdf,
                                                        double* __restrict__ rscale_out, int32_t* __restrict__ piv,
-                                                       int64_t* __restrict__ rank_out, int32_t* status) {
+                                                       int64_t* __restrict__ rank_out, int32_t* status,
+                                                       int withhold) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int G = gridDim.x, me = blockIdx.x;
     const int ncl = (d - me + G - 1) / G;                        // columns me, me + G, ...
@@ -544,7 +545,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
                     col[i] = v;
                     if (i != pn) {
                         ubuf[i] = v;
-                        st_relaxed_gpu_u64(urow_n + i, df_bits(v));
+                        if (j + 1 != withhold) st_relaxed_gpu_u64(urow_n + i, df_bits(v));
                     }
                 }
         }
@@ -619,7 +620,8 @@ __global__ void __launch_bounds__(kClRows * T, 1) k_pchol_cluster(const double* 
                                                                   int forced_rank, float2* __restrict__ Rdf,
                                                                   double* __restrict__ rscale_out,
                                                                   int32_t* __restrict__ piv,
-                                                                  int64_t* __restrict__ rank_out, int32_t* status) {
+                                                                  int64_t* __restrict__ rank_out, int32_t* status,
+                                                                  int withhold) {
     constexpr int NQ = NCL / T;                                           // columns a thread holds
     static_assert(NQ * T == NCL, "columns split evenly over a row's threads");
     extern __shared__ __align__(16) uint8_t smem[];
@@ -792,7 +794,7 @@ __global__ void __launch_bounds__(kClRows * T, 1) k_pchol_cluster(const double* 
                     S[k] = df_sub_mul(S[k], r, rc);
                     v = S[k];
                 }
-            if (active && i != pn)
+            if (active && i != pn && j + 1 != withhold)
                 cl_st_local_u64((uint32_t)__cvta_generic_to_shared(F + (size_t)(pn / C) * d + i), df_bits(v));
         }
         // 4. the other held columns
@@ -969,8 +971,9 @@ cudaError_t launch_pchol_cluster(int C, int64_t m, int64_t d, double tau, const 
     const double* S = q.G;
     float2* Rdf = reinterpret_cast<float2*>(q.Rorig);
     double* rscale = q.norms;
+    const int withhold = fault_pivot_wait() ? 1 : -1;    // LEV_FAULT=pivwait: step 1's column is never published
     e = cudaLaunchKernelEx(&cfg, k_pchol_cluster<NCL, T>, S, (int)d, (int)m, tau, forced, (int)forced_rank, Rdf, rscale,
-                           (int32_t*)q.piv, (int64_t*)q.rank, status);
+                           (int32_t*)q.piv, (int64_t*)q.rank, status, withhold);
     if (e != cudaSuccess) return e;
     k_df_to_fp64<<<152 * 2, 256, 0, st>>>(q.Rorig, q.norms, d * d);
     return cudaGetLastError();
@@ -1012,7 +1015,8 @@ cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int3
     unsigned long long* U = reinterpret_cast<unsigned long long*>(q.U);
     float2* Rdf = reinterpret_cast<float2*>(q.Rorig);
     double* rscale = q.norms;                                    // unused by the Gram route otherwise
-    void* kargs[] = {&S, &di, &mi, &tau, &fp, &fr, &U, &Rdf, &rscale, (void*)&q.piv, (void*)&q.rank, &status};
+    int withhold = fault_pivot_wait() ? 1 : -1;          // LEV_FAULT=pivwait: step 1's column is never published
+    void* kargs[] = {&S, &di, &mi, &tau, &fp, &fr, &U, &Rdf, &rscale, (void*)&q.piv, (void*)&q.rank, &status, &withhold};
     e = cudaLaunchCooperativeKernel((const void*)k_pchol_grid, dim3((unsigned)pgrid), dim3(256), kargs, smem, st);
     if (e != cudaSuccess) return e;
     k_df_to_fp64<<<152 * 2, 256, 0, st>>>(q.Rorig, q.norms, d * d);

@@ -84,6 +84,8 @@ cudaError_t launch_heavy_rows(const int64_t* row_ptr, int64_t n, int64_t max_len
                               int32_t* idx, cudaStream_t st);
 cudaError_t launch_densify_rows(const int64_t* row_ptr, const int32_t* col, const float* val, const int32_t* idx,
                                 const unsigned long long* count, int64_t nh, int64_t d, float* H, cudaStream_t st);
+// LEV_FAULT=pivwait is set (api.cu): the pivoted Cholesky withholds the pivot column of step 1.
+bool fault_pivot_wait();
 // The grid pivoted Cholesky of q.G (rank test as lev_rrqr's with min(m, d) steps; forced pivots
 // optional): fills q.Rorig, q.piv, q.rank.
 cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int32_t* forced, int64_t forced_rank,

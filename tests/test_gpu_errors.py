@@ -1,10 +1,13 @@
-"""Error paths through the C ABI: failures injected on the host (LEV_FAULT), malformed CSR input.
+"""Error paths through the C ABI: failures injected on the host (LEV_FAULT), malformed CSR input,
+and a device wait that runs out.
 
-Nothing here faults the GPU or lets a wait expire on it: LEV_FAULT makes the library report a
-failed allocation, a failed launch or an expired device wait at its host-side checks, and the CSR
-check rejects malformed row pointers before any kernel reads the column or value arrays. After
-each error the same handle must serve a clean call whose result is bit-identical to that of a
-fresh handle, and the device status word must read 0.
+Nothing here faults the GPU: LEV_FAULT makes the library report a failed allocation, a failed
+launch or an expired device wait at its host-side checks, and the CSR check rejects malformed row
+pointers before any kernel reads the column or value arrays. LEV_FAULT=pivwait has the pivoted
+Cholesky withhold one published pivot column, so that the other CTAs' bounded waits for it (about
+a second) really run out on the device: the kernels record the timeout in the status word and
+return, with no trap. After each error the same handle must serve a clean call whose result is
+bit-identical to that of a fresh handle, and the device status word must read 0.
 """
 import numpy as np
 import pytest
@@ -102,3 +105,48 @@ def test_malformed_csr_is_rejected_before_any_kernel_reads_it(L, defect):
         assert L.lev_device_status(h) == 0
     finally:
         h.close()
+
+
+def _sketch(m, d, r, seed):
+    rs = np.random.default_rng(seed)
+    X = rs.standard_normal((m, r)) @ rs.standard_normal((r, d))
+    X *= np.exp(rs.standard_normal(d))[None, :]
+    return X.astype(np.float32)
+
+
+@pytest.mark.parametrize("m,d,r", [(192, 48, 40), (1024, 256, 200), (2048, 512, 450)])
+def test_device_wait_runs_out_then_clean_call(L, monkeypatch, m, d, r):
+    """The pivoted Cholesky of the Gram route (the cluster form up to d = 256, the grid form above)
+    never publishes its second pivot column: the waits for it expire on the device, the call reports
+    LEV_ETIMEOUT, and the handle then factors the same sketch exactly as a fresh handle does."""
+    import torch
+    At = to_dev(_sketch(m, d, r, seed=d))
+    tau = 1e-5
+
+    def rrqr(h):
+        perm = torch.empty(d, dtype=torch.int32, device="cuda")
+        R = torch.empty((d, d), dtype=torch.float64, device="cuda")
+        return L.lev_rrqr(h, At, tau, perm, R), perm, R
+
+    h0 = L.Handle(0)
+    try:
+        r0, p0, R0 = rrqr(h0)
+    finally:
+        h0.close()
+    assert r0 == r
+    h = L.Handle(0)
+    try:
+        monkeypatch.setenv("LEV_FAULT", "pivwait")
+        with pytest.raises(L.LevError) as e:
+            rrqr(h)
+        assert e.value.code == L.LEV_ETIMEOUT
+        assert "bounded device wait" in str(e.value)
+        monkeypatch.delenv("LEV_FAULT")
+        assert L.lev_device_status(h) == 0
+        r1, p1, R1 = rrqr(h)
+        assert r1 == r0
+        assert torch.equal(p1, p0) and torch.equal(R1, R0)
+        assert L.lev_device_status(h) == 0
+    finally:
+        h.close()
+
