@@ -15,6 +15,11 @@ Reverse mode, with W = diag(w):
          copyltu(X) = tril(X) + tril(X, -1)^T; Walter and Lehmann 2018);
   dg/dA_K = Z M^T + S^T G^T Xbar;  dg/dA = 0 on the columns outside K.
 
+With the SRHT after the CountSketch (Sec. 3.4.2, 4.1), A~_K = G F S A_K with
+F = sqrt(s/t) P H D (t x s) and G m x t, so the sketch term of the gradient is
+S^T F^T G^T Xbar, F^T = D H P^T / sqrt(t) (H the unnormalised Walsh-Hadamard
+matrix, symmetric; P^T scatters the t drawn rows, repeated draws adding up).
+
 In the identity-sketch mode with Omega = I the estimator equals the exact
 leverage theta, whose gradient has the closed form 2 (I - H) W (A^+)^T.
 """
@@ -24,7 +29,7 @@ import numpy as np
 from scipy.linalg import solve_triangular
 
 from . import rng
-from .estimator import count_sketch, gaussian_stage
+from .estimator import count_sketch, fwht, gaussian_stage, sketch
 from .linalg import pivoted_qr
 
 
@@ -32,12 +37,12 @@ def _copyltu(X: np.ndarray) -> np.ndarray:
     return np.tril(X) + np.tril(X, -1).T
 
 
-def theta_fixed(A, perm, r, s, m, k, seed, sketch_identity=False, omega_identity=False):
+def theta_fixed(A, perm, r, s, m, k, seed, sketch_identity=False, omega_identity=False, srht_t=0):
     """theta~(A) with P and r fixed (the function whose gradient is taken)."""
     A = np.asarray(A, dtype=np.float64)
     cols = np.asarray(perm[:r])
     AK = A[:, cols]
-    At = AK if sketch_identity else gaussian_stage(count_sketch(AK, s, seed), m, seed)
+    At = AK if sketch_identity else sketch(AK, s, m, seed, srht_t=srht_t)
     qr = pivoted_qr(At, 0.0, forced_perm=np.arange(r), forced_rank=r)
     R11 = qr.R[:, :r]
     Om = np.eye(r) if omega_identity else rng.omega(r, k, seed)
@@ -46,14 +51,22 @@ def theta_fixed(A, perm, r, s, m, k, seed, sketch_identity=False, omega_identity
     return np.sum(Y * Y, axis=1)
 
 
-def gradient(A, w, perm, r, s, m, k, seed, sketch_identity=False, omega_identity=False):
+def srht_adjoint(Tt: np.ndarray, s: int, seed: int) -> np.ndarray:
+    """F^T Tt (s x r) for Tt (t x r): D H P^T Tt / sqrt(t), the adjoint of estimator.srht."""
+    t = Tt.shape[0]
+    X = np.zeros((s,) + Tt.shape[1:])
+    np.add.at(X, rng.srht_rows(t, s, seed), Tt)
+    return rng.srht_signs(s, seed)[:, None] * fwht(X) / np.sqrt(t)
+
+
+def gradient(A, w, perm, r, s, m, k, seed, sketch_identity=False, omega_identity=False, srht_t=0):
     """dg/dA (n x d) for g = sum_i w_i theta~_i, FP64."""
     A = np.asarray(A, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64)
     n, d = A.shape
     cols = np.asarray(perm[:r])
     AK = A[:, cols]
-    At = AK if sketch_identity else gaussian_stage(count_sketch(AK, s, seed), m, seed)
+    At = AK if sketch_identity else sketch(AK, s, m, seed, srht_t=srht_t)
     qr = pivoted_qr(At, 0.0, forced_perm=np.arange(r), forced_rank=r)
     R11 = qr.R[:, :r]
     Q1 = qr.q_thin(r)
@@ -67,12 +80,16 @@ def gradient(A, w, perm, r, s, m, k, seed, sketch_identity=False, omega_identity
     if sketch_identity:
         T_rows = Xbar
     else:
-        # G^T Xbar (s x r), then S^T: row i takes sigma_i * (G^T Xbar)[h(i), :]
-        Gt = np.zeros((s, r))
+        # G^T Xbar (s x r, or t x r after an SRHT, then F^T), then S^T: row i takes
+        # sigma_i * (...)[h(i), :]
+        cg = srht_t if srht_t else s
+        Gt = np.zeros((cg, r))
         blk = 1 << 14
-        for c0 in range(0, s, blk):
-            c1 = min(s, c0 + blk)
-            Gt[c0:c1] = rng.gaussian_sketch_block(m, s, seed, c0, c1).T @ Xbar
+        for c0 in range(0, cg, blk):
+            c1 = min(cg, c0 + blk)
+            Gt[c0:c1] = rng.gaussian_sketch_block(m, cg, seed, c0, c1).T @ Xbar
+        if srht_t:
+            Gt = srht_adjoint(Gt, s, seed)
         b, sign = rng.bucket_and_sign(n, s, seed)
         T_rows = sign[:, None] * Gt[b]
     gK = Z @ M.T + T_rows
