@@ -373,7 +373,10 @@ int lev_estimate_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, 
  * Alg. 10 (QR adjoint with a zero Q cotangent): with Y = A_K M, Z = 2 W Y,
  * C = A_K^T Z, Rbar = -R_11^{-T} C M^T, Xbar = Q_1 copyltu(R_11 Rbar^T) R_11^{-T}
  * and T = G^T Xbar, row i of the gradient on the columns of K is
- * Z_i M^T + sigma_i T[h(i), :]; the columns outside K are 0. The n x k
+ * Z_i M^T + sigma_i T[h(i), :]; the columns outside K are 0. With
+ * LEV_SKETCH_SRHT in p->flags (the sketch G F S A), T = F^T G^T Xbar with
+ * F^T = D H P^T / sqrt(t): the t drawn rows scattered back (repeated draws
+ * added in draw order), the Walsh-Hadamard butterflies, the signs. The n x k
  * intermediate Y is recomputed in both passes, never stored.
  * The forward state is passed explicitly (all device pointers), as produced by
  * lev_sketch_dense / lev_rrqr / lev_omega_factor with the same p: Atilde

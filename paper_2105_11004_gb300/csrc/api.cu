@@ -1306,26 +1306,34 @@ int lev_backward_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int6
     if (!A || !Atilde || !perm || !d_rank || !R || !Mfull || !w || !gradA) return fail(LEV_EINVAL, "NULL array");
     if (lda < d) return fail(LEV_EINVAL, "lda < d");
     if (d > 256 || z.k > 256) return fail(LEV_EINVAL, "lev_backward_dense needs d <= 256 and k <= 256");
-    if (p->flags & LEV_SKETCH_SRHT) return fail(LEV_EINVAL, "lev_backward_dense has no adjoint of the SRHT sketch");
     LEV_TRY(check_prec(p->sketch_prec, "sketch"));
     cudaStream_t st = (cudaStream_t)stream;
     const bool identity = (p->flags & LEV_SKETCH_IDENTITY) != 0;
+    // with the SRHT after the CountSketch the forward's G is m x t
+    int64_t srht_t = 0;
+    if (!identity && (p->flags & LEV_SKETCH_SRHT)) {
+        srht_t = p->srht_t;
+        if ((z.s & (z.s - 1)) != 0 || z.s > (int64_t(1) << 24))
+            return fail(LEV_EINVAL, "LEV_SKETCH_SRHT needs s a power of two <= 2^24 (s = %lld)", (long long)z.s);
+        if (srht_t < 1 || srht_t > z.s) return fail(LEV_EINVAL, "LEV_SKETCH_SRHT needs 1 <= srht_t <= s");
+    }
+    const int64_t gcols = srht_t > 0 ? srht_t : z.s;
     const float* g32 = nullptr;
     const __nv_bfloat16* ghi = nullptr;
-    int64_t ldg = z.s;
+    int64_t ldg = gcols;
     if (!identity) {
         // the G image the forward's sketch used (cached in the handle)
         const int kind = p->sketch_prec == LEV_FP32 ? 0 : (p->sketch_prec == LEV_TF32 ? 3 : 2);
-        LEV_TRY(ensure_g(h, z.m, z.s, p->seed, kind, st, &g32, &ghi));
-        if (kind != 0) ldg = (z.s + 63) / 64 * 64;
+        LEV_TRY(ensure_g(h, z.m, gcols, p->seed, kind, st, &g32, &ghi));
+        if (kind != 0) ldg = (gcols + 63) / 64 * 64;
     }
     // the BF16 pair (kind 2) and the TF32 image (kind 3) hold the unscaled draws; the FP32 image is
     // N / sqrt(m)
     const float g_scale = (identity || p->sketch_prec == LEV_FP32) ? 1.f : (float)(1.0 / std::sqrt((double)z.m));
     const int chunks = lev::backward_chunks(n, d, z.k);
-    LEV_TRY(ensure(h->bwd, lev::backward_scratch_bytes(n, d, z.k, z.s, z.m, chunks)));
+    LEV_TRY(ensure(h->bwd, lev::backward_scratch_bytes(n, d, z.k, z.s, z.m, srht_t, chunks)));
     LEV_CUDA(lev::launch_backward_dense(A, lda, n, d, z.s, z.m, z.k, p->seed, Atilde, perm, d_rank, R, Mfull, w, g32,
-                                        ghi, ldg, g_scale, identity, h->bwd.ptr, chunks, gradA, st));
+                                        ghi, ldg, g_scale, identity, srht_t, h->bwd.ptr, chunks, gradA, st));
     return LEV_OK;
 }
 

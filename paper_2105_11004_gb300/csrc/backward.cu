@@ -421,7 +421,7 @@ int grid_cap(int64_t work, int block, int cap) {
 
 }  // namespace
 
-size_t backward_scratch_bytes(int64_t n, int64_t d, int64_t k, int64_t s, int64_t m, int chunks) {
+size_t backward_scratch_bytes(int64_t n, int64_t d, int64_t k, int64_t s, int64_t m, int64_t srht_t, int chunks) {
     size_t b = 0;
     b += sizeof(float) * (size_t)chunks * h_tiles((int)d) * HT * HT;   // H partials
     b += sizeof(double) * (size_t)d * d;            // H
@@ -430,7 +430,12 @@ size_t backward_scratch_bytes(int64_t n, int64_t d, int64_t k, int64_t s, int64_
     b += 2 * sizeof(double) * (size_t)d * d;        // CMt/Rbar, K/V/N
     b += sizeof(float) * (size_t)m * d;             // Xbar_full
     b += sizeof(float) * (size_t)s * d;             // T (unused in the identity-sketch mode)
-    return b + 10 * 256;
+    if (srht_t > 0) {
+        b += sizeof(float) * (size_t)srht_t * d;    // G^T Xbar before the SRHT adjoint
+        b += 2 * sizeof(int) * (size_t)(s + 1);     // draws per row of s, offsets
+        b += 2 * sizeof(uint32_t) * (size_t)srht_t; // draws ordered by row, then by draw
+    }
+    return b + 14 * 256;
 }
 
 int backward_chunks(int64_t n, int64_t d, int64_t /*k*/) {
@@ -446,7 +451,7 @@ cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_
                                   uint64_t seed, const float* Atilde, const int32_t* perm, const int64_t* d_rank,
                                   const double* R, const float* Mfull, const float* w, const float* G32,
                                   const __nv_bfloat16* Ghi, int64_t ldg, float g_scale, bool identity,
-                                  void* scratch, int chunks, float* gradA, cudaStream_t st) {
+                                  int64_t srht_t, void* scratch, int chunks, float* gradA, cudaStream_t st) {
     char* p = static_cast<char*>(scratch);
     auto take = [&](size_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return r; };
     const int ht = h_tiles((int)d);
@@ -460,6 +465,16 @@ cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_
     double* B2 = reinterpret_cast<double*>(take(sizeof(double) * (size_t)d * d));
     float* Xf = reinterpret_cast<float*>(take(sizeof(float) * (size_t)m * d));
     float* T = reinterpret_cast<float*>(take(sizeof(float) * (size_t)s * d));
+    float* Tt = nullptr;
+    int *cnt = nullptr, *off = nullptr;
+    uint32_t *tmp = nullptr, *ord = nullptr;
+    if (srht_t > 0) {
+        Tt = reinterpret_cast<float*>(take(sizeof(float) * (size_t)srht_t * d));
+        cnt = reinterpret_cast<int*>(take(sizeof(int) * (size_t)(s + 1)));
+        off = reinterpret_cast<int*>(take(sizeof(int) * (size_t)(s + 1)));
+        tmp = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)srht_t));
+        ord = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)srht_t));
+    }
     cudaError_t e;
     // pass 1: H = A^T W A, then C = 2 H Mfull and P = Mfull Mfull^T
     const int rows_per_chunk = (int)(((n + chunks - 1) / chunks + H_RB - 1) / H_RB * H_RB);
@@ -481,14 +496,20 @@ cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_
     k_trsm_r11<<<(unsigned)d, 32, 0, st>>>(R, d_rank, (int)d, B2, 1, d, 0, 1.0);
     if ((e = cudaMemsetAsync(Xf, 0, sizeof(float) * (size_t)m * d, st)) != cudaSuccess) return e;
     k_xbar<<<grid_cap(m * d, 256, 152 * 8), 256, 0, st>>>(Atilde, B2, perm, d_rank, (int)m, (int)d, Xf);
-    // T = G^T Xbar_full (G = I in the identity-sketch mode: T = Xbar_full)
-    dim3 gt((unsigned)((s + 63) / 64), (unsigned)((d + 63) / 64));
+    // T = G^T Xbar_full (G = I in the identity-sketch mode: T = Xbar_full); after an SRHT, G is m x t and
+    // T = F^T (G^T Xbar_full)
+    const int64_t cg = srht_t > 0 ? srht_t : s;     // columns of G
+    float* Tg = srht_t > 0 ? Tt : T;
+    dim3 gt((unsigned)((cg + 63) / 64), (unsigned)((d + 63) / 64));
     if (identity)
         T = Xf;
     else if (Ghi)
-        k_gt_x<true><<<gt, 256, 0, st>>>(nullptr, Ghi, ldg, (int)m, s, g_scale, Xf, (int)d, T);
+        k_gt_x<true><<<gt, 256, 0, st>>>(nullptr, Ghi, ldg, (int)m, cg, g_scale, Xf, (int)d, Tg);
     else
-        k_gt_x<false><<<gt, 256, 0, st>>>(G32, nullptr, ldg, (int)m, s, g_scale, Xf, (int)d, T);
+        k_gt_x<false><<<gt, 256, 0, st>>>(G32, nullptr, ldg, (int)m, cg, g_scale, Xf, (int)d, Tg);
+    if (!identity && srht_t > 0 &&
+        (e = launch_srht_adjoint(Tt, s, d, srht_t, seed, cnt, off, tmp, ord, T, st)) != cudaSuccess)
+        return e;
     // pass 2
     const size_t sm2 = sizeof(float) * ((size_t)P2_R * P2_AS + (size_t)P2_J * P2_C);
     if ((e = cudaFuncSetAttribute(k_bwd_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) != cudaSuccess)

@@ -62,6 +62,14 @@ struct QrScratch {
 // C (t x d) = F B with the SRHT F = sqrt(s/t) P H D (srht.cu); B (s x d, s a power of two) is
 // overwritten with H' D B, H' the unscaled Walsh-Hadamard matrix.
 cudaError_t launch_srht(float* B, int64_t s, int64_t d, int64_t t, uint64_t seed, float* C, cudaStream_t st);
+// X (s x d) = F^T Y for Y (t x d): D H' P^T Y / sqrt(t), the adjoint of launch_srht's F. The drawn rows of
+// each row of s are added in increasing draw order (bit-reproducible). count, off: s + 1 int each;
+// tmp, ord: t uint32 each.
+cudaError_t launch_srht_adjoint(const float* Y, int64_t s, int64_t d, int64_t t, uint64_t seed, int* count, int* off,
+                                uint32_t* tmp, uint32_t* ord, float* X, cudaStream_t st);
+// The exclusive scan and the per-segment rank sort of the bucket permutation (sketch.cu).
+cudaError_t launch_scan_offsets(const int* count, int* off, int64_t s, cudaStream_t st);
+cudaError_t launch_segment_sort(const int* off, int64_t s, const uint32_t* in, uint32_t* out, cudaStream_t st);
 
 // Gram route of the pivoted QR (gramqr.cu): G = A~^T A~ in FP64, then a
 // pivoted Cholesky on one cooperative grid; fills Rorig, piv and rank.
@@ -161,14 +169,16 @@ cudaError_t launch_omega_chol(const double* Omega, int64_t d, int64_t k, const Q
 cudaError_t launch_gen_omega(uint64_t seed, int64_t d, int64_t k, double* Omega, cudaStream_t st);
 
 // ---- backward.cu: gradient of sum_i w_i theta~_i ----
+// srht_t > 0: the sketch had the SRHT to srht_t rows after the CountSketch (G is m x srht_t and the
+// G image's columns are srht_t); 0: plain CountGauss.
 
 int backward_chunks(int64_t n, int64_t d, int64_t k);
-size_t backward_scratch_bytes(int64_t n, int64_t d, int64_t k, int64_t s, int64_t m, int chunks);
+size_t backward_scratch_bytes(int64_t n, int64_t d, int64_t k, int64_t s, int64_t m, int64_t srht_t, int chunks);
 cudaError_t launch_backward_dense(const float* A, int64_t lda, int64_t n, int64_t d, int64_t s, int64_t m, int64_t k,
                                   uint64_t seed, const float* Atilde, const int32_t* perm, const int64_t* d_rank,
                                   const double* R, const float* Mfull, const float* w, const float* G32,
                                   const __nv_bfloat16* Ghi, int64_t ldg, float g_scale, bool identity,
-                                  void* scratch, int chunks, float* gradA, cudaStream_t st);
+                                  int64_t srht_t, void* scratch, int chunks, float* gradA, cudaStream_t st);
 
 // ---- final.cu: fused final pass (SIMT) ----
 

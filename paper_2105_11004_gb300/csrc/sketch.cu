@@ -411,6 +411,16 @@ int grid_for(int64_t work, int block, int cap = 1 << 20) {
 
 }  // namespace
 
+cudaError_t launch_scan_offsets(const int* count, int* off, int64_t s, cudaStream_t st) {
+    k_scan_offsets<<<1, 1024, 0, st>>>(count, off, (int)s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segment_sort(const int* off, int64_t s, const uint32_t* in, uint32_t* out, cudaStream_t st) {
+    k_segment_sort<<<grid_for(s * 32, 256), 256, 0, st>>>(off, (int)s, in, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bucket_perm(int64_t n, int64_t s, uint64_t seed, int64_t row0, int* count, int* off,
                                uint32_t* tmp, uint32_t* perm, cudaStream_t st) {
     const uint64_t key = stream_key(seed, kStreamHash);

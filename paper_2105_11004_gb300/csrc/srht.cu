@@ -9,6 +9,8 @@
 // pass's stages couple (consecutive rows in the first pass, rows 2^9 apart in the second, ...)
 // for 32 columns in shared memory, so each pass reads and writes B once. A gather then scales the
 // t drawn rows by 1/sqrt(t) (= sqrt(s/t) / sqrt(s)).
+#include <algorithm>
+
 #include "lev_common.cuh"
 #include "lev_kernels.cuh"
 
@@ -92,6 +94,37 @@ __global__ void __launch_bounds__(256) k_fwht_pass(float* __restrict__ B, int64_
     }
 }
 
+// Row b of B times its sign D_b (the adjoint applies D after the butterflies).
+__global__ void k_row_signs(float* __restrict__ B, int64_t s, int d, uint64_t sign_key) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < s * d; e += (int64_t)gridDim.x * blockDim.x)
+        B[e] *= sign_of(splitmix64(sign_key, (uint64_t)(e / d)));
+}
+
+// Adjoint scatter, deterministic: count the draws per row of s, order each row's draws by q (counting
+// sort, then a rank sort within each row's segment), and sum them in that order.
+__global__ void k_srht_hist(int64_t t, uint32_t s, uint64_t rows_key, int* count) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < t; q += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&count[bucket_of(splitmix64(rows_key, (uint64_t)q), s)], 1);
+}
+__global__ void k_srht_scatter_q(int64_t t, uint32_t s, uint64_t rows_key, const int* off, int* cursor, uint32_t* out) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < t; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = bucket_of(splitmix64(rows_key, (uint64_t)q), s);
+        out[off[b] + atomicAdd(&cursor[b], 1)] = (uint32_t)q;
+    }
+}
+// X[b, :] = sum over the draws q of row b, in increasing q, of Y[q, :] / sqrt(t)
+__global__ void k_srht_gather_adj(const float* __restrict__ Y, const int* __restrict__ off,
+                                  const uint32_t* __restrict__ ord, int64_t s, int d, float inv_sqrt_t,
+                                  float* __restrict__ X) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < s * d; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / d;
+        const int c = (int)(e % d);
+        float acc = 0.f;
+        for (int f = off[b]; f < off[b + 1]; ++f) acc += Y[(int64_t)ord[f] * d + c];
+        X[e] = acc * inv_sqrt_t;
+    }
+}
+
 // C[q, :] = B[pi(q), :] / sqrt(t), pi(q) the q-th row draw.
 __global__ void k_srht_gather(const float* __restrict__ B, int64_t s, int d, int64_t t, uint64_t rows_key,
                               float inv_sqrt_t, float* __restrict__ C) {
@@ -105,11 +138,12 @@ __global__ void k_srht_gather(const float* __restrict__ B, int64_t s, int d, int
 
 }  // namespace
 
-cudaError_t launch_srht(float* B, int64_t s, int64_t d, int64_t t, uint64_t seed, float* C, cudaStream_t st) {
+// H' B in place (the unnormalised Walsh-Hadamard transform of the columns), with B first multiplied
+// by the signs D when sign_key is nonzero.
+static cudaError_t launch_fwht(float* B, int64_t s, int64_t d, uint64_t sign_key, bool apply_sign, cudaStream_t st) {
     int p = 0;
     while ((int64_t(1) << p) < s) ++p;
-    if ((int64_t(1) << p) != s || t < 1 || t > s || p > 24) return cudaErrorInvalidValue;   // groups fit grid.y
-    const uint64_t sign_key = stream_key(seed, kStreamSrhtSign), rows_key = stream_key(seed, kStreamSrhtRows);
+    if ((int64_t(1) << p) != s || p > 24) return cudaErrorInvalidValue;   // groups fit grid.y
     const size_t smem = sizeof(float) * ((size_t)1 << kSrhtMaxStages) * kSrhtCols;
     cudaError_t e = cudaFuncSetAttribute(k_fwht_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -120,13 +154,41 @@ cudaError_t launch_srht(float* B, int64_t s, int64_t d, int64_t t, uint64_t seed
         const int L = p - h0 < kSrhtMaxStages ? p - h0 : kSrhtMaxStages;
         const int64_t groups = s >> L;
         k_fwht_pass<<<dim3(tiles, (unsigned)groups), 256, sizeof(float) * ((size_t)1 << L) * kSrhtCols, st>>>(
-            B, s, (int)d, L, h0, sign_key, h0 == 0 ? 1 : 0, vec);
+            B, s, (int)d, L, h0, sign_key, (h0 == 0 && apply_sign) ? 1 : 0, vec);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         h0 += L;
     } while (h0 < p);
+    return cudaSuccess;
+}
+
+cudaError_t launch_srht(float* B, int64_t s, int64_t d, int64_t t, uint64_t seed, float* C, cudaStream_t st) {
+    if (t < 1 || t > s) return cudaErrorInvalidValue;
+    const uint64_t sign_key = stream_key(seed, kStreamSrhtSign), rows_key = stream_key(seed, kStreamSrhtRows);
+    cudaError_t e = launch_fwht(B, s, d, sign_key, true, st);
+    if (e != cudaSuccess) return e;
     int grid = (int)((t * d + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
     k_srht_gather<<<grid, 256, 0, st>>>(B, s, (int)d, t, rows_key, (float)(1.0 / sqrt((double)t)), C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_srht_adjoint(const float* Y, int64_t s, int64_t d, int64_t t, uint64_t seed, int* count, int* off,
+                                uint32_t* tmp, uint32_t* ord, float* X, cudaStream_t st) {
+    if (t < 1 || t > s || t > (int64_t(1) << 31)) return cudaErrorInvalidValue;
+    const uint64_t sign_key = stream_key(seed, kStreamSrhtSign), rows_key = stream_key(seed, kStreamSrhtRows);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(s + 1), st);
+    if (e != cudaSuccess) return e;
+    const int gq = (int)std::min<int64_t>((t + 255) / 256, 152 * 8);
+    k_srht_hist<<<gq, 256, 0, st>>>(t, (uint32_t)s, rows_key, count);
+    if ((e = launch_scan_offsets(count, off, s, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(s + 1), st)) != cudaSuccess) return e;
+    k_srht_scatter_q<<<gq, 256, 0, st>>>(t, (uint32_t)s, rows_key, off, count, tmp);
+    if ((e = launch_segment_sort(off, s, tmp, ord, st)) != cudaSuccess) return e;
+    const int gx = (int)std::min<int64_t>((s * d + 255) / 256, 152 * 16);
+    k_srht_gather_adj<<<gx, 256, 0, st>>>(Y, off, ord, s, (int)d, (float)(1.0 / sqrt((double)t)), X);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_fwht(X, s, d, 0, false, st)) != cudaSuccess) return e;
+    k_row_signs<<<gx, 256, 0, st>>>(X, s, (int)d, sign_key);
     return cudaGetLastError();
 }
 

@@ -122,3 +122,34 @@ def test_autograd_function(L, h):
     g_auto = to_np(A.grad).astype(np.float64)
     g_direct, perm, r, _ = _gpu_gradient(L, h, A32, w32, s=512, m=64, k=32, tau=1e-8, seed=4)
     assert np.array_equal(g_auto, g_direct)
+
+
+@pytest.mark.parametrize("sketch_prec,t", [("fp32", 64), ("bf16x3", 64), ("bf16x3", 256)])
+def test_backward_srht_matches_oracle(L, h, sketch_prec, t):
+    """The SRHT after the CountSketch (t = 256 = s draws many rows twice): the gradient against the
+    oracle's, whose SRHT adjoint D H P^T / sqrt(t) is pinned by <F B, Y> = <B, F^T Y> and finite
+    differences."""
+    A = W.dense_heavy_rows(500, 8, seed=3)
+    w = W.uniform_weights(500, seed=4)
+    cfg = dict(s=256, m=32, k=16, tau=1e-10, seed=7)
+    g, perm, r, _ = _gpu_gradient(L, h, A, w, sketch_prec=sketch_prec, srht_t=t, **cfg)
+    assert r == 8
+    ref = Bk.gradient(A.astype(np.float64), w.astype(np.float64), perm, r, 256, 32, 16, 7, srht_t=t)
+    assert _rel(g, ref) <= 1e-4
+
+
+def test_backward_srht_full_size_and_repeatable(L, h):
+    """The 200,000 x 64 backward workload with an SRHT to t = 2,048 rows: against the oracle, and two
+    runs bit-identical (the scatter of repeated draws adds in draw order)."""
+    cfg = W.CONFIGS["dense_2e5x64_backward"]
+    A = W.dense_heavy_rows(cfg["n"], cfg["d"], seed=cfg["data_seed"])
+    w = W.uniform_weights(cfg["n"], seed=cfg["weight_seed"])
+    kw = dict(s=cfg["s"], m=cfg["m"], k=cfg["k"], tau=cfg["tau"], seed=cfg["seed"], sketch_prec="bf16x3", srht_t=2048)
+    g, perm, r, _ = _gpu_gradient(L, h, A, w, **kw)
+    g2, _, _, _ = _gpu_gradient(L, h, A, w, **kw)
+    assert np.array_equal(g, g2)
+    assert r == 64
+    ref = Bk.gradient(A.astype(np.float64), w.astype(np.float64), perm, r, cfg["s"], cfg["m"], cfg["k"],
+                      cfg["seed"], srht_t=2048)
+    assert _rel(g, ref) <= 1e-3
+

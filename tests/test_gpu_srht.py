@@ -78,7 +78,8 @@ def test_srht_estimate_csr_matches_oracle(L, h):
     assert max_rel(to_np(theta), e.theta) <= 1e-4
 
 
-def test_srht_rejects_bad_sizes_and_backward(L, h):
+def test_srht_rejects_bad_sizes(L, h):
+    """s not a power of two, or t > s: the sketch and the backward reject them (LEV_EINVAL)."""
     import torch
     A = to_dev(W.dense_gaussian(500, 8, 0).astype(np.float32))
     At = torch.empty((32, 8), device="cuda")
@@ -89,7 +90,8 @@ def test_srht_rejects_bad_sizes_and_backward(L, h):
     p = L.make_params(s=1024, m=32, k=8, srht_t=256)
     _, st = L.forward_state(A, p, handle=h)
     g = torch.empty_like(A)
+    bad = L.make_params(s=1024, m=32, k=8, srht_t=2048)
     with pytest.raises(L.LevError) as e:
-        L.lev_backward_dense(h, A, p, st["Atilde"], st["perm"], st["d_rank"], st["R"], st["Mfull"],
+        L.lev_backward_dense(h, A, bad, st["Atilde"], st["perm"], st["d_rank"], st["R"], st["Mfull"],
                              torch.ones(500, device="cuda"), g)
     assert e.value.code == L.LEV_EINVAL
