@@ -391,8 +391,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     float2* rbuf = ubuf + d;                                      // d: row j of R
     float2* diag = rbuf + d;                                      // d: replicated Schur diagonal
     int* active = reinterpret_cast<int*>(diag + d);               // d
-    __shared__ unsigned long long red_k[8];
-    __shared__ int red_i[8];
+    __shared__ __align__(16) uint4 red4[8];                      // per warp: key lo, key hi, index
     __shared__ double red_d[8];
     __shared__ volatile int s_abort;
     __shared__ float2 s_inv;
@@ -421,7 +420,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     __syncthreads();
     // largest active diagonal entry, ties to the lowest index: per thread over its own indices,
     // per warp by three redux operations (max of the key's high and low words, min index among
-    // the maxima), one barrier, then every thread reduces the eight warp results itself
+    // the maxima), one barrier, then every warp reduces the eight warp results the same way
     auto pick = [&]() -> int {
         unsigned long long bk = 0;
         int bi = INT_MAX;
@@ -434,14 +433,14 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
         const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
         const unsigned mi = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? (unsigned)bi : 0xffffffffu);
-        if (lane == 0) { red_k[wid] = ((unsigned long long)mh << 32) | ml; red_i[wid] = (int)mi; }
+        if (lane == 0) red4[wid] = make_uint4(ml, mh, mi, 0u);
         __syncthreads();
-        bk = red_k[0];
-        bi = red_i[0];
-#pragma unroll
-        for (int w = 1; w < 8; ++w)
-            if (red_k[w] > bk || (red_k[w] == bk && red_i[w] < bi)) { bk = red_k[w]; bi = red_i[w]; }
-        return bk == 0 ? INT_MAX : bi;
+        // lane w reads warp w's result (one 16-byte load), three redux operations combine the eight
+        const uint4 e = red4[lane & 7];
+        const unsigned bh = __reduce_max_sync(0xffffffffu, e.y);
+        const unsigned bl = __reduce_max_sync(0xffffffffu, e.y == bh ? e.x : 0u);
+        const unsigned bm = __reduce_min_sync(0xffffffffu, (e.y == bh && e.x == bl) ? e.z : 0xffffffffu);
+        return (bh == 0u && bl == 0u) ? INT_MAX : (int)bm;
     };
     // rank test on the pivot's squared trailing norm: stop at a pivot that is not positive and
     // finite, or (unforced) at s_pp <= tau^2 s_00, compared through keys; the same in every thread
