@@ -296,7 +296,7 @@ __device__ __forceinline__ uint64_t gtimer() {
 // The owner writes row j of R (scaled, original column order) to Rorig off the
 // critical path; nothing reads Rorig before the kernel ends.
 constexpr unsigned long long kUnwritten = 0xFFF40000DEADBEEFull;
-constexpr int kRowsPerThread = 4;                  // d <= 1024 rows over 256 threads
+constexpr int kGridMaxD = 1024;                    // rows of the grid factorisation
 __device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -377,7 +377,8 @@ __device__ __forceinline__ void st_relaxed_gpu_u64(unsigned long long* p, unsign
 // double-float pairs into the bytes of Rorig, scaled by 2^(-e/2); k_df_to_fp64 turns them into
 // FP64 with rscale_out = 2^(e/2) afterwards. The published rows U hold the pairs' 8-byte patterns
 // (the "unwritten" sentinel has a NaN low part, which no pair has).
-__global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict__ Gm, int d, int m, double tau,
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_pchol_grid(const double* __restrict__ Gm, int d, int m, double tau,
                                                        const int32_t* __restrict__ forced, int forced_rank,
                                                        unsigned long long* __restrict__ U, float2* __restrict__ Rdf,
                                                        double* __restrict__ rscale_out, int32_t* __restrict__ piv,
@@ -391,28 +392,29 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     float2* rbuf = ubuf + d;                                      // d: row j of R
     float2* diag = rbuf + d;                                      // d: replicated Schur diagonal
     int* active = reinterpret_cast<int*>(diag + d);               // d
-    __shared__ __align__(16) uint4 red4[8];                      // per warp: key lo, key hi, index
-    __shared__ double red_d[8];
+    constexpr int NW = NT / 32, RPT = kGridMaxD / NT;           // warps; rows a thread
+    __shared__ __align__(16) uint4 red4[NW];                     // per warp: key lo, key hi, index
+    __shared__ double red_d[NW];
     __shared__ volatile int s_abort;
     __shared__ float2 s_inv;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // prescale 2^-e from the largest diagonal entry (the same in every CTA)
     double mx = 0.0;
-    for (int i = tid; i < d; i += 256) mx = fmax(mx, Gm[(int64_t)i * d + i]);
+    for (int i = tid; i < d; i += NT) mx = fmax(mx, Gm[(int64_t)i * d + i]);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) red_d[wid] = mx;
     __syncthreads();
     mx = red_d[0];
-    for (int w = 1; w < 8; ++w) mx = fmax(mx, red_d[w]);
+    for (int w = 1; w < NW; ++w) mx = fmax(mx, red_d[w]);
     int ex = 0;
     if (mx > 0.0 && mx < 1.0e300) ex = ilogb(mx) & ~1;
     const double scale = ldexp(1.0, -ex);
     if (me == 0 && tid == 0) *rscale_out = ldexp(1.0, ex / 2);
     for (int lc = 0; lc < ncl; ++lc) {
         const double* src = Gm + (int64_t)(lc * G + me) * d;     // column = row (symmetric)
-        for (int i = tid; i < d; i += 256) S[(size_t)lc * d + i] = df_from_double(src[i] * scale);
+        for (int i = tid; i < d; i += NT) S[(size_t)lc * d + i] = df_from_double(src[i] * scale);
     }
-    for (int i = tid; i < d; i += 256) {
+    for (int i = tid; i < d; i += NT) {
         active[i] = 1;
         diag[i] = df_from_double(Gm[(int64_t)i * d + i] * scale);
     }
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     auto pick = [&]() -> int {
         unsigned long long bk = 0;
         int bi = INT_MAX;
-        for (int i = tid; i < d; i += 256)
+        for (int i = tid; i < d; i += NT)
             if (active[i]) {
                 const unsigned long long k = df_key(diag[i]);
                 if (k > bk) { bk = k; bi = i; }                       // i increases: ties keep the lowest
@@ -435,8 +437,8 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         const unsigned mi = __reduce_min_sync(0xffffffffu, (hi == mh && lo == ml) ? (unsigned)bi : 0xffffffffu);
         if (lane == 0) red4[wid] = make_uint4(ml, mh, mi, 0u);
         __syncthreads();
-        // lane w reads warp w's result (one 16-byte load), three redux operations combine the eight
-        const uint4 e = red4[lane & 7];
+        // lane w reads warp w's result (one 16-byte load), three redux operations combine the NW
+        const uint4 e = red4[lane & (NW - 1)];
         const unsigned bh = __reduce_max_sync(0xffffffffu, e.y);
         const unsigned bl = __reduce_max_sync(0xffffffffu, e.y == bh ? e.x : 0u);
         const unsigned bm = __reduce_min_sync(0xffffffffu, (e.y == bh && e.x == bl) ? e.z : 0xffffffffu);
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
     if (go) {
         if (p % G == me) {
             const float2* col = S + (size_t)(p / G) * d;
-            for (int i = tid; i < d; i += 256)
+            for (int i = tid; i < d; i += NT)
                 if (i != p) {
                     ubuf[i] = col[i];
                     st_relaxed_gpu_u64(U + i, df_bits(col[i]));
@@ -477,17 +479,17 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         // 1. row j of R: unscaled entries (own copy or the published row, bounded spin), scaled,
         //    and the replicated diagonal updated, index by index
         const unsigned long long* urow = U + (int64_t)j * d;
-        // the published entries of this thread (at most kRowsPerThread), all loads issued before any
+        // the published entries of this thread (at most RPT), all loads issued before any
         // is waited on, so that they share one L2 round trip
-        unsigned long long first[kRowsPerThread];
+        unsigned long long first[RPT];
 #pragma unroll
-        for (int k = 0; k < kRowsPerThread; ++k) {
-            const int i = tid + 256 * k;
+        for (int k = 0; k < RPT; ++k) {
+            const int i = tid + NT * k;
             first[k] = (!owner && i < d && active[i] && i != p) ? ld_relaxed_gpu_u64(urow + i) : 0ull;
         }
 #pragma unroll
-        for (int k = 0; k < kRowsPerThread; ++k) {
-            const int i = tid + 256 * k;
+        for (int k = 0; k < RPT; ++k) {
+            const int i = tid + NT * k;
             if (i >= d) break;
             float2 r = make_float2(0.f, 0.f);
             if (active[i] && i != p) {
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
         }
         if (owner) {
             float2* row = Rdf + (int64_t)j * d;
-            for (int i = tid; i < d; i += 256)
+            for (int i = tid; i < d; i += NT)
                 if (i != p && active[i]) row[i] = rbuf[i];
             if (tid == 0) row[p] = df_mul(diag[p], inv);              // R_jj = s_pp / sqrt(s_pp)
         }
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
             float2* col = S + (size_t)(pn / G) * d;
             const float2 rc = rbuf[pn];
             unsigned long long* urow_n = U + (int64_t)(j + 1) * d;
-            for (int i = tid; i < d; i += 256)
+            for (int i = tid; i < d; i += NT)
                 if (active[i]) {
                     const float2 v = df_sub_mul(col[i], rbuf[i], rc);
                     col[i] = v;
@@ -556,7 +558,7 @@ __global__ void __launch_bounds__(256, 1) k_pchol_grid(const double* __restrict_
             if (c == pn || !active[c]) continue;
             const float2 rc = rbuf[c];
             float2* col = S + (size_t)lc * d;
-            for (int i = tid; i < d; i += 256)
+            for (int i = tid; i < d; i += NT)
                 if (active[i]) col[i] = df_sub_mul(col[i], rbuf[i], rc);
         }
         __syncthreads();
@@ -999,13 +1001,18 @@ cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int3
     int sms = 0, dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if (sms < 1 || d < 1 || d > 256 * kRowsPerThread) return cudaErrorInvalidValue;
+    if (sms < 1 || d < 1 || d > kGridMaxD) return cudaErrorInvalidValue;
     int pgrid = sms < (int)d ? sms : (int)d;
     if (d <= 256 && pgrid > (int)(d + 2) / 3) pgrid = (int)(d + 2) / 3;
     const size_t ncl = ((size_t)d + pgrid - 1) / pgrid;
     if (ncl > 32) return cudaErrorInvalidConfiguration;          // per-CTA bookkeeping holds 32 columns
     const size_t smem = sizeof(float2) * (ncl * d + 3 * (size_t)d) + sizeof(int) * (size_t)d + 64;
-    if ((e = cudaFuncSetAttribute(k_pchol_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    // one row of the sketch's Gram matrix a thread where d > 256 (512 or 1,024 threads): the Schur
+    // updates of a step are a chain of dependent FP32 operations per row, so more threads shorten it
+    const int nt = d <= 256 ? 256 : d <= 512 ? 512 : 1024;
+    const void* fn = nt == 256 ? (const void*)k_pchol_grid<256>
+                   : nt == 512 ? (const void*)k_pchol_grid<512> : (const void*)k_pchol_grid<1024>;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
     k_fill_unwritten<<<152 * 4, 256, 0, st>>>(reinterpret_cast<unsigned long long*>(q.U), d * d);
     const double* S = q.G;
@@ -1016,7 +1023,7 @@ cudaError_t launch_pivoted_cholesky(int64_t m, int64_t d, double tau, const int3
     double* rscale = q.norms;                                    // unused by the Gram route otherwise
     int withhold = fault_pivot_wait() ? 1 : -1;          // LEV_FAULT=pivwait: step 1's column is never published
     void* kargs[] = {&S, &di, &mi, &tau, &fp, &fr, &U, &Rdf, &rscale, (void*)&q.piv, (void*)&q.rank, &status, &withhold};
-    e = cudaLaunchCooperativeKernel((const void*)k_pchol_grid, dim3((unsigned)pgrid), dim3(256), kargs, smem, st);
+    e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)pgrid), dim3((unsigned)nt), kargs, smem, st);
     if (e != cudaSuccess) return e;
     k_df_to_fp64<<<152 * 2, 256, 0, st>>>(q.Rorig, q.norms, d * d);
     return cudaGetLastError();
