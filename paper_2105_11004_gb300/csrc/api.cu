@@ -400,6 +400,17 @@ int sketch_common_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int
         return LEV_OK;
     }
     LEV_TRY(bucket_perm(h, n, z.s, p->seed, z.row0, st));
+    // BF16 forms without the SRHT: the CountSketch writes the Gaussian stage's BF16 operand itself
+    // (no FP32 B, no transpose); the operand's values are those the transpose would produce
+    if (!(p->flags & LEV_SKETCH_SRHT) && (p->sketch_prec == LEV_BF16 || p->sketch_prec == LEV_BF16X3)) {
+        __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+        int64_t ld = 0;
+        LEV_TRY(lev::tc_gaussian_operand(h, z.s, d, p->sketch_prec, &hi, &lo, &ld));
+        const cudaError_t e = lev::launch_countsketch_dense_op(A, lda, d, z.s, ld, (const int*)h->off.ptr,
+                                                               (const uint32_t*)h->perm_rows.ptr, hi, lo, st);
+        if (e == cudaSuccess) return lev::tc_gaussian_stage_blocked(h, z.m, z.s, d, p->seed, p->sketch_prec, Atilde, st);
+        if (e != cudaErrorNotSupported) return fail(LEV_ECUDA, "CountSketch: %s", cudaGetErrorString(e));
+    }
     LEV_TRY(ensure(h->B, sizeof(float) * (size_t)z.s * d));
     LEV_CUDA(lev::launch_countsketch_dense(A, lda, d, z.s, (const int*)h->off.ptr,
                                            (const uint32_t*)h->perm_rows.ptr, (float*)h->B.ptr, st));

@@ -19,6 +19,14 @@ cudaError_t launch_bucket_perm(int64_t n, int64_t s, uint64_t seed, int64_t row0
 cudaError_t launch_countsketch_dense(const float* A, int64_t lda, int64_t d, int64_t s,
                                      const int* off, const uint32_t* perm, float* B, cudaStream_t st);
 
+// The same B = S A written as the K-major BF16 operand of the tensor-core Gaussian stage, blocked by
+// 64 buckets (img[g][c][k] = B[64 g + k][c], g < ld / 64, buckets s..ld zero): hi = bf16(B) and,
+// when lo is not null, lo = bf16(B - hi). cudaErrorNotSupported when A, lda or d do not allow
+// 16-byte loads, d > 1024, or ld is not a multiple of 64 at least s (the caller then writes B).
+cudaError_t launch_countsketch_dense_op(const float* A, int64_t lda, int64_t d, int64_t s, int64_t ld,
+                                        const int* off, const uint32_t* perm, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                        cudaStream_t st);
+
 // B (s x d, ld = d, FP32) = S A for CSR A.
 cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, const float* val,
                                    int64_t d, int64_t s, const int* off, const uint32_t* perm,

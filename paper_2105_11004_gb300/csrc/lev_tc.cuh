@@ -24,6 +24,15 @@ int handle_fail(int code, const char* msg);
 int tc_gaussian_stage(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d, uint64_t seed,
                       int32_t prec, float* Atilde, cudaStream_t st);
 
+// The K-major BF16 operand of the Gaussian stage blocked by 64 rows of B (img[g][c][k] =
+// B[64 g + k][c], K padded to ld = s rounded up to 64), in scratch slot 2: hi, and lo for
+// LEV_BF16X3 (null for LEV_BF16). LEV_EINVAL for the other precisions.
+int tc_gaussian_operand(lev_handle* h, int64_t s, int64_t d, int32_t prec, __nv_bfloat16** hi, __nv_bfloat16** lo,
+                        int64_t* ld);
+// A~ = G B with B already written as that operand (prec LEV_BF16 or LEV_BF16X3).
+int tc_gaussian_stage_blocked(lev_handle* h, int64_t m, int64_t s, int64_t d, uint64_t seed, int32_t prec,
+                              float* Atilde, cudaStream_t st);
+
 // theta = rowsum((A Mfull)^2) with prec in {LEV_TF32, LEV_BF16, LEV_BF16X3}.
 int tc_final_dense(lev_handle* h, const float* A, int64_t n, int64_t d, int64_t lda, const float* Mfull,
                    int64_t k, int32_t prec, float* theta, cudaStream_t st);

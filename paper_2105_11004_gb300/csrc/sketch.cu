@@ -162,6 +162,88 @@ __global__ void __launch_bounds__(256) k_countsketch_dense_v4(
     }
 }
 
+// The same sums, written as the K-major operand of the tensor-core Gaussian stage instead of B:
+// the BF16 image (and, split, the BF16 image of the remainder) of B^T, blocked by 64 buckets,
+//   img[g][c][k] = B[64 g + k][c]   (g < ld / 64, c < d, k < 64; buckets s..ld zero),
+// so that a 2-D tensor copy of 64 x rows over (ld / 64) d rows of 64 elements takes K block g of
+// rows c. A CTA takes eight consecutive buckets (one a warp, the loop of k_countsketch_dense_v4),
+// stages their rows in shared memory (two buffers, one barrier an octet), and thread c writes the
+// eight buckets of column c as one 16-byte piece per image. The rounding is the transpose
+// kernel's: hi = bf16(x), lo = bf16(x - hi), pairwise.
+template <int NC, int U, bool SPLIT>
+__global__ void __launch_bounds__(256) k_countsketch_dense_op(
+        const float* __restrict__ A, int64_t lda, int d, const int* __restrict__ off,
+        const uint32_t* __restrict__ perm, int s, int64_t ld, __nv_bfloat16* __restrict__ hi,
+        __nv_bfloat16* __restrict__ lo) {
+    extern __shared__ float4 stage4[];                           // [2][8][d / 4]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int dq = d >> 2;
+    const int noct = (int)(ld >> 3);
+    int buf = 0;
+    for (int o = blockIdx.x; o < noct; o += gridDim.x, buf ^= 1) {
+        const int b = 8 * o + w;
+        float4 acc[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (b < s) {
+            const int t0 = off[b], t1 = off[b + 1];
+            for (int t = t0; t < t1; t += U) {
+                float4 v[U][NC];
+                float sg[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool ok = (t + u) < t1;
+                    const uint32_t e = ok ? perm[t + u] : 0u;
+                    sg[u] = ok ? ((e & kSignBit) ? -1.f : 1.f) : 0.f;
+                    const float* row = A + (int64_t)(e & ~kSignBit) * lda;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const int col = c * 128 + lane * 4;
+                        v[u][c] = (ok && col < d) ? ld_stream_f4(row + col) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        acc[c].x = fmaf(sg[u], v[u][c].x, acc[c].x);
+                        acc[c].y = fmaf(sg[u], v[u][c].y, acc[c].y);
+                        acc[c].z = fmaf(sg[u], v[u][c].z, acc[c].z);
+                        acc[c].w = fmaf(sg[u], v[u][c].w, acc[c].w);
+                    }
+                }
+            }
+        }
+        float4* mine = stage4 + (size_t)(buf * 8 + w) * dq;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int q = c * 32 + lane;
+            if (q < dq) mine[q] = acc[c];
+        }
+        // the buffer written here was last read two octets ago, before the previous barrier
+        __syncthreads();
+        const float* rows = reinterpret_cast<const float*>(stage4 + (size_t)buf * 8 * dq);
+        const int64_t base = ((int64_t)(o >> 3) * d) * 64 + (o & 7) * 8;
+        for (int c = threadIdx.x; c < d; c += blockDim.x) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float x0 = rows[(2 * k) * d + c], x1 = rows[(2 * k + 1) * d + c];
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+                hw[k] = *reinterpret_cast<const uint32_t*>(&h2);
+                if constexpr (SPLIT) {
+                    const float2 hf = __bfloat1622float2(h2);
+                    const __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+                    lw[k] = *reinterpret_cast<const uint32_t*>(&l2);
+                }
+            }
+            const int64_t at = base + (int64_t)c * 64;
+            *reinterpret_cast<uint4*>(hi + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            if constexpr (SPLIT) *reinterpret_cast<uint4*>(lo + at) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+    }
+}
+
 // Any alignment: lane j holds columns j, j+32, ...; one column block at a time.
 __global__ void __launch_bounds__(256) k_countsketch_dense_scalar(
         const float* __restrict__ A, int64_t lda, int d, const int* __restrict__ off,
@@ -409,6 +491,27 @@ int grid_for(int64_t work, int block, int cap = 1 << 20) {
     return (int)g;
 }
 
+template <int NC, int U>
+cudaError_t launch_op(const float* A, int64_t lda, int d, int s, int64_t ld, const int* off, const uint32_t* perm,
+                      __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st) {
+    const size_t smem = sizeof(float) * 16 * (size_t)d;
+    const int64_t noct = ld / 8;
+    const int grid = (int)std::min<int64_t>(noct, 152 * 8);
+    cudaError_t e;
+    if (lo) {
+        if ((e = cudaFuncSetAttribute(k_countsketch_dense_op<NC, U, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        k_countsketch_dense_op<NC, U, true><<<grid, 256, smem, st>>>(A, lda, d, off, perm, s, ld, hi, lo);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_countsketch_dense_op<NC, U, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
+            return e;
+        k_countsketch_dense_op<NC, U, false><<<grid, 256, smem, st>>>(A, lda, d, off, perm, s, ld, hi, lo);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_scan_offsets(const int* count, int* off, int64_t s, cudaStream_t st) {
@@ -452,6 +555,20 @@ cudaError_t launch_countsketch_dense(const float* A, int64_t lda, int64_t d, int
     }
     return cudaGetLastError();
 }
+
+cudaError_t launch_countsketch_dense_op(const float* A, int64_t lda, int64_t d, int64_t s, int64_t ld,
+                                        const int* off, const uint32_t* perm, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                        cudaStream_t st) {
+    const bool vec = (reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda % 4 == 0) && (d % 4 == 0);
+    if (!vec || d < 4 || d > 1024 || ld % 64 != 0 || ld < s || (reinterpret_cast<uintptr_t>(hi) % 16) != 0 ||
+        (lo && reinterpret_cast<uintptr_t>(lo) % 16 != 0))
+        return cudaErrorNotSupported;
+    if (d <= 128) return launch_op<1, 8>(A, lda, (int)d, (int)s, ld, off, perm, hi, lo, st);
+    if (d <= 256) return launch_op<2, 4>(A, lda, (int)d, (int)s, ld, off, perm, hi, lo, st);
+    if (d <= 512) return launch_op<4, 2>(A, lda, (int)d, (int)s, ld, off, perm, hi, lo, st);
+    return launch_op<8, 1>(A, lda, (int)d, (int)s, ld, off, perm, hi, lo, st);
+}
+
 
 cudaError_t launch_countsketch_csr(const int64_t* row_ptr, const int32_t* col, const float* val,
                                    int64_t d, int64_t s, const int* off, const uint32_t* perm,

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(192, 1) k_gauss_tc(const __grid_constant__ CUt
                                                      const __grid_constant__ CUtensorMap tmB,
                                                      const __grid_constant__ CUtensorMap tmBlo, int m, int d, int nt,
                                                      int n_tiles, int stages, int kb_per_slice, int kb_total,
-                                                     float* __restrict__ P, int32_t* status) {
+                                                     int bd, float* __restrict__ P, int32_t* status) {
     using T = GTraits<F>;
     constexpr int NOPS = T::kSplit ? 2 : 1;               // hi (and lo) images of each operand
     const int A_BYTES = kRowsM * 128;                     // one image of this CTA's rows of G
@@ -159,10 +159,14 @@ __global__ void __launch_bounds__(192, 1) k_gauss_tc(const __grid_constant__ CUt
                 const uint32_t bar = smem_u32(&ctl->full[q]);
                 mbar_arrive_expect_tx(bar, (uint32_t)STAGE_BYTES);
                 const int x = (kb0 + i) * T::kKbe;
+                // B^T rows yb.. of K block kb0 + i: plain (d x ld) or blocked by K block (rows of
+                // 64 elements, block kb at rows kb d..; a box that runs past d takes rows of the next
+                // block, which only reach accumulator columns >= d, never stored)
+                const int xb = bd ? 0 : x, ybk = bd ? (kb0 + i) * bd + yb : yb;
                 tma_load_2d(sb, &tmG, x, yg, bar);
                 if constexpr (T::kSplit) tma_load_2d(sb + A_BYTES, &tmGlo, x, yg, bar);
-                tma_load_2d(sb + NOPS * A_BYTES, &tmB, x, yb, bar);
-                if constexpr (T::kSplit) tma_load_2d(sb + NOPS * A_BYTES + B_BYTES, &tmBlo, x, yb, bar);
+                tma_load_2d(sb + NOPS * A_BYTES, &tmB, xb, ybk, bar);
+                if constexpr (T::kSplit) tma_load_2d(sb + NOPS * A_BYTES + B_BYTES, &tmBlo, xb, ybk, bar);
                 ++issued;
                 if (++q == stages) { q = 0; phase ^= 1u; }
             }
@@ -350,6 +354,7 @@ int resident_pairs(size_t smem, cudaLaunchConfig_t cfg, int sms) {
     return pairs;
 }
 
+// B == nullptr: the operand is already in scratch slot 2, blocked by K block (tc_gaussian_operand).
 template <int F>
 int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d, uint64_t seed, float* Atilde,
                  cudaStream_t st) {
@@ -366,8 +371,12 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
     rc = handle_scratch(h, 2, bt_elems * T::kElem * (T::kSplit ? 2 : 1), &bt);
     if (rc != LEV_OK) return rc;
     void* bt_lo = T::kSplit ? static_cast<void*>(static_cast<uint8_t*>(bt) + bt_elems * T::kElem) : nullptr;
-    dim3 tg((unsigned)((ld + 63) / 64), (unsigned)((d + 31) / 32));
-    k_transpose_operand<F><<<tg, 256, 0, st>>>(B, s, (int)d, ld, bt, bt_lo);
+    const bool blocked = B == nullptr;
+    if (blocked && (T::kTf32 || T::kKbe != 64)) return handle_fail(LEV_EINVAL, "blocked operand needs a BF16 form");
+    if (!blocked) {
+        dim3 tg((unsigned)((ld + 63) / 64), (unsigned)((d + 31) / 32));
+        k_transpose_operand<F><<<tg, 256, 0, st>>>(B, s, (int)d, ld, bt, bt_lo);
+    }
     // tiles: a pair covers 256 rows of G and nt columns of B (nt a multiple of 16, each CTA nt / 2)
     const int nt_full = (int)std::min<int64_t>(kMaxNt, (d + 15) / 16 * 16);
     const int n_tiles = (int)((d + nt_full - 1) / nt_full);
@@ -413,11 +422,13 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
     if (rc != LEV_OK) return rc;
     CUtensorMap mG, mGlo, mB, mBlo;
     const void* gimg = T::kTf32 ? static_cast<const void*>(g32) : static_cast<const void*>(ghi);
+    // B^T: d rows of ld, or (blocked) ld / 64 d rows of 64
+    const int64_t b_rows = blocked ? (ld / 64) * d : d, b_cols = blocked ? 64 : ld;
     bool ok = make_map(&mG, gimg, T::kTf32, m, ld, ld, T::kKbe, kRowsM) &&
-              make_map(&mB, bt, T::kTf32, d, ld, ld, T::kKbe, nt / 2);
+              make_map(&mB, bt, T::kTf32, b_rows, b_cols, b_cols, T::kKbe, nt / 2);
     if (T::kSplit)
         ok = ok && make_map(&mGlo, ghi + (size_t)m * ld, false, m, ld, ld, T::kKbe, kRowsM) &&
-             make_map(&mBlo, bt_lo, false, d, ld, ld, T::kKbe, nt / 2);
+             make_map(&mBlo, bt_lo, false, b_rows, b_cols, b_cols, T::kKbe, nt / 2);
     else {
         mGlo = mG;
         mBlo = mB;
@@ -425,7 +436,7 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
     if (!ok) return handle_fail(LEV_ECUDA, "cuTensorMapEncodeTiled failed for the Gaussian stage");
     cfg.gridDim = dim3((unsigned)(2 * units), (unsigned)splits);
     e = cudaLaunchKernelEx(&cfg, k_gauss_tc<F>, mG, mGlo, mB, mBlo, (int)m, (int)d, nt, n_tiles, stages, kb_per_slice,
-                           kb_total, static_cast<float*>(part), handle_status(h));
+                           kb_total, blocked ? (int)d : 0, static_cast<float*>(part), handle_status(h));
     if (e != cudaSuccess) return handle_fail(LEV_ECUDA, cudaGetErrorString(e));
     k_gauss_reduce<<<152 * 4, 256, 0, st>>>(static_cast<const float*>(part), splits, (int)m, (int)d,
                                             (float)(1.0 / std::sqrt((double)m)), Atilde);
@@ -436,8 +447,33 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
 
 }  // namespace
 
+int tc_gaussian_operand(lev_handle* h, int64_t s, int64_t d, int32_t prec, __nv_bfloat16** hi, __nv_bfloat16** lo,
+                        int64_t* ld_out) {
+    if (prec != LEV_BF16 && prec != LEV_BF16X3) return handle_fail(LEV_EINVAL, "blocked operand needs a BF16 form");
+    const int64_t ld = (s + 63) / 64 * 64;
+    const size_t elems = (size_t)d * ld;
+    void* bt = nullptr;
+    // the same slot and size as run_gauss_tc asks for, so that the stage finds this buffer
+    const int rc = handle_scratch(h, 2, elems * 2 * (prec == LEV_BF16X3 ? 2 : 1), &bt);
+    if (rc != LEV_OK) return rc;
+    *hi = static_cast<__nv_bfloat16*>(bt);
+    *lo = prec == LEV_BF16X3 ? static_cast<__nv_bfloat16*>(bt) + elems : nullptr;
+    *ld_out = ld;
+    return LEV_OK;
+}
+
+int tc_gaussian_stage_blocked(lev_handle* h, int64_t m, int64_t s, int64_t d, uint64_t seed, int32_t prec,
+                              float* Atilde, cudaStream_t st) {
+    switch (prec) {
+        case LEV_BF16: return run_gauss_tc<gBF16>(h, nullptr, m, s, d, seed, Atilde, st);
+        case LEV_BF16X3: return run_gauss_tc<gBF16X3>(h, nullptr, m, s, d, seed, Atilde, st);
+        default: return handle_fail(LEV_EINVAL, "blocked operand needs a BF16 form");
+    }
+}
+
 int tc_gaussian_stage(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d, uint64_t seed, int32_t prec,
                       float* Atilde, cudaStream_t st) {
+    if (!B) return handle_fail(LEV_EINVAL, "null B for the Gaussian stage");
     switch (prec) {
         case LEV_BF16: return run_gauss_tc<gBF16>(h, B, m, s, d, seed, Atilde, st);
         case LEV_BF16X3: return run_gauss_tc<gBF16X3>(h, B, m, s, d, seed, Atilde, st);

@@ -129,6 +129,30 @@ def test_sketch_dense_strided_and_repeatable(L, h):
     assert np.max(np.abs(to_np(out1) - want)) <= 2e-5 * np.max(sketch_abs_scale(A.astype(np.float64), 512, 128, 9))
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("n,d,s,m", [(20000, 256, 2048, 1024), (777, 300, 5000, 300), (3000, 1000, 3000, 256),
+                                     (5000, 24, 1024, 96), (1, 4, 3, 8)])
+def test_sketch_operand_written_by_countsketch_is_the_transposed_one(L, h, prec, n, d, s, m):
+    """BF16 forms: the CountSketch writes the Gaussian stage's operand itself (blocked by 64
+    buckets) when A allows 16-byte loads; a view of A 4 bytes off that alignment takes the other
+    route (FP32 B, then the transpose kernel). Both round the same sums the same way, so A~ is
+    bit-identical."""
+    import torch
+    A = W.dense_gaussian(n, d, seed=n + d).astype(np.float32)
+    p = L.make_params(s=s, m=m, seed=5, sketch_prec=prec)
+    flat = torch.zeros(n * d + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = to_dev(A).reshape(-1)
+    off_view = flat[1:].view(n, d)                       # data pointer 4 bytes past a 16-byte boundary
+    assert off_view.data_ptr() % 16 != 0
+    out_fused = torch.full((m, d), float("nan"), device="cuda")
+    out_plain = torch.full((m, d), float("nan"), device="cuda")
+    L.lev_sketch_dense(h, to_dev(A), p, out_fused)
+    L.lev_sketch_dense(h, off_view, p, out_plain)
+    torch.cuda.synchronize()
+    assert torch.equal(out_fused, out_plain)
+    assert L.lev_device_status(h) == 0
+
+
 def test_sketch_csr_parity(L, h):
     import torch
     C = W.csr_uniform(6000, 200, nnz_per_row=5, heavy_frac=0.02, heavy_nnz=60, seed=4)
