@@ -575,13 +575,14 @@ __global__ void __launch_bounds__(NT, 1) k_pchol_grid(const double* __restrict__
 // with pivot p: thread i of an active row reads entry i of column p from the owner's array F (shared
 // memory; each column written once when it becomes a pivot, sentinel-filled before; a remote load
 // repeated, bounded, until it is not the sentinel), forms r_i = u_i / sqrt(s_pp) and the new
-// diagonal entry, and writes r_i to the CTA's row buffer and its warp's argmax to shared memory; one
-// block barrier, after which the row's other threads read r_i; every thread takes the next pivot from the eight warp results
-// (ties to the lowest index, the same in every CTA). The thread holding the next pivot's column
-// applies row j to it first and publishes it; every thread then applies row j to its other columns
-// while that column travels. A retired row or
-// column has r = 0, so its updates leave it unchanged and no per-column flags are needed. Same
-// arithmetic, outputs and stopping rule as k_pchol_grid.
+// diagonal entry, and writes r_i to the CTA's row buffer and its warp's argmax to shared memory;
+// one block barrier, after which the row's other threads read r_i; every thread takes the next
+// pivot from the eight warp results (ties to the lowest index, the same in every CTA). The thread
+// holding the next pivot's column applies row j to it first and publishes it; every thread then
+// applies row j to its other columns while that column travels, skipping the held columns that
+// were pivots (a warp's threads hold the same columns, so the skip is uniform). A retired row has
+// r = 0, so its updates leave it unchanged. Same arithmetic, outputs and stopping rule as
+// k_pchol_grid.
 constexpr int kClRows = 256;
 
 __device__ __forceinline__ uint32_t cl_rank() {
@@ -723,8 +724,10 @@ __global__ void __launch_bounds__(kClRows * T, 1) k_pchol_cluster(const double* 
             cl_st_local_u64((uint32_t)__cvta_generic_to_shared(F + (size_t)(p / C) * d + i), df_bits(own_value(p)));
     }
     float2 inv = go ? df_inv_sqrt(sp) : make_float2(0.f, 0.f);
+    unsigned retired = 0u;                            // held columns that were pivots (no longer read)
     for (; go && j < steps; ++j) {
         const int b = j & 1;
+        if (p % C == me && (p / C) / NQ == t) retired |= 1u << ((p / C) - t * NQ);
         // 1. (threads t = 0) entry i of the pivot column (own copy, or the owner's F), row j of R, the
         //    diagonal; the other threads of the row take r_i from the row buffer after the barrier
         float2 r = make_float2(0.f, 0.f);
@@ -798,11 +801,11 @@ __global__ void __launch_bounds__(kClRows * T, 1) k_pchol_cluster(const double* 
             if (active && i != pn && j + 1 != withhold)
                 cl_st_local_u64((uint32_t)__cvta_generic_to_shared(F + (size_t)(pn / C) * d + i), df_bits(v));
         }
-        // 4. the other held columns
+        // 4. the other held columns that are not yet pivots (the same for the whole warp)
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
             const int c = (t * NQ + k) * C + me;
-            if (k != kn && c < d) S[k] = df_sub_mul(S[k], r, rj[c]);
+            if (k != kn && c < d && !((retired >> k) & 1u)) S[k] = df_sub_mul(S[k], r, rj[c]);
         }
         if (!go_on) {
             ++j;

@@ -4,7 +4,8 @@
 //    (hash and sign of Sec. 3.4.3), rows ascending inside a bucket, so that the
 //    sums below run in a fixed order (bit-identical repeat runs);
 //  * CountSketch: one warp per bucket gathers its rows with 128-bit loads and
-//    writes the bucket row of B = S A once (no atomics);
+//    writes the bucket row of B = S A once (no atomics), or, for the BF16 forms
+//    of the Gaussian stage, writes B directly as that stage's K-major operand;
 //  * G: Box-Muller by counter, generated once per (seed, m, s) into a cache;
 //  * Gaussian stage A~ = G B: FP32 SIMT split-K GEMM with a fixed-order
 //    reduction of the split partials (tensor-core forms live in tc_sketch.cu).
@@ -495,8 +496,10 @@ template <int NC, int U>
 cudaError_t launch_op(const float* A, int64_t lda, int d, int s, int64_t ld, const int* off, const uint32_t* perm,
                       __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t st) {
     const size_t smem = sizeof(float) * 16 * (size_t)d;
+    // one octet a CTA: the block scheduler balances the buckets' lengths (a grid-stride loop over
+    // fewer CTAs left a tail of about 15%)
     const int64_t noct = ld / 8;
-    const int grid = (int)std::min<int64_t>(noct, 152 * 8);
+    const int grid = (int)noct;
     cudaError_t e;
     if (lo) {
         if ((e = cudaFuncSetAttribute(k_countsketch_dense_op<NC, U, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
