@@ -19,6 +19,7 @@
 
 #include <mutex>
 
+#include "df.cuh"
 #include "lev_common.cuh"
 #include "lev_kernels.cuh"
 #include "lev_tc.cuh"
@@ -311,50 +312,64 @@ __global__ void k_scaled_transpose(const double* __restrict__ R, const int64_t* 
     }
 }
 
-// M = R_11^{-1} Omega column by column, one CTA per column q and one thread per row i (r <= 1024):
-// with the unit-diagonal form x_i = w_i / R_ii - sum_{j > i} (R_ij / R_ii) x_j, step j (from the
-// bottom) publishes x_j through shared memory (double-buffered by step parity, one barrier per
-// step) and every thread i < j subtracts Rs[j][i] x_j. The coefficients of the next four steps
-// are loaded ahead. Row i of M goes to row perm[i] of Mfull.
+// The same coefficients as double-float pairs (the solve below runs in FP32 arithmetic only).
+__global__ void k_scaled_transpose_df(const double* __restrict__ R, const int64_t* __restrict__ d_rank, int d,
+                                      float2* __restrict__ Rs) {
+    const int r = (int)min(max(*d_rank, (int64_t)0), (int64_t)d);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)r * r;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / r), i = (int)(e % r);
+        if (i < j) Rs[(int64_t)j * d + i] = df_from_double(R[(int64_t)i * d + j] / R[(int64_t)i * d + i]);
+    }
+}
+
+// M = R_11^{-1} Omega column by column, one CTA per column q and one thread per row i (r <= 1024),
+// in double-float arithmetic (FP32 pairs, about 48 bits; FP64 runs at 1/64 of the FP32 rate on
+// GB300 and bound this solve at d = 1,024): with the unit-diagonal form
+// x_i = w_i / R_ii - sum_{j > i} (R_ij / R_ii) x_j, step j (from the bottom) publishes x_j through
+// shared memory (double-buffered by step parity, one barrier per step) and every thread i < j
+// subtracts Rs[j][i] x_j, so each row sees its updates in the order j = r-1, ..., i+1. The
+// coefficients of the next eight steps are loaded ahead. Row i of M goes to row perm[i] of Mfull,
+// rounded to FP32.
 // With the factor Lc of Omega's Gram matrix (upper U, row q holding column q of L = U^T) and
 // r < k, r <= *d_kc, the right-hand side is column q of L_r instead and the CTAs q >= r leave
 // their column 0.
-constexpr int OMEGA_PF = 4;
-__global__ void __launch_bounds__(1024) k_omega_solve(const double* __restrict__ R, const double* __restrict__ Rs,
+constexpr int OMEGA_PF = 8;
+__global__ void __launch_bounds__(1024) k_omega_solve(const double* __restrict__ R, const float2* __restrict__ Rs,
                                                       const double* __restrict__ Om, const double* __restrict__ Lc,
                                                       int kc, const int64_t* __restrict__ d_kc,
                                                       const int32_t* __restrict__ perm,
                                                       const int64_t* __restrict__ d_rank, int d, int k, int identity,
                                                       float* __restrict__ Mfull) {
-    __shared__ double xs[2];
+    __shared__ float2 xs[2];
     const int q = blockIdx.x, i = threadIdx.x;
     const int r = (int)min(max(*d_rank, (int64_t)0), (int64_t)d);
     const bool reduced = Lc != nullptr && !identity && r < k && r <= kc && (int64_t)r <= *d_kc;
     if (reduced && q >= r) return;                               // the whole CTA: Mfull column q stays 0
-    double x = 0.0;
+    float2 x = make_float2(0.f, 0.f);
     if (i < r) {
         const double w = identity ? (i == q ? 1.0 : 0.0)
                                   : (reduced ? Lc[(int64_t)q * kc + i] : Om[(int64_t)i * k + q]);
-        x = w / R[(int64_t)i * d + i];
+        x = df_from_double(w / R[(int64_t)i * d + i]);
     }
     // ring of coefficients: c[t] holds Rs[j - t][i] for the current step j
-    double c[OMEGA_PF];
+    float2 c[OMEGA_PF];
 #pragma unroll
     for (int t = 0; t < OMEGA_PF; ++t) {
         const int j = r - 1 - t;
-        c[t] = (j > i) ? Rs[(int64_t)j * d + i] : 0.0;
+        c[t] = (j > i) ? Rs[(int64_t)j * d + i] : make_float2(0.f, 0.f);
     }
     for (int j = r - 1; j >= 0; --j) {
-        const double cj = c[0];
+        const float2 cj = c[0];
 #pragma unroll
         for (int t = 0; t + 1 < OMEGA_PF; ++t) c[t] = c[t + 1];
         const int jn = j - OMEGA_PF;
-        c[OMEGA_PF - 1] = (jn > i) ? Rs[(int64_t)jn * d + i] : 0.0;
+        c[OMEGA_PF - 1] = (jn > i) ? Rs[(int64_t)jn * d + i] : make_float2(0.f, 0.f);
         if (i == j) xs[j & 1] = x;
         __syncthreads();
-        if (i < j) x = fma(-cj, xs[j & 1], x);
+        if (i < j) x = df_sub_mul(x, cj, xs[j & 1]);
     }
-    if (i < r) Mfull[(int64_t)perm[i] * k + q] = (float)x;
+    if (i < r) Mfull[(int64_t)perm[i] * k + q] = (float)df_to_double(x);
 }
 
 }  // namespace
@@ -482,9 +497,10 @@ cudaError_t launch_omega_factor(const double* R, const int32_t* perm, const int6
     if (d <= 1024 && Rs && (Omega || omega_identity)) {
         int grid = (int)((d * d + 255) / 256);
         if (grid > 152 * 8) grid = 152 * 8;
-        k_scaled_transpose<<<grid, 256, 0, st>>>(R, d_rank, (int)d, Rs);
+        float2* Rs2 = reinterpret_cast<float2*>(Rs);                // the same d x d bytes
+        k_scaled_transpose_df<<<grid, 256, 0, st>>>(R, d_rank, (int)d, Rs2);
         const int threads = (int)((d + 31) / 32 * 32);
-        k_omega_solve<<<(unsigned)k, threads, 0, st>>>(R, Rs, Omega, Lc && d_kc ? Lc : nullptr, (int)kc, d_kc,
+        k_omega_solve<<<(unsigned)k, threads, 0, st>>>(R, Rs2, Omega, Lc && d_kc ? Lc : nullptr, (int)kc, d_kc,
                                                        perm, d_rank, (int)d, (int)k, omega_identity ? 1 : 0, Mfull);
         return cudaGetLastError();
     }

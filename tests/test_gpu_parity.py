@@ -243,8 +243,9 @@ def test_omega_factor_parity(L, h, k, identity):
 
 @pytest.mark.parametrize("d,r,k", [(1024, 1000, 24), (1100, 1050, 8)])
 def test_omega_factor_wide(L, h, d, r, k):
-    """d = 1024 (the row-parallel solve at its 1024-thread limit) and d > 1024 (the one-warp-per-
-    column kernel): a synthetic upper-triangular R with a dominant diagonal, a random pivot order."""
+    """d = 1024 (the double-float solve with 32 rows a lane, its largest form) and d > 1024 (the
+    FP64 kernel that draws Omega itself): a synthetic upper-triangular R with a dominant diagonal,
+    a random pivot order."""
     import torch
     rs = np.random.default_rng(d)
     R = np.triu(rs.standard_normal((d, d)) * 0.05) + np.diag(1.0 + rs.random(d))
