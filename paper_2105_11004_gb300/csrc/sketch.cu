@@ -163,14 +163,39 @@ __global__ void __launch_bounds__(256) k_countsketch_dense_v4(
     }
 }
 
+// Octet o of buckets (rows: 8 x d FP32 in shared memory, bucket 8 o + w in row w) written into
+// the blocked K-major operand img[g][c][k] = B[64 g + k][c]: thread c writes the eight buckets of
+// column c as one 16-byte piece of hi (and of lo), rounded pairwise: hi = bf16(x), lo = bf16(x - hi).
+template <bool SPLIT>
+__device__ __forceinline__ void write_operand_octet(const float* rows, int d, int o, __nv_bfloat16* __restrict__ hi,
+                                                    __nv_bfloat16* __restrict__ lo) {
+    const int64_t base = ((int64_t)(o >> 3) * d) * 64 + (o & 7) * 8;
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float x0 = rows[(2 * k) * d + c], x1 = rows[(2 * k + 1) * d + c];
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+            hw[k] = *reinterpret_cast<const uint32_t*>(&h2);
+            if constexpr (SPLIT) {
+                const float2 hf = __bfloat1622float2(h2);
+                const __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+                lw[k] = *reinterpret_cast<const uint32_t*>(&l2);
+            }
+        }
+        const int64_t at = base + (int64_t)c * 64;
+        *reinterpret_cast<uint4*>(hi + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        if constexpr (SPLIT) *reinterpret_cast<uint4*>(lo + at) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+}
+
 // The same sums, written as the K-major operand of the tensor-core Gaussian stage instead of B:
 // the BF16 image (and, split, the BF16 image of the remainder) of B^T, blocked by 64 buckets,
 //   img[g][c][k] = B[64 g + k][c]   (g < ld / 64, c < d, k < 64; buckets s..ld zero),
 // so that a 2-D tensor copy of 64 x rows over (ld / 64) d rows of 64 elements takes K block g of
 // rows c. A CTA takes eight consecutive buckets (one a warp, the loop of k_countsketch_dense_v4),
-// stages their rows in shared memory (two buffers, one barrier an octet), and thread c writes the
-// eight buckets of column c as one 16-byte piece per image. The rounding is the transpose
-// kernel's: hi = bf16(x), lo = bf16(x - hi), pairwise.
+// stages their rows in shared memory (two buffers, one barrier an octet) and writes them with
+// write_operand_octet, whose rounding is the transpose kernel's.
 template <int NC, int U, bool SPLIT>
 __global__ void __launch_bounds__(256) k_countsketch_dense_op(
         const float* __restrict__ A, int64_t lda, int d, const int* __restrict__ off,
@@ -223,25 +248,7 @@ __global__ void __launch_bounds__(256) k_countsketch_dense_op(
         }
         // the buffer written here was last read two octets ago, before the previous barrier
         __syncthreads();
-        const float* rows = reinterpret_cast<const float*>(stage4 + (size_t)buf * 8 * dq);
-        const int64_t base = ((int64_t)(o >> 3) * d) * 64 + (o & 7) * 8;
-        for (int c = threadIdx.x; c < d; c += blockDim.x) {
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float x0 = rows[(2 * k) * d + c], x1 = rows[(2 * k + 1) * d + c];
-                const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-                hw[k] = *reinterpret_cast<const uint32_t*>(&h2);
-                if constexpr (SPLIT) {
-                    const float2 hf = __bfloat1622float2(h2);
-                    const __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-                    lw[k] = *reinterpret_cast<const uint32_t*>(&l2);
-                }
-            }
-            const int64_t at = base + (int64_t)c * 64;
-            *reinterpret_cast<uint4*>(hi + at) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            if constexpr (SPLIT) *reinterpret_cast<uint4*>(lo + at) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
+        write_operand_octet<SPLIT>(reinterpret_cast<const float*>(stage4 + (size_t)buf * 8 * dq), d, o, hi, lo);
     }
 }
 
@@ -285,6 +292,56 @@ __global__ void __launch_bounds__(256) k_countsketch_dense_scalar(
 // bucket overlap instead of running one row at a time; entries past the 32nd
 // of a row (the heavy rows) follow in that row's turn.
 constexpr int CS_PF = 8;
+// Bucket b added into the warp's zeroed accumulator row sacc (d floats).
+__device__ __forceinline__ void csr_bucket_sum(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                               const float* __restrict__ val, int d, const int* __restrict__ off,
+                                               const uint32_t* __restrict__ perm, int b, int lane, float* sacc) {
+    const int t0 = off[b], t1 = off[b + 1];
+    for (int tb = t0; tb < t1; tb += 32) {
+        const int nr = min(32, t1 - tb);
+        int64_t my_p0 = 0, my_p1 = 0;
+        float my_sg = 0.f;
+        if (lane < nr) {
+            const uint32_t e = perm[tb + lane];
+            const int64_t row = e & ~kSignBit;
+            my_sg = (e & kSignBit) ? -1.f : 1.f;
+            my_p0 = row_ptr[row];
+            my_p1 = row_ptr[row + 1];
+        }
+        for (int r0 = 0; r0 < nr; r0 += CS_PF) {
+            int cc[CS_PF];
+            float vv[CS_PF];
+#pragma unroll
+            for (int u = 0; u < CS_PF; ++u) {                // loads of CS_PF rows in flight together
+                const int r = r0 + u;
+                const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, r & 31);
+                const int64_t p1 = __shfl_sync(0xffffffffu, my_p1, r & 31);
+                cc[u] = -1;
+                vv[u] = 0.f;
+                if (r < nr && p0 + lane < p1) {
+                    cc[u] = col[p0 + lane];
+                    vv[u] = val[p0 + lane];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CS_PF; ++u) {                // rows added in order
+                const int r = r0 + u;
+                const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, r & 31);
+                const int64_t p1 = __shfl_sync(0xffffffffu, my_p1, r & 31);
+                const float sg = __shfl_sync(0xffffffffu, my_sg, r & 31);
+                if (r < nr) {
+                    if ((unsigned)cc[u] < (unsigned)d) atomicAdd(&sacc[cc[u]], sg * vv[u]);
+                    for (int64_t p = p0 + 32 + lane; p < p1; p += 32) {
+                        const int c = col[p];
+                        if ((unsigned)c < (unsigned)d) atomicAdd(&sacc[c], sg * val[p]);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128) k_countsketch_csr(
         const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
         const float* __restrict__ val, int d, const int* __restrict__ off,
@@ -298,55 +355,13 @@ __global__ void __launch_bounds__(128) k_countsketch_csr(
     for (int b = warp; b < s; b += nwarps) {
         for (int c = lane; c < d; c += 32) sacc[c] = 0.f;
         __syncwarp();
-        const int t0 = off[b], t1 = off[b + 1];
-        for (int tb = t0; tb < t1; tb += 32) {
-            const int nr = min(32, t1 - tb);
-            int64_t my_p0 = 0, my_p1 = 0;
-            float my_sg = 0.f;
-            if (lane < nr) {
-                const uint32_t e = perm[tb + lane];
-                const int64_t row = e & ~kSignBit;
-                my_sg = (e & kSignBit) ? -1.f : 1.f;
-                my_p0 = row_ptr[row];
-                my_p1 = row_ptr[row + 1];
-            }
-            for (int r0 = 0; r0 < nr; r0 += CS_PF) {
-                int cc[CS_PF];
-                float vv[CS_PF];
-#pragma unroll
-                for (int u = 0; u < CS_PF; ++u) {            // loads of CS_PF rows in flight together
-                    const int r = r0 + u;
-                    const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, r & 31);
-                    const int64_t p1 = __shfl_sync(0xffffffffu, my_p1, r & 31);
-                    cc[u] = -1;
-                    vv[u] = 0.f;
-                    if (r < nr && p0 + lane < p1) {
-                        cc[u] = col[p0 + lane];
-                        vv[u] = val[p0 + lane];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < CS_PF; ++u) {            // rows added in order
-                    const int r = r0 + u;
-                    const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, r & 31);
-                    const int64_t p1 = __shfl_sync(0xffffffffu, my_p1, r & 31);
-                    const float sg = __shfl_sync(0xffffffffu, my_sg, r & 31);
-                    if (r < nr) {
-                        if ((unsigned)cc[u] < (unsigned)d) atomicAdd(&sacc[cc[u]], sg * vv[u]);
-                        for (int64_t p = p0 + 32 + lane; p < p1; p += 32) {
-                            const int c = col[p];
-                            if ((unsigned)c < (unsigned)d) atomicAdd(&sacc[c], sg * val[p]);
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
-        }
+        csr_bucket_sum(row_ptr, col, val, d, off, perm, b, lane, sacc);
         float* out = B + (int64_t)b * d;
         for (int c = lane; c < d; c += 32) out[c] = sacc[c];
         __syncwarp();
     }
 }
+
 
 // G (m x s) by counter into an image with leading dimension ld (columns s..ld are 0). G[j, b] =
 // N_{j s + b} / sqrt(m), N the Box-Muller draw of stream 2 evaluated in FP32 (box_muller_f32: a

@@ -166,6 +166,32 @@ def test_sketch_csr_parity(L, h):
     assert np.all(np.abs(to_np(At) - want) <= 2e-5 * scale + 1e-30)
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("n,d,s,m,heavy", [(6000, 200, 1500, 400, 60), (3000, 1024, 2000, 256, 300),
+                                           (50, 8, 3, 8, 8)])
+def test_sketch_csr_operand_matches_dense_of_the_same_matrix(L, h, prec, n, d, s, m, heavy):
+    """BF16 forms: the dense CountSketch writes the Gaussian stage's operand itself, the CSR one
+    writes FP32 B for the transpose kernel. A bucket's sum runs over the same rows in the same order
+    on both paths, and each entry adds sign x value once (the dense kernel's zeros leave its sums
+    unchanged), and both round B to the operand the same way, so the CSR sketch equals the dense
+    sketch of the densified matrix bit for bit; and both are within the form's bound of the
+    oracle."""
+    import torch
+    C = W.csr_uniform(n, d, nnz_per_row=5, heavy_frac=0.02, heavy_nnz=heavy, seed=n + d)
+    p = L.make_params(s=s, m=m, seed=6, sketch_prec=prec)
+    dense = C.to_dense()
+    out_csr = torch.full((m, d), float("nan"), device="cuda")
+    out_dense = torch.full((m, d), float("nan"), device="cuda")
+    L.lev_sketch_csr(h, to_dev(C.row_ptr), to_dev(C.col), to_dev(C.val), n, d, p, out_csr)
+    L.lev_sketch_dense(h, to_dev(dense.astype(np.float32)), p, out_dense)
+    torch.cuda.synchronize()
+    assert torch.equal(out_csr, out_dense)
+    want = E.sketch(dense, s, m, 6)
+    scale = sketch_abs_scale(dense, s, m, 6)
+    assert np.all(np.abs(to_np(out_csr) - want) <= SKETCH_TC_TOL[prec] * scale + 1e-30)
+    assert L.lev_device_status(h) == 0
+
+
 # ---------------------------------------------------------------- rrqr + omega
 
 def _rank_deficient_sketch(m, d, r, seed):
