@@ -428,11 +428,13 @@ def main():
     setup["what"] = (f"G ({cfg['m']} x {cfg['s']}, BF16 hi + lo pair of the FP32 draws), the CountSketch bucket "
                      f"permutation ({n} rows) and Omega ({d} x {cfg['k']}) for a new seed (lev_prepare)")
     # kernels of one lev_estimate_dense step with the bucket permutation, G and Omega cached:
-    # CountSketch, then the Gaussian stage (split-K SGEMM + reduce, or operand transpose + tcgen05
-    # GEMM + reduce), Gram + reduce + row fill + pivoted Cholesky + two assembly kernels, the scaled
-    # transpose and the solve of the omega factor, and the final pass (plus its operand packing)
-    kernels_per_step = (1 + (2 if args.sketch_prec == "fp32" else 3) + 6 + 2
-                        + (1 if args.final_prec == "fp32" else 2))
+    # CountSketch (FP32 B, or for the BF16 forms the Gaussian stage's operand itself), the Gaussian
+    # stage (split-K SGEMM or tcgen05 GEMM) and its reduction; Gram + reduce + pivoted Cholesky (one
+    # cluster at d <= 256) + the FP64 conversion of R + two assembly kernels; the coefficient split
+    # and the solve of the right factor; the final pass (tensor-core forms: plus its width and
+    # operand packing kernels)
+    kernels_per_step = (3 + (1 if args.sketch_prec == "tf32" else 0) + 6 + 2
+                        + (1 if args.final_prec == "fp32" else 3))
 
     rank_found = L.lev_estimate_dense(h, A, p, theta)          # also generates and caches G
     # S batches in flight: handle i and stream i take steps i, i + S, ... (each handle holds its own
