@@ -637,7 +637,11 @@ def main():
 
     rooflines = {"final": final_roof(args.final_prec)}
     sk_bytes = n * d * 4 + cfg["s"] * d * 4
-    rooflines["sketch"] = {"kernels": "k_countsketch_dense_v4 + k_gauss_tc + permutation", "bound": "mixed",
+    sk_kernels = {"bf16x3": "k_countsketch_dense_op (writes the operand) + k_gauss_tc + k_gauss_reduce",
+                  "bf16": "k_countsketch_dense_op (writes the operand) + k_gauss_tc + k_gauss_reduce",
+                  "tf32": "k_countsketch_dense_v4 + k_transpose_operand + k_gauss_tc + k_gauss_reduce",
+                  "fp32": "k_countsketch_dense_v4 + split-K SGEMM + reduction"}[args.sketch_prec]
+    rooflines["sketch"] = {"kernels": sk_kernels, "bound": "mixed",
                            "ms": stages["sketch"],
                            "countsketch_bytes": sk_bytes, "gemm_flops": 2.0 * cfg["m"] * cfg["s"] * d}
     qf = qr_flops(cfg["m"], d, r)
