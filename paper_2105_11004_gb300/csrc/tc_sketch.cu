@@ -328,6 +328,66 @@ __global__ void k_transpose_operand(const float* __restrict__ B, int64_t s, int 
     }
 }
 
+// B (s x d FP32 row-major) -> the blocked K-major BF16 operand img[g][c][k] = B[64 g + k][c]
+// (rows s..ld zero): hi, and lo = bf16(x - hi) when SPLIT, rounded pairwise as above. A tile is one
+// K block g by 64 columns, whose image rows are 64 consecutive 128-byte rows: read as 16-byte
+// pieces of rows of B, written as 8 KB runs per image (four threads a 128-byte row).
+template <bool SPLIT>
+__global__ void __launch_bounds__(256) k_transpose_blocked(const float* __restrict__ B, int64_t s, int d,
+                                                           __nv_bfloat16* __restrict__ hi,
+                                                           __nv_bfloat16* __restrict__ lo) {
+    __shared__ float tile[64][65];
+    const int g = blockIdx.x, c0 = blockIdx.y * 64;
+    const int64_t k0 = (int64_t)g * 64;
+    const bool vec = (d & 3) == 0;                               // rows of B start on 16-byte boundaries
+    const int cq = (threadIdx.x & 15) * 4;
+    for (int r = threadIdx.x >> 4; r < 64; r += 16) {
+        const int64_t k = k0 + r;
+        const int c = c0 + cq;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < s) {
+            const float* row = B + k * d;
+            if (vec && c < d) {
+                v = *reinterpret_cast<const float4*>(row + c);
+            } else {
+                v.x = c < d ? row[c] : 0.f;
+                v.y = c + 1 < d ? row[c + 1] : 0.f;
+                v.z = c + 2 < d ? row[c + 2] : 0.f;
+                v.w = c + 3 < d ? row[c + 3] : 0.f;
+            }
+        }
+        tile[r][cq] = v.x;
+        tile[r][cq + 1] = v.y;
+        tile[r][cq + 2] = v.z;
+        tile[r][cq + 3] = v.w;
+    }
+    __syncthreads();
+    const int cc = threadIdx.x >> 2, q = threadIdx.x & 3;         // column, quarter of the K block
+    const int c = c0 + cc;
+    if (c >= d) return;
+    uint32_t hw[8], lw[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const float x0 = tile[q * 16 + 2 * p][cc], x1 = tile[q * 16 + 2 * p + 1][cc];
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+        hw[p] = *reinterpret_cast<const uint32_t*>(&h2);
+        if constexpr (SPLIT) {
+            const float2 hf = __bfloat1622float2(h2);
+            const __nv_bfloat162 l2 = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+            lw[p] = *reinterpret_cast<const uint32_t*>(&l2);
+        }
+    }
+    const int64_t at = ((int64_t)g * d + c) * 64 + q * 16;
+    uint4* dh = reinterpret_cast<uint4*>(hi + at);
+    dh[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    dh[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+    if constexpr (SPLIT) {
+        uint4* dl = reinterpret_cast<uint4*>(lo + at);
+        dl[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        dl[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+    }
+}
+
 // Row-major matrix rows x cols (elements) with leading dimension ld, box (box_cols x box_rows).
 bool make_map(CUtensorMap* map, const void* ptr, bool tf32, int64_t rows, int64_t cols, int64_t ld, int box_cols,
               int box_rows) {
@@ -354,7 +414,8 @@ int resident_pairs(size_t smem, cudaLaunchConfig_t cfg, int sms) {
     return pairs;
 }
 
-// B == nullptr: the operand is already in scratch slot 2, blocked by K block (tc_gaussian_operand).
+// B == nullptr: the operand is already in scratch slot 2, blocked by K block (tc_gaussian_operand);
+// otherwise it is made here from the FP32 B.
 template <int F>
 int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d, uint64_t seed, float* Atilde,
                  cudaStream_t st) {
@@ -371,9 +432,15 @@ int run_gauss_tc(lev_handle* h, const float* B, int64_t m, int64_t s, int64_t d,
     rc = handle_scratch(h, 2, bt_elems * T::kElem * (T::kSplit ? 2 : 1), &bt);
     if (rc != LEV_OK) return rc;
     void* bt_lo = T::kSplit ? static_cast<void*>(static_cast<uint8_t*>(bt) + bt_elems * T::kElem) : nullptr;
-    const bool blocked = B == nullptr;
-    if (blocked && (T::kTf32 || T::kKbe != 64)) return handle_fail(LEV_EINVAL, "blocked operand needs a BF16 form");
-    if (!blocked) {
+    // BF16 forms: B^T blocked by K block (written by the CountSketch, B == nullptr, or here); TF32:
+    // plain d x ld
+    const bool blocked = !T::kTf32;
+    if (!B && !blocked) return handle_fail(LEV_EINVAL, "blocked operand needs a BF16 form");
+    if (B && blocked) {
+        dim3 tg((unsigned)(ld / 64), (unsigned)((d + 63) / 64));
+        k_transpose_blocked<T::kSplit><<<tg, 256, 0, st>>>(B, s, (int)d, static_cast<__nv_bfloat16*>(bt),
+                                                           static_cast<__nv_bfloat16*>(bt_lo));
+    } else if (B) {
         dim3 tg((unsigned)((ld + 63) / 64), (unsigned)((d + 31) / 32));
         k_transpose_operand<F><<<tg, 256, 0, st>>>(B, s, (int)d, ld, bt, bt_lo);
     }
