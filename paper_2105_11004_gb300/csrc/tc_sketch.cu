@@ -7,8 +7,11 @@
 // CTA issues M = 256 MMAs for the pair; each CTA's TMEM receives its own 128 rows of the
 // accumulator with all the tile's columns. The pair accumulates its 256 x NT block over its slice
 // of s and writes the FP32 partial (row-major, one slice after another); a second kernel adds the
-// partials of the slices in a fixed order. Operands are K-major (rows of G; rows of B^T, produced
-// by a transpose kernel), loaded by 2-D tensor TMA with the 128-byte swizzle into a ring of stages:
+// partials of the slices in a fixed order. Operands are K-major: rows of G, and rows of B^T. For
+// the BF16 forms B^T is blocked by K block (K block g of rows c.. is a run of 128-byte rows at row
+// g d + c), written by the dense CountSketch itself or by k_transpose_blocked from the FP32 B; for
+// TF32 it is d x ld from k_transpose_operand. Both are loaded by 2-D tensor TMA with the 128-byte
+// swizzle into a ring of stages:
 //   warp 0: TMA producer (one thread); warp 1: TMEM allocation, and in the even CTA the MMA issuer
 //   (one thread), in the odd CTA the relay that reports each landed stage to the even CTA;
 //   warps 2..5: epilogue (tcgen05.ld, partial stores).
