@@ -230,43 +230,60 @@ __device__ __forceinline__ void round_half_row(const HalfRow<F>& v, HalfWords<F>
 }
 
 // Sum of the squares of `cols` (a multiple of 16) consecutive accumulator columns of this thread's
-// TMEM lane from taddr on: two 32-column loads in flight per wait, then the 32- and 16-column rest.
-__device__ __forceinline__ float tmem_sum_squares(uint32_t taddr, int cols) {
-    float sum = 0.f;
+// TMEM lane from taddr on: two 32-column loads in flight per wait, then the 32- and 16-column rest,
+// summed in four independent chains (combined as (s0 + s1) + (s2 + s3)). release() runs once, right
+// after the last load has completed, so that the accumulator is handed back before the last sums.
+template <class Release>
+__device__ __forceinline__ float tmem_sum_squares(uint32_t taddr, int cols, Release&& release) {
+    if (cols <= 0) {
+        release();
+        return 0.f;
+    }
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
     int c = 0;
     for (; c + 64 <= cols; c += 64) {
         uint32_t r[32], q[32];
         tmem_ld32(taddr + (uint32_t)c, r);
         tmem_ld32(taddr + (uint32_t)c + 32u, q);
         tmem_ld_wait();
+        if (c + 64 == cols) release();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const float y = __uint_as_float(r[j]), z = __uint_as_float(q[j]);
-            sum = fmaf(y, y, sum);
-            sum = fmaf(z, z, sum);
+        for (int j = 0; j < 32; j += 2) {
+            const float y0 = __uint_as_float(r[j]), y1 = __uint_as_float(r[j + 1]);
+            const float z0 = __uint_as_float(q[j]), z1 = __uint_as_float(q[j + 1]);
+            s0 = fmaf(y0, y0, s0);
+            s1 = fmaf(y1, y1, s1);
+            s2 = fmaf(z0, z0, s2);
+            s3 = fmaf(z1, z1, s3);
         }
     }
     for (; c + 32 <= cols; c += 32) {
         uint32_t r[32];
         tmem_ld32(taddr + (uint32_t)c, r);
         tmem_ld_wait();
+        if (c + 32 == cols) release();
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const float y = __uint_as_float(r[j]);
-            sum = fmaf(y, y, sum);
+        for (int j = 0; j < 32; j += 4) {
+            s0 = fmaf(__uint_as_float(r[j]), __uint_as_float(r[j]), s0);
+            s1 = fmaf(__uint_as_float(r[j + 1]), __uint_as_float(r[j + 1]), s1);
+            s2 = fmaf(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 2]), s2);
+            s3 = fmaf(__uint_as_float(r[j + 3]), __uint_as_float(r[j + 3]), s3);
         }
     }
-    if (c < cols) {
+    if (c < cols) {                                               // the last 16 columns
         uint32_t r[16];
         tmem_ld16(taddr + (uint32_t)c, r);
         tmem_ld_wait();
+        release();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float y = __uint_as_float(r[j]);
-            sum = fmaf(y, y, sum);
+        for (int j = 0; j < 16; j += 4) {
+            s0 = fmaf(__uint_as_float(r[j]), __uint_as_float(r[j]), s0);
+            s1 = fmaf(__uint_as_float(r[j + 1]), __uint_as_float(r[j + 1]), s1);
+            s2 = fmaf(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 2]), s2);
+            s3 = fmaf(__uint_as_float(r[j + 3]), __uint_as_float(r[j + 3]), s3);
         }
     }
-    return sum;
+    return (s0 + s1) + (s2 + s3);
 }
 
 template <int F>
@@ -459,10 +476,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_final_tc(const __grid_constant_
             const int64_t t = group + tt * ngroups;
             if (!wait_bar(smem_u32(&ctl->tfull), (uint32_t)(tt & 1), ctl, status)) break;
             tc_fence_after();
-            const float sum = tmem_sum_squares(lanes, cols);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) arrive_leader_tmem<PAIR>(smem_u32(&ctl->tempty), me);
+            // the accumulator goes back to the MMA warp as soon as its last columns are read
+            const float sum = tmem_sum_squares(lanes, cols, [&] {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) arrive_leader_tmem<PAIR>(smem_u32(&ctl->tempty), me);
+            });
             // the second column half's warps hand their sums to the first's through part[tt & 1]
             // (two buffers; each is refilled once the first half has read it)
             const int pb = (int)(tt & 1);
