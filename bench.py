@@ -627,8 +627,8 @@ def main():
                               + (" x 1/2 (TF32 nominal ratio)" if f == "tf32" else "")}
         roof["frac"] = roof["achieved"] / roof["peak"]
         # DRAM bytes per launch from the ncu capture of this kernel (split BF16) on 262,144 x 256 with
-        # an Mfull of 208 nonzero columns, scaled by rows: read 268,707,072 + write 3,934,720 bytes
-        roof["traffic"] = ((268707072 + 3934720) * n / 262144
+        # an Mfull of 208 nonzero columns, scaled by rows: read 268,712,704 + write 3,499,264 bytes
+        roof["traffic"] = ((268712704 + 3499264) * n / 262144
                            if (f == "bf16x3" and d == 256 and mma_n == 208) else None)
         roof["ms"] = final_ms[f]
         roof["call_ms"] = final_call_ms[f]
