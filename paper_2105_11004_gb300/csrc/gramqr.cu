@@ -21,7 +21,8 @@
 //     Upper 32 x 32 tiles split over rows, split partials reduced in a fixed
 //     order and mirrored;
 //   k_pchol_grid: one cooperative grid (at most one CTA per SM; ceil(d/3) CTAs
-//     up to d = 256, where a step is latency-bound); CTA c owns the
+//     up to d = 256, where a step is latency-bound; above d = 256 one thread a
+//     row, 512 or 1,024 threads a CTA); CTA c owns the
 //     columns l = c mod gridDim of the Schur complement in shared memory, in
 //     double-float arithmetic (FP32 pairs, about 48 bits; FP64 runs at 1/64 of
 //     the FP32 rate here). All CTAs keep a replicated Schur diagonal and take the
@@ -33,7 +34,7 @@
 //     cluster of 8 or 16 CTAs, the columns in registers, the pivot column pulled
 //     from the owner's shared memory (a remote hop of about 250 ns instead of an
 //     L2 round trip); it holds 16 SMs instead of ceil(d/3), which the other
-//     kernels of batches in flight use.
+//     kernels of batches in flight use. The double-float helpers live in df.cuh.
 //
 // The Gram route resolves |R_jj| / |R_00| down to about sqrt(m u) ~ 1e-7; the
 // caller uses the Householder kernel when tau is below 1e-6 or d > 1024.
