@@ -1,4 +1,5 @@
-// Rank-revealing QR of the sketch and the small factor M = R_11^{-1} Omega, FP64.
+// Rank-revealing QR of the sketch (FP64) and the small factor M = R_11^{-1} Omega (FP64 inputs and
+// factor, a double-float triangular solve for d <= 1,024, FP64 above).
 //
 // Pivoted QR (Alg. 4 step 2 with the xGEQP3-style pivoting the paper's
 // implementation uses, Sec. 7): one cooperatively launched persistent kernel.
