@@ -259,7 +259,8 @@ int lev_lsqr_csr(lev_handle* h, const int64_t* row_ptr, const int32_t* col, cons
                  double* rnorm, void* stream);
 
 /* The small factor of the final pass (Alg. 8 step 4 with the QR
- * orthogonaliser): M = R_11^{-1} Omega (r x k) by FP64 back-substitution, with
+ * orthogonaliser): M = R_11^{-1} Omega (r x k) by back-substitution (d <= 1024: in
+ * double-float arithmetic, FP32 pairs of about 48 bits, on the FP64 R and Omega; above: FP64), with
  * Omega drawn from stream 3 of `seed` (or I_r with LEV_OMEGA_IDENTITY, k = r),
  * scattered into Mfull (device, d x k FP32 row-major): row perm[p] holds M[p, :]
  * and the d - r rows outside K are 0. R, perm as produced by lev_rrqr; d_rank:

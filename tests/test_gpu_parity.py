@@ -5,7 +5,8 @@ Tolerances (FP32 path):
   sums of at most a few thousand terms per split, fixed order;
 * pivots bit-exact on the first r positions, rank bit-exact;
 * R: relative 1e-10 (FP64 on both sides, different summation order);
-* Mfull: relative 1e-6 to the FP64 solve rounded once to FP32;
+* Mfull: relative 1e-6 to the FP64 solve rounded once to FP32 (the GPU solve runs in double-float
+  arithmetic, about 48 bits, for d <= 1024);
 * final pass with identical inputs: relative 1e-5 per row (FP32 products);
 * end to end theta~: max relative error 1e-4 against the oracle's FP64 theta~.
 """
